@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the DBL reachability index on GB300.
+
+Workload "social" (the stand-in for LiveJournal's size in Table 2 of the
+paper): directed R-MAT (a,b,c,d = .57,.19,.19,.05), n = 4,847,571,
+m = 68,993,773, seed 2; k = 64 landmarks by M(u) = |Pre(u)|*|Suc(u)|,
+k' = 64 leaf buckets.  One step = restore the built index, insert 1,000,000
+new edges in batches (default 100,000; label repair of Algorithm 3 and its
+mirrors) and answer 10,000,000 mixed queries (Algorithm 2: half uniform
+pairs, half (u, end of a random forward walk from u)).  All inputs are
+resident in HBM before the timed region; the label array (155 MB), the pair
+arrays (80 MB) and the adjacency (590 MB) exceed the 126 MB L2, so no flush
+is needed between steps.
+
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle
+(the repository's plain sequential statement of the method) on the same
+step instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "queries/s + inserted edges/s, learned+batched vs plain GPU form, 100% exact"
+UNIT = "ops/s (queries + inserted edges)"
+
+# DRAM traffic per launch from an ncu capture, valid only while the kernel
+# source is unchanged: {kernel class: (bytes per launch, sha1 of source file)}.
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {}
+KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_kernels.cuh",
+                 "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
+
+
+def source_sha(kind: str) -> str:
+    p = os.path.join(ROOT, "paper_2101_09441_gb300", "csrc", KERNEL_SOURCE.get(kind, "dbl_api.cu"))
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def measured_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(float(r[1]) for r in rows), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace('.', '', 1).isdigit())
+                if any(r[3].replace('.', '', 1).isdigit() for r in rows) else None}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_batches(n_edges: int, batch: int):
+    return [(b, min(b + batch, n_edges)) for b in range(0, n_edges, batch)]
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_step(ref, w, batches, nq, threads):
+    ref.rewind()
+    t0 = time.perf_counter()
+    for a, b in batches:
+        ref.insert_edges(w["ins_src"][a:b], w["ins_dst"][a:b])
+    t1 = time.perf_counter()
+    ref.query(w["q_u"][:nq], w["q_v"][:nq], nthreads=threads)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+# ------------------------------------------------------------------ reference arm
+def bench_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import dbl_inputs
+    import oracle
+    w = dbl_inputs.workload(args.workload)
+    cores = cpu_cores()
+    ref = oracle.OracleIndex(w["row_ptr"], w["col"], args.k, args.kprime).build(nthreads=cores)
+    ref.mark()
+    E, Q = w["ins_src"].shape[0], w["q_u"].shape[0]
+    batches = step_batches(E, args.batch)
+    for _ in range(args.warmup):
+        run_oracle_step(ref, w, batches, Q, cores)
+    t_ins = t_q = 0.0
+    for _ in range(args.steps):
+        a, b = run_oracle_step(ref, w, batches, Q, cores)
+        t_ins += a
+        t_q += b
+    total = t_ins + t_q
+    value = args.steps * (E + Q) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "components": {"queries_per_s": args.steps * Q / t_q, "inserted_edges_per_s": args.steps * E / t_ins},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"full step: {E} sequential insertions (Algorithm 3) + {Q} queries "
+                                       f"(Algorithm 2, {cores} threads)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, w):
+    return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "k": args.k, "kprime": args.kprime,
+            "insert_batch": args.batch, "inserted_edges_per_step": int(w["ins_src"].shape[0]),
+            "queries_per_step": int(w["q_u"].shape[0]), "form": "plain",
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes):
+    """Algorithmic bytes of label repair for one step: per direction, over the
+    vertices whose half-record changes in a batch, offsets (8 B) + adjacency
+    (4 B/edge) + neighbour record sectors (32 B/edge) + own write."""
+    import torch
+    ix.restore(0)
+    dev = torch.device("cuda")
+    deg_out = deg_out0.clone()
+    deg_in = deg_in0.clone()
+    total = 0.0
+    src_all = torch.from_numpy(w["ins_src"]).to(dev).long()
+    dst_all = torch.from_numpy(w["ins_dst"]).to(dev).long()
+    prev = ix.labels()
+    for a, b in batches:
+        ix.insert_edges(src_all[a:b].int(), dst_all[a:b].int())
+        cur = ix.labels()
+        s, d = src_all[a:b], dst_all[a:b]
+        keep = s != d
+        deg_out += torch.bincount(s[keep], minlength=deg_out.numel())
+        deg_in += torch.bincount(d[keep], minlength=deg_in.numel())
+        chf = ((cur[0] != prev[0]).any(1) | (cur[2] != prev[2]).any(1))
+        chb = ((cur[1] != prev[1]).any(1) | (cur[3] != prev[3]).any(1))
+        total += float((8 + 36 * deg_out[chf].double() + rec_half_bytes).sum())
+        total += float((8 + 36 * deg_in[chb].double() + rec_half_bytes).sum())
+        prev = cur
+    ix.restore(0)
+    return total
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as tdist
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    dbl.build()
+    w = dbl_inputs.workload(args.workload)
+    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
+    batches = step_batches(E, args.batch)
+    rp = torch.from_numpy(w["row_ptr"]).to(dev)
+    col = torch.from_numpy(w["col"]).to(dev)
+    src = torch.from_numpy(w["ins_src"]).to(dev)
+    dst = torch.from_numpy(w["ins_dst"]).to(dev)
+    qu = torch.from_numpy(w["q_u"]).to(dev)
+    qv = torch.from_numpy(w["q_v"]).to(dev)
+    ans = torch.empty(Q, dtype=torch.uint8, device=dev)
+    code = torch.empty(Q, dtype=torch.uint8, device=dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, flags=dbl.FLAG_TIMING, team=args.team,
+                      edge_capacity=max(E, 1 << 20))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    build_t = ix.timings()
+    ix.snapshot(0)
+    info = ix.info()
+    rec_bytes = info["record_bytes"]
+
+    def step():
+        ix.restore(0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        for a, b in batches:
+            ix.insert_edges(src[a:b], dst[a:b])
+        ev[1].record()
+        ix.query(qu, qv, out=(ans, code))
+        ev[2].record()
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ix.timings()  # reset
+    launches0 = ix.info()["launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    evs = [step() for _ in range(args.steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    clocks = sampler.stop()
+    total_ms = e0.elapsed_time(e1)
+    launches = ix.info()["launches"] - launches0
+    kern = ix.timings()
+    ins_ms = sum(ev[0].elapsed_time(ev[1]) for ev in evs)
+    q_ms = sum(ev[1].elapsed_time(ev[2]) for ev in evs)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # answers of the last step, for the record
+    answered = torch.bincount(code.long(), minlength=8).cpu().numpy()
+
+    # ---------------- end-to-end through the host-buffer C-ABI calls
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
+    h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.restore(0)
+        for a, b in batches:
+            ix.insert_edges_host(h_src[a:b], h_dst[a:b])
+        ix.query_host(h_qu, h_qv, out=(h_ans, None))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    ix.timings()
+
+    # ---------------- roofline of the dominant kernel class
+    peaks, peak_src = measured_peaks()
+    kernels = {}
+    alg = {}
+    alg["query_label"] = args.steps * Q * (8 + 2 * rec_bytes + 2)
+    if kern["propagate"][1]:
+        alg["propagate"] = args.steps * changed_bytes(ix, w, batches, torch.diff(rp).long(),
+                                                      torch.bincount(col.long(), minlength=w["n"]),
+                                                      rec_bytes // 2)
+    for name, (ms, cnt) in kern.items():
+        if cnt:
+            ent = {"ms_total": ms, "launches": cnt, "ms_per_launch": ms / cnt}
+            if name in alg and ms > 0:
+                ent["algorithmic_bytes_per_launch"] = alg[name] / cnt
+                ent["achieved_gbs"] = alg[name] / (ms * 1e-3) / 1e9
+            kernels[name] = ent
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    roof = None
+    cand = dom if "achieved_gbs" in kernels[dom] else max(
+        (k for k in kernels if "achieved_gbs" in kernels[k]), key=lambda k: kernels[k]["ms_total"])
+    ach = kernels[cand]["achieved_gbs"]
+    traffic = None
+    if cand in NCU_TRAFFIC and NCU_TRAFFIC[cand][1] == source_sha(cand):
+        traffic = NCU_TRAFFIC[cand][0]
+    roof = {"kernel": cand, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {peak_src}",
+            "dominant_kernel_by_time": dom}
+
+    value = world * args.steps * (E + Q) / (total_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "components": {"queries_per_s": world * args.steps * Q / (q_ms * 1e-3),
+                           "inserted_edges_per_s": world * args.steps * E / (ins_ms * 1e-3),
+                           "build_s": build_s,
+                           "build_kernel_ms": {k: v[0] for k, v in build_t.items() if v[1]},
+                           "decided_by": {n: int(answered[i]) for i, n in
+                                          enumerate(["undecided", "self", "dl", "bl", "thm1", "thm2",
+                                                     "bfs_pos", "bfs_neg"])}},
+            "roofline": roof,
+            "kernels": kernels,
+            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
+            "clocks": clocks,
+            "gpu_launches": launches}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, w)
+    ix.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def cpu_baseline(args, w):
+    """The oracle, as it stands, on a bounded sample of the same step."""
+    import oracle
+    cores = cpu_cores()
+    ref = oracle.OracleIndex(w["row_ptr"], w["col"], args.k, args.kprime).build(nthreads=cores)
+    ref.mark()
+    e_s = min(100_000, w["ins_src"].shape[0])
+    q_s = min(1_000_000, w["q_u"].shape[0])
+    t_ins, t_q = run_oracle_step(ref, w, step_batches(e_s, args.batch), q_s, cores)
+    return {"value": (e_s + q_s) / (t_ins + t_q), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {e_s} insertions (sequential, Algorithm 3) + first {q_s} queries "
+                      f"(Algorithm 2, {cores} threads) of the step; same 1:10 mix",
+            "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dbl", "reference"], default="dbl")
+    ap.add_argument("--workload", default="social", choices=["social", "tiny"])
+    ap.add_argument("--batch", type=int, default=100_000)
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--kprime", type=int, default=64)
+    ap.add_argument("--team", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

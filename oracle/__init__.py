@@ -85,6 +85,8 @@ def _load():
             lib.orc_csr.restype = None
             lib.orc_insert_stats.argtypes = [P, P]
             lib.orc_insert_stats.restype = None
+            lib.orc_mark.argtypes = [P]
+            lib.orc_rewind.argtypes = [P]
             _lib = lib
     return _lib
 
@@ -176,6 +178,16 @@ class OracleIndex:
             raise ValueError(f"orc_query failed ({rc})")
         self.last_query_stats = stats
         return ans, code
+
+    def mark(self):
+        """Remember the current labels and graph (one mark per process)."""
+        if _load().orc_mark(self._h):
+            raise MemoryError("orc_mark")
+
+    def rewind(self):
+        """Return to the state saved by mark()."""
+        if _load().orc_rewind(self._h):
+            raise ValueError("orc_rewind: no mark for this index")
 
     def labels(self):
         """(dl_in, dl_out, bl_in, bl_out) as uint64 [n, words]."""

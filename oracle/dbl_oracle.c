@@ -523,6 +523,47 @@ void orc_csr(const orc_index *h, int64_t *row_ptr, int32_t *col)
     }
 }
 
+/* Save the labels and adjacency lengths; orc_rewind returns to them (so a
+ * timed step can be repeated from the same state).  Returns 0 or 2. */
+static uint64_t *g_mark_lab[4];
+static int32_t *g_mark_len[2];
+static const orc_index *g_mark_owner;
+
+int orc_mark(orc_index *h)
+{
+    size_t nn = h->n > 0 ? (size_t)h->n : 1;
+    size_t sz[4] = {nn * h->wd, nn * h->wd, nn * h->wb, nn * h->wb};
+    uint64_t *src[4] = {h->dl_in, h->dl_out, h->bl_in, h->bl_out};
+    for (int i = 0; i < 4; ++i) {
+        free(g_mark_lab[i]);
+        g_mark_lab[i] = (uint64_t *)malloc(8 * sz[i]);
+        if (!g_mark_lab[i]) return 2;
+        memcpy(g_mark_lab[i], src[i], 8 * sz[i]);
+    }
+    for (int d = 0; d < 2; ++d) {
+        free(g_mark_len[d]);
+        g_mark_len[d] = (int32_t *)malloc(sizeof(int32_t) * nn);
+        if (!g_mark_len[d]) return 2;
+        for (int32_t v = 0; v < h->n; ++v) g_mark_len[d][v] = d ? h->pre[v].len : h->suc[v].len;
+    }
+    g_mark_owner = h;
+    return 0;
+}
+
+int orc_rewind(orc_index *h)
+{
+    if (g_mark_owner != h) return 1;
+    size_t nn = h->n > 0 ? (size_t)h->n : 1;
+    size_t sz[4] = {nn * h->wd, nn * h->wd, nn * h->wb, nn * h->wb};
+    uint64_t *dst[4] = {h->dl_in, h->dl_out, h->bl_in, h->bl_out};
+    for (int i = 0; i < 4; ++i) memcpy(dst[i], g_mark_lab[i], 8 * sz[i]);
+    for (int32_t v = 0; v < h->n; ++v) {
+        h->suc[v].len = g_mark_len[0][v];
+        h->pre[v].len = g_mark_len[1][v];
+    }
+    return 0;
+}
+
 void orc_insert_stats(const orc_index *h, uint64_t *out3)
 {
     out3[0] = h->ins_skipped;

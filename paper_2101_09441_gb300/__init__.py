@@ -1,0 +1,270 @@
+"""GB300-native DBL reachability index (arXiv 2101.09441).
+
+Python binding of ``libdbl.so`` (C ABI in ``include/dbl.h``): argument
+marshalling only.  Every step of the index runs in the library's CUDA
+kernels; PyTorch provides device memory (through the library's allocator
+callbacks) and streams.  There is no CPU fallback: importing works without a
+GPU, but every index operation needs the built library and a CUDA device and
+raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdbl.so")
+
+DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAPACITY, DBL_ERR_BUSY, \
+    DBL_ERR_POISONED = range(8)
+STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned"]
+CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
+FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING = 1, 2, 4
+KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "insert_append", "insert_seed",
+                "build_prep", "other"]
+
+EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", "dbl_query_host",
+           "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_snapshot", "dbl_restore", "dbl_sync",
+           "dbl_stats", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy"]
+
+
+class DblError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p),
+                ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
+                ("team", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    from . import native_build
+    return native_build.build(force=force)
+
+
+def lib():
+    """The loaded ``libdbl.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2101_09441_gb300.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            L.dbl_default_options.argtypes = [P]
+            L.dbl_default_options.restype = None
+            L.dbl_build.argtypes = [P, P, i32, P, P, i32, P, P, P]
+            L.dbl_insert_edges.argtypes = [P, P, P, i64, P]
+            L.dbl_query.argtypes = [P, P, P, i64, P, P, P]
+            L.dbl_query_host.argtypes = [P, P, P, i64, P, P, P]
+            L.dbl_insert_edges_host.argtypes = [P, P, P, i64, P]
+            L.dbl_labels.argtypes = [P, P, P, P, P, P]
+            L.dbl_selection.argtypes = [P, P, P, P, P]
+            L.dbl_snapshot.argtypes = [P, ctypes.c_int, P]
+            L.dbl_restore.argtypes = [P, ctypes.c_int, P]
+            L.dbl_sync.argtypes = [P, P]
+            L.dbl_stats.argtypes = [P, P, P]
+            L.dbl_info.argtypes = [P, P]
+            L.dbl_timings.argtypes = [P, P, P, P]
+            L.dbl_last_error.argtypes = [P]
+            L.dbl_last_error.restype = ctypes.c_char_p
+            L.dbl_destroy.argtypes = [P, P]
+            L.dbl_destroy.restype = None
+            for name in EXPORTS:
+                fn = getattr(L, name)
+                if fn.restype is ctypes.c_int:  # default restype: dbl_status
+                    fn.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class DBLIndex:
+    """A DBL index resident on one GPU (see ``include/dbl.h``).
+
+    All tensor arguments are CUDA tensors (int32 ids, uint8 answers) on the
+    index's device; they are used on ``stream`` (default: the current one).
+    """
+
+    def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
+                 leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 8, stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("DBLIndex needs a CUDA device")
+        L = lib()
+        self._stream = stream
+        self.device = row_ptr.device
+        self.row_ptr = row_ptr.to(torch.int32).contiguous()
+        self.col = col.to(torch.int32).contiguous()
+        self.n = int(self.row_ptr.numel() - 1)
+        self.m = int(self.col.numel())
+        self.k, self.kprime = int(k), int(kprime)
+        opt = _Options()
+        L.dbl_default_options(ctypes.byref(opt))
+        opt.edge_capacity = int(edge_capacity)
+        opt.flags = int(flags)
+        opt.team = int(team)
+        if torch_allocator:
+            dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
+
+            def _alloc(nbytes, strm, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream=int(strm or 0))
+                except Exception:
+                    return None
+
+            def _free(p, nbytes, strm, ctx):
+                try:
+                    torch.cuda.caching_allocator_delete(int(p))
+                except Exception:
+                    pass
+
+            self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+            opt.alloc, opt.free = self._cb
+        self._opt = opt
+        g = _Graph(self.n, self.m, _ptr(self.row_ptr), _ptr(self.col))
+        self._keep = [t.to(torch.int32).contiguous() if t is not None and t.dtype != torch.uint8 else t
+                      for t in (landmarks, leaf_buckets, leaf_roles)]
+        lm, lb, lr = self._keep
+        h = ctypes.c_void_p()
+        st = L.dbl_build(ctypes.byref(g), _ptr(lm), self.k, _ptr(lb), _ptr(lr), self.kprime, ctypes.byref(opt),
+                         _stream_handle(stream), ctypes.byref(h))
+        if st != DBL_OK:
+            raise DblError(st, L.dbl_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def _check(self, st):
+        if st != DBL_OK:
+            raise DblError(st, lib().dbl_last_error(self._h).decode())
+
+    def _s(self, stream):
+        return _stream_handle(stream if stream is not None else self._stream)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.dbl_destroy(h, self._s(None))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def insert_edges(self, src, dst, stream=None):
+        import torch
+        src = src.to(torch.int32).contiguous()
+        dst = dst.to(torch.int32).contiguous()
+        self._check(lib().dbl_insert_edges(self._h, _ptr(src), _ptr(dst), int(src.numel()), self._s(stream)))
+
+    def query(self, u, v, with_code: bool = True, out=None, stream=None):
+        """Answer q(u[i], v[i]); returns (ans uint8, code uint8 or None)."""
+        import torch
+        u = u.to(torch.int32).contiguous()
+        v = v.to(torch.int32).contiguous()
+        q = int(u.numel())
+        if out is None:
+            ans = torch.empty(q, dtype=torch.uint8, device=u.device)
+            code = torch.empty(q, dtype=torch.uint8, device=u.device) if with_code else None
+        else:
+            ans, code = out
+        self._check(lib().dbl_query(self._h, _ptr(u), _ptr(v), q, _ptr(ans), _ptr(code), self._s(stream)))
+        return ans, code
+
+    def query_host(self, u: np.ndarray, v: np.ndarray, with_code: bool = False, out=None, stream=None):
+        """Host-buffer form: numpy in, numpy out (transfers inside the call)."""
+        u = np.ascontiguousarray(u, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        q = int(u.shape[0])
+        if out is None:
+            ans = np.empty(q, dtype=np.uint8)
+            code = np.empty(q, dtype=np.uint8) if with_code else None
+        else:
+            ans, code = out
+        self._check(lib().dbl_query_host(self._h, u.ctypes.data, v.ctypes.data, q, ans.ctypes.data,
+                                         code.ctypes.data if code is not None else None, self._s(stream)))
+        return ans, code
+
+    def insert_edges_host(self, src: np.ndarray, dst: np.ndarray, stream=None):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        self._check(lib().dbl_insert_edges_host(self._h, src.ctypes.data, dst.ctypes.data, int(src.shape[0]),
+                                                self._s(stream)))
+
+    def labels(self, stream=None):
+        """(dl_in, dl_out, bl_in, bl_out) as int64 tensors [n, words] (uint64 bit patterns)."""
+        import torch
+        wd, wb = self.k // 64, self.kprime // 64
+        out = [torch.empty((self.n, w), dtype=torch.int64, device=self.device) for w in (wd, wd, wb, wb)]
+        self._check(lib().dbl_labels(self._h, *[_ptr(t) for t in out], self._s(stream)))
+        return tuple(out)
+
+    def selection(self, stream=None):
+        import torch
+        lm = torch.empty(self.k, dtype=torch.int32, device=self.device)
+        lb = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        lr = torch.empty(self.n, dtype=torch.uint8, device=self.device)
+        self._check(lib().dbl_selection(self._h, _ptr(lm), _ptr(lb), _ptr(lr), self._s(stream)))
+        return lm, lb, lr
+
+    def snapshot(self, slot: int = 0, stream=None):
+        self._check(lib().dbl_snapshot(self._h, slot, self._s(stream)))
+
+    def restore(self, slot: int = 0, stream=None):
+        self._check(lib().dbl_restore(self._h, slot, self._s(stream)))
+
+    def sync(self, stream=None):
+        self._check(lib().dbl_sync(self._h, self._s(stream)))
+
+    def stats(self, stream=None) -> np.ndarray:
+        out = np.zeros(16, dtype=np.uint64)
+        self._check(lib().dbl_stats(self._h, out.ctypes.data, self._s(stream)))
+        return out
+
+    def timings(self, stream=None) -> dict:
+        """Per kernel class: (ms, launches) since the last call (needs FLAG_TIMING)."""
+        ms = np.zeros(8, dtype=np.float64)
+        cnt = np.zeros(8, dtype=np.uint64)
+        self._check(lib().dbl_timings(self._h, ms.ctypes.data, cnt.ctypes.data, self._s(stream)))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(KERNEL_NAMES)}
+
+    def info(self) -> dict:
+        out = np.zeros(16, dtype=np.int64)
+        self._check(lib().dbl_info(self._h, out.ctypes.data))
+        return dict(n=int(out[0]), k=int(out[1]), kprime=int(out[2]), edges_stored=int(out[3]),
+                    edge_capacity=int(out[4]), m=int(out[5]), record_bytes=int(out[6]), flags=int(out[7]),
+                    launches=int(out[8]), half_words=int(out[9]))

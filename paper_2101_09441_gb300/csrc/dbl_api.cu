@@ -1,0 +1,563 @@
+// C-ABI entry points of the DBL library (declared in include/dbl.h).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dbl_internal.cuh"
+
+namespace dbl {
+
+static thread_local std::string g_build_error;
+
+dbl_status fail(dbl_index *ix, dbl_status st, const std::string &msg)
+{
+    if (ix) ix->err = msg;
+    else g_build_error = msg;
+    return st;
+}
+
+dbl_status cuda_fail(dbl_index *ix, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ix, DBL_ERR_OOM, m);
+    return fail(ix, DBL_ERR_CUDA, m);
+}
+
+dbl_status alloc_buf(dbl_index *ix, void **p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *q = nullptr;
+    if (ix->opt.alloc) {
+        q = ix->opt.alloc(bytes, (void *)s, ix->opt.ctx);
+        if (!q) return fail(ix, DBL_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMallocAsync(&q, bytes, s);
+        if (e) {
+            cudaGetLastError();
+            return fail(ix, DBL_ERR_OOM, "cudaMallocAsync(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        }
+    }
+    ix->owned.push_back(Buf{q, bytes});
+    *p = q;
+    return DBL_OK;
+}
+
+void free_buf(dbl_index *ix, void *p, cudaStream_t s)
+{
+    if (!p) return;
+    for (size_t i = 0; i < ix->owned.size(); ++i) {
+        if (ix->owned[i].p == p) {
+            size_t bytes = ix->owned[i].bytes;
+            ix->owned[i] = ix->owned.back();
+            ix->owned.pop_back();
+            if (ix->opt.alloc) ix->opt.free(p, bytes, (void *)s, ix->opt.ctx);
+            else cudaFreeAsync(p, s);
+            return;
+        }
+    }
+}
+
+dbl_status read_status(dbl_index *ix, cudaStream_t s)
+{
+    cudaMemcpyAsync(ix->h_pinned + 8, ix->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "synchronize");
+    uint32_t st = ix->h_pinned[8];
+    if (st) cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);  // consumed
+    return (dbl_status)st;
+}
+
+void atomic_add_host_stat(dbl_index *ix, int idx, uint64_t v, cudaStream_t)
+{
+    ix->h_stats[idx] += v;
+}
+
+static cudaEvent_t take_event(dbl_index *ix)
+{
+    if (!ix->ev_free.empty()) {
+        cudaEvent_t e = ix->ev_free.back();
+        ix->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void tbegin(dbl_index *ix, int kind, cudaStream_t s)
+{
+    if (!(ix->opt.flags & DBL_FLAG_TIMING)) return;
+    if (ix->open_kind >= 0) tend(ix, s);
+    dbl_index::TimedRange r{kind, take_event(ix), take_event(ix)};
+    cudaEventRecord(r.a, s);
+    ix->tranges.push_back(r);
+    ix->open_kind = kind;
+}
+
+void tend(dbl_index *ix, cudaStream_t s)
+{
+    if (!(ix->opt.flags & DBL_FLAG_TIMING) || ix->open_kind < 0) return;
+    cudaEventRecord(ix->tranges.back().b, s);
+    ix->open_kind = -1;
+}
+
+static int64_t pow2_at_least(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+dbl_status ensure_search_scratch(dbl_index *ix, int64_t q, cudaStream_t s)
+{
+    dbl_status st;
+    const int64_t W = 1 + ix->wd + 2 * ix->wb;
+    if (q > ix->und_cap) {
+        free_buf(ix, ix->und, s);
+        free_buf(ix, ix->qtab, s);
+        free_buf(ix, ix->found, s);
+        ix->und = nullptr;
+        ix->qtab = nullptr;
+        ix->found = nullptr;
+        int64_t cap = std::max<int64_t>(q, 1 << 16);
+        if ((st = alloc_buf(ix, (void **)&ix->und, sizeof(int32_t) * (size_t)cap, s))) return st;
+        if ((st = alloc_buf(ix, (void **)&ix->qtab, sizeof(uint64_t) * (size_t)(cap + 64) * W, s))) return st;
+        if ((st = alloc_buf(ix, (void **)&ix->found, sizeof(unsigned long long) * (size_t)(cap / 64 + 2), s)))
+            return st;
+        ix->und_cap = cap;
+    }
+    if (!ix->table) {
+        int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n));
+        if ((st = alloc_buf(ix, (void **)&ix->table, sizeof(SearchSlot) * (size_t)slots, s))) return st;
+        if ((st = alloc_buf(ix, (void **)&ix->claimed, sizeof(int32_t) * (size_t)slots, s))) return st;
+        if ((st = alloc_buf(ix, (void **)&ix->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return st;
+        if ((st = alloc_buf(ix, (void **)&ix->slot_list[1], sizeof(int32_t) * (size_t)slots, s))) return st;
+        cudaMemsetAsync(ix->table, 0, sizeof(SearchSlot) * (size_t)slots, s);
+        // key = empty (all ones) in every slot: set the key words with a strided memset
+        cudaMemset2DAsync(ix->table, sizeof(SearchSlot), 0xff, sizeof(unsigned long long), (size_t)slots, s);
+        ix->table_slots = slots;
+        int64_t tcap = (int64_t)ix->n + (ix->m + ix->edge_cap) / kChunk + 4096;
+        if ((st = alloc_buf(ix, (void **)&ix->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
+        ix->stask_cap = tcap;
+    }
+    return DBL_OK;
+}
+
+__global__ void k_extract_labels(const uint64_t *rec, int32_t n, int32_t rw, int32_t hs, int32_t wd, int32_t wb,
+                                 uint64_t *dl_in, uint64_t *dl_out, uint64_t *bl_in, uint64_t *bl_out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *r = rec + (size_t)v * rw;
+        for (int w = 0; w < wd; ++w) {
+            if (dl_in) dl_in[(size_t)v * wd + w] = r[w];
+            if (dl_out) dl_out[(size_t)v * wd + w] = r[hs + w];
+        }
+        for (int w = 0; w < wb; ++w) {
+            if (bl_in) bl_in[(size_t)v * wb + w] = r[wd + w];
+            if (bl_out) bl_out[(size_t)v * wb + w] = r[hs + wd + w];
+        }
+    }
+}
+
+}  // namespace dbl
+
+using namespace dbl;
+
+static int hs_for(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
+
+static bool width_ok(int32_t bits) { return bits == 64 || bits == 128 || bits == 256; }
+
+extern "C" {
+
+void dbl_default_options(dbl_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->bfs_words = 16;
+    opt->team = 8;
+}
+
+static void destroy_impl(dbl_index *ix, cudaStream_t s)
+{
+    if (!ix) return;
+    for (auto &b : ix->owned) {
+        if (ix->opt.alloc) ix->opt.free(b.p, b.bytes, (void *)s, ix->opt.ctx);
+        else cudaFreeAsync(b.p, s);
+    }
+    ix->owned.clear();
+    if (ix->h_pinned) cudaFreeHost(ix->h_pinned);
+    if (ix->copy_stream) cudaStreamDestroy(ix->copy_stream);
+    for (auto &r : ix->tranges) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ix->ev_free) cudaEventDestroy(e);
+    delete ix;
+}
+
+void dbl_destroy(dbl_index *ix, void *stream)
+{
+    if (!ix) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamSynchronize(s);
+    destroy_impl(ix, s);
+}
+
+dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, const int32_t *leaf_buckets,
+                     const uint8_t *leaf_roles, int32_t kprime, const dbl_options *opt, void *stream,
+                     dbl_index **out)
+{
+    if (!out) return fail(nullptr, DBL_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!g || g->n < 0 || g->m < 0 || g->m >= (1ll << 31) || !g->row_ptr || (g->m > 0 && !g->col))
+        return fail(nullptr, DBL_ERR_INVALID, "graph: need n >= 0, 0 <= m < 2^31 and device row_ptr/col");
+    if (!width_ok(k) || !width_ok(kprime)) return fail(nullptr, DBL_ERR_INVALID, "k and kprime must be 64, 128 or 256");
+    if (leaf_buckets && !leaf_roles) return fail(nullptr, DBL_ERR_INVALID, "leaf_roles required with leaf_buckets");
+    if (opt && ((opt->alloc == nullptr) != (opt->free == nullptr)))
+        return fail(nullptr, DBL_ERR_INVALID, "options: alloc and free must be set together");
+    if (opt && opt->team && opt->team != 4 && opt->team != 8 && opt->team != 16 && opt->team != 32)
+        return fail(nullptr, DBL_ERR_INVALID, "options: team must be 4, 8, 16 or 32");
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_index *ix = new (std::nothrow) dbl_index();
+    if (!ix) return fail(nullptr, DBL_ERR_OOM, "host allocation");
+    dbl_default_options(&ix->opt);
+    if (opt) {
+        ix->opt = *opt;
+        if (!ix->opt.team) ix->opt.team = 8;
+        if (!ix->opt.bfs_words) ix->opt.bfs_words = 16;
+    }
+    cudaGetDevice(&ix->device);
+    ix->n = g->n;
+    ix->m = g->m;
+    ix->k = k;
+    ix->kp = kprime;
+    ix->wd = k / 64;
+    ix->wb = kprime / 64;
+    ix->hs = hs_for(ix->wd + ix->wb);
+    ix->rw = 2 * ix->hs;
+    ix->edge_cap = ix->opt.edge_capacity > 0 ? ix->opt.edge_capacity : std::max<int64_t>(1 << 20, g->m / 4);
+    if (ix->edge_cap + g->m >= (1ll << 31)) ix->edge_cap = (1ll << 31) - 1 - g->m;
+    ix->pool_cap = 4 * ix->edge_cap + 64;
+    if (ix->pool_cap >= (1ll << 31)) ix->pool_cap = (1ll << 31) - 1;
+
+    const size_t n = (size_t)ix->n, m = (size_t)ix->m;
+    dbl_status st;
+    auto A = [&](void **p, size_t bytes) { return alloc_buf(ix, p, bytes, s); };
+    if (cudaMallocHost((void **)&ix->h_pinned, 64 * sizeof(uint32_t))) {
+        cudaGetLastError();
+        destroy_impl(ix, s);
+        return fail(nullptr, DBL_ERR_OOM, "pinned host words");
+    }
+    std::memset(ix->h_pinned, 0, 64 * sizeof(uint32_t));
+    ix->front_cap = 2 * ((int64_t)n + (int64_t)(m + ix->edge_cap) / kChunk + 64);
+    if ((st = A((void **)&ix->out_ptr, 4 * (n + 1))) || (st = A((void **)&ix->out_col, 4 * m)) ||
+        (st = A((void **)&ix->in_ptr, 4 * (n + 1))) || (st = A((void **)&ix->in_col, 4 * m)) ||
+        (st = A((void **)&ix->ovo, 12 * n)) || (st = A((void **)&ix->ovi, 12 * n)) ||
+        (st = A((void **)&ix->pool_out, 4 * (size_t)ix->pool_cap)) ||
+        (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
+        (st = A((void **)&ix->rec, 8 * n * ix->rw)) || (st = A((void **)&ix->landmarks, 4 * (size_t)k)) ||
+        (st = A((void **)&ix->leaf_bucket, 4 * n)) || (st = A((void **)&ix->leaf_role, n)) ||
+        (st = A((void **)&ix->stamp, 8 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
+        (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
+        (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
+        (st = A((void **)&ix->ins_cnt, 8 * n))) {
+        std::string msg = ix->err;
+        destroy_impl(ix, s);
+        return fail(nullptr, st, msg);
+    }
+    cudaMemsetAsync(ix->ovo, 0, 12 * n, s);
+    cudaMemsetAsync(ix->ovi, 0, 12 * n, s);
+    cudaMemsetAsync(ix->d_pool_top, 0, 16, s);
+    cudaMemsetAsync(ix->stamp, 0, 8 * n, s);
+    cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
+    cudaMemsetAsync(ix->d_status, 0, 16, s);
+    cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);
+    cudaMemsetAsync(ix->ins_cnt, 0, 8 * n, s);
+
+    tbegin(ix, DBL_KERNEL_BUILD_PREP, s);
+    if ((st = prep_graph(ix, g, s)) || (st = select_landmarks(ix, landmarks, s)) ||
+        (st = select_leaves(ix, leaf_buckets, leaf_roles, s)) || (st = seed_labels(ix, s)) ||
+        (tend(ix, s), st = propagate(ix, s))) {
+        std::string msg = ix->err;
+        destroy_impl(ix, s);
+        return fail(nullptr, st, msg);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) {
+        destroy_impl(ix, s);
+        return cuda_fail(nullptr, e, "build");
+    }
+    *out = ix;
+    return DBL_OK;
+}
+
+#define DBL_CHECK_IX(ix)                                                                   \
+    do {                                                                                   \
+        if (!(ix)) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");                 \
+        if ((ix)->poisoned) return fail(ix, DBL_ERR_POISONED, "index poisoned by a timeout; dbl_restore it"); \
+    } while (0)
+
+static dbl_status finish(dbl_index *ix, dbl_status st, cudaStream_t s)
+{
+    if (st) return st;
+    if (ix->opt.flags & DBL_FLAG_ASYNC) return DBL_OK;
+    return read_status(ix, s);
+}
+
+dbl_status dbl_insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, void *stream)
+{
+    DBL_CHECK_IX(ix);
+    if (b < 0 || b >= (1ll << 31) || (b > 0 && (!src || !dst))) return fail(ix, DBL_ERR_INVALID, "insert: bad batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    return finish(ix, insert_edges(ix, src, dst, b, s), s);
+}
+
+dbl_status dbl_query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
+                     void *stream)
+{
+    DBL_CHECK_IX(ix);
+    if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u || !v || !ans))) return fail(ix, DBL_ERR_INVALID, "query: bad batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    return finish(ix, query(ix, u, v, q, ans, code, s), s);
+}
+
+static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
+{
+    if (ix->stage_chunk >= chunk) return DBL_OK;
+    dbl_status st;
+    for (int b = 0; b < 2; ++b) {
+        free_buf(ix, ix->dstage[b], s);
+        ix->dstage[b] = nullptr;
+        // u, v (int32) + ans, code (uint8) per pair
+        if ((st = alloc_buf(ix, (void **)&ix->dstage[b], (size_t)chunk * 10 + 64, s))) return st;
+    }
+    if (!ix->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ix->copy_stream, cudaStreamNonBlocking);
+        if (e) return cuda_fail(ix, e, "copy stream");
+    }
+    ix->stage_chunk = chunk;
+    return DBL_OK;
+}
+
+dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v_host, int64_t q, uint8_t *ans_host,
+                          uint8_t *code_host, void *stream)
+{
+    DBL_CHECK_IX(ix);
+    if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u_host || !v_host || !ans_host)))
+        return fail(ix, DBL_ERR_INVALID, "query_host: bad batch");
+    if (q == 0) return DBL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t chunk = std::min<int64_t>(q, 1 << 22);
+    dbl_status st = ensure_stage(ix, chunk, s);
+    if (st) return st;
+    const int64_t nch = (q + chunk - 1) / chunk;
+    cudaEvent_t ev_in[2], ev_used[2];
+    for (int b = 0; b < 2; ++b) {
+        cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&ev_used[b], cudaEventDisableTiming);
+        cudaEventRecord(ev_used[b], s);
+    }
+    auto stage_in = [&](int64_t c) {
+        const int b = (int)(c & 1);
+        const int64_t off = c * chunk, len = std::min(chunk, q - off);
+        char *d = (char *)ix->dstage[b];
+        cudaStreamWaitEvent(ix->copy_stream, ev_used[b], 0);
+        cudaMemcpyAsync(d, u_host + off, 4 * (size_t)len, cudaMemcpyHostToDevice, ix->copy_stream);
+        cudaMemcpyAsync(d + 4 * chunk, v_host + off, 4 * (size_t)len, cudaMemcpyHostToDevice, ix->copy_stream);
+        cudaEventRecord(ev_in[b], ix->copy_stream);
+    };
+    stage_in(0);
+    for (int64_t c = 0; c < nch && !st; ++c) {
+        const int b = (int)(c & 1);
+        const int64_t off = c * chunk, len = std::min(chunk, q - off);
+        char *d = (char *)ix->dstage[b];
+        if (c + 1 < nch) stage_in(c + 1);  // overlaps this chunk's compute (Section 6.6)
+        cudaStreamWaitEvent(s, ev_in[b], 0);
+        uint8_t *da = (uint8_t *)(d + 8 * chunk), *dc = (uint8_t *)(d + 9 * chunk);
+        st = query(ix, (int32_t *)d, (int32_t *)(d + 4 * chunk), len, da, code_host ? dc : nullptr, s);
+        if (st) break;
+        cudaMemcpyAsync(ans_host + off, da, (size_t)len, cudaMemcpyDeviceToHost, s);
+        if (code_host) cudaMemcpyAsync(code_host + off, dc, (size_t)len, cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(ev_used[b], s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaStreamSynchronize(ix->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+        cudaEventDestroy(ev_in[b]);
+        cudaEventDestroy(ev_used[b]);
+    }
+    if (st) return st;
+    if (e) return cuda_fail(ix, e, "query_host");
+    return read_status(ix, s);
+}
+
+dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const int32_t *dst_host, int64_t b,
+                                 void *stream)
+{
+    DBL_CHECK_IX(ix);
+    if (b < 0 || b >= (1ll << 31) || (b > 0 && (!src_host || !dst_host)))
+        return fail(ix, DBL_ERR_INVALID, "insert_host: bad batch");
+    if (b == 0) return DBL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st = ensure_stage(ix, std::max<int64_t>(b, 1 << 16), s);
+    if (st) return st;
+    char *d = (char *)ix->dstage[0];
+    cudaMemcpyAsync(d, src_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d + 4 * ix->stage_chunk, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
+    st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->stage_chunk), b, s);
+    if (st) return st;
+    return read_status(ix, s);
+}
+
+dbl_status dbl_labels(dbl_index *ix, uint64_t *dl_in, uint64_t *dl_out, uint64_t *bl_in, uint64_t *bl_out,
+                      void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t blocks = ((int64_t)ix->n + kBlock - 1) / kBlock;
+    blocks = std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)num_sms() * 16);
+    k_extract_labels<<<(unsigned)blocks, kBlock, 0, s>>>(ix->rec, ix->n, ix->rw, ix->hs, ix->wd, ix->wb, dl_in, dl_out,
+                                                         bl_in, bl_out);
+    ++ix->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "labels");
+    return finish(ix, DBL_OK, s);
+}
+
+dbl_status dbl_selection(dbl_index *ix, int32_t *landmarks, int32_t *leaf_buckets, uint8_t *leaf_roles, void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (landmarks)
+        cudaMemcpyAsync(landmarks, ix->landmarks, 4 * (size_t)ix->k, cudaMemcpyDeviceToDevice, s);
+    if (leaf_buckets)
+        cudaMemcpyAsync(leaf_buckets, ix->leaf_bucket, 4 * (size_t)ix->n, cudaMemcpyDeviceToDevice, s);
+    if (leaf_roles) cudaMemcpyAsync(leaf_roles, ix->leaf_role, (size_t)ix->n, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "selection");
+    return finish(ix, DBL_OK, s);
+}
+
+dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    if (slot < 0 || slot >= 4) return fail(ix, DBL_ERR_INVALID, "snapshot slot must be 0..3");
+    if (ix->poisoned) return fail(ix, DBL_ERR_POISONED, "cannot snapshot a poisoned index");
+    cudaStream_t s = (cudaStream_t)stream;
+    Snapshot &sn = ix->snaps[slot];
+    dbl_status st;
+    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = 12 * (size_t)ix->n;
+    if (!sn.rec.p) {
+        if ((st = alloc_buf(ix, &sn.rec.p, rec_b, s)) || (st = alloc_buf(ix, &sn.ovo.p, meta_b, s)) ||
+            (st = alloc_buf(ix, &sn.ovi.p, meta_b, s)))
+            return st;
+    }
+    cudaMemcpyAsync(sn.rec.p, ix->rec, rec_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(sn.ovo.p, ix->ovo, meta_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(sn.ovi.p, ix->ovi, meta_b, cudaMemcpyDeviceToDevice, s);
+    // pool tops: read them once (small, synchronous)
+    cudaMemcpyAsync(sn.pool_top, ix->d_pool_top, 16, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "snapshot");
+    sn.edges_stored = ix->edges_stored;
+    sn.valid = true;
+    return DBL_OK;
+}
+
+dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    if (slot < 0 || slot >= 4 || !ix->snaps[slot].valid) return fail(ix, DBL_ERR_INVALID, "no snapshot in that slot");
+    cudaStream_t s = (cudaStream_t)stream;
+    Snapshot &sn = ix->snaps[slot];
+    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = 12 * (size_t)ix->n;
+    cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ix->ovo, sn.ovo.p, meta_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ix->ovi, sn.ovi.p, meta_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ix->d_pool_top, sn.pool_top, 16, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
+    ix->edges_stored = sn.edges_stored;
+    ix->poisoned = false;
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "restore");
+    return finish(ix, DBL_OK, s);
+}
+
+dbl_status dbl_sync(dbl_index *ix, void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    return read_status(ix, (cudaStream_t)stream);
+}
+
+dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream)
+{
+    if (!ix || !counters) return fail(ix, DBL_ERR_INVALID, "stats: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *h = (unsigned long long *)(ix->h_pinned + 16);  // 16 words = 8 u64; use two copies
+    uint64_t dev[16];
+    cudaMemcpyAsync(h, ix->d_stats, 8 * 8, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "stats");
+    std::memcpy(dev, h, 64);
+    cudaMemcpyAsync(h, ix->d_stats + 8, 8 * 8, cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "stats");
+    std::memcpy(dev + 8, h, 64);
+    for (int i = 0; i < 16; ++i) counters[i] = dev[i] + ix->h_stats[i];
+    return DBL_OK;
+}
+
+dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *stream)
+{
+    if (!ix || !ms || !launches) return fail(ix, DBL_ERR_INVALID, "timings: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    tend(ix, s);
+    for (int i = 0; i < 8; ++i) {
+        ms[i] = 0;
+        launches[i] = 0;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "timings");
+    for (auto &r : ix->tranges) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < 8) {
+            ms[r.kind] += t;
+            launches[r.kind] += 1;
+        }
+        ix->ev_free.push_back(r.a);
+        ix->ev_free.push_back(r.b);
+    }
+    cudaGetLastError();
+    ix->tranges.clear();
+    return DBL_OK;
+}
+
+dbl_status dbl_info(const dbl_index *ix, int64_t info[16])
+{
+    if (!ix || !info) return DBL_ERR_INVALID;
+    for (int i = 8; i < 16; ++i) info[i] = 0;
+    info[8] = (int64_t)ix->launches;
+    info[9] = ix->hs;
+    info[0] = ix->n;
+    info[1] = ix->k;
+    info[2] = ix->kp;
+    info[3] = ix->edges_stored;
+    info[4] = ix->edge_cap;
+    info[5] = ix->m;
+    info[6] = ix->rw * 8;
+    info[7] = ix->opt.flags;
+    return DBL_OK;
+}
+
+const char *dbl_last_error(const dbl_index *ix)
+{
+    if (!ix) return g_build_error.c_str();
+    return ix->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Frontier helpers shared by label build, insertion repair and propagation.
+//
+// A frontier is a list of tasks (vertex, chunk, direction); a vertex whose
+// edge list in that direction has d edges contributes ceil(d / kChunk) tasks,
+// so a hub of degree 10^5 is spread over many teams instead of one.
+// Vertices are deduplicated per level by an epoch stamp per direction.
+#pragma once
+
+#include "dbl_internal.cuh"
+
+namespace dbl {
+
+struct FrontierOut {
+    uint64_t *tasks;
+    uint32_t *count;
+    int64_t cap;
+    uint32_t *stamp;   // [2][n]
+    uint32_t epoch;    // stamp value of the level being filled
+    uint32_t *status;
+};
+
+// Warp-cooperative enqueue: every lane of the warp must call it (lanes with
+// want == false pass through).  One atomicAdd per warp reserves the slots.
+__device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, const DevGraph &g,
+                                             const FrontierOut &f)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t nchunks = 0;
+    if (want) {
+        uint32_t *st = f.stamp + (size_t)dir * (size_t)g.n + x;
+        if (atomicExch(st, f.epoch) != f.epoch) {
+            int32_t d = deg_of(g, dir, x);
+            nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
+        }
+    }
+    uint32_t incl = nchunks;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(f.count, total);
+    base = __shfl_sync(kFull, base, 31);
+    uint32_t pos = base + incl - nchunks;
+    for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
+        if ((int64_t)pos < f.cap) f.tasks[pos] = make_task(x, c, dir);
+        else set_status(f.status, DBL_ERR_CAPACITY);
+    }
+}
+
+// Same, for callers whose loop is not warp-uniform: uses the active mask.
+__device__ __forceinline__ void any_enqueue(int32_t x, int dir, const DevGraph &g, const FrontierOut &f)
+{
+    uint32_t *st = f.stamp + (size_t)dir * (size_t)g.n + x;
+    if (atomicExch(st, f.epoch) == f.epoch) return;
+    int32_t d = deg_of(g, dir, x);
+    uint32_t nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
+    if (!nchunks) return;
+    uint32_t pos = atomicAdd(f.count, nchunks);
+    for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
+        if ((int64_t)pos < f.cap) f.tasks[pos] = make_task(x, c, dir);
+        else set_status(f.status, DBL_ERR_CAPACITY);
+    }
+}
+
+}  // namespace dbl

@@ -1,0 +1,237 @@
+// Batched edge insertion and label repair (Section 5).
+//
+// Appending: each vertex keeps its inserted out-edges (and in-edges) in one
+// contiguous segment of an edge pool, (offset, length, capacity), grown by
+// doubling; a batch counts edges per vertex, grows the segments that
+// overflow (old segments are abandoned, so snapshots stay valid), and writes
+// the new ids.  The pool never holds more than 4 entries per stored edge.
+//
+// Repair: Algorithm 3 skips an edge (u, v) when DL_out(u) and DL_in(v) already
+// intersect (u already reaches v, so no label changes).  Otherwise its BFS from
+// v adds DL_in(u) to every descendant, and the mirror adds DL_out(v) to every
+// ancestor of u; BL_in / BL_out the same.  Here the seed step ORs fwd(u) into
+// fwd(v) and bwd(v) into bwd(u) for every edge of the batch, and the ordinary
+// propagation (which sees the appended edges) carries the change to the
+// fixpoint: the result equals one-by-one insertion in any order.
+#include "dbl_frontier.cuh"
+#include "dbl_internal.cuh"
+#include "dbl_kernels.cuh"
+
+namespace dbl {
+
+__global__ void k_ins_validate(const int32_t *src, const int32_t *dst, int64_t b, int32_t n, uint32_t *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        if ((uint32_t)src[i] >= (uint32_t)n || (uint32_t)dst[i] >= (uint32_t)n) set_status(status, DBL_ERR_INVALID);
+    }
+}
+
+// per-edge rank inside its source (out) and destination (in) vertex batch
+__global__ void k_ins_count(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
+                            int32_t *pos_out, int32_t *pos_in, unsigned long long *stats)
+{
+    unsigned long long loops = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[i], v = dst[i];
+        if (u == v) {
+            pos_out[i] = -1;
+            pos_in[i] = -1;
+            ++loops;
+            continue;
+        }
+        pos_out[i] = atomicAdd(cnt_out + u, 1);
+        pos_in[i] = atomicAdd(cnt_in + v, 1);
+    }
+    if (loops) atomicAdd(stats + 13, loops);
+}
+
+__device__ __forceinline__ int32_t grown_cap(int32_t need)
+{
+    int32_t c = 4;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+// The first edge of each vertex batch grows that vertex's segment if needed.
+__global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *cnt_out,
+                           const int32_t *cnt_in, const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo,
+                           int32_t *ovi, int32_t *pool_out, int32_t *pool_in, int64_t *pool_top, int32_t n,
+                           int64_t pool_cap, uint32_t *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int dir = 0; dir < 2; ++dir) {
+            const int32_t pos = dir ? pos_in[i] : pos_out[i];
+            if (pos != 0) continue;
+            const int32_t x = dir ? dst[i] : src[i];
+            int32_t *meta = dir ? ovi : ovo;  // [off | len | cap]
+            int32_t *pool = dir ? pool_in : pool_out;
+            const int32_t len = meta[n + x], cap = meta[2 * n + x];
+            const int32_t need = len + (dir ? cnt_in[x] : cnt_out[x]);
+            if (need <= cap) continue;
+            const int32_t nc = grown_cap(need);
+            const long long off = atomicAdd((unsigned long long *)(pool_top + dir), (unsigned long long)nc);
+            if (off + nc > pool_cap) {
+                set_status(status, DBL_ERR_CAPACITY);  // cannot happen: pool holds 4x the edge capacity
+                continue;
+            }
+            const int32_t old = meta[x];
+            for (int32_t j = 0; j < len; ++j) pool[off + j] = pool[old + j];
+            meta[x] = (int32_t)off;
+            meta[2 * n + x] = nc;
+        }
+    }
+}
+
+__global__ void k_ins_write(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *pos_out,
+                            const int32_t *pos_in, const int32_t *ovo, const int32_t *ovi, int32_t *pool_out,
+                            int32_t *pool_in, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t po = pos_out[i];
+        if (po < 0) continue;
+        const int32_t u = src[i], v = dst[i];
+        // a segment that could not grow (pool exhausted, status already set) is not written past its end
+        if (ovo[n + u] + po < ovo[2 * n + u]) pool_out[(int64_t)ovo[u] + ovo[n + u] + po] = v;
+        if (ovi[n + v] + pos_in[i] < ovi[2 * n + v]) pool_in[(int64_t)ovi[v] + ovi[n + v] + pos_in[i]] = u;
+    }
+}
+
+__global__ void k_ins_commit(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
+                             const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo, int32_t *ovi, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+        if (pos_out[i] == 0) {
+            const int32_t u = src[i];
+            ovo[n + u] += cnt_out[u];
+            cnt_out[u] = 0;
+        }
+        if (pos_in[i] == 0) {
+            const int32_t v = dst[i];
+            ovi[n + v] += cnt_in[v];
+            cnt_in[v] = 0;
+        }
+    }
+}
+
+// Seeds of the repair: the skip test of Algorithm 3, then fwd(v) |= fwd(u),
+// bwd(u) |= bwd(v); changed endpoints start the frontier.
+template <int HS, int WD>
+__global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const int32_t *dst, int64_t b, DevGraph g,
+                                                     uint64_t *rec, FrontierOut f, unsigned long long *stats)
+{
+    constexpr int RW = 2 * HS;
+    unsigned long long skipped = 0, applied = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < b; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        bool want_f = false, want_b = false;
+        int32_t u = 0, v = 0;
+        if (i < b) {
+            u = src[i];
+            v = dst[i];
+            if (u != v) {
+                uint64_t *fu = rec + (size_t)u * RW, *bu = fu + HS;
+                uint64_t *fv = rec + (size_t)v * RW, *bv = fv + HS;
+                uint64_t a[HS], c[HS];
+                load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
+                load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
+                uint64_t inter = 0;
+#pragma unroll
+                for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
+                if (inter) {
+                    ++skipped;
+                } else {
+                    ++applied;
+                    uint64_t x[HS];
+                    load_half<HS>(fu, x);
+#pragma unroll
+                    for (int w = 0; w < HS; ++w)
+                        if (x[w] & ~c[w]) {
+                            unsigned long long old = atomicOr((unsigned long long *)(fv + w), x[w]);
+                            want_f |= (x[w] & ~old) != 0;
+                        }
+                    load_half<HS>(bv, x);
+#pragma unroll
+                    for (int w = 0; w < HS; ++w)
+                        if (x[w] & ~a[w]) {
+                            unsigned long long old = atomicOr((unsigned long long *)(bu + w), x[w]);
+                            want_b |= (x[w] & ~old) != 0;
+                        }
+                }
+            }
+        }
+        warp_enqueue(want_f, v, 0, g, f);
+        warp_enqueue(want_b, u, 1, g, f);
+    }
+    warp_stat_add(stats, 12, skipped);
+    warp_stat_add(stats, 11, applied);
+}
+
+static unsigned blocks_for(int64_t work, int64_t cap_mult = 16)
+{
+    int64_t bl = (work + kBlock - 1) / kBlock;
+    int64_t cap = (int64_t)num_sms() * cap_mult;
+    if (bl > cap) bl = cap;
+    if (bl < 1) bl = 1;
+    return (unsigned)bl;
+}
+
+dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s)
+{
+    if (b == 0) return DBL_OK;
+    if (ix->edges_stored + b > ix->edge_cap)
+        return fail(ix, DBL_ERR_CAPACITY, "insert: edge capacity exhausted (dbl_options.edge_capacity)");
+    if (b > ix->ins_bcap) {
+        if (ix->ins_pos) free_buf(ix, ix->ins_pos, s);
+        ix->ins_pos = nullptr;
+        int64_t nb = b < (1 << 16) ? (1 << 16) : b;
+        dbl_status st = alloc_buf(ix, (void **)&ix->ins_pos, sizeof(int32_t) * 2 * (size_t)nb, s);
+        if (st) return st;
+        ix->ins_bcap = nb;
+    }
+    const int32_t n = ix->n;
+    const unsigned grid = blocks_for(b);
+    // 1. validate before anything changes
+    tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
+    k_ins_validate<<<grid, kBlock, 0, s>>>(src, dst, b, n, ix->d_status);
+    ++ix->launches;
+    tend(ix, s);
+    dbl_status st = read_status(ix, s);
+    if (st) return fail(ix, st, "insert: vertex id out of range");
+    // 2. append
+    int32_t *pos_out = ix->ins_pos, *pos_in = ix->ins_pos + ix->ins_bcap;
+    int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + n;
+    tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
+    k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats);
+    ++ix->launches;
+    k_ins_grow<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out,
+                                       ix->pool_in, ix->d_pool_top, n, ix->pool_cap, ix->d_status);
+    ++ix->launches;
+    k_ins_write<<<grid, kBlock, 0, s>>>(src, dst, b, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out, ix->pool_in, n);
+    ++ix->launches;
+    k_ins_commit<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, n);
+    ++ix->launches;
+    ix->edges_stored += b;
+    atomic_add_host_stat(ix, 15, (uint64_t)b, s);
+    // 3. seed the repair frontier, then propagate to the fixpoint
+    ix->epoch += 1;
+    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, ix->epoch, ix->d_status};
+    cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
+    const DevGraph g = dev_graph(ix);
+    tbegin(ix, DBL_KERNEL_INSERT_SEED, s);
+    switch (ix->hs * 16 + ix->wd) {
+    case 2 * 16 + 1: k_ins_seed<2, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    case 4 * 16 + 1: k_ins_seed<4, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    case 4 * 16 + 2: k_ins_seed<4, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 1: k_ins_seed<8, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 2: k_ins_seed<8, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 4: k_ins_seed<8, 4><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    default: return fail(ix, DBL_ERR_INVALID, "insert: unsupported label width");
+    }
+    tend(ix, s);
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "insert kernels");
+    return propagate(ix, s);
+}
+
+}  // namespace dbl

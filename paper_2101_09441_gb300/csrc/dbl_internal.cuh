@@ -1,0 +1,282 @@
+// Internal declarations of the GB300 DBL library (not part of the C ABI).
+//
+// Device data layout (one GPU, all resident in HBM):
+//   rec     uint64 [n][RW]      per-vertex label record, RW = 2*HS words.
+//                               words [0, HS): forward half  = DL_in | BL_in | 0-pad
+//                               words [HS, 2HS): backward half = DL_out | BL_out | 0-pad
+//                               HS = next power of two >= k/64 + kprime/64, so a
+//                               half is 16, 32 or 64 bytes and, for k = kprime = 64,
+//                               a whole record is one 32-byte DRAM sector.
+//   out_ptr/out_col, in_ptr/in_col   base CSR of Suc and Pre (int32).
+//   ovo_*/ovi_*              inserted edges: per-vertex contiguous segments
+//                            (offset, length, capacity) in an edge pool, grown
+//                            by doubling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dbl.h"
+
+namespace dbl {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kChunk = 64;     // edges per propagation / search task
+constexpr int kBlock = 256;    // threads per block for frontier kernels
+
+// ------------------------------------------------------------ device views
+struct DevGraph {
+    int32_t n;
+    const int32_t *out_ptr, *out_col;
+    const int32_t *in_ptr, *in_col;
+    const int32_t *ovo_off, *ovo_len, *pool_out;
+    const int32_t *ovi_off, *ovi_len, *pool_in;
+};
+
+// degree of x in direction dir (0 = Suc, 1 = Pre), base + inserted
+__device__ __forceinline__ int32_t deg_of(const DevGraph &g, int dir, int32_t x)
+{
+    const int32_t *ptr = dir ? g.in_ptr : g.out_ptr;
+    const int32_t *ovl = dir ? g.ovi_len : g.ovo_len;
+    return __ldg(ptr + x + 1) - __ldg(ptr + x) + __ldcg(ovl + x);
+}
+
+// Edge range of x: base part [b0, b0+bd) of col, then inserted part [o0, o0+od) of pool.
+struct AdjRange {
+    int32_t b0, bd, o0, od;
+};
+
+__device__ __forceinline__ AdjRange adj_of(const DevGraph &g, int dir, int32_t x)
+{
+    AdjRange r;
+    const int32_t *ptr = dir ? g.in_ptr : g.out_ptr;
+    r.b0 = __ldg(ptr + x);
+    r.bd = __ldg(ptr + x + 1) - r.b0;
+    r.o0 = __ldcg((dir ? g.ovi_off : g.ovo_off) + x);
+    r.od = __ldcg((dir ? g.ovi_len : g.ovo_len) + x);
+    return r;
+}
+
+__device__ __forceinline__ int32_t adj_at(const DevGraph &g, int dir, const AdjRange &r, int32_t e)
+{
+    if (e < r.bd) return __ldg((dir ? g.in_col : g.out_col) + r.b0 + e);
+    return __ldcg((dir ? g.pool_in : g.pool_out) + r.o0 + (e - r.bd));
+}
+
+// Latch the first error code in the device status word.
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t code)
+{
+    atomicCAS(status, 0u, code);
+}
+
+template <int HS>
+__device__ __forceinline__ void load_half(const uint64_t *p, uint64_t (&w)[HS])
+{
+#pragma unroll
+    for (int i = 0; i < HS; i += 2) {
+        ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i));
+        w[i] = t.x;
+        w[i + 1] = t.y;
+    }
+}
+
+// Propagation task: vertex, chunk of its edge list, direction.
+__device__ __forceinline__ uint64_t make_task(int32_t v, uint32_t chunk, int dir)
+{
+    return (uint64_t)(uint32_t)v | ((uint64_t)chunk << 32) | ((uint64_t)dir << 63);
+}
+
+// Search task: (group, vertex) state slot, chunk, and the query bits to expand.
+struct SearchTask {
+    int32_t x;
+    uint32_t g;
+    uint32_t chunk;
+    uint32_t pad;
+    uint64_t mask;
+};
+
+// Search state slot, keyed by (group << 32 | vertex); 32 bytes = one sector.
+struct SearchSlot {
+    unsigned long long key;
+    unsigned long long visit;
+    unsigned long long pend;
+    uint32_t stamp;
+    uint32_t pad;
+};
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+// ------------------------------------------------------------ host side
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Snapshot {
+    bool valid = false;
+    Buf rec, ovo, ovi;  // labels; (off, len, cap) triples for both directions
+    int64_t pool_top[2] = {0, 0};
+    int64_t edges_stored = 0;
+};
+
+}  // namespace dbl
+
+struct dbl_index {
+    int device = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t k = 0, kp = 0, wd = 0, wb = 0, hs = 0, rw = 0;
+    dbl_options opt{};
+    std::string err;
+    bool poisoned = false;
+
+    // graph
+    int32_t *out_ptr = nullptr, *out_col = nullptr, *in_ptr = nullptr, *in_col = nullptr;
+    // inserted adjacency: [off | len | cap] blocks of n int32 each, per direction
+    int32_t *ovo = nullptr, *ovi = nullptr;
+    int32_t *pool_out = nullptr, *pool_in = nullptr;
+    int64_t pool_cap = 0, edge_cap = 0;
+    int64_t edges_stored = 0;     // host mirror of inserted edges stored
+    int64_t *d_pool_top = nullptr; // [2] device bump pointers (out, in)
+    int64_t h_pool_top[2] = {0, 0};
+
+    // labels and selection
+    uint64_t *rec = nullptr;
+    int32_t *landmarks = nullptr, *leaf_bucket = nullptr;
+    uint8_t *leaf_role = nullptr;
+
+    // frontier scratch
+    uint32_t *stamp = nullptr;        // [2][n] enqueue stamps per direction
+    uint64_t *front[2] = {nullptr, nullptr};
+    int64_t front_cap = 0;
+    uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
+    uint32_t epoch = 0;               // last stamp epoch used
+
+    // insertion scratch
+    int32_t *ins_cnt = nullptr;       // [2][n] per-vertex batch counts
+    int32_t *ins_pos = nullptr;       // [2][bcap] per-edge slot in its vertex batch
+    int64_t ins_bcap = 0;
+
+    // query scratch
+    int32_t *und = nullptr;           // undecided query indices
+    int64_t und_cap = 0;
+    uint64_t *qtab = nullptr;         // per undecided query: u, v, DL_out(u), BL_in(v), BL_out(v)
+    int64_t qtab_cap = 0;
+    unsigned long long *found = nullptr;  // per 64-query group
+    int64_t found_cap = 0;
+    dbl::SearchSlot *table = nullptr;
+    int64_t table_slots = 0;          // power of two
+    int32_t *claimed = nullptr;       // slots claimed in the current wave
+    int32_t *slot_list[2] = {nullptr, nullptr};
+    dbl::SearchTask *stask = nullptr;
+    int64_t stask_cap = 0;
+    int32_t *wave_groups = nullptr;   // group ids of the current wave
+    int64_t wave_groups_cap = 0;
+
+    // status, counters
+    uint32_t *d_status = nullptr;
+    unsigned long long *d_stats = nullptr;  // [16]
+    uint32_t *h_pinned = nullptr;     // pinned host words for small readbacks
+
+    // host-buffer staging (dbl_query_host / dbl_insert_edges_host)
+    void *dstage[2] = {nullptr, nullptr};
+    int64_t stage_chunk = 0;
+    cudaStream_t copy_stream = nullptr;
+
+    // DBL_FLAG_TIMING: event pairs per kernel class, harvested by dbl_timings
+    struct TimedRange {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<TimedRange> tranges;
+    std::vector<cudaEvent_t> ev_free;
+    int open_kind = -1;
+
+    uint64_t h_stats[16] = {0};       // host-side counters merged into dbl_stats
+    uint64_t launches = 0;            // kernels launched by this index
+    dbl::Snapshot snaps[4];
+    std::vector<dbl::Buf> owned;      // for teardown
+};
+
+// small device counter slots in d_counts
+enum {
+    kCntFront0 = 0,     // size of frontier buffer 0
+    kCntFront1 = 1,     // size of frontier buffer 1
+    kCntUnd = 2,        // undecided queries
+    kCntSlots0 = 3,     // search slot list 0
+    kCntSlots1 = 4,     // search slot list 1
+    kCntTasks = 5,      // search tasks
+    kCntClaimed = 6,    // claimed slots
+    kCntOverflow = 7,   // search wave overflow flag
+    kCntGrow = 8,       // (2 words) pool growth request, int64
+    kCntWords = 16
+};
+
+namespace dbl {
+
+// allocation helpers (dbl_api.cu)
+dbl_status alloc_buf(dbl_index *ix, void **p, size_t bytes, cudaStream_t s);
+void free_buf(dbl_index *ix, void *p, cudaStream_t s);
+dbl_status fail(dbl_index *ix, dbl_status st, const std::string &msg);
+dbl_status cuda_fail(dbl_index *ix, cudaError_t e, const char *what);
+dbl_status read_status(dbl_index *ix, cudaStream_t s);
+dbl_status ensure_search_scratch(dbl_index *ix, int64_t und, cudaStream_t s);
+void atomic_add_host_stat(dbl_index *ix, int idx, uint64_t v, cudaStream_t s);
+// bracket the launches between tbegin and tend (no-op without DBL_FLAG_TIMING)
+void tbegin(dbl_index *ix, int kind, cudaStream_t s);
+void tend(dbl_index *ix, cudaStream_t s);
+
+inline DevGraph dev_graph(const dbl_index *ix)
+{
+    DevGraph g;
+    g.n = ix->n;
+    g.out_ptr = ix->out_ptr;
+    g.out_col = ix->out_col;
+    g.in_ptr = ix->in_ptr;
+    g.in_col = ix->in_col;
+    g.ovo_off = ix->ovo;
+    g.ovo_len = ix->ovo + ix->n;
+    g.pool_out = ix->pool_out;
+    g.ovi_off = ix->ovi;
+    g.ovi_len = ix->ovi + ix->n;
+    g.pool_in = ix->pool_in;
+    return g;
+}
+
+inline int num_sms()
+{
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 1;
+    }
+    return v;
+}
+
+// prep (dbl_prep.cu)
+dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s);
+dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s);
+dbl_status select_leaves(dbl_index *ix, const int32_t *bucket, const uint8_t *role, cudaStream_t s);
+dbl_status seed_labels(dbl_index *ix, cudaStream_t s);
+dbl_status exclusive_scan_i32(dbl_index *ix, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+// propagation (dbl_propagate.cu): run the fixpoint from frontier buffer 0
+// (count in d_counts[kCntFront0]) until no record changes.
+dbl_status propagate(dbl_index *ix, cudaStream_t s);
+dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
+void launch_seed_frontier(dbl_index *ix, cudaStream_t s);  // all vertices with a non-zero half
+
+// insertion (dbl_insert.cu)
+dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);
+
+// query (dbl_query.cu)
+dbl_status query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
+                 cudaStream_t s);
+
+}  // namespace dbl

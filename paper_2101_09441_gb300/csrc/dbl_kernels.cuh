@@ -1,0 +1,81 @@
+// Device bodies shared by the per-level kernels and the persistent kernels.
+#pragma once
+
+#include "dbl_frontier.cuh"
+#include "dbl_internal.cuh"
+
+namespace dbl {
+
+__device__ __forceinline__ void warp_stat_add(unsigned long long *stats, int idx, unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + idx, v);
+}
+
+// One level of label propagation over `ntasks` tasks, processed by warps
+// [warp0, warp0 + nwarps*k) in steps of nwarps.  Every lane of a warp runs the
+// same number of iterations (warp_enqueue needs the whole warp).
+template <int HS, int TEAM>
+__device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
+                                             uint32_t ntasks, const FrontierOut &f, unsigned long long *stats,
+                                             int64_t warp0, int64_t nwarps)
+{
+    constexpr int TPW = 32 / TEAM;
+    constexpr int RW = 2 * HS;
+    const int lane = threadIdx.x & 31;
+    const int team = lane / TEAM, tl = lane % TEAM;
+    unsigned long long relaxed = 0, ntask = 0;
+    if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
+    for (int64_t wb = warp0 * TPW; wb < (int64_t)ntasks; wb += nwarps * TPW) {
+        const int64_t t = wb + team;
+        const bool has = t < (int64_t)ntasks;
+        int32_t v = 0, lo = 0, hi = 0;
+        int dir = 0;
+        AdjRange r{0, 0, 0, 0};
+        uint64_t rv[HS];
+#pragma unroll
+        for (int i = 0; i < HS; ++i) rv[i] = 0;
+        if (has) {
+            const uint64_t tk = __ldcg(tasks + t);
+            v = (int32_t)(uint32_t)tk;
+            const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
+            dir = (int)(tk >> 63);
+            r = adj_of(g, dir, v);
+            const int32_t d = r.bd + r.od;
+            lo = (int32_t)chunk * kChunk;
+            hi = min(d, lo + kChunk);
+            load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
+            if (tl == 0) ++ntask;
+        }
+        int iters = has && hi > lo ? (hi - lo + TEAM - 1) / TEAM : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) iters = max(iters, __shfl_xor_sync(kFull, iters, o));
+        for (int it = 0; it < iters; ++it) {
+            const int32_t e = lo + it * TEAM + tl;
+            bool want = false;
+            int32_t x = 0;
+            if (has && e < hi) {
+                x = adj_at(g, dir, r, e);
+                ++relaxed;
+                uint64_t *px = rec + (size_t)x * RW + (dir ? HS : 0);
+                uint64_t rx[HS];
+                load_half<HS>(px, rx);
+                bool changed = false;
+#pragma unroll
+                for (int i = 0; i < HS; ++i) {
+                    if (rv[i] & ~rx[i]) {
+                        unsigned long long old = atomicOr((unsigned long long *)(px + i), rv[i]);
+                        changed |= (rv[i] & ~old) != 0;
+                    }
+                }
+                want = changed;
+            }
+            warp_enqueue(want, x, dir, g, f);
+        }
+    }
+    warp_stat_add(stats, 9, ntask);
+    warp_stat_add(stats, 10, relaxed);
+}
+
+}  // namespace dbl

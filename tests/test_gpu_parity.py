@@ -1,0 +1,305 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Integer work throughout: every label word, every answer and every deciding
+rule must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import dbl_inputs
+import oracle
+import paper_2101_09441_gb300 as dbl
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    dbl.build()
+    dbl_inputs.build()
+    oracle.build()
+
+
+def D(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def labels_np(ix):
+    return [t.cpu().numpy().view(np.uint64) for t in ix.labels()]
+
+
+def assert_labels(ix, ref, what=""):
+    for a, b, name in zip(labels_np(ix), ref.labels(), ("dl_in", "dl_out", "bl_in", "bl_out")):
+        if not np.array_equal(a, b):
+            bad = np.nonzero((a != b).any(axis=1))[0]
+            raise AssertionError(f"{what}: {name} differs at {bad.size} vertices, first {bad[:8]}")
+
+
+def assert_queries(ix, ref, qu, qv, what=""):
+    ans, code = ix.query(D(qu), D(qv))
+    rans, rcode = ref.query(qu, qv, nthreads=8)
+    a, c = ans.cpu().numpy(), code.cpu().numpy()
+    bad = np.nonzero((a != rans) | (c != rcode))[0]
+    assert bad.size == 0, f"{what}: {bad.size} queries differ, e.g. {[(int(qu[i]), int(qv[i]), int(a[i]), int(c[i]), int(rans[i]), int(rcode[i])) for i in bad[:5]]}"
+    return rans, rcode
+
+
+# ---------------------------------------------------------------- worked example
+def test_running_example():
+    ex = H.load_running_example()
+    rp, col, lm, bucket, role = H.running_example_inputs(ex, 64, 64)
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64, landmarks=D(lm), leaf_buckets=D(bucket), leaf_roles=D(role))
+    ref = oracle.OracleIndex(rp, col, 64, 64).build(lm, bucket, role)
+    assert_labels(ix, ref, "build")
+    dl_in, dl_out, bl_in, bl_out = labels_np(ix)
+    for v, (e_in, e_out) in ex["dl"].items():
+        assert H.set_bits(dl_in[v]) == {ex["landmarks"].index(x) for x in e_in}
+        assert H.set_bits(dl_out[v]) == {ex["landmarks"].index(x) for x in e_out}
+    for v, (e_in, e_out) in ex["bl"].items():
+        assert H.set_bits(bl_in[v]) == e_in and H.set_bits(bl_out[v]) == e_out
+    u = np.array([q[0] for q in ex["queries"]], np.int32)
+    v = np.array([q[1] for q in ex["queries"]], np.int32)
+    ans, code = ix.query(D(u), D(v))
+    assert list(ans.cpu().numpy()) == [q[2] for q in ex["queries"]]
+    assert list(code.cpu().numpy()) == [H.CODES[q[3]] for q in ex["queries"]]
+    s, d = zip(*ex["inserts"])
+    ix.insert_edges(D(np.array(s, np.int32)), D(np.array(d, np.int32)))
+    ref.insert_edges(s, d)
+    assert_labels(ix, ref, "after (v9, v2)")
+    dl_in = labels_np(ix)[0]
+    for x, e in ex["dl_in_after"].items():
+        assert H.set_bits(dl_in[x]) == {ex["landmarks"].index(y) for y in e}
+
+
+# ---------------------------------------------------------------- tiny config
+@pytest.fixture(scope="module")
+def tiny():
+    return dbl_inputs.workload("tiny")
+
+
+def test_tiny_selection_matches_oracle(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64)
+    lm, lb, lr = [t.cpu().numpy() for t in ix.selection()]
+    assert np.array_equal(lm, ref.degree_landmarks())
+    rb, rr = ref.zero_degree_leaves()
+    assert np.array_equal(lb, rb) and np.array_equal(lr, rr)
+
+
+def test_tiny_full_pipeline(tiny):
+    """Plain DBL, tiny: build, 10k insertions in batches of 1k (labels after
+    every batch), then 100k mixed queries (answers and deciding rules)."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    assert_labels(ix, ref, "build")
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    for b in range(0, s.shape[0], 1000):
+        ix.insert_edges(D(s[b:b + 1000]), D(d[b:b + 1000]))
+        ref.insert_edges(s[b:b + 1000], d[b:b + 1000])
+        assert_labels(ix, ref, f"after batch {b // 1000}")
+    rans, rcode = assert_queries(ix, ref, tiny["q_u"], tiny["q_v"], "tiny queries")
+    assert (rcode == oracle.BFS_POS).sum() > 100          # the search really runs
+    st = ix.stats()
+    assert st[oracle.BFS_POS] == (rcode == oracle.BFS_POS).sum()
+    assert st[11] + st[12] == s.shape[0]                  # applied + skipped
+
+
+# ---------------------------------------------------------------- label widths
+@pytest.mark.parametrize("k,kprime", [(64, 64), (128, 64), (64, 128), (128, 128), (256, 64), (64, 256),
+                                      (256, 256), (128, 256), (256, 128)])
+def test_widths_random_selection(k, kprime):
+    rp, col = dbl_inputs.rmat_csr(3000, 12_000, 31 + k + kprime)
+    n = 3000
+    lm = H.random_slots(n, k, k - 5, k * 7 + kprime)
+    bucket, role = H.random_leaves(n, kprime, 0.25, kprime)
+    ix = dbl.DBLIndex(D(rp), D(col), k, kprime, landmarks=D(lm), leaf_buckets=D(bucket), leaf_roles=D(role))
+    ref = oracle.OracleIndex(rp, col, k, kprime).build(lm, bucket, role)
+    assert_labels(ix, ref, f"k={k} k'={kprime} build")
+    s, dd = dbl_inputs.insertions(rp, col, 500, 3)
+    ix.insert_edges(D(s), D(dd))
+    ref.insert_edges(s, dd)
+    assert_labels(ix, ref, f"k={k} k'={kprime} insert")
+    qu, qv = dbl_inputs.queries(rp, col, 20_000, 4, True, s, dd)
+    assert_queries(ix, ref, qu, qv, f"k={k} k'={kprime}")
+
+
+@pytest.mark.parametrize("team", [4, 8, 16, 32])
+def test_team_sizes(team, tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, team=team)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ix.insert_edges(D(tiny["ins_src"]), D(tiny["ins_dst"]))
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    assert_labels(ix, ref, f"team {team}")
+    assert_queries(ix, ref, tiny["q_u"][:20000], tiny["q_v"][:20000], f"team {team}")
+
+
+# ---------------------------------------------------------------- closure shapes
+@pytest.mark.parametrize("shape", ["path", "cycle", "two_cycles", "star_in", "star_out", "dense"])
+def test_shapes_match_closure(shape):
+    if shape == "path":
+        n = 300
+        s, d = H.path_graph(n)
+    elif shape == "cycle":
+        n = 257
+        s, d = H.path_graph(n, cycle=True)
+    elif shape == "two_cycles":
+        n = 200
+        s1, d1 = H.path_graph(100, cycle=True)
+        s, d = np.concatenate([s1, s1 + 100, [5]]), np.concatenate([d1, d1 + 100, [150]])
+    elif shape == "star_in":
+        n = 5000
+        s, d = np.arange(1, n, dtype=np.int32), np.zeros(n - 1, np.int32)
+    elif shape == "star_out":
+        n = 5000
+        s, d = np.zeros(n - 1, np.int32), np.arange(1, n, dtype=np.int32)
+    else:
+        n = 200
+        s, d = H.random_graph(n, 6000, 77)
+    rp, col = H.csr_from_edges(n, s, d)
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    assert_labels(ix, ref, shape)
+    rng = np.random.default_rng(1)
+    qu = rng.integers(0, n, 20000).astype(np.int32)
+    qv = rng.integers(0, n, 20000).astype(np.int32)
+    rans, _ = assert_queries(ix, ref, qu, qv, shape)
+    if n <= 400:
+        R = H.closure(n, s, d)
+        assert np.array_equal(rans.astype(bool), R[qu, qv])
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_and_single_vertex():
+    for n in (1, 7):
+        rp = np.zeros(n + 1, np.int32)
+        ix = dbl.DBLIndex(D(rp), D(np.zeros(0, np.int32)), 64, 64)
+        ref = oracle.OracleIndex(rp, np.zeros(0, np.int32), 64, 64).build()
+        assert_labels(ix, ref, f"empty n={n}")
+        qu = np.arange(n, dtype=np.int32)
+        qv = np.roll(qu, 1)
+        assert_queries(ix, ref, qu, qv, "empty")
+        ix.insert_edges(D(np.zeros(0, np.int32)), D(np.zeros(0, np.int32)))  # b = 0
+        a, c = ix.query(D(np.zeros(0, np.int32)), D(np.zeros(0, np.int32)))  # q = 0
+        assert a.numel() == 0
+
+
+def test_self_loops_and_duplicates():
+    rp, col = dbl_inputs.rmat_csr(2000, 8000, 9)
+    src, dst = H.edges_from_csr(rp, col)
+    # a CSR with self-loops and duplicate edges is accepted; labels as without them
+    s2 = np.concatenate([src, [3, 3, 10], src[:50]])
+    d2 = np.concatenate([dst, [3, 3, 10], dst[:50]])
+    rp2, col2 = H.csr_from_edges(2000, s2, d2)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    ix = dbl.DBLIndex(D(rp2), D(col2), 64, 64, landmarks=D(ref.landmarks), leaf_buckets=D(ref.leaf_bucket),
+                      leaf_roles=D(ref.leaf_role))
+    assert_labels(ix, ref, "self-loops/duplicates")
+    ix.insert_edges(D(np.array([5, 5, 7], np.int32)), D(np.array([5, 9, 9], np.int32)))
+    ref.insert_edges([5, 5, 7], [5, 9, 9])
+    assert_labels(ix, ref, "inserted self-loop")
+    assert ix.stats()[13] == 1
+
+
+def test_invalid_ids_leave_index_unchanged(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    before = labels_np(ix)
+    n = tiny["n"]
+    with pytest.raises(dbl.DblError) as e:
+        ix.insert_edges(D(np.array([1, 2], np.int32)), D(np.array([3, n], np.int32)))
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    with pytest.raises(dbl.DblError):
+        ix.insert_edges(D(np.array([-1], np.int32)), D(np.array([3], np.int32)))
+    for a, b in zip(before, labels_np(ix)):
+        assert np.array_equal(a, b)
+    assert ix.info()["edges_stored"] == 0
+    with pytest.raises(dbl.DblError) as e:
+        ix.query(D(np.array([0], np.int32)), D(np.array([n], np.int32)))
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    # still usable
+    ix.insert_edges(D(np.array([1], np.int32)), D(np.array([2], np.int32)))
+
+
+def test_invalid_build_inputs():
+    rp = np.array([0, 2, 1], np.int32)  # decreasing
+    with pytest.raises(dbl.DblError):
+        dbl.DBLIndex(D(rp), D(np.array([1, 0], np.int32)), 64, 64)
+    with pytest.raises(dbl.DblError):
+        dbl.DBLIndex(D(np.array([0, 1], np.int32)), D(np.array([5], np.int32)), 64, 64)
+    with pytest.raises(dbl.DblError):
+        dbl.DBLIndex(D(np.array([0, 0], np.int32)), D(np.zeros(0, np.int32)), 96, 64)
+    with pytest.raises(dbl.DblError):
+        dbl.DBLIndex(D(np.array([0, 0, 0], np.int32)), D(np.zeros(0, np.int32)), 64, 64,
+                     landmarks=D(np.full(64, 2, np.int32)))
+
+
+def test_capacity_exhaustion(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, edge_capacity=1500)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    ix.insert_edges(D(s[:1000]), D(d[:1000]))
+    ref.insert_edges(s[:1000], d[:1000])
+    with pytest.raises(dbl.DblError) as e:
+        ix.insert_edges(D(s[1000:1600]), D(d[1000:1600]))
+    assert e.value.status == dbl.DBL_ERR_CAPACITY
+    assert_labels(ix, ref, "after refused batch")
+    ix.insert_edges(D(s[1000:1500]), D(d[1000:1500]))
+    ref.insert_edges(s[1000:1500], d[1000:1500])
+    assert_labels(ix, ref, "after filling capacity")
+
+
+def test_snapshot_restore(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    base = labels_np(ix)
+    ix.snapshot(0)
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    ix.insert_edges(D(s), D(d))
+    ix.restore(0)
+    for a, b in zip(base, labels_np(ix)):
+        assert np.array_equal(a, b)
+    # the restored index behaves like the original: same insertions, same result
+    ix.insert_edges(D(s[:4000]), D(d[:4000]))
+    ref.insert_edges(s[:4000], d[:4000])
+    assert_labels(ix, ref, "after restore + insert")
+    assert_queries(ix, ref, tiny["q_u"][:30000], tiny["q_v"][:30000], "after restore")
+
+
+def test_batch_size_invariance(tiny):
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    results = []
+    for bs in (1, 37, 1000, 10_000):
+        ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+        lim = 400 if bs == 1 else 10_000
+        for b in range(0, lim, bs):
+            ix.insert_edges(D(s[b:min(b + bs, lim)]), D(d[b:min(b + bs, lim)]))
+        results.append((lim, labels_np(ix)))
+    full = [r for lim, r in results if lim == 10_000]
+    for r in full[1:]:
+        for a, b in zip(full[0], r):
+            assert np.array_equal(a, b)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ref.insert_edges(s[:400], d[:400])
+    for a, b in zip(results[0][1], ref.labels()):
+        assert np.array_equal(a, b)
+
+
+def test_host_buffer_forms(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ix.insert_edges_host(tiny["ins_src"], tiny["ins_dst"])
+    a1, c1 = ix.query(D(tiny["q_u"]), D(tiny["q_v"]))
+    a2, c2 = ix.query_host(tiny["q_u"], tiny["q_v"], with_code=True)
+    assert np.array_equal(a1.cpu().numpy(), a2) and np.array_equal(c1.cpu().numpy(), c2)
+
+
+def test_torch_and_default_allocators_agree(tiny):
+    a = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, torch_allocator=False)
+    b = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, torch_allocator=True)
+    for x, y in zip(labels_np(a), labels_np(b)):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
