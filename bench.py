@@ -258,10 +258,14 @@ def bench_gpu(args):
         tdist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile:
+        torch.cuda.profiler.start()
     e0.record()
     evs = [step() for _ in range(args.steps)]
     e1.record()
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.profiler.stop()
     if world > 1:
         tdist.barrier()
     clocks = sampler.stop()
@@ -282,7 +286,7 @@ def bench_gpu(args):
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
     h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -336,7 +340,7 @@ def bench_gpu(args):
                                                      "bfs_pos", "bfs_neg"])}},
             "roofline": roof,
             "kernels": kernels,
-            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s, "unit": UNIT,
+            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
             "clocks": clocks,
             "gpu_launches": launches}
@@ -376,6 +380,9 @@ def main():
     ap.add_argument("--kprime", type=int, default=64)
     ap.add_argument("--team", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -53,6 +53,15 @@ static void launch_expand_team(dbl_index *ix, int cur, uint32_t ntasks, const Fr
     }
 }
 
+// A device error during propagation (a frontier overflow, which the sizing
+// rules out) leaves labels short of the fixpoint: poison the index.
+static dbl_status propagate_error(dbl_index *ix, uint32_t code, cudaStream_t s)
+{
+    cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
+    ix->poisoned = true;
+    return fail(ix, (dbl_status)code, "propagate: device error; index poisoned until dbl_restore");
+}
+
 dbl_status propagate(dbl_index *ix, cudaStream_t s)
 {
     if (ix->opt.flags & DBL_FLAG_PERSISTENT) return propagate_persistent(ix, s);
@@ -66,7 +75,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
     int64_t levels = 0;
     const int64_t max_levels = (int64_t)ix->n + 2;
     while (ntasks > 0) {
-        if (h[8]) return fail(ix, (dbl_status)h[8], "propagate: device error");
+        if (h[8]) return propagate_error(ix, h[8], s);
         if (++levels > max_levels) {
             ix->poisoned = true;
             return fail(ix, DBL_ERR_TIMEOUT, "propagate: level bound exceeded");
@@ -90,7 +99,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
         cur = nxt;
         ntasks = h[cur];
     }
-    if (h[8]) return fail(ix, (dbl_status)h[8], "propagate: device error");
+    if (h[8]) return propagate_error(ix, h[8], s);
     // the fixpoint leaves frontier 0 as the (empty) starting buffer for the next call
     if (cur != 0) {
         cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);

@@ -449,7 +449,10 @@ static dbl_status query_t(dbl_index *ix, const int32_t *u, const int32_t *v, int
     cudaMemcpyAsync(h + 8, ix->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(ix, e, "query label test");
-    if (h[8]) return fail(ix, (dbl_status)h[8], "query: vertex id out of range");
+    if (h[8]) {
+        cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);  // consumed; nothing was changed
+        return fail(ix, (dbl_status)h[8], "query: vertex id out of range");
+    }
     const int64_t U = h[0];
     if (!U) return DBL_OK;
     // waves: all groups at once; on overflow rerun the unanswered in halves
