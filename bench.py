@@ -165,7 +165,7 @@ def bench_reference(args):
 def workload_config(args, w):
     return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "k": args.k, "kprime": args.kprime,
             "insert_batch": args.batch, "inserted_edges_per_step": int(w["ins_src"].shape[0]),
-            "queries_per_step": int(w["q_u"].shape[0]), "form": "plain",
+            "queries_per_step": int(w["q_u"].shape[0]), "form": getattr(args, "form", "plain"),
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
 
 
@@ -226,8 +226,11 @@ def bench_gpu(args):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, flags=dbl.FLAG_TIMING, team=args.team,
-                      edge_capacity=max(E, 1 << 20))
+    flags = dbl.FLAG_TIMING
+    if args.form == "batched":
+        flags |= dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC
+    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
+    ix.sync()
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     build_t = ix.timings()
@@ -266,6 +269,7 @@ def bench_gpu(args):
     torch.cuda.synchronize()
     if args.profile:
         torch.cuda.profiler.stop()
+    ix.sync()  # raises if any device-side error latched during the timed steps
     if world > 1:
         tdist.barrier()
     clocks = sampler.stop()
@@ -379,6 +383,8 @@ def main():
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--kprime", type=int, default=64)
     ap.add_argument("--team", type=int, default=8)
+    ap.add_argument("--form", choices=["plain", "batched"], default="plain",
+                    help="plain: host-driven levels; batched: persistent kernels, no host round trips")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true",

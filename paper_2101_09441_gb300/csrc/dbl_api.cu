@@ -68,6 +68,12 @@ dbl_status read_status(dbl_index *ix, cudaStream_t s)
     if (e) return cuda_fail(ix, e, "synchronize");
     uint32_t st = ix->h_pinned[8];
     if (st) cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);  // consumed
+    if (st == DBL_ERR_TIMEOUT || st == DBL_ERR_CAPACITY) {
+        // a device loop gave up or a device buffer overflowed mid-update: labels
+        // may be short of the fixpoint, so refuse further use until dbl_restore
+        ix->poisoned = true;
+        fail(ix, (dbl_status)st, "device loop timed out or overflowed; index poisoned until dbl_restore");
+    }
     return (dbl_status)st;
 }
 
@@ -143,6 +149,7 @@ dbl_status ensure_search_scratch(dbl_index *ix, int64_t q, cudaStream_t s)
         int64_t tcap = (int64_t)ix->n + (ix->m + ix->edge_cap) / kChunk + 4096;
         if ((st = alloc_buf(ix, (void **)&ix->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
         ix->stask_cap = tcap;
+        if ((st = alloc_buf(ix, &ix->pstate, persist_state_bytes(), s))) return st;
     }
     return DBL_OK;
 }
@@ -261,7 +268,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
         (st = A((void **)&ix->rec, 8 * n * ix->rw)) || (st = A((void **)&ix->landmarks, 4 * (size_t)k)) ||
         (st = A((void **)&ix->leaf_bucket, 4 * n)) || (st = A((void **)&ix->leaf_role, n)) ||
-        (st = A((void **)&ix->stamp, 8 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
+        (st = A((void **)&ix->stamp, 16 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
         (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
         (st = A((void **)&ix->ins_cnt, 8 * n))) {
@@ -272,7 +279,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     cudaMemsetAsync(ix->ovo, 0, 12 * n, s);
     cudaMemsetAsync(ix->ovi, 0, 12 * n, s);
     cudaMemsetAsync(ix->d_pool_top, 0, 16, s);
-    cudaMemsetAsync(ix->stamp, 0, 8 * n, s);
+    cudaMemsetAsync(ix->stamp, 0, 16 * n, s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
     cudaMemsetAsync(ix->d_status, 0, 16, s);
     cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);

@@ -14,8 +14,8 @@ struct FrontierOut {
     uint64_t *tasks;
     uint32_t *count;
     int64_t cap;
-    uint32_t *stamp;   // [2][n]
-    uint32_t epoch;    // stamp value of the level being filled
+    unsigned long long *stamp;  // [2][n] epoch of the last enqueue per direction
+    unsigned long long epoch;   // stamp value of the level being filled (64-bit: never wraps)
     uint32_t *status;
 };
 
@@ -27,7 +27,7 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
     const int lane = threadIdx.x & 31;
     uint32_t nchunks = 0;
     if (want) {
-        uint32_t *st = f.stamp + (size_t)dir * (size_t)g.n + x;
+        unsigned long long *st = f.stamp + (size_t)dir * (size_t)g.n + x;
         if (atomicExch(st, f.epoch) != f.epoch) {
             int32_t d = deg_of(g, dir, x);
             nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
@@ -54,7 +54,7 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
 // Same, for callers whose loop is not warp-uniform: uses the active mask.
 __device__ __forceinline__ void any_enqueue(int32_t x, int dir, const DevGraph &g, const FrontierOut &f)
 {
-    uint32_t *st = f.stamp + (size_t)dir * (size_t)g.n + x;
+    unsigned long long *st = f.stamp + (size_t)dir * (size_t)g.n + x;
     if (atomicExch(st, f.epoch) == f.epoch) return;
     int32_t d = deg_of(g, dir, x);
     uint32_t nchunks = (uint32_t)((d + kChunk - 1) / kChunk);

@@ -27,9 +27,15 @@ __global__ void k_ins_validate(const int32_t *src, const int32_t *dst, int64_t b
 }
 
 // per-edge rank inside its source (out) and destination (in) vertex batch
+// Every mutating kernel of an insertion first reads the status word: after a
+// failed validation (or any latched error) it changes nothing, so the
+// asynchronous form needs no host round trip between validation and append.
+__device__ __forceinline__ bool status_set(const uint32_t *status) { return *(const volatile uint32_t *)status != 0; }
+
 __global__ void k_ins_count(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
-                            int32_t *pos_out, int32_t *pos_in, unsigned long long *stats)
+                            int32_t *pos_out, int32_t *pos_in, unsigned long long *stats, const uint32_t *status)
 {
+    if (status_set(status)) return;
     unsigned long long loops = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t u = src[i], v = dst[i];
@@ -53,27 +59,45 @@ __device__ __forceinline__ int32_t grown_cap(int32_t need)
 }
 
 // The first edge of each vertex batch grows that vertex's segment if needed.
+// New segments are reserved with one atomicAdd per warp (a warp-wide prefix
+// sum of the sizes) instead of one per vertex on the shared pool top.
 __global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *cnt_out,
                            const int32_t *cnt_in, const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo,
                            int32_t *ovi, int32_t *pool_out, int32_t *pool_in, int64_t *pool_top, int32_t n,
                            int64_t pool_cap, uint32_t *status)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+    if (status_set(status)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < b; base += stride) {
+        const int64_t i = base + threadIdx.x;
         for (int dir = 0; dir < 2; ++dir) {
-            const int32_t pos = dir ? pos_in[i] : pos_out[i];
-            if (pos != 0) continue;
-            const int32_t x = dir ? dst[i] : src[i];
+            int32_t x = 0, len = 0, nc = 0;
             int32_t *meta = dir ? ovi : ovo;  // [off | len | cap]
-            int32_t *pool = dir ? pool_in : pool_out;
-            const int32_t len = meta[n + x], cap = meta[2 * n + x];
-            const int32_t need = len + (dir ? cnt_in[x] : cnt_out[x]);
-            if (need <= cap) continue;
-            const int32_t nc = grown_cap(need);
-            const long long off = atomicAdd((unsigned long long *)(pool_top + dir), (unsigned long long)nc);
+            if (i < b && (dir ? pos_in[i] : pos_out[i]) == 0) {
+                x = dir ? dst[i] : src[i];
+                len = meta[n + x];
+                const int32_t need = len + (dir ? cnt_in[x] : cnt_out[x]);
+                if (need > meta[2 * n + x]) nc = grown_cap(need);
+            }
+            unsigned long long incl = (unsigned long long)nc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned long long total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) continue;
+            unsigned long long wbase = 0;
+            if (lane == 31) wbase = atomicAdd((unsigned long long *)(pool_top + dir), total);
+            wbase = __shfl_sync(kFull, wbase, 31);
+            if (!nc) continue;
+            const long long off = (long long)(wbase + incl - (unsigned long long)nc);
             if (off + nc > pool_cap) {
                 set_status(status, DBL_ERR_CAPACITY);  // cannot happen: pool holds 4x the edge capacity
                 continue;
             }
+            int32_t *pool = dir ? pool_in : pool_out;
             const int32_t old = meta[x];
             for (int32_t j = 0; j < len; ++j) pool[off + j] = pool[old + j];
             meta[x] = (int32_t)off;
@@ -84,8 +108,9 @@ __global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, co
 
 __global__ void k_ins_write(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *pos_out,
                             const int32_t *pos_in, const int32_t *ovo, const int32_t *ovi, int32_t *pool_out,
-                            int32_t *pool_in, int32_t n)
+                            int32_t *pool_in, int32_t n, const uint32_t *status)
 {
+    if (status_set(status)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t po = pos_out[i];
         if (po < 0) continue;
@@ -97,8 +122,10 @@ __global__ void k_ins_write(const int32_t *src, const int32_t *dst, int64_t b, c
 }
 
 __global__ void k_ins_commit(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
-                             const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo, int32_t *ovi, int32_t n)
+                             const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo, int32_t *ovi, int32_t n,
+                             const uint32_t *status)
 {
+    if (status_set(status)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
         if (pos_out[i] == 0) {
             const int32_t u = src[i];
@@ -119,6 +146,7 @@ template <int HS, int WD>
 __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const int32_t *dst, int64_t b, DevGraph g,
                                                      uint64_t *rec, FrontierOut f, unsigned long long *stats)
 {
+    if (status_set(f.status)) return;
     constexpr int RW = 2 * HS;
     unsigned long long skipped = 0, applied = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -196,20 +224,28 @@ dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, i
     k_ins_validate<<<grid, kBlock, 0, s>>>(src, dst, b, n, ix->d_status);
     ++ix->launches;
     tend(ix, s);
-    dbl_status st = read_status(ix, s);
-    if (st) return fail(ix, st, "insert: vertex id out of range");
+    // The synchronous form reports a bad id before anything else runs; the
+    // asynchronous persistent form leaves it latched (every mutating kernel
+    // below then does nothing) and dbl_sync reports it.
+    const bool no_sync = (ix->opt.flags & DBL_FLAG_ASYNC) && (ix->opt.flags & DBL_FLAG_PERSISTENT);
+    if (!no_sync) {
+        dbl_status st = read_status(ix, s);
+        if (st) return fail(ix, st, "insert: vertex id out of range");
+    }
     // 2. append
     int32_t *pos_out = ix->ins_pos, *pos_in = ix->ins_pos + ix->ins_bcap;
     int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + n;
     tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
-    k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats);
+    k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status);
     ++ix->launches;
     k_ins_grow<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out,
                                        ix->pool_in, ix->d_pool_top, n, ix->pool_cap, ix->d_status);
     ++ix->launches;
-    k_ins_write<<<grid, kBlock, 0, s>>>(src, dst, b, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out, ix->pool_in, n);
+    k_ins_write<<<grid, kBlock, 0, s>>>(src, dst, b, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out, ix->pool_in, n,
+                                        ix->d_status);
     ++ix->launches;
-    k_ins_commit<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, n);
+    k_ins_commit<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, n,
+                                         ix->d_status);
     ++ix->launches;
     ix->edges_stored += b;
     atomic_add_host_stat(ix, 15, (uint64_t)b, s);

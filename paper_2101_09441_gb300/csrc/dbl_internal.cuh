@@ -150,11 +150,11 @@ struct dbl_index {
     uint8_t *leaf_role = nullptr;
 
     // frontier scratch
-    uint32_t *stamp = nullptr;        // [2][n] enqueue stamps per direction
+    unsigned long long *stamp = nullptr;  // [2][n] enqueue epoch per direction
     uint64_t *front[2] = {nullptr, nullptr};
     int64_t front_cap = 0;
     uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
-    uint32_t epoch = 0;               // last stamp epoch used
+    unsigned long long epoch = 0;     // last frontier epoch used
 
     // insertion scratch
     int32_t *ins_cnt = nullptr;       // [2][n] per-vertex batch counts
@@ -174,8 +174,7 @@ struct dbl_index {
     int32_t *slot_list[2] = {nullptr, nullptr};
     dbl::SearchTask *stask = nullptr;
     int64_t stask_cap = 0;
-    int32_t *wave_groups = nullptr;   // group ids of the current wave
-    int64_t wave_groups_cap = 0;
+    void *pstate = nullptr;           // device state of the persistent search
 
     // status, counters
     uint32_t *d_status = nullptr;
@@ -213,6 +212,9 @@ enum {
     kCntClaimed = 6,    // claimed slots
     kCntOverflow = 7,   // search wave overflow flag
     kCntGrow = 8,       // (2 words) pool growth request, int64
+    kCntP0 = 10,        // (3 words) persistent propagation level counts
+    kCntBarArrived = 13,  // grid barrier: blocks arrived
+    kCntBarPhase = 14,    // grid barrier: generation
     kCntWords = 16
 };
 
@@ -226,6 +228,7 @@ dbl_status cuda_fail(dbl_index *ix, cudaError_t e, const char *what);
 dbl_status read_status(dbl_index *ix, cudaStream_t s);
 dbl_status ensure_search_scratch(dbl_index *ix, int64_t und, cudaStream_t s);
 void atomic_add_host_stat(dbl_index *ix, int idx, uint64_t v, cudaStream_t s);
+size_t persist_state_bytes();  // dbl_query.cu
 // bracket the launches between tbegin and tend (no-op without DBL_FLAG_TIMING)
 void tbegin(dbl_index *ix, int kind, cudaStream_t s);
 void tend(dbl_index *ix, cudaStream_t s);

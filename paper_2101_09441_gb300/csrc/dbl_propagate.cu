@@ -15,6 +15,7 @@
 #include "dbl_frontier.cuh"
 #include "dbl_internal.cuh"
 #include "dbl_kernels.cuh"
+#include "dbl_persistent.cuh"
 
 namespace dbl {
 
@@ -108,13 +109,104 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
     return DBL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form: one cooperative launch runs every level.  Level L reads
+// frontier buffer L%2 with count c[L%3] and fills buffer (L+1)%2 / c[(L+1)%3];
+// block 0 zeroes c[(L+2)%3], which nobody touches during level L.  One grid
+// barrier per level; every block sees the same counts after it, so all take
+// the same exit.  The level bound and the barrier's bounded wait turn any
+// runaway into DBL_ERR_TIMEOUT instead of a hang.
+template <int HS, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0,
+                                                                 uint64_t *f1, uint32_t *c3, int64_t cap,
+                                                                 unsigned long long *stamp,
+                                                                 unsigned long long epoch0, uint32_t *status,
+                                                                 unsigned long long *stats, GridBarrier bar,
+                                                                 int64_t max_levels)
+{
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long epoch = epoch0;
+    int64_t L = 0;
+    for (;; ++L) {
+        const uint32_t nt = ld_volatile_u32(c3 + L % 3);
+        if (nt == 0 || ld_volatile_u32(status)) break;
+        if (L >= max_levels) {
+            set_status(status, DBL_ERR_TIMEOUT);
+            break;
+        }
+        ++epoch;
+        if (blockIdx.x == 0 && threadIdx.x == 0) c3[(L + 2) % 3] = 0;
+        FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, stamp, epoch, status};
+        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, f, stats, warp0, nwarps);
+        if (!grid_sync(bar, status)) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        stats[8] += (unsigned long long)L;
+        c3[L % 3] = 0;
+    }
+}
+
+template <int HS, int TEAM>
+static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
+{
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_propagate_persistent<HS, TEAM>, kBlock, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    DevGraph g = dev_graph(ix);
+    uint64_t *f0 = ix->front[0], *f1 = ix->front[1];
+    uint32_t *c3 = ix->d_counts + kCntP0;
+    int64_t cap = ix->front_cap;
+    unsigned long long *stamp = ix->stamp;
+    unsigned long long epoch0 = ix->epoch;
+    uint32_t *status = ix->d_status;
+    unsigned long long *stats = ix->d_stats;
+    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
+    int64_t max_levels = (int64_t)ix->n + 2;
+    // the level count is unknown on the host: reserve every epoch the launch may use
+    ix->epoch += (unsigned long long)max_levels + 2;
+    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &stamp, &epoch0, &status, &stats, &bar, &max_levels};
+    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_propagate_persistent<HS, TEAM>, grid, block, args, 0, s);
+    ++ix->launches;
+    return e ? cuda_fail(ix, e, "persistent propagate launch") : DBL_OK;
+}
+
+template <int HS>
+static dbl_status launch_persistent_team(dbl_index *ix, cudaStream_t s)
+{
+    switch (ix->opt.team) {
+    case 4: return launch_persistent<HS, 4>(ix, s);
+    case 16: return launch_persistent<HS, 16>(ix, s);
+    case 32: return launch_persistent<HS, 32>(ix, s);
+    default: return launch_persistent<HS, 8>(ix, s);
+    }
+}
+
 dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s)
 {
-    const int32_t flags = ix->opt.flags;
-    ix->opt.flags &= ~DBL_FLAG_PERSISTENT;
-    dbl_status st = propagate(ix, s);
-    ix->opt.flags = flags;
-    return st;
+    // the starting frontier is buffer 0 with its count in kCntFront0
+    cudaMemcpyAsync(ix->d_counts + kCntP0, ix->d_counts + kCntFront0, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(ix->d_counts + kCntP0 + 1, 0, 2 * sizeof(uint32_t), s);
+    tbegin(ix, DBL_KERNEL_PROPAGATE, s);
+    dbl_status st;
+    switch (ix->hs) {
+    case 2: st = launch_persistent_team<2>(ix, s); break;
+    case 4: st = launch_persistent_team<4>(ix, s); break;
+    default: st = launch_persistent_team<8>(ix, s); break;
+    }
+    tend(ix, s);
+    cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
+    if (st) return st;
+    if (ix->opt.flags & DBL_FLAG_ASYNC) return DBL_OK;  // errors surface through dbl_sync
+    uint32_t code = 0;
+    cudaMemcpyAsync(ix->h_pinned + 8, ix->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "persistent propagate");
+    code = ix->h_pinned[8];
+    return code ? propagate_error(ix, code, s) : DBL_OK;
 }
 
 }  // namespace dbl

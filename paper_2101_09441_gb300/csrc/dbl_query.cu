@@ -23,6 +23,7 @@
 #include "dbl_frontier.cuh"
 #include "dbl_internal.cuh"
 #include "dbl_kernels.cuh"
+#include "dbl_persistent.cuh"
 
 namespace dbl {
 
@@ -115,6 +116,41 @@ struct SearchCtx {
     uint32_t *overflow;
 };
 
+struct SlotList {
+    int32_t *items;
+    uint32_t *count;
+    int64_t cap;
+};
+
+// Everything a search phase needs (both forms).
+struct SearchArgs {
+    DevGraph g;
+    const uint64_t *rec;
+    uint64_t *qtab;
+    unsigned long long *found;
+    SearchCtx c;
+    SearchTask *tasks;
+    int64_t task_cap;
+    const int32_t *und;
+    const int32_t *qu, *qv;
+    uint8_t *ans, *code;
+    unsigned long long *stats;
+    int32_t *lists[2];
+    int64_t list_cap;
+};
+
+// Device-side state of the persistent search.
+struct PersistState {
+    uint32_t list_count[2];
+    uint32_t task_count[2];
+    uint32_t n_claimed;
+    uint32_t overflow;
+    int32_t top;
+    int32_t pad;
+    long long range[2];
+    long long stack[64][2];
+};
+
 constexpr int kMaxProbe = 2048;
 
 __device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsigned long long key)
@@ -128,7 +164,7 @@ __device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsig
             unsigned long long prev = atomicCAS(&s->key, kEmptyKey, key);
             if (prev == kEmptyKey) {
                 uint32_t pos = atomicAdd(c.n_claimed, 1u);
-                c.claimed[pos] = (int32_t)h;  // pos < slots: each slot is claimed once
+                c.claimed[pos] = (int32_t)h;  // pos < slots: each slot is claimed once per wave
                 return (int64_t)h;
             }
             if (prev == key) return (int64_t)h;
@@ -145,12 +181,6 @@ struct QT {
     static constexpr int W = 1 + WD + 2 * WB;
 };
 
-struct SlotList {
-    int32_t *items;
-    uint32_t *count;
-    int64_t cap;
-};
-
 __device__ __forceinline__ void mark_pending(const SearchCtx &c, int64_t slot, unsigned long long bits,
                                              uint32_t epoch, const SlotList &next)
 {
@@ -163,21 +193,24 @@ __device__ __forceinline__ void mark_pending(const SearchCtx &c, int64_t slot, u
     }
 }
 
-// Wave setup: queries [j0, j1) of the undecided list (groups j/64).
+// Wave setup: queries [j0, j1) of the undecided list (group j/64, bit j%64):
+// fill the query table, zero the groups' found words, and start every search
+// at its u (visited and pending there).
 template <int WD, int WB>
-__global__ void k_search_setup(const int32_t *und, int64_t j0, int64_t j1, const int32_t *qu, const int32_t *qv,
-                               const uint64_t *rec, uint64_t *qtab, SearchCtx c, uint32_t epoch, SlotList first)
+__device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, int64_t j1, uint32_t epoch,
+                                             const SlotList &first)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
     constexpr int W = QT<WD, WB>::W;
-    for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = und[j];
-        const int32_t u = qu[i], v = qv[i];
-        uint64_t *t = qtab + (size_t)j * W;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t gq = (j0 >> 6) + t0; gq < ((j1 + 63) >> 6); gq += nt) a.found[gq] = 0;
+    for (int64_t j = j0 + t0; j < j1; j += nt) {
+        const int64_t i = a.und[j];
+        const int32_t u = a.qu[i], v = a.qv[i];
+        uint64_t *t = a.qtab + (size_t)j * W;
         t[0] = (uint64_t)(uint32_t)u | ((uint64_t)(uint32_t)v << 32);
-        const uint64_t *ru = rec + (size_t)u * RW, *rv = rec + (size_t)v * RW;
+        const uint64_t *ru = a.rec + (size_t)u * RW, *rv = a.rec + (size_t)v * RW;
 #pragma unroll
         for (int w = 0; w < WD; ++w) t[1 + w] = ru[HS + w];              // DL_out(u)
 #pragma unroll
@@ -187,32 +220,49 @@ __global__ void k_search_setup(const int32_t *und, int64_t j0, int64_t j1, const
         }
         const unsigned long long g = (unsigned long long)(j >> 6);
         const unsigned long long bit = 1ull << (j & 63);
-        int64_t s = slot_find_or_insert(c, (g << 32) | (uint32_t)u);
+        int64_t s = slot_find_or_insert(a.c, (g << 32) | (uint32_t)u);
         if (s < 0) continue;
-        atomicOr(&c.table[s].visit, bit);
-        mark_pending(c, s, bit, epoch, first);
+        atomicOr(&a.c.table[s].visit, bit);
+        mark_pending(a.c, s, bit, epoch, first);
     }
 }
 
-// Slots listed for the next level -> tasks (x, g, chunk, mask) over Suc(x).
-__global__ void k_search_finalize(const SlotList cur, DevGraph g, SearchCtx c, SearchTask *tasks,
-                                  uint32_t *n_tasks, int64_t task_cap)
+// Slots listed for the next level -> tasks (x, g, chunk, mask) over Suc(x);
+// one task-list reservation per warp.
+__device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotList &cur, uint32_t *n_tasks)
 {
-    const uint32_t n = *cur.count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n && i < cur.cap;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        SearchSlot *s = c.table + cur.items[i];
-        const unsigned long long mask = atomicExch(&s->pend, 0ull);
-        if (!mask) continue;
-        const unsigned long long key = s->key;
-        const int32_t x = (int32_t)(uint32_t)key;
-        const int32_t d = deg_of(g, 0, x);
-        const uint32_t nch = (uint32_t)((d + kChunk - 1) / kChunk);
-        if (!nch) continue;
-        uint32_t pos = atomicAdd(n_tasks, nch);
+    const int64_t n = min((int64_t)ld_volatile_u32(cur.count), cur.cap);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        unsigned long long mask = 0, key = 0;
+        uint32_t nch = 0;
+        int32_t x = 0;
+        if (i < n) {
+            SearchSlot *s = a.c.table + cur.items[i];
+            mask = atomicExch(&s->pend, 0ull);
+            if (mask) {
+                key = s->key;
+                x = (int32_t)(uint32_t)key;
+                nch = (uint32_t)((deg_of(a.g, 0, x) + kChunk - 1) / kChunk);
+            }
+        }
+        uint32_t incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        uint32_t wbase = 0;
+        if (lane == 31) wbase = atomicAdd(n_tasks, total);
+        wbase = __shfl_sync(kFull, wbase, 31);
+        uint32_t pos = wbase + incl - nch;
         for (uint32_t ch = 0; ch < nch; ++ch, ++pos) {
-            if ((int64_t)pos >= task_cap) {
-                atomicExch(c.overflow, 1u);
+            if ((int64_t)pos >= a.task_cap) {
+                atomicExch(a.c.overflow, 1u);
                 break;
             }
             SearchTask t;
@@ -221,17 +271,17 @@ __global__ void k_search_finalize(const SlotList cur, DevGraph g, SearchCtx c, S
             t.chunk = ch;
             t.pad = 0;
             t.mask = mask;
-            tasks[pos] = t;
+            a.tasks[pos] = t;
         }
     }
 }
 
+// One search level: for each task's edges x -> y and each live query j of the
+// task's mask, in Algorithm 2's order: y == v_j -> found; DL prune; BL prune;
+// otherwise y is visited for j, and bits new at y are pending for next level.
 template <int WD, int WB, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_search_expand(const SearchTask *tasks, const uint32_t *n_tasks_p,
-                                                          int64_t task_cap, DevGraph g, const uint64_t *rec,
-                                                          const uint64_t *qtab, unsigned long long *found,
-                                                          SearchCtx c, uint32_t epoch, SlotList next,
-                                                          unsigned long long *stats)
+__device__ __forceinline__ void search_expand(const SearchArgs &a, uint32_t n_tasks_in, uint32_t epoch,
+                                              const SlotList &next)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
@@ -239,29 +289,27 @@ __global__ void __launch_bounds__(kBlock) k_search_expand(const SearchTask *task
     constexpr int TPW = 32 / TEAM;
     const int lane = threadIdx.x & 31;
     const int team = lane / TEAM, tl = lane % TEAM;
-    int64_t ntasks = *n_tasks_p;
-    if (ntasks > task_cap) ntasks = task_cap;
+    const int64_t ntasks = min((int64_t)n_tasks_in, a.task_cap);
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long relaxed = 0;
     for (int64_t wb = warp0 * TPW; wb < ntasks; wb += nwarps * TPW) {
         const int64_t t = wb + team;
         if (t >= ntasks) continue;
-        const SearchTask tk = tasks[t];
-        const unsigned long long fg = __ldcg(found + tk.g);
-        const unsigned long long m = tk.mask & ~fg;
+        const SearchTask tk = a.tasks[t];
+        const unsigned long long m = tk.mask & ~__ldcg(a.found + tk.g);
         if (!m) continue;
-        const AdjRange r = adj_of(g, 0, tk.x);
+        const AdjRange r = adj_of(a.g, 0, tk.x);
         const int32_t d = r.bd + r.od;
         const int32_t lo = (int32_t)tk.chunk * kChunk;
         const int32_t hi = min(d, lo + kChunk);
-        const uint64_t *qg = qtab + (size_t)tk.g * 64 * W;
+        const uint64_t *qg = a.qtab + (size_t)tk.g * 64 * W;
         for (int32_t e = lo + tl; e < hi; e += TEAM) {
-            const int32_t y = adj_at(g, 0, r, e);
+            const int32_t y = adj_at(a.g, 0, r, e);
             ++relaxed;
             uint64_t fy[HS], by[HS];
-            load_half<HS>(rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
-            load_half<HS>(rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
+            load_half<HS>(a.rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
+            load_half<HS>(a.rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
             unsigned long long hits = 0, allowed = 0, rest = m;
             while (rest) {
                 const int b = __ffsll((long long)rest) - 1;
@@ -283,57 +331,165 @@ __global__ void __launch_bounds__(kBlock) k_search_expand(const SearchTask *task
                 if (bl) continue;
                 allowed |= bit;
             }
-            if (hits) atomicOr(found + tk.g, hits);
+            if (hits) atomicOr(a.found + tk.g, hits);
             if (allowed) {
-                const int64_t s = slot_find_or_insert(c, ((unsigned long long)tk.g << 32) | (uint32_t)y);
+                const int64_t s = slot_find_or_insert(a.c, ((unsigned long long)tk.g << 32) | (uint32_t)y);
                 if (s < 0) continue;
-                const unsigned long long old = atomicOr(&c.table[s].visit, allowed);
+                const unsigned long long old = atomicOr(&a.c.table[s].visit, allowed);
                 const unsigned long long nb = allowed & ~old;
-                if (nb) mark_pending(c, s, nb, epoch, next);
+                if (nb) mark_pending(a.c, s, nb, epoch, next);
             }
         }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) relaxed += __shfl_xor_sync(kFull, relaxed, o);
-    if (lane == 0 && relaxed) atomicAdd(stats + 10, relaxed);
+    if (lane == 0 && relaxed) atomicAdd(a.stats + 10, relaxed);
 }
 
-__global__ void k_search_answer(const int32_t *und, int64_t j0, int64_t j1, const unsigned long long *found,
-                                int final_wave, uint8_t *ans, uint8_t *code, unsigned long long *stats)
+// Answers of queries [j0, j1): found -> true (bfs_pos); otherwise false
+// (bfs_neg) when the wave ran to exhaustion (final), else left for a rerun.
+__device__ __forceinline__ void search_answer(const SearchArgs &a, int64_t j0, int64_t j1, bool final_wave)
 {
     __shared__ unsigned int cnt[2];
     if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const bool hit = (found[j >> 6] >> (j & 63)) & 1ull;
-        const int64_t i = und[j];
+        const bool hit = (__ldcg(a.found + (j >> 6)) >> (j & 63)) & 1ull;
+        const int64_t i = a.und[j];
         if (hit) {
-            ans[i] = 1;
-            if (code) code[i] = DBL_CODE_BFS_POS;
+            a.ans[i] = 1;
+            if (a.code) a.code[i] = DBL_CODE_BFS_POS;
             atomicAdd(&cnt[0], 1u);
         } else if (final_wave) {
-            ans[i] = 0;
-            if (code) code[i] = DBL_CODE_BFS_NEG;
+            a.ans[i] = 0;
+            if (a.code) a.code[i] = DBL_CODE_BFS_NEG;
             atomicAdd(&cnt[1], 1u);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (cnt[0]) atomicAdd(stats + DBL_CODE_BFS_POS, (unsigned long long)cnt[0]);
-        if (cnt[1]) atomicAdd(stats + DBL_CODE_BFS_NEG, (unsigned long long)cnt[1]);
+        if (cnt[0]) atomicAdd(a.stats + DBL_CODE_BFS_POS, (unsigned long long)cnt[0]);
+        if (cnt[1]) atomicAdd(a.stats + DBL_CODE_BFS_NEG, (unsigned long long)cnt[1]);
     }
 }
 
-__global__ void k_search_clear(SearchSlot *table, const int32_t *claimed, const uint32_t *n_claimed)
+// Return every slot claimed in the wave to empty.
+__device__ __forceinline__ void search_clear(const SearchArgs &a)
 {
-    const uint32_t n = *n_claimed;
+    const uint32_t n = ld_volatile_u32(a.c.n_claimed);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        SearchSlot *s = table + claimed[i];
+        SearchSlot *s = a.c.table + a.c.claimed[i];
         s->key = kEmptyKey;
         s->visit = 0;
         s->pend = 0;
         s->stamp = 0;
+    }
+}
+
+// ------------------------------------------------------------ per-level kernels
+template <int WD, int WB>
+__global__ void k_search_setup(SearchArgs a, int64_t j0, int64_t j1, uint32_t epoch, SlotList first)
+{
+    search_setup<WD, WB>(a, j0, j1, epoch, first);
+}
+
+__global__ void k_search_finalize(SearchArgs a, SlotList cur, uint32_t *n_tasks) { search_finalize(a, cur, n_tasks); }
+
+template <int WD, int WB, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_search_expand(SearchArgs a, const uint32_t *n_tasks, uint32_t epoch,
+                                                          SlotList next)
+{
+    search_expand<WD, WB, TEAM>(a, ld_volatile_u32(n_tasks), epoch, next);
+}
+
+__global__ void k_search_answer(SearchArgs a, int64_t j0, int64_t j1, int final_wave)
+{
+    search_answer(a, j0, j1, final_wave != 0);
+}
+
+__global__ void k_search_clear(SearchArgs a) { search_clear(a); }
+
+// ------------------------------------------------------------ persistent kernel
+// All waves and levels of one query batch in one cooperative launch.  Block 0
+// keeps a stack of query ranges (an overflowing wave is split in halves) and
+// the phase counters; every decision is read by all blocks after a barrier.
+// Per level: finalize, barrier, expand, barrier.
+template <int WD, int WB, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_search_persistent(SearchArgs a, PersistState *ps, const uint32_t *n_und,
+                                                              GridBarrier bar, uint32_t *status, int64_t max_levels)
+{
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    const uint32_t U = ld_volatile_u32(n_und);
+    if (U == 0) return;
+    if (leader) {
+        ps->top = 1;
+        ps->stack[0][0] = 0;
+        ps->stack[0][1] = U;
+    }
+    unsigned long long levels = 0, waves = 0;
+    for (;;) {
+        if (leader) {
+            if (ps->top > 0) {
+                --ps->top;
+                ps->range[0] = ps->stack[ps->top][0];
+                ps->range[1] = ps->stack[ps->top][1];
+            } else {
+                ps->range[0] = ps->range[1] = -1;
+            }
+            ps->list_count[0] = ps->list_count[1] = 0;
+            ps->task_count[0] = ps->task_count[1] = 0;
+            ps->n_claimed = 0;
+            ps->overflow = 0;
+        }
+        if (!grid_sync(bar, status)) return;
+        const long long j0 = *(volatile long long *)&ps->range[0], j1 = *(volatile long long *)&ps->range[1];
+        if (j0 < 0 || ld_volatile_u32(status)) break;
+        ++waves;
+        SlotList lists[2] = {{a.lists[0], &ps->list_count[0], a.list_cap}, {a.lists[1], &ps->list_count[1], a.list_cap}};
+        uint32_t sep = 1;
+        search_setup<WD, WB>(a, j0, j1, sep, lists[0]);
+        if (!grid_sync(bar, status)) return;
+        for (int64_t L = 0;; ++L) {
+            const int cur = (int)(L & 1);
+            if (!ld_volatile_u32(&ps->list_count[cur]) || ld_volatile_u32(&ps->overflow) || ld_volatile_u32(status))
+                break;
+            if (L >= max_levels) {
+                set_status(status, DBL_ERR_TIMEOUT);
+                break;
+            }
+            ++levels;
+            search_finalize(a, lists[cur], &ps->task_count[cur]);
+            if (!grid_sync(bar, status)) return;
+            ++sep;
+            if (leader) {
+                ps->list_count[cur] = 0;
+                ps->task_count[cur ^ 1] = 0;
+            }
+            search_expand<WD, WB, TEAM>(a, ld_volatile_u32(&ps->task_count[cur]), sep, lists[cur ^ 1]);
+            if (!grid_sync(bar, status)) return;
+        }
+        const bool over = ld_volatile_u32(&ps->overflow) != 0;
+        search_answer(a, j0, j1, !over);
+        search_clear(a);
+        if (!grid_sync(bar, status)) return;
+        if (over && leader) {
+            const long long groups = (j1 - j0 + 63) / 64;
+            if (groups <= 1 || ps->top + 2 > 64) {
+                set_status(status, DBL_ERR_CAPACITY);
+            } else {
+                const long long mid = j0 + (groups / 2) * 64;
+                ps->stack[ps->top][0] = mid;
+                ps->stack[ps->top][1] = j1;
+                ps->stack[ps->top + 1][0] = j0;
+                ps->stack[ps->top + 1][1] = mid;
+                ps->top += 2;
+            }
+        }
+    }
+    if (leader) {
+        a.stats[8] += levels;
+        a.stats[14] += waves;
     }
 }
 
@@ -347,23 +503,57 @@ static unsigned blocks_for(int64_t work)
     return (unsigned)b;
 }
 
+static SearchArgs search_args(dbl_index *ix, const int32_t *qu, const int32_t *qv, uint8_t *ans, uint8_t *code,
+                              uint32_t *n_claimed, uint32_t *overflow)
+{
+    SearchArgs a;
+    a.g = dev_graph(ix);
+    a.rec = ix->rec;
+    a.qtab = ix->qtab;
+    a.found = ix->found;
+    a.c = SearchCtx{ix->table, (unsigned long long)(ix->table_slots - 1), ix->claimed, n_claimed, overflow};
+    a.tasks = ix->stask;
+    a.task_cap = ix->stask_cap;
+    a.und = ix->und;
+    a.qu = qu;
+    a.qv = qv;
+    a.ans = ans;
+    a.code = code;
+    a.stats = ix->d_stats;
+    a.lists[0] = ix->slot_list[0];
+    a.lists[1] = ix->slot_list[1];
+    a.list_cap = ix->table_slots;
+    return a;
+}
+
+template <int WD, int WB>
+static void launch_search_expand(dbl_index *ix, const SearchArgs &a, int64_t est, uint32_t sep, const SlotList &next,
+                                 cudaStream_t s)
+{
+    uint32_t *nt = ix->d_counts + kCntTasks;
+    switch (ix->opt.team) {
+    case 4: k_search_expand<WD, WB, 4><<<blocks_for(est * 4), kBlock, 0, s>>>(a, nt, sep, next); break;
+    case 16:
+    case 32: k_search_expand<WD, WB, 16><<<blocks_for(est * 16), kBlock, 0, s>>>(a, nt, sep, next); break;
+    default: k_search_expand<WD, WB, 8><<<blocks_for(est * 8), kBlock, 0, s>>>(a, nt, sep, next); break;
+    }
+    ++ix->launches;
+}
+
 template <int WD, int WB>
 static dbl_status run_search_wave(dbl_index *ix, const int32_t *qu, const int32_t *qv, int64_t j0, int64_t j1,
                                   uint8_t *ans, uint8_t *code, bool *overflowed, cudaStream_t s)
 {
     uint32_t *cnt = ix->d_counts;
     uint32_t *h = ix->h_pinned;
-    SearchCtx c{ix->table, (unsigned long long)(ix->table_slots - 1), ix->claimed, cnt + kCntClaimed,
-                cnt + kCntOverflow};
-    const int64_t g0 = j0 >> 6, g1 = (j1 + 63) >> 6;
-    cudaMemsetAsync(ix->found + g0, 0, sizeof(unsigned long long) * (size_t)(g1 - g0), s);
+    const SearchArgs a = search_args(ix, qu, qv, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
     cudaMemsetAsync(cnt + kCntSlots0, 0, sizeof(uint32_t) * 5, s);  // slots0, slots1, tasks, claimed, overflow
-    ix->epoch += 1;
+    // slot stamps are per wave (slots are cleared after each wave): level epochs 1, 2, ...
+    uint32_t sep = 1;
     SlotList lists[2] = {{ix->slot_list[0], cnt + kCntSlots0, ix->table_slots},
                          {ix->slot_list[1], cnt + kCntSlots1, ix->table_slots}};
     tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
-    k_search_setup<WD, WB><<<blocks_for(j1 - j0), kBlock, 0, s>>>(ix->und, j0, j1, qu, qv, ix->rec, ix->qtab, c,
-                                                                   ix->epoch, lists[0]);
+    k_search_setup<WD, WB><<<blocks_for(j1 - j0), kBlock, 0, s>>>(a, j0, j1, sep, lists[0]);
     ++ix->launches;
     tend(ix, s);
     int cur = 0;
@@ -384,48 +574,52 @@ static dbl_status run_search_wave(dbl_index *ix, const int32_t *qu, const int32_
         cudaMemsetAsync(cnt + kCntTasks, 0, sizeof(uint32_t), s);
         cudaMemsetAsync(cnt + kCntSlots0 + nxt, 0, sizeof(uint32_t), s);
         tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
-        k_search_finalize<<<blocks_for(nslots), kBlock, 0, s>>>(lists[cur], dev_graph(ix), c, ix->stask,
-                                                                 cnt + kCntTasks, ix->stask_cap);
+        k_search_finalize<<<blocks_for(nslots), kBlock, 0, s>>>(a, lists[cur], cnt + kCntTasks);
         ++ix->launches;
         tbegin(ix, DBL_KERNEL_SEARCH_EXPAND, s);
-        ix->epoch += 1;
+        ++sep;
         // tasks are at most nslots * (1 + maxdeg/kChunk); size the grid generously and let it stride
-        const int64_t est = (int64_t)nslots * 2;
-        switch (ix->opt.team) {
-        case 4:
-            k_search_expand<WD, WB, 4><<<blocks_for(est * 4), kBlock, 0, s>>>(
-                ix->stask, cnt + kCntTasks, ix->stask_cap, dev_graph(ix), ix->rec, ix->qtab, ix->found, c, ix->epoch,
-                lists[nxt], ix->d_stats);
-            ++ix->launches;
-            break;
-        case 16:
-            k_search_expand<WD, WB, 16><<<blocks_for(est * 16), kBlock, 0, s>>>(
-                ix->stask, cnt + kCntTasks, ix->stask_cap, dev_graph(ix), ix->rec, ix->qtab, ix->found, c, ix->epoch,
-                lists[nxt], ix->d_stats);
-            ++ix->launches;
-            break;
-        default:
-            k_search_expand<WD, WB, 8><<<blocks_for(est * 8), kBlock, 0, s>>>(
-                ix->stask, cnt + kCntTasks, ix->stask_cap, dev_graph(ix), ix->rec, ix->qtab, ix->found, c, ix->epoch,
-                lists[nxt], ix->d_stats);
-            ++ix->launches;
-            break;
-        }
+        launch_search_expand<WD, WB>(ix, a, (int64_t)nslots * 2, sep, lists[nxt], s);
         tend(ix, s);
         cur = nxt;
     }
     *overflowed = h[kCntOverflow] != 0;
     tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
-    k_search_answer<<<blocks_for(j1 - j0), kBlock, 0, s>>>(ix->und, j0, j1, ix->found, *overflowed ? 0 : 1, ans, code,
-                                                            ix->d_stats);
+    k_search_answer<<<blocks_for(j1 - j0), kBlock, 0, s>>>(a, j0, j1, *overflowed ? 0 : 1);
     ++ix->launches;
-    k_search_clear<<<blocks_for(ix->table_slots / 4), kBlock, 0, s>>>(ix->table, ix->claimed, cnt + kCntClaimed);
+    k_search_clear<<<blocks_for(ix->table_slots / 4), kBlock, 0, s>>>(a);
     ++ix->launches;
     tend(ix, s);
     atomic_add_host_stat(ix, 14, 1, s);
     atomic_add_host_stat(ix, 8, (uint64_t)levels, s);
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(ix, e, "search wave") : DBL_OK;
+}
+
+template <int WD, int WB, int TEAM>
+static dbl_status launch_search_persistent(dbl_index *ix, const int32_t *qu, const int32_t *qv, uint8_t *ans,
+                                           uint8_t *code, cudaStream_t s)
+{
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search_persistent<WD, WB, TEAM>, kBlock, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    PersistState *ps = (PersistState *)ix->pstate;
+    cudaMemsetAsync(ps, 0, sizeof(PersistState), s);
+    SearchArgs a = search_args(ix, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
+    const uint32_t *n_und = ix->d_counts + kCntUnd;
+    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
+    uint32_t *status = ix->d_status;
+    int64_t max_levels = (int64_t)ix->n + 2;
+    void *args[] = {&a, &ps, &n_und, &bar, &status, &max_levels};
+    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    tbegin(ix, DBL_KERNEL_SEARCH_EXPAND, s);
+    cudaError_t e =
+        cudaLaunchCooperativeKernel((const void *)k_search_persistent<WD, WB, TEAM>, grid, block, args, 0, s);
+    ++ix->launches;
+    tend(ix, s);
+    return e ? cuda_fail(ix, e, "persistent search launch") : DBL_OK;
 }
 
 template <int WD, int WB>
@@ -444,6 +638,16 @@ static dbl_status query_t(dbl_index *ix, const int32_t *u, const int32_t *v, int
                                                               cnt + kCntUnd, ix->d_status, ix->d_stats);
     ++ix->launches;
     tend(ix, s);
+    if (ix->opt.flags & DBL_FLAG_PERSISTENT) {
+        // the undecided count stays on the device; one launch runs every wave
+        switch (ix->opt.team) {
+        case 4: st = launch_search_persistent<WD, WB, 4>(ix, u, v, ans, code, s); break;
+        case 16:
+        case 32: st = launch_search_persistent<WD, WB, 16>(ix, u, v, ans, code, s); break;
+        default: st = launch_search_persistent<WD, WB, 8>(ix, u, v, ans, code, s); break;
+        }
+        return st;  // device errors (invalid ids, timeout) latch in the status word
+    }
     uint32_t *h = ix->h_pinned;
     cudaMemcpyAsync(h, cnt + kCntUnd, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + 8, ix->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
@@ -495,5 +699,7 @@ dbl_status query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, u
     default: return fail(ix, DBL_ERR_INVALID, "unsupported (k, kprime) combination");
     }
 }
+
+size_t persist_state_bytes() { return sizeof(PersistState); }
 
 }  // namespace dbl

@@ -303,3 +303,45 @@ def test_torch_and_default_allocators_agree(tiny):
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------- persistent / async forms
+@pytest.mark.parametrize("flags", [dbl.FLAG_PERSISTENT, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
+@pytest.mark.parametrize("k", [64, 128])
+def test_persistent_forms_match_oracle(tiny, flags, k):
+    """One cooperative launch per propagation and per query batch; with
+    FLAG_ASYNC no call waits for the device."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), k, 64, flags=flags)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], k, 64).build()
+    ix.sync()
+    assert_labels(ix, ref, "persistent build")
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    sizes = [1, 7, 100, 1000, 2892, 6000]
+    b = 0
+    for sz in sizes:
+        ix.insert_edges(D(s[b:b + sz]), D(d[b:b + sz]))
+        ref.insert_edges(s[b:b + sz], d[b:b + sz])
+        b += sz
+        ix.sync()
+        assert_labels(ix, ref, f"persistent after {b} edges")
+    ans, code = ix.query(D(tiny["q_u"]), D(tiny["q_v"]))
+    ix.sync()
+    rans, rcode = ref.query(tiny["q_u"], tiny["q_v"], nthreads=8)
+    assert np.array_equal(ans.cpu().numpy(), rans) and np.array_equal(code.cpu().numpy(), rcode)
+
+
+def test_async_invalid_batch_is_latched(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC)
+    ix.sync()
+    before = labels_np(ix)
+    ix.insert_edges(D(np.array([1, 2], np.int32)), D(np.array([3, tiny["n"] + 5], np.int32)))  # returns at once
+    with pytest.raises(dbl.DblError) as e:
+        ix.sync()
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    for a, b in zip(before, labels_np(ix)):
+        assert np.array_equal(a, b)
+    ix.insert_edges(D(tiny["ins_src"][:500]), D(tiny["ins_dst"][:500]))
+    ix.sync()
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ref.insert_edges(tiny["ins_src"][:500], tiny["ins_dst"][:500])
+    assert_labels(ix, ref, "after the latched error was read")
