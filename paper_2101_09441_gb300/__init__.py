@@ -185,17 +185,24 @@ class DBLIndex:
             pass
 
     # ------------------------------------------------------------------
-    def insert_edges(self, src, dst, stream=None):
+    @staticmethod
+    def _pair(a, b):
+        """Two equally long int32 device vectors."""
         import torch
-        src = src.to(torch.int32).contiguous()
-        dst = dst.to(torch.int32).contiguous()
+        a = a.to(torch.int32).contiguous()
+        b = b.to(torch.int32).contiguous()
+        if a.numel() != b.numel():
+            raise ValueError(f"paired id arrays differ in length ({a.numel()} vs {b.numel()})")
+        return a, b
+
+    def insert_edges(self, src, dst, stream=None):
+        src, dst = self._pair(src, dst)
         self._check(lib().dbl_insert_edges(self._h, _ptr(src), _ptr(dst), int(src.numel()), self._s(stream)))
 
     def query(self, u, v, with_code: bool = True, out=None, stream=None):
         """Answer q(u[i], v[i]); returns (ans uint8, code uint8 or None)."""
         import torch
-        u = u.to(torch.int32).contiguous()
-        v = v.to(torch.int32).contiguous()
+        u, v = self._pair(u, v)
         q = int(u.numel())
         if out is None:
             ans = torch.empty(q, dtype=torch.uint8, device=u.device)
@@ -209,6 +216,8 @@ class DBLIndex:
         """Host-buffer form: numpy in, numpy out (transfers inside the call)."""
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
+        if u.shape != v.shape:
+            raise ValueError("u and v differ in length")
         q = int(u.shape[0])
         if out is None:
             ans = np.empty(q, dtype=np.uint8)
@@ -222,6 +231,8 @@ class DBLIndex:
     def insert_edges_host(self, src: np.ndarray, dst: np.ndarray, stream=None):
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
+        if src.shape != dst.shape:
+            raise ValueError("src and dst differ in length")
         self._check(lib().dbl_insert_edges_host(self._h, src.ctypes.data, dst.ctypes.data, int(src.shape[0]),
                                                 self._s(stream)))
 
