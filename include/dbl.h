@@ -153,6 +153,31 @@ dbl_status dbl_insert_edges(dbl_index *ix, const int32_t *src, const int32_t *ds
 dbl_status dbl_query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
                      uint8_t *code, void *stream);
 
+/*
+ * dbl_insert_edges without any memory allocation.  (The paper has no
+ * counterpart: this is an interface for callers that cannot allocate.)
+ *
+ * dbl_insert_edges may allocate per-edge scratch (8 bytes per edge) from the
+ * index's allocator when a batch is larger than any before it.  Callers whose
+ * device memory is already fully handed to their own pool allocator, or that
+ * must not wait on an allocator in the middle of a latency-bound loop, cannot
+ * allow that.  This variant takes the scratch from a fixed 8 MiB array in the
+ * library's device memory instead (every GPU that loads the library holds it
+ * until the process exits); everything else it touches was allocated by
+ * dbl_build.  Same arguments, results and errors as dbl_insert_edges, plus:
+ *   - b > 1,048,576 edges is rejected with DBL_ERR_INVALID (split the batch);
+ *   - the device holding the index must be the current device;
+ *   - the first call on a device looks up the array's device address (a
+ *     cudaGetSymbolAddress, which allocates nothing); make that first call
+ *     before any stream capture;
+ *   - all calls in the process share the one array: calls whose device work
+ *     overlaps (on different streams, or on different indexes of the same
+ *     device) race on it and must be ordered by the caller.  Each call writes
+ *     every scratch entry it reads, so nothing left by an earlier call is used.
+ */
+dbl_status dbl_insert_edges_noalloc(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b,
+                                    void *stream);
+
 /* Host-buffer forms: copy inputs from host memory (pinned or pageable) to
  * the device, run the call, and copy results back, in overlapped chunks
  * (the transfer overlap of Section 6.6).  Synchronous. */

@@ -78,6 +78,7 @@ def lib():
             L.dbl_query.argtypes = [P, P, P, i64, P, P, P]
             L.dbl_query_host.argtypes = [P, P, P, i64, P, P, P]
             L.dbl_insert_edges_host.argtypes = [P, P, P, i64, P]
+            L.dbl_insert_edges_noalloc.argtypes = [P, P, P, i64, P]
             L.dbl_labels.argtypes = [P, P, P, P, P, P]
             L.dbl_selection.argtypes = [P, P, P, P, P]
             L.dbl_snapshot.argtypes = [P, ctypes.c_int, P]
@@ -198,6 +199,13 @@ class DBLIndex:
     def insert_edges(self, src, dst, stream=None):
         src, dst = self._pair(src, dst)
         self._check(lib().dbl_insert_edges(self._h, _ptr(src), _ptr(dst), int(src.numel()), self._s(stream)))
+
+    def insert_edges_noalloc(self, src, dst, stream=None):
+        """dbl_insert_edges_noalloc: the same insertion without allocating device
+        memory (scratch in a fixed library array; at most 2^20 edges per call)."""
+        src, dst = self._pair(src, dst)
+        self._check(lib().dbl_insert_edges_noalloc(self._h, _ptr(src), _ptr(dst), int(src.numel()),
+                                                   self._s(stream)))
 
     def query(self, u, v, with_code: bool = True, out=None, stream=None):
         """Answer q(u[i], v[i]); returns (ans uint8, code uint8 or None)."""

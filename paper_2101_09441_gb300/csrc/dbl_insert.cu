@@ -217,6 +217,17 @@ dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, i
         if (st) return st;
         ix->ins_bcap = nb;
     }
+    return insert_edges_core(ix, src, dst, b, ix->ins_pos, ix->ins_pos + ix->ins_bcap, s);
+}
+
+// The insertion itself, with the per-edge scratch (2 x b int32: each edge's
+// rank in its source's and its destination's batch) supplied by the caller.
+dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
+                             int32_t *pos_in, cudaStream_t s)
+{
+    if (b == 0) return DBL_OK;
+    if (ix->edges_stored + b > ix->edge_cap)
+        return fail(ix, DBL_ERR_CAPACITY, "insert: edge capacity exhausted (dbl_options.edge_capacity)");
     const int32_t n = ix->n;
     const unsigned grid = blocks_for(b);
     // 1. validate before anything changes
@@ -233,7 +244,6 @@ dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, i
         if (st) return fail(ix, st, "insert: vertex id out of range");
     }
     // 2. append
-    int32_t *pos_out = ix->ins_pos, *pos_in = ix->ins_pos + ix->ins_bcap;
     int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + n;
     tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
     k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status);

@@ -277,6 +277,8 @@ void launch_seed_frontier(dbl_index *ix, cudaStream_t s);  // all vertices with 
 
 // insertion (dbl_insert.cu)
 dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);
+dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
+                             int32_t *pos_in, cudaStream_t s);
 
 // query (dbl_query.cu)
 dbl_status query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
