@@ -3,18 +3,23 @@
 
 Workload "social" (the stand-in for LiveJournal's size in Table 2 of the
 paper): directed R-MAT (a,b,c,d = .57,.19,.19,.05), n = 4,847,571,
-m = 68,993,773, seed 2; k = 64 landmarks by M(u) = |Pre(u)|*|Suc(u)|,
-k' = 64 leaf buckets.  One step = restore the built index, insert 1,000,000
-new edges in batches (default 100,000; label repair of Algorithm 3 and its
-mirrors) and answer 10,000,000 mixed queries (Algorithm 2: half uniform
-pairs, half (u, end of a random forward walk from u)).  All inputs are
-resident in HBM before the timed region; the label array (155 MB), the pair
-arrays (80 MB) and the adjacency (590 MB) exceed the 126 MB L2, so no flush
-is needed between steps.
+m = 68,993,773, seed 2; k = 64 landmarks, k' = 64 leaf buckets.  One step =
+restore the built index, insert 1,000,000 new edges in batches of 100,000
+(label repair, Algorithm 3 and its mirrors) and answer 10,000,000 mixed
+queries (Algorithm 2: half uniform pairs, half (u, end of a random forward
+walk from u)).  Inputs are resident in HBM before the timed region; the
+labels (155 MB), pair arrays (80 MB) and adjacency (590 MB) exceed the 126 MB
+L2, so no flush is needed between steps.
 
-Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle
-(the repository's plain sequential statement of the method) on the same
-step instead.
+Forms, all on the same graph and inputs:
+  plain    degree landmarks; frontier levels driven from the host (one launch
+           and one read-back per level)
+  batched  degree landmarks; persistent cooperative kernels, no host round trip
+  graph    batched, with the whole step captured once as a CUDA graph
+  learned  learned landmarks (scorer trained on sampled query outcomes),
+           batched + graph: the headline `value`
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the same step instead.
 """
 from __future__ import annotations
 
@@ -37,8 +42,8 @@ if ROOT not in sys.path:
 METRIC = "queries/s + inserted edges/s, learned+batched vs plain GPU form, 100% exact"
 UNIT = "ops/s (queries + inserted edges)"
 
-# DRAM traffic per launch from an ncu capture, valid only while the kernel
-# source is unchanged: {kernel class: (bytes per launch, sha1 of source file)}.
+# DRAM traffic per launch from an ncu capture, valid only while the kernel's
+# source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
 NCU_TRAFFIC: dict[str, tuple[float, str]] = {}
 KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_kernels.cuh",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
@@ -92,18 +97,15 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
         return {"sm_mhz": statistics.median(float(r[1]) for r in rows), "sm_max_mhz": float(rows[0][2]),
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace('.', '', 1).isdigit())
-                if any(r[3].replace('.', '', 1).isdigit() for r in rows) else None}
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
 # ------------------------------------------------------------------ helpers
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def step_batches(n_edges: int, batch: int):
@@ -126,6 +128,13 @@ def run_oracle_step(ref, w, batches, nq, threads):
     ref.query(w["q_u"][:nq], w["q_v"][:nq], nthreads=threads)
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1
+
+
+def workload_config(args, w, form="learned+batched (persistent kernels, CUDA graph)"):
+    return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "k": args.k, "kprime": args.kprime,
+            "insert_batch": args.batch, "inserted_edges_per_step": int(w["ins_src"].shape[0]),
+            "queries_per_step": int(w["q_u"].shape[0]), "form": form,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -153,208 +162,13 @@ def bench_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(args, w),
+            "config": workload_config(args, w, "CPU oracle (sequential insertion repair, threaded queries)"),
             "components": {"queries_per_s": args.steps * Q / t_q, "inserted_edges_per_s": args.steps * E / t_ins},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"full step: {E} sequential insertions (Algorithm 3) + {Q} queries "
                                        f"(Algorithm 2, {cores} threads)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def workload_config(args, w):
-    return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "k": args.k, "kprime": args.kprime,
-            "insert_batch": args.batch, "inserted_edges_per_step": int(w["ins_src"].shape[0]),
-            "queries_per_step": int(w["q_u"].shape[0]), "form": getattr(args, "form", "plain"),
-            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
-
-
-# ------------------------------------------------------------------ GPU arm
-def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes):
-    """Algorithmic bytes of label repair for one step: per direction, over the
-    vertices whose half-record changes in a batch, offsets (8 B) + adjacency
-    (4 B/edge) + neighbour record sectors (32 B/edge) + own write."""
-    import torch
-    ix.restore(0)
-    dev = torch.device("cuda")
-    deg_out = deg_out0.clone()
-    deg_in = deg_in0.clone()
-    total = 0.0
-    src_all = torch.from_numpy(w["ins_src"]).to(dev).long()
-    dst_all = torch.from_numpy(w["ins_dst"]).to(dev).long()
-    prev = ix.labels()
-    for a, b in batches:
-        ix.insert_edges(src_all[a:b].int(), dst_all[a:b].int())
-        cur = ix.labels()
-        s, d = src_all[a:b], dst_all[a:b]
-        keep = s != d
-        deg_out += torch.bincount(s[keep], minlength=deg_out.numel())
-        deg_in += torch.bincount(d[keep], minlength=deg_in.numel())
-        chf = ((cur[0] != prev[0]).any(1) | (cur[2] != prev[2]).any(1))
-        chb = ((cur[1] != prev[1]).any(1) | (cur[3] != prev[3]).any(1))
-        total += float((8 + 36 * deg_out[chf].double() + rec_half_bytes).sum())
-        total += float((8 + 36 * deg_in[chb].double() + rec_half_bytes).sum())
-        prev = cur
-    ix.restore(0)
-    return total
-
-
-def bench_gpu(args):
-    import torch
-    import torch.distributed as tdist
-
-    import dbl_inputs
-    import paper_2101_09441_gb300 as dbl
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        tdist.init_process_group("nccl", device_id=dev)
-    dbl.build()
-    w = dbl_inputs.workload(args.workload)
-    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
-    batches = step_batches(E, args.batch)
-    rp = torch.from_numpy(w["row_ptr"]).to(dev)
-    col = torch.from_numpy(w["col"]).to(dev)
-    src = torch.from_numpy(w["ins_src"]).to(dev)
-    dst = torch.from_numpy(w["ins_dst"]).to(dev)
-    qu = torch.from_numpy(w["q_u"]).to(dev)
-    qv = torch.from_numpy(w["q_v"]).to(dev)
-    ans = torch.empty(Q, dtype=torch.uint8, device=dev)
-    code = torch.empty(Q, dtype=torch.uint8, device=dev)
-
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    flags = dbl.FLAG_TIMING
-    if args.form == "batched":
-        flags |= dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC
-    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
-    ix.sync()
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    build_t = ix.timings()
-    ix.snapshot(0)
-    info = ix.info()
-    rec_bytes = info["record_bytes"]
-
-    def step():
-        ix.restore(0)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record()
-        for a, b in batches:
-            ix.insert_edges(src[a:b], dst[a:b])
-        ev[1].record()
-        ix.query(qu, qv, out=(ans, code))
-        ev[2].record()
-        return ev
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ix.timings()  # reset
-    launches0 = ix.info()["launches"]
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if world > 1:
-        tdist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.profile:
-        torch.cuda.profiler.start()
-    e0.record()
-    evs = [step() for _ in range(args.steps)]
-    e1.record()
-    torch.cuda.synchronize()
-    if args.profile:
-        torch.cuda.profiler.stop()
-    ix.sync()  # raises if any device-side error latched during the timed steps
-    if world > 1:
-        tdist.barrier()
-    clocks = sampler.stop()
-    total_ms = e0.elapsed_time(e1)
-    launches = ix.info()["launches"] - launches0
-    kern = ix.timings()
-    ins_ms = sum(ev[0].elapsed_time(ev[1]) for ev in evs)
-    q_ms = sum(ev[1].elapsed_time(ev[2]) for ev in evs)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
-
-    # answers of the last step, for the record
-    answered = torch.bincount(code.long(), minlength=8).cpu().numpy()
-
-    # ---------------- end-to-end through the host-buffer C-ABI calls
-    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-    h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
-    h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ix.restore(0)
-        for a, b in batches:
-            ix.insert_edges_host(h_src[a:b], h_dst[a:b])
-        ix.query_host(h_qu, h_qv, out=(h_ans, None))
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    ix.timings()
-
-    # ---------------- roofline of the dominant kernel class
-    peaks, peak_src = measured_peaks()
-    kernels = {}
-    alg = {}
-    alg["query_label"] = args.steps * Q * (8 + 2 * rec_bytes + 2)
-    if kern["propagate"][1]:
-        alg["propagate"] = args.steps * changed_bytes(ix, w, batches, torch.diff(rp).long(),
-                                                      torch.bincount(col.long(), minlength=w["n"]),
-                                                      rec_bytes // 2)
-    for name, (ms, cnt) in kern.items():
-        if cnt:
-            ent = {"ms_total": ms, "launches": cnt, "ms_per_launch": ms / cnt}
-            if name in alg and ms > 0:
-                ent["algorithmic_bytes_per_launch"] = alg[name] / cnt
-                ent["achieved_gbs"] = alg[name] / (ms * 1e-3) / 1e9
-            kernels[name] = ent
-    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
-    roof = None
-    cand = dom if "achieved_gbs" in kernels[dom] else max(
-        (k for k in kernels if "achieved_gbs" in kernels[k]), key=lambda k: kernels[k]["ms_total"])
-    ach = kernels[cand]["achieved_gbs"]
-    traffic = None
-    if cand in NCU_TRAFFIC and NCU_TRAFFIC[cand][1] == source_sha(cand):
-        traffic = NCU_TRAFFIC[cand][0]
-    roof = {"kernel": cand, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {peak_src}",
-            "dominant_kernel_by_time": dom}
-
-    value = world * args.steps * (E + Q) / (total_ms * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(args, w),
-            "components": {"queries_per_s": world * args.steps * Q / (q_ms * 1e-3),
-                           "inserted_edges_per_s": world * args.steps * E / (ins_ms * 1e-3),
-                           "build_s": build_s,
-                           "build_kernel_ms": {k: v[0] for k, v in build_t.items() if v[1]},
-                           "decided_by": {n: int(answered[i]) for i, n in
-                                          enumerate(["undecided", "self", "dl", "bl", "thm1", "thm2",
-                                                     "bfs_pos", "bfs_neg"])}},
-            "roofline": roof,
-            "kernels": kernels,
-            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
-            "clocks": clocks,
-            "gpu_launches": launches}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, w)
-    ix.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        tdist.destroy_process_group()
 
 
 def cpu_baseline(args, w):
@@ -372,6 +186,277 @@ def cpu_baseline(args, w):
             "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q}
 
 
+# ------------------------------------------------------------------ GPU arm
+def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes, src_all, dst_all):
+    """Algorithmic bytes of label repair for one step: per direction, over the
+    vertices whose half-record changes in a batch, offsets (8 B) + adjacency
+    (4 B/edge) + neighbour record sectors (32 B/edge) + own write."""
+    import torch
+    ix.restore(0)
+    ix.sync()
+    deg_out = deg_out0.clone()
+    deg_in = deg_in0.clone()
+    total = 0.0
+    prev = ix.labels()
+    for a, b in batches:
+        ix.insert_edges(src_all[a:b], dst_all[a:b])
+        cur = ix.labels()
+        s, d = src_all[a:b].long(), dst_all[a:b].long()
+        keep = s != d
+        deg_out += torch.bincount(s[keep], minlength=deg_out.numel())
+        deg_in += torch.bincount(d[keep], minlength=deg_in.numel())
+        chf = (cur[0] != prev[0]).any(1) | (cur[2] != prev[2]).any(1)
+        chb = (cur[1] != prev[1]).any(1) | (cur[3] != prev[3]).any(1)
+        total += float((8 + 36 * deg_out[chf].double() + rec_half_bytes).sum())
+        total += float((8 + 36 * deg_in[chb].double() + rec_half_bytes).sum())
+        prev = cur
+    ix.restore(0)
+    ix.sync()
+    return total
+
+
+class Inputs:
+    def __init__(self, w, dev):
+        import torch
+        self.rp = torch.from_numpy(w["row_ptr"]).to(dev)
+        self.col = torch.from_numpy(w["col"]).to(dev)
+        self.src = torch.from_numpy(w["ins_src"]).to(dev)
+        self.dst = torch.from_numpy(w["ins_dst"]).to(dev)
+        self.qu = torch.from_numpy(w["q_u"]).to(dev)
+        self.qv = torch.from_numpy(w["q_v"]).to(dev)
+        self.ans = torch.empty(w["q_u"].shape[0], dtype=torch.uint8, device=dev)
+        self.code = torch.empty(w["q_u"].shape[0], dtype=torch.uint8, device=dev)
+
+
+def make_step(ix, I, batches, events=False):
+    import torch
+
+    def step():
+        ix.restore(0)
+        if events:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+        for a, b in batches:
+            ix.insert_edges(I.src[a:b], I.dst[a:b])
+        if events:
+            ev[1].record()
+        ix.query(I.qu, I.qv, out=(I.ans, I.code))
+        if events:
+            ev[2].record()
+            return ev
+    return step
+
+
+def time_steps(step, steps, world, tdist, sampler=None, profile=False):
+    import torch
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = [step() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    if profile:
+        torch.cuda.profiler.stop()
+    if world > 1:
+        tdist.barrier()
+    clocks = sampler.stop() if sampler else None
+    return e0.elapsed_time(e1), outs, clocks
+
+
+def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
+    """Build the form's index and time `steps` steps.  Returns a dict."""
+    import torch
+
+    import paper_2101_09441_gb300 as dbl
+    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
+    flags = {"plain": dbl.FLAG_TIMING, "batched": dbl.FLAG_TIMING | dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC,
+             "graph": dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC, "learned": dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC,
+             "learned_timing": dbl.FLAG_TIMING | dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC}[name]
+    kw = dict(flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
+    if landmarks is not None:
+        kw.update(landmarks=landmarks, leaf_buckets=leaves[0], leaf_roles=leaves[1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = dbl.DBLIndex(I.rp, I.col, args.k, args.kprime, **kw)
+    ix.sync()
+    build_s = time.perf_counter() - t0
+    build_t = ix.timings() if flags & dbl.FLAG_TIMING else {}
+    ix.snapshot(0)
+    res = {"build_s": build_s}
+    if build_t:
+        res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
+    use_graph = name in ("graph", "learned")
+    step = make_step(ix, I, batches, events=not use_graph)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ix.sync()
+    if use_graph:
+        g = torch.cuda.CUDAGraph()
+        l0 = ix.info()["launches"]
+        with torch.cuda.graph(g):
+            step()
+        launches_per_step = ix.info()["launches"] - l0
+        g.replay()
+        torch.cuda.synchronize()
+        ix.sync()
+        timed = g.replay
+    else:
+        timed = step
+        ix.timings()
+        l0 = ix.info()["launches"]
+    sampler = ClockSampler(local) if name == "learned" else None
+    total_ms, outs, clocks = time_steps(timed, args.steps, world, tdist, sampler,
+                                        profile=args.profile and name == args.profile_form)
+    ix.sync()
+    if world > 1:
+        t = torch.tensor([total_ms], device=I.qu.device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    res.update(ms_per_step=total_ms / args.steps, value=world * args.steps * (E + Q) / (total_ms * 1e-3),
+               gpu_launches=(launches_per_step * args.steps) if use_graph else ix.info()["launches"] - l0)
+    if not use_graph:
+        ins_ms = sum(ev[0].elapsed_time(ev[1]) for ev in outs)
+        q_ms = sum(ev[1].elapsed_time(ev[2]) for ev in outs)
+        res["queries_per_s"] = world * args.steps * Q / (q_ms * 1e-3)
+        res["inserted_edges_per_s"] = world * args.steps * E / (ins_ms * 1e-3)
+        res["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in ix.timings().items() if v[1]}
+    code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
+    res["decided_by"] = {n: int(code[i]) for i, n in enumerate(
+        ["undecided", "self", "dl", "bl", "thm1", "thm2", "bfs_pos", "bfs_neg"])}
+    res["clocks"] = clocks
+    res["ix"] = ix
+    return res
+
+
+def roofline(form, ix, args, w, I, batches):
+    """Achieved GB/s of the form's dominant kernel class (library CUDA events
+    over the timed region) against the measured HBM copy peak."""
+    import torch
+    peaks, src = measured_peaks()
+    Q = int(w["q_u"].shape[0])
+    info = ix.info()
+    rec = info["record_bytes"]
+    alg = {"query_label": args.steps * Q * (8 + 2 * rec + 2)}
+    kern = form["kernels"]
+    if "propagate" in kern:
+        alg["propagate"] = args.steps * changed_bytes(ix, w, batches, torch.diff(I.rp).long(),
+                                                      torch.bincount(I.col.long(), minlength=w["n"]), rec // 2,
+                                                      I.src, I.dst)
+    for k, v in kern.items():
+        v["ms_per_launch"] = v["ms_total"] / v["launches"]
+        if k in alg and v["ms_total"] > 0:
+            v["algorithmic_bytes_per_launch"] = alg[k] / v["launches"]
+            v["achieved_gbs"] = alg[k] / (v["ms_total"] * 1e-3) / 1e9
+            v["frac_of_hbm"] = v["achieved_gbs"] / peaks["hbm_gbs"]
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    cand = dom if "achieved_gbs" in kern[dom] else max((k for k in kern if "achieved_gbs" in kern[k]),
+                                                       key=lambda k: kern[k]["ms_total"])
+    ach = kern[cand]["achieved_gbs"]
+    traffic = NCU_TRAFFIC[cand][0] if cand in NCU_TRAFFIC and NCU_TRAFFIC[cand][1] == source_sha(cand) else None
+    return {"kernel": cand, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
+            "dominant_kernel_by_time": dom}
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as tdist
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    from paper_2101_09441_gb300 import learned as L
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    dbl.build()
+    w = dbl_inputs.workload(args.workload)
+    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
+    batches = step_batches(E, args.batch)
+    I = Inputs(w, dev)
+    forms = {}
+    for name in ("plain", "batched", "graph"):
+        if name in args.forms:
+            forms[name] = run_form(name, args, w, I, None, None, batches, world, tdist, local)
+
+    # ---- learned landmarks: trained on the outcomes of a separate sample of
+    # 1M queries on the index after the step's insertions
+    t0 = time.perf_counter()
+    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], args.train_queries, w["seed"] + 300, False,
+                                w["ins_src"], w["ins_dst"])
+    tu, tv = torch.from_numpy(tu).to(dev), torch.from_numpy(tv).to(dev)
+    plain_ix = dbl.DBLIndex(I.rp, I.col, args.k, args.kprime, edge_capacity=max(E, 1 << 20))
+    for a, b in batches:
+        plain_ix.insert_edges(I.src[a:b], I.dst[a:b])
+    base_slots = max(1, args.k // 8)
+    scores, tinfo = L.train_scorer(plain_ix, tu, tv, base_slots, steps=args.train_steps)
+    lm = L.select_landmarks(plain_ix, scores, args.k, base_slots)
+    _, lb, lr_ = plain_ix.selection()
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    plain_ix.close()
+    learned = run_form("learned", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
+    learned_t = run_form("learned_timing", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
+    # fallback: keep the degree rule if the learned set decides fewer pairs by the labels
+    dec_l = learned["decided_by"]
+    dec_p = (forms.get("graph") or forms.get("plain"))["decided_by"]
+    fallback = dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
+    head = forms["graph"] if (fallback and "graph" in forms) else learned
+    roof = roofline(learned_t, learned_t["ix"], args, w, I, batches)
+
+    # ---- end to end through the host-buffer C-ABI calls, headline index
+    ix = learned["ix"]
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
+    h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.restore(0)
+        for a, b in batches:
+            ix.insert_edges_host(h_src[a:b], h_dst[a:b])
+        ix.query_host(h_qu, h_qv, out=(h_ans, None))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    def public(f):
+        return {k: v for k, v in f.items() if k not in ("ix", "clocks")}
+
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(args, w),
+            "forms": {**{k: public(v) for k, v in forms.items()}, "learned": public(learned),
+                      "learned_timing_pass": public(learned_t)},
+            "learned_vs_plain": head["value"] / forms["plain"]["value"] if "plain" in forms else None,
+            "learned": {"fallback_to_degree_rule": bool(fallback), "train_s": train_s, "base_slots": base_slots,
+                        **{k: v for k, v in tinfo.items() if k != "losses"}, "final_loss": tinfo["losses"][-1]},
+            "roofline": roof,
+            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
+            "clocks": learned["clocks"],
+            "gpu_launches": head["gpu_launches"]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, w)
+    for f in list(forms.values()) + [learned, learned_t]:
+        f["ix"].close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,13 +468,16 @@ def main():
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--kprime", type=int, default=64)
     ap.add_argument("--team", type=int, default=8)
-    ap.add_argument("--form", choices=["plain", "batched"], default="plain",
-                    help="plain: host-driven levels; batched: persistent kernels, no host round trips")
+    ap.add_argument("--forms", default="plain,batched,graph", help="comparison forms to time besides the headline")
+    ap.add_argument("--train-queries", type=int, default=1_000_000)
+    ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true",
-                    help="bracket the timed region with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+                    help="bracket one form's timed region with cudaProfilerStart/Stop (ncu --profile-from-start off)")
+    ap.add_argument("--profile-form", default="learned_timing")
     args = ap.parse_args()
+    args.forms = [f for f in args.forms.split(",") if f]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -225,6 +225,114 @@ dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *
  * [10..15] zero. */
 dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
 
+/* ---------------------------------------------------------------------------
+ * Concurrent query batches.  A query context holds the scratch of one query
+ * batch in flight (undecided list, search state); batches on different
+ * contexts may run at the same time on different streams and host threads,
+ * as long as no insertion runs meanwhile (queries only read the labels).
+ * dbl_query uses the index's own context.  Explicit contexts always use the
+ * per-level search (no cooperative launch).
+ * ------------------------------------------------------------------------- */
+typedef struct dbl_qctx dbl_qctx;
+dbl_status dbl_qctx_create(dbl_index *ix, dbl_qctx **out, void *stream);
+void dbl_qctx_destroy(dbl_qctx *c, void *stream);
+/* dbl_query on context c; synchronous; errors are also in dbl_qctx_last_error. */
+dbl_status dbl_query_ctx(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
+                         uint8_t *code, void *stream);
+const char *dbl_qctx_last_error(const dbl_qctx *c);
+
+/* ---------------------------------------------------------------------------
+ * Serving engine (continuous batching over one resident index).  Requests
+ * are query batches (kind 0: pairs a[i], b[i], answers to ans) or insertion
+ * batches (kind 1: edges a[i] -> b[i]) in HOST memory, which the caller keeps
+ * alive until dbl_server_wait returns for the ticket.  Admission is in arrival
+ * order; consecutive queued queries are packed into one device batch of at
+ * most max_batch pairs on a free slot, so several batches overlap on the GPU;
+ * an insertion waits until no query batch is in flight and every request
+ * behind it waits for it, so each request observes exactly the insertions
+ * submitted before it (the labels change only at these epoch boundaries).
+ * The number of slots is capped by mem_fraction of the free device memory at
+ * creation; each slot's scratch is allocated then.  Submit returns
+ * DBL_ERR_BUSY when max_pending requests are queued.  The index must not use
+ * DBL_FLAG_ASYNC and must not be used directly while a server runs on it.
+ * ------------------------------------------------------------------------- */
+typedef struct dbl_server dbl_server;
+typedef struct {
+    int32_t slots;        /* worker slots (streams); default 4 */
+    int64_t max_batch;    /* pairs per device batch; default 2^18 */
+    int64_t max_pending;  /* queued requests before DBL_ERR_BUSY; default 2^16 */
+    double mem_fraction;  /* share of free device memory slots may take; default 0.5 */
+} dbl_server_options;
+void dbl_server_default_options(dbl_server_options *o);
+dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_server **out);
+dbl_status dbl_server_submit(dbl_server *s, int32_t kind, const int32_t *a_host, const int32_t *b_host, int64_t n,
+                             uint8_t *ans_host, uint64_t *ticket);
+/* Block until the request is done; returns its status and latency (s). */
+dbl_status dbl_server_wait(dbl_server *s, uint64_t ticket, double *latency_s);
+dbl_status dbl_server_drain(dbl_server *s);
+/* [0] query p50 s, [1] query p99 s, [2] insertion p50 s, [3] insertion p99 s,
+ * [4] pairs answered, [5] edges inserted, [6] query requests, [7] insertion
+ * requests, [8] slots, [9] seconds since creation or reset, [10] device
+ * query batches, [11] query requests in them, [12] insertion epochs. */
+dbl_status dbl_server_report(dbl_server *s, double out[16]);
+dbl_status dbl_server_reset_stats(dbl_server *s);
+void dbl_server_destroy(dbl_server *s);
+
+/* ---------------------------------------------------------------------------
+ * Learned landmark scorer.  The paper ranks landmarks by M(u) = |Pre(u)| *
+ * |Suc(u)| (Section 4.1; Table 3 compares other rankings) and notes that the
+ * best choice is NP-hard.  These calls score vertices with a 16-128-128-1 ReLU
+ * network instead; answers stay exact for any landmark set (Lemma 1), only
+ * how many pairs the DL test decides changes.  Build a new index with
+ * dbl_build(landmarks = the selected vertices) to use the result.
+ * ------------------------------------------------------------------------- */
+
+typedef struct dbl_mlp dbl_mlp;
+
+/* Number of network parameters and their order in a flat float vector:
+ * W1 [16][128] (input x hidden, row-major), b1 [128], W2 [128][128], b2 [128],
+ * w3 [128], b3 [1]. */
+#define DBL_MLP_PARAMS 18817
+
+/* 16 per-vertex features of the built index, bf16 bit patterns [n][16]:
+ * log1p of indeg, outdeg, indeg*outdeg, indeg+outdeg, the sums over Pre(x)
+ * of indeg and of outdeg, over Suc(x) of outdeg and of indeg (features 4-7 in
+ * that order: Pre-indeg, Suc-outdeg, Pre-outdeg, Suc-indeg), popcounts of
+ * DL_in, DL_out, BL_in, BL_out, popc(DL_in)*popc(DL_out), in-neighbours with
+ * zero in-degree, out-neighbours with zero out-degree, and 1 for a landmark. */
+dbl_status dbl_features(dbl_index *ix, uint16_t *feat, void *stream);
+
+/* Coverage of sampled reachable pairs: count[c] = #{j : u[j] reaches c and c
+ * reaches v[j]} over the pairs j kept (the pairs DL would decide if c were a
+ * landmark, Lemma 1), by bit-parallel propagation, 256 pairs per pass.  A pair
+ * is kept if reach[j] != 0 (reach may be NULL: all kept) and the index's first
+ * base_slots landmark slots do not already decide it by the DL test; *kept
+ * (may be NULL) receives their number.  target (may be NULL) receives
+ * log1p(count[c]) / log1p(max count).  Synchronous. */
+dbl_status dbl_coverage(dbl_index *ix, const int32_t *u, const int32_t *v, const uint8_t *reach, int64_t pairs,
+                        int32_t base_slots, uint32_t *count, float *target, int64_t *kept, void *stream);
+
+/* out[k]: the k vertices with the largest scores[n], ties by smaller id. */
+dbl_status dbl_select_by_score(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream);
+
+/* Network with initial parameters params_host[DBL_MLP_PARAMS] (host fp32).
+ * Weights are kept in fp32 with bf16 copies for the tensor-core kernels. */
+dbl_status dbl_mlp_create(const float *params_host, dbl_mlp **out, void *stream);
+void dbl_mlp_destroy(dbl_mlp *m, void *stream);
+/* Copy the current fp32 parameters to params_host[DBL_MLP_PARAMS]. */
+dbl_status dbl_mlp_params(dbl_mlp *m, float *params_host, void *stream);
+/* y[r] = network(X[rows_idx ? rows_idx[r] : r]) for r < rows; X bf16 [.][16]. */
+dbl_status dbl_mlp_forward(dbl_mlp *m, const uint16_t *X, const int32_t *rows_idx, int64_t rows, float *y,
+                           void *stream);
+/* Gradients (device fp32 [DBL_MLP_PARAMS]) and loss (device fp32, may be
+ * NULL) of mean((y - target)^2)/2 over the rows, without changing the network. */
+dbl_status dbl_mlp_gradients(dbl_mlp *m, const uint16_t *X, const float *target, const int32_t *rows_idx,
+                             int64_t rows, float *grads, float *loss, void *stream);
+/* One SGD-with-momentum step on the rows: v = momentum*v + grad; p -= lr*v. */
+dbl_status dbl_mlp_train_step(dbl_mlp *m, const uint16_t *X, const float *target, const int32_t *rows_idx,
+                              int64_t rows, float lr, float momentum, float *loss, void *stream);
+const char *dbl_mlp_last_error(const dbl_mlp *m);
+
 /* Message of the last error on this index (or of the last failed build when
  * ix is NULL).  Valid until the next call on the index. */
 const char *dbl_last_error(const dbl_index *ix);

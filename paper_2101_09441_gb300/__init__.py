@@ -28,7 +28,18 @@ KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "in
 
 EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", "dbl_query_host",
            "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_snapshot", "dbl_restore", "dbl_sync",
-           "dbl_stats", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy"]
+           "dbl_stats", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy", "dbl_insert_edges_noalloc",
+           "dbl_features", "dbl_coverage", "dbl_select_by_score", "dbl_mlp_create", "dbl_mlp_destroy",
+           "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_last_error",
+           "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
+           "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
+           "dbl_server_reset_stats", "dbl_server_destroy"]
+MLP_PARAMS = 18817
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("max_pending", ctypes.c_int64),
+                ("mem_fraction", ctypes.c_double)]
 
 
 class DblError(RuntimeError):
@@ -91,6 +102,35 @@ def lib():
             L.dbl_last_error.restype = ctypes.c_char_p
             L.dbl_destroy.argtypes = [P, P]
             L.dbl_destroy.restype = None
+            f32 = ctypes.c_float
+            L.dbl_qctx_create.argtypes = [P, P, P]
+            L.dbl_qctx_destroy.argtypes = [P, P]
+            L.dbl_qctx_destroy.restype = None
+            L.dbl_query_ctx.argtypes = [P, P, P, P, i64, P, P, P]
+            L.dbl_qctx_last_error.argtypes = [P]
+            L.dbl_qctx_last_error.restype = ctypes.c_char_p
+            L.dbl_server_default_options.argtypes = [P]
+            L.dbl_server_default_options.restype = None
+            L.dbl_server_create.argtypes = [P, P, P]
+            L.dbl_server_submit.argtypes = [P, i32, P, P, i64, P, P]
+            L.dbl_server_wait.argtypes = [P, ctypes.c_uint64, P]
+            L.dbl_server_drain.argtypes = [P]
+            L.dbl_server_report.argtypes = [P, P]
+            L.dbl_server_reset_stats.argtypes = [P]
+            L.dbl_server_destroy.argtypes = [P]
+            L.dbl_server_destroy.restype = None
+            L.dbl_features.argtypes = [P, P, P]
+            L.dbl_coverage.argtypes = [P, P, P, P, i64, i32, P, P, P, P]
+            L.dbl_select_by_score.argtypes = [P, P, i32, P, P]
+            L.dbl_mlp_create.argtypes = [P, P, P]
+            L.dbl_mlp_destroy.argtypes = [P, P]
+            L.dbl_mlp_destroy.restype = None
+            L.dbl_mlp_params.argtypes = [P, P, P]
+            L.dbl_mlp_forward.argtypes = [P, P, P, i64, P, P]
+            L.dbl_mlp_gradients.argtypes = [P, P, P, P, i64, P, P, P]
+            L.dbl_mlp_train_step.argtypes = [P, P, P, P, i64, f32, f32, P, P]
+            L.dbl_mlp_last_error.argtypes = [P]
+            L.dbl_mlp_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
                 fn = getattr(L, name)
                 if fn.restype is ctypes.c_int:  # default restype: dbl_status
@@ -287,3 +327,207 @@ class DBLIndex:
         return dict(n=int(out[0]), k=int(out[1]), kprime=int(out[2]), edges_stored=int(out[3]),
                     edge_capacity=int(out[4]), m=int(out[5]), record_bytes=int(out[6]), flags=int(out[7]),
                     launches=int(out[8]), half_words=int(out[9]))
+
+    # ------------------------------------------------------------------ learned scorer
+    def features(self, stream=None):
+        """dbl_features: bf16 [n, 16] (log1p-scaled per-vertex counts)."""
+        import torch
+        out = torch.empty((self.n, 16), dtype=torch.bfloat16, device=self.device)
+        self._check(lib().dbl_features(self._h, _ptr(out), self._s(stream)))
+        return out
+
+    def coverage(self, u, v, reach=None, base_slots: int = 0, stream=None):
+        """dbl_coverage: (count int32 [n], target float32 [n], pairs kept)."""
+        import torch
+        u, v = self._pair(u, v)
+        if reach is not None:
+            reach = reach.to(torch.uint8).contiguous()
+        count = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        target = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        kept = ctypes.c_int64(0)
+        self._check(lib().dbl_coverage(self._h, _ptr(u), _ptr(v), _ptr(reach), int(u.numel()), int(base_slots),
+                                       _ptr(count), _ptr(target), ctypes.byref(kept), self._s(stream)))
+        return count, target, int(kept.value)
+
+    def select_by_score(self, scores, k: int, stream=None):
+        """dbl_select_by_score: the k best-scored vertices (ties by id), int32 [k]."""
+        import torch
+        scores = scores.to(torch.float32).contiguous()
+        out = torch.empty(int(k), dtype=torch.int32, device=self.device)
+        self._check(lib().dbl_select_by_score(self._h, _ptr(scores), int(k), _ptr(out), self._s(stream)))
+        return out
+
+
+class QueryContext:
+    """dbl_qctx: scratch for one query batch in flight; batches on different
+    contexts may run concurrently (different streams / threads)."""
+
+    def __init__(self, ix: "DBLIndex", stream=None):
+        self.ix = ix
+        h = ctypes.c_void_p()
+        st = lib().dbl_qctx_create(ix._h, ctypes.byref(h), _stream_handle(stream))
+        if st != DBL_OK:
+            raise DblError(st, lib().dbl_last_error(ix._h).decode())
+        self._h = h
+
+    def query(self, u, v, with_code: bool = True, stream=None):
+        import torch
+        u, v = DBLIndex._pair(u, v)
+        q = int(u.numel())
+        ans = torch.empty(q, dtype=torch.uint8, device=u.device)
+        code = torch.empty(q, dtype=torch.uint8, device=u.device) if with_code else None
+        st = lib().dbl_query_ctx(self.ix._h, self._h, _ptr(u), _ptr(v), q, _ptr(ans), _ptr(code),
+                                 _stream_handle(stream))
+        if st != DBL_OK:
+            raise DblError(st, lib().dbl_qctx_last_error(self._h).decode())
+        return ans, code
+
+    def close(self, stream=None):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.dbl_qctx_destroy(self._h, _stream_handle(stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """dbl_server: continuous-batching request loop over one index (host
+    buffers in, host buffers out).  Keep the arrays of a request alive until
+    wait() returns for its ticket."""
+
+    def __init__(self, ix: "DBLIndex", slots: int = 4, max_batch: int = 1 << 18, max_pending: int = 1 << 16,
+                 mem_fraction: float = 0.5):
+        self.ix = ix
+        o = _ServerOptions()
+        lib().dbl_server_default_options(ctypes.byref(o))
+        o.slots, o.max_batch, o.max_pending, o.mem_fraction = int(slots), int(max_batch), int(max_pending), \
+            float(mem_fraction)
+        h = ctypes.c_void_p()
+        st = lib().dbl_server_create(ix._h, ctypes.byref(o), ctypes.byref(h))
+        if st != DBL_OK:
+            raise DblError(st, lib().dbl_last_error(ix._h).decode())
+        self._h = h
+        self._keep = {}
+
+    def submit(self, kind: int, a: np.ndarray, b: np.ndarray, ans: np.ndarray | None = None) -> int:
+        """kind 0: query pairs (answers into ans, uint8); kind 1: insert edges."""
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        b = np.ascontiguousarray(b, dtype=np.int32)
+        if a.shape != b.shape:
+            raise ValueError("a and b differ in length")
+        if kind == 0 and ans is None:
+            ans = np.empty(a.shape[0], dtype=np.uint8)
+        t = ctypes.c_uint64(0)
+        st = lib().dbl_server_submit(self._h, int(kind), a.ctypes.data, b.ctypes.data, int(a.shape[0]),
+                                     ans.ctypes.data if ans is not None else None, ctypes.byref(t))
+        if st != DBL_OK:
+            raise DblError(st, "server submit")
+        self._keep[t.value] = (a, b, ans)
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        """(answers or None, latency seconds)."""
+        lat = ctypes.c_double(0)
+        st = lib().dbl_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(lat))
+        a, b, ans = self._keep.pop(ticket)
+        if st != DBL_OK:
+            raise DblError(st, "server request failed")
+        return ans, float(lat.value)
+
+    def drain(self):
+        lib().dbl_server_drain(self._h)
+
+    def report(self) -> dict:
+        out = np.zeros(16, dtype=np.float64)
+        lib().dbl_server_report(self._h, out.ctypes.data)
+        keys = ["query_p50_s", "query_p99_s", "insert_p50_s", "insert_p99_s", "pairs", "edges", "query_requests",
+                "insert_requests", "slots", "elapsed_s", "device_batches", "batched_requests", "epochs"]
+        return {k: float(out[i]) for i, k in enumerate(keys)}
+
+    def reset_stats(self):
+        lib().dbl_server_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.dbl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MLP:
+    """The 16-128-128-1 landmark scorer (dbl_mlp_*): bf16 tensor-core kernels,
+    fp32 master weights.  Parameters are a flat float vector in the order
+    W1 [16,128], b1, W2 [128,128], b2, w3 [128], b3."""
+
+    def __init__(self, params: np.ndarray, stream=None):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        if params.shape != (MLP_PARAMS,):
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = lib().dbl_mlp_create(params.ctypes.data, ctypes.byref(h), _stream_handle(stream))
+        if st != DBL_OK:
+            raise DblError(st, "dbl_mlp_create")
+        self._h = h
+
+    def _check(self, st):
+        if st != DBL_OK:
+            raise DblError(st, lib().dbl_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.dbl_mlp_destroy(self._h, _stream_handle(self._stream))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def init_params(seed: int) -> np.ndarray:
+        """He-normal weights, zero biases (numpy Generator keyed by seed)."""
+        rng = np.random.Generator(np.random.PCG64(seed))
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        p[0:2048] = rng.normal(0, np.sqrt(2 / 16) / 4, 2048)   # features are log-counts up to ~20
+        p[2176:2176 + 16384] = rng.normal(0, np.sqrt(2 / 128), 16384)
+        p[18688:18816] = rng.normal(0, np.sqrt(1 / 128), 128)
+        return p
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(lib().dbl_mlp_params(self._h, out.ctypes.data, _stream_handle(self._stream)))
+        return out
+
+    def forward(self, X, rows_idx=None, stream=None):
+        import torch
+        R = int(rows_idx.numel()) if rows_idx is not None else int(X.shape[0])
+        y = torch.empty(R, dtype=torch.float32, device=X.device)
+        self._check(lib().dbl_mlp_forward(self._h, _ptr(X), _ptr(rows_idx), R, _ptr(y),
+                                          _stream_handle(stream or self._stream)))
+        return y
+
+    def gradients(self, X, target, rows_idx=None, stream=None):
+        import torch
+        R = int(rows_idx.numel()) if rows_idx is not None else int(X.shape[0])
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self._check(lib().dbl_mlp_gradients(self._h, _ptr(X), _ptr(target), _ptr(rows_idx), R, _ptr(g), _ptr(loss),
+                                            _stream_handle(stream or self._stream)))
+        return g, loss
+
+    def train_step(self, X, target, rows_idx=None, lr: float = 0.05, momentum: float = 0.9, loss=None,
+                   stream=None):
+        R = int(rows_idx.numel()) if rows_idx is not None else int(X.shape[0])
+        self._check(lib().dbl_mlp_train_step(self._h, _ptr(X), _ptr(target), _ptr(rows_idx), R, float(lr),
+                                             float(momentum), _ptr(loss), _stream_handle(stream or self._stream)))

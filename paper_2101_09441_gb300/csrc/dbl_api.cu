@@ -118,38 +118,115 @@ static int64_t pow2_at_least(int64_t x)
     return p;
 }
 
-dbl_status ensure_search_scratch(dbl_index *ix, int64_t q, cudaStream_t s)
+dbl_status qfail(dbl_qctx *c, dbl_status st, const std::string &msg)
 {
+    c->err = msg;
+    if (c == c->ix->qc) c->ix->err = msg;
+    return st;
+}
+
+// Context memory comes from the index's allocator, recorded in the context.
+static dbl_status ctx_alloc(dbl_qctx *c, void **p, size_t bytes, cudaStream_t s)
+{
+    dbl_index *ix = c->ix;
+    *p = nullptr;
+    bytes = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+    void *q = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(ix->alloc_mu);
+        if (ix->opt.alloc) {
+            q = ix->opt.alloc(bytes, (void *)s, ix->opt.ctx);
+        } else if (cudaMallocAsync(&q, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            q = nullptr;
+        }
+    }
+    if (!q) return qfail(c, DBL_ERR_OOM, "query context: allocation of " + std::to_string(bytes) + " bytes failed");
+    c->owned.push_back(Buf{q, bytes});
+    *p = q;
+    return DBL_OK;
+}
+
+static void ctx_free(dbl_qctx *c, void *p, cudaStream_t s)
+{
+    if (!p) return;
+    dbl_index *ix = c->ix;
+    for (size_t i = 0; i < c->owned.size(); ++i) {
+        if (c->owned[i].p != p) continue;
+        size_t bytes = c->owned[i].bytes;
+        c->owned[i] = c->owned.back();
+        c->owned.pop_back();
+        std::lock_guard<std::mutex> lock(ix->alloc_mu);
+        if (ix->opt.alloc) ix->opt.free(p, bytes, (void *)s, ix->opt.ctx);
+        else cudaFreeAsync(p, s);
+        return;
+    }
+}
+
+dbl_status qctx_create(dbl_index *ix, dbl_qctx **out, cudaStream_t s)
+{
+    dbl_qctx *c = new (std::nothrow) dbl_qctx();
+    if (!c) return fail(ix, DBL_ERR_OOM, "query context");
+    c->ix = ix;
+    dbl_status st;
+    if ((st = ctx_alloc(c, (void **)&c->d_counts, 4 * kCntWords, s)) || (st = ctx_alloc(c, (void **)&c->d_status, 16, s))) {
+        std::string m = c->err;
+        qctx_destroy(c, s);
+        return fail(ix, st, m);
+    }
+    if (cudaMallocHost((void **)&c->h_pinned, 64 * sizeof(uint32_t))) {
+        cudaGetLastError();
+        qctx_destroy(c, s);
+        return fail(ix, DBL_ERR_OOM, "query context: pinned words");
+    }
+    std::memset(c->h_pinned, 0, 64 * sizeof(uint32_t));
+    cudaMemsetAsync(c->d_counts, 0, 4 * kCntWords, s);
+    cudaMemsetAsync(c->d_status, 0, 16, s);
+    *out = c;
+    return DBL_OK;
+}
+
+void qctx_destroy(dbl_qctx *c, cudaStream_t s)
+{
+    if (!c) return;
+    while (!c->owned.empty()) ctx_free(c, c->owned.back().p, s);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+}
+
+dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
+{
+    dbl_index *ix = c->ix;
     dbl_status st;
     const int64_t W = 1 + ix->wd + 2 * ix->wb;
-    if (q > ix->und_cap) {
-        free_buf(ix, ix->und, s);
-        free_buf(ix, ix->qtab, s);
-        free_buf(ix, ix->found, s);
-        ix->und = nullptr;
-        ix->qtab = nullptr;
-        ix->found = nullptr;
+    if (q > c->und_cap) {
+        ctx_free(c, c->und, s);
+        ctx_free(c, c->qtab, s);
+        ctx_free(c, c->found, s);
+        c->und = nullptr;
+        c->qtab = nullptr;
+        c->found = nullptr;
         int64_t cap = std::max<int64_t>(q, 1 << 16);
-        if ((st = alloc_buf(ix, (void **)&ix->und, sizeof(int32_t) * (size_t)cap, s))) return st;
-        if ((st = alloc_buf(ix, (void **)&ix->qtab, sizeof(uint64_t) * (size_t)(cap + 64) * W, s))) return st;
-        if ((st = alloc_buf(ix, (void **)&ix->found, sizeof(unsigned long long) * (size_t)(cap / 64 + 2), s)))
+        if ((st = ctx_alloc(c, (void **)&c->und, sizeof(int32_t) * (size_t)cap, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->qtab, sizeof(uint64_t) * (size_t)(cap + 64) * W, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->found, sizeof(unsigned long long) * (size_t)(cap / 64 + 2), s)))
             return st;
-        ix->und_cap = cap;
+        c->und_cap = cap;
     }
-    if (!ix->table) {
+    if (!c->table) {
         int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n));
-        if ((st = alloc_buf(ix, (void **)&ix->table, sizeof(SearchSlot) * (size_t)slots, s))) return st;
-        if ((st = alloc_buf(ix, (void **)&ix->claimed, sizeof(int32_t) * (size_t)slots, s))) return st;
-        if ((st = alloc_buf(ix, (void **)&ix->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return st;
-        if ((st = alloc_buf(ix, (void **)&ix->slot_list[1], sizeof(int32_t) * (size_t)slots, s))) return st;
-        cudaMemsetAsync(ix->table, 0, sizeof(SearchSlot) * (size_t)slots, s);
+        if ((st = ctx_alloc(c, (void **)&c->table, sizeof(SearchSlot) * (size_t)slots, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->claimed, sizeof(int32_t) * (size_t)slots, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->slot_list[1], sizeof(int32_t) * (size_t)slots, s))) return st;
+        cudaMemsetAsync(c->table, 0, sizeof(SearchSlot) * (size_t)slots, s);
         // key = empty (all ones) in every slot: set the key words with a strided memset
-        cudaMemset2DAsync(ix->table, sizeof(SearchSlot), 0xff, sizeof(unsigned long long), (size_t)slots, s);
-        ix->table_slots = slots;
+        cudaMemset2DAsync(c->table, sizeof(SearchSlot), 0xff, sizeof(unsigned long long), (size_t)slots, s);
+        c->table_slots = slots;
         int64_t tcap = (int64_t)ix->n + (ix->m + ix->edge_cap) / kChunk + 4096;
-        if ((st = alloc_buf(ix, (void **)&ix->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
-        ix->stask_cap = tcap;
-        if ((st = alloc_buf(ix, &ix->pstate, persist_state_bytes(), s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
+        c->stask_cap = tcap;
+        if ((st = ctx_alloc(c, &c->pstate, persist_state_bytes(), s))) return st;
     }
     return DBL_OK;
 }
@@ -191,6 +268,8 @@ void dbl_default_options(dbl_options *opt)
 static void destroy_impl(dbl_index *ix, cudaStream_t s)
 {
     if (!ix) return;
+    qctx_destroy(ix->qc, s);
+    ix->qc = nullptr;
     for (auto &b : ix->owned) {
         if (ix->opt.alloc) ix->opt.free(b.p, b.bytes, (void *)s, ix->opt.ctx);
         else cudaFreeAsync(b.p, s);
@@ -271,6 +350,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->stamp, 16 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
         (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
+        (st = A((void **)&ix->d_epoch, 16)) ||
         (st = A((void **)&ix->ins_cnt, 8 * n))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
@@ -283,12 +363,18 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
     cudaMemsetAsync(ix->d_status, 0, 16, s);
     cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);
+    cudaMemsetAsync(ix->d_epoch, 0, 16, s);
     cudaMemsetAsync(ix->ins_cnt, 0, 8 * n, s);
 
     tbegin(ix, DBL_KERNEL_BUILD_PREP, s);
     if ((st = prep_graph(ix, g, s)) || (st = select_landmarks(ix, landmarks, s)) ||
         (st = select_leaves(ix, leaf_buckets, leaf_roles, s)) || (st = seed_labels(ix, s)) ||
         (tend(ix, s), st = propagate(ix, s))) {
+        std::string msg = ix->err;
+        destroy_impl(ix, s);
+        return fail(nullptr, st, msg);
+    }
+    if ((st = qctx_create(ix, &ix->qc, s))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
         return fail(nullptr, st, msg);
@@ -329,8 +415,39 @@ dbl_status dbl_query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t 
     DBL_CHECK_IX(ix);
     if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u || !v || !ans))) return fail(ix, DBL_ERR_INVALID, "query: bad batch");
     cudaStream_t s = (cudaStream_t)stream;
-    return finish(ix, query(ix, u, v, q, ans, code, s), s);
+    return finish(ix, query(ix, ix->qc, u, v, q, ans, code, s), s);
 }
+
+dbl_status dbl_qctx_create(dbl_index *ix, dbl_qctx **out, void *stream)
+{
+    if (!ix || !out) return fail(ix, DBL_ERR_INVALID, "qctx_create: NULL argument");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st = qctx_create(ix, out, s);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    return e ? cuda_fail(ix, e, "qctx_create") : DBL_OK;
+}
+
+void dbl_qctx_destroy(dbl_qctx *c, void *stream)
+{
+    if (!c) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamSynchronize(s);
+    qctx_destroy(c, s);
+    cudaStreamSynchronize(s);
+}
+
+dbl_status dbl_query_ctx(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
+                         uint8_t *code, void *stream)
+{
+    if (!ix || !c || c->ix != ix) return fail(ix, DBL_ERR_INVALID, "query_ctx: context of another index");
+    if (ix->poisoned) return qfail(c, DBL_ERR_POISONED, "index poisoned by a timeout; dbl_restore it");
+    if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u || !v || !ans))) return qfail(c, DBL_ERR_INVALID, "query: bad batch");
+    return query(ix, c, u, v, q, ans, code, (cudaStream_t)stream);
+}
+
+const char *dbl_qctx_last_error(const dbl_qctx *c) { return c ? c->err.c_str() : ""; }
 
 static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
 {
@@ -385,7 +502,7 @@ dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v
         if (c + 1 < nch) stage_in(c + 1);  // overlaps this chunk's compute (Section 6.6)
         cudaStreamWaitEvent(s, ev_in[b], 0);
         uint8_t *da = (uint8_t *)(d + 8 * chunk), *dc = (uint8_t *)(d + 9 * chunk);
-        st = query(ix, (int32_t *)d, (int32_t *)(d + 4 * chunk), len, da, code_host ? dc : nullptr, s);
+        st = query(ix, ix->qc, (int32_t *)d, (int32_t *)(d + 4 * chunk), len, da, code_host ? dc : nullptr, s);
         if (st) break;
         cudaMemcpyAsync(ans_host + off, da, (size_t)len, cudaMemcpyDeviceToHost, s);
         if (code_host) cudaMemcpyAsync(code_host + off, dc, (size_t)len, cudaMemcpyDeviceToHost, s);
@@ -460,14 +577,15 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = 12 * (size_t)ix->n;
     if (!sn.rec.p) {
         if ((st = alloc_buf(ix, &sn.rec.p, rec_b, s)) || (st = alloc_buf(ix, &sn.ovo.p, meta_b, s)) ||
-            (st = alloc_buf(ix, &sn.ovi.p, meta_b, s)))
+            (st = alloc_buf(ix, &sn.ovi.p, meta_b, s)) || (st = alloc_buf(ix, &sn.top.p, 16, s)))
             return st;
     }
     cudaMemcpyAsync(sn.rec.p, ix->rec, rec_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(sn.ovo.p, ix->ovo, meta_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(sn.ovi.p, ix->ovi, meta_b, cudaMemcpyDeviceToDevice, s);
-    // pool tops: read them once (small, synchronous)
-    cudaMemcpyAsync(sn.pool_top, ix->d_pool_top, 16, cudaMemcpyDeviceToHost, s);
+    // pool tops stay on the device, so that a restore is all device-to-device
+    // copies (and can be captured in a CUDA graph)
+    cudaMemcpyAsync(sn.top.p, ix->d_pool_top, 16, cudaMemcpyDeviceToDevice, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(ix, e, "snapshot");
     sn.edges_stored = ix->edges_stored;
@@ -485,7 +603,7 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->ovo, sn.ovo.p, meta_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->ovi, sn.ovi.p, meta_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(ix->d_pool_top, sn.pool_top, 16, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(ix->d_pool_top, sn.top.p, 16, cudaMemcpyDeviceToDevice, s);
     cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
     ix->edges_stored = sn.edges_stored;
@@ -498,7 +616,19 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
 dbl_status dbl_sync(dbl_index *ix, void *stream)
 {
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
-    return read_status(ix, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st = read_status(ix, s);
+    // queries latch their errors in the status word of the default query context
+    cudaMemcpyAsync(ix->qc->h_pinned + 8, ix->qc->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "sync");
+    const uint32_t q = ix->qc->h_pinned[8];
+    if (q) {
+        cudaMemsetAsync(ix->qc->d_status, 0, sizeof(uint32_t), s);
+        if (q == DBL_ERR_TIMEOUT) ix->poisoned = true;
+        if (!st) st = fail(ix, (dbl_status)q, "query: device error (invalid id or search timeout)");
+    }
+    return st;
 }
 
 dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream)

@@ -10,14 +10,28 @@
 
 namespace dbl {
 
+// Epochs: a propagation (its seed level and every level after it) uses
+// stamps base+1, base+2, ... where base lives in device memory and is advanced
+// on the device when the propagation ends, so a captured and replayed launch
+// sequence never meets a stamp of an earlier replay.  64-bit: never wraps.
 struct FrontierOut {
     uint64_t *tasks;
     uint32_t *count;
     int64_t cap;
-    unsigned long long *stamp;  // [2][n] epoch of the last enqueue per direction
-    unsigned long long epoch;   // stamp value of the level being filled (64-bit: never wraps)
+    unsigned long long *stamp;        // [2][n] epoch of the last enqueue per direction
+    unsigned long long epoch;         // stamp value of the level being filled
     uint32_t *status;
+    const unsigned long long *epoch_base = nullptr;  // if set, epoch = *epoch_base + epoch_off
+    unsigned long long epoch_off = 0;
 };
+
+// Resolve the level's epoch from the device base (once, at kernel start).
+__device__ __forceinline__ void resolve_epoch(FrontierOut &f)
+{
+    if (f.epoch_base) f.epoch = *(const volatile unsigned long long *)f.epoch_base + f.epoch_off;
+}
+
+__global__ void k_epoch_advance(unsigned long long *base, unsigned long long by);
 
 // Warp-cooperative enqueue: every lane of the warp must call it (lanes with
 // want == false pass through).  One atomicAdd per warp reserves the slots.

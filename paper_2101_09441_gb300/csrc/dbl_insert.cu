@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
                                                      uint64_t *rec, FrontierOut f, unsigned long long *stats)
 {
     if (status_set(f.status)) return;
+    resolve_epoch(f);
     constexpr int RW = 2 * HS;
     unsigned long long skipped = 0, applied = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -260,8 +261,7 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     ix->edges_stored += b;
     atomic_add_host_stat(ix, 15, (uint64_t)b, s);
     // 3. seed the repair frontier, then propagate to the fixpoint
-    ix->epoch += 1;
-    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, ix->epoch, ix->d_status};
+    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, 0, ix->d_status, ix->d_epoch, 1};
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     const DevGraph g = dev_graph(ix);
     tbegin(ix, DBL_KERNEL_INSERT_SEED, s);

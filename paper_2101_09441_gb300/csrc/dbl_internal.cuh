@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -119,7 +121,7 @@ struct Buf {
 struct Snapshot {
     bool valid = false;
     Buf rec, ovo, ovi;  // labels; (off, len, cap) triples for both directions
-    int64_t pool_top[2] = {0, 0};
+    Buf top;            // the two pool tops (device)
     int64_t edges_stored = 0;
 };
 
@@ -154,27 +156,15 @@ struct dbl_index {
     uint64_t *front[2] = {nullptr, nullptr};
     int64_t front_cap = 0;
     uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
-    unsigned long long epoch = 0;     // last frontier epoch used
+    unsigned long long *d_epoch = nullptr;  // device base of the frontier epochs (see dbl_frontier.cuh)
 
     // insertion scratch
     int32_t *ins_cnt = nullptr;       // [2][n] per-vertex batch counts
     int32_t *ins_pos = nullptr;       // [2][bcap] per-edge slot in its vertex batch
     int64_t ins_bcap = 0;
 
-    // query scratch
-    int32_t *und = nullptr;           // undecided query indices
-    int64_t und_cap = 0;
-    uint64_t *qtab = nullptr;         // per undecided query: u, v, DL_out(u), BL_in(v), BL_out(v)
-    int64_t qtab_cap = 0;
-    unsigned long long *found = nullptr;  // per 64-query group
-    int64_t found_cap = 0;
-    dbl::SearchSlot *table = nullptr;
-    int64_t table_slots = 0;          // power of two
-    int32_t *claimed = nullptr;       // slots claimed in the current wave
-    int32_t *slot_list[2] = {nullptr, nullptr};
-    dbl::SearchTask *stask = nullptr;
-    int64_t stask_cap = 0;
-    void *pstate = nullptr;           // device state of the persistent search
+    // query scratch of calls without an explicit context (dbl_query)
+    struct dbl_qctx *qc = nullptr;
 
     // status, counters
     uint32_t *d_status = nullptr;
@@ -195,10 +185,36 @@ struct dbl_index {
     std::vector<cudaEvent_t> ev_free;
     int open_kind = -1;
 
-    uint64_t h_stats[16] = {0};       // host-side counters merged into dbl_stats
-    uint64_t launches = 0;            // kernels launched by this index
+    std::atomic<uint64_t> h_stats[16] = {};  // host-side counters merged into dbl_stats
+    std::atomic<uint64_t> launches{0};       // kernels launched by this index
     dbl::Snapshot snaps[4];
     std::vector<dbl::Buf> owned;      // for teardown
+    std::mutex alloc_mu;              // allocations may come from several query contexts
+};
+
+// Scratch of one query batch in flight: the undecided list, the search's
+// query table, state hash table, slot lists and tasks, plus its own counters,
+// status word and pinned read-back words.  Batches on different contexts may
+// run concurrently on different streams (the labels are only read); one
+// context runs one batch at a time.
+struct dbl_qctx {
+    dbl_index *ix = nullptr;
+    int32_t *und = nullptr;           // undecided query indices
+    int64_t und_cap = 0;
+    uint64_t *qtab = nullptr;         // per undecided query: u, v, DL_out(u), BL_in(v), BL_out(v)
+    unsigned long long *found = nullptr;  // per 64-query group
+    dbl::SearchSlot *table = nullptr;
+    int64_t table_slots = 0;          // power of two
+    int32_t *claimed = nullptr;       // slots claimed in the current wave
+    int32_t *slot_list[2] = {nullptr, nullptr};
+    dbl::SearchTask *stask = nullptr;
+    int64_t stask_cap = 0;
+    void *pstate = nullptr;           // device state of the persistent search
+    uint32_t *d_counts = nullptr;     // own counter words (kCnt*)
+    uint32_t *d_status = nullptr;     // own latched status
+    uint32_t *h_pinned = nullptr;     // pinned read-back words
+    std::vector<dbl::Buf> owned;
+    std::string err;
 };
 
 // small device counter slots in d_counts
@@ -226,7 +242,10 @@ void free_buf(dbl_index *ix, void *p, cudaStream_t s);
 dbl_status fail(dbl_index *ix, dbl_status st, const std::string &msg);
 dbl_status cuda_fail(dbl_index *ix, cudaError_t e, const char *what);
 dbl_status read_status(dbl_index *ix, cudaStream_t s);
-dbl_status ensure_search_scratch(dbl_index *ix, int64_t und, cudaStream_t s);
+dbl_status ensure_search_scratch(dbl_qctx *c, int64_t und, cudaStream_t s);
+dbl_status qctx_create(dbl_index *ix, dbl_qctx **out, cudaStream_t s);
+void qctx_destroy(dbl_qctx *c, cudaStream_t s);
+dbl_status qfail(dbl_qctx *c, dbl_status st, const std::string &msg);
 void atomic_add_host_stat(dbl_index *ix, int idx, uint64_t v, cudaStream_t s);
 size_t persist_state_bytes();  // dbl_query.cu
 // bracket the launches between tbegin and tend (no-op without DBL_FLAG_TIMING)
@@ -265,6 +284,8 @@ inline int num_sms()
 // prep (dbl_prep.cu)
 dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s);
 dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s);
+dbl_status select_top(dbl_index *ix, const int32_t *op, const int32_t *ip, const unsigned long long *keys, int32_t n,
+                      int32_t k, int32_t *out, cudaStream_t s);
 dbl_status select_leaves(dbl_index *ix, const int32_t *bucket, const uint8_t *role, cudaStream_t s);
 dbl_status seed_labels(dbl_index *ix, cudaStream_t s);
 dbl_status exclusive_scan_i32(dbl_index *ix, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
@@ -273,6 +294,7 @@ dbl_status exclusive_scan_i32(dbl_index *ix, const int32_t *in, int32_t *out, in
 // (count in d_counts[kCntFront0]) until no record changes.
 dbl_status propagate(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
+dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s);
 void launch_seed_frontier(dbl_index *ix, cudaStream_t s);  // all vertices with a non-zero half
 
 // insertion (dbl_insert.cu)
@@ -281,7 +303,7 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
                              int32_t *pos_in, cudaStream_t s);
 
 // query (dbl_query.cu)
-dbl_status query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
-                 cudaStream_t s);
+dbl_status query(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
+                 uint8_t *code, cudaStream_t s);
 
 }  // namespace dbl

@@ -198,10 +198,19 @@ dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s)
 }
 
 // ------------------------------------------------------------ landmarks
-__device__ __forceinline__ unsigned long long M_of(const int32_t *op, const int32_t *ip, int32_t v)
+// The ranking key of a vertex: M(u) = |Suc(u)| * |Pre(u)| from the two CSRs,
+// or an explicit 64-bit key array (e.g. learned scores); larger ranks first,
+// ties by smaller id.
+struct KeySrc {
+    const int32_t *op, *ip;
+    const unsigned long long *keys;
+};
+
+__device__ __forceinline__ unsigned long long key_of(const KeySrc &ks, int32_t v)
 {
-    unsigned long long o = (unsigned long long)(op[v + 1] - op[v]);
-    unsigned long long i = (unsigned long long)(ip[v + 1] - ip[v]);
+    if (ks.keys) return ks.keys[v];
+    unsigned long long o = (unsigned long long)(ks.op[v + 1] - ks.op[v]);
+    unsigned long long i = (unsigned long long)(ks.ip[v + 1] - ks.ip[v]);
     return o * i;
 }
 
@@ -213,14 +222,14 @@ struct SelState {
     unsigned int hist[256];
 };
 
-__global__ void k_sel_hist(const int32_t *op, const int32_t *ip, int32_t n, SelState *st, int shift)
+__global__ void k_sel_hist(KeySrc ks, int32_t n, SelState *st, int shift)
 {
     __shared__ unsigned int h[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned long long pre = st->prefix, pm = st->pmask;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long M = M_of(op, ip, (int32_t)v);
+        unsigned long long M = key_of(ks, (int32_t)v);
         if ((M & pm) == pre) atomicAdd(&h[(M >> shift) & 255], 1u);
     }
     __syncthreads();
@@ -246,12 +255,12 @@ __global__ void k_sel_pick(SelState *st, int shift)
 }
 
 // vertices with M > T (unordered) and flags of M == T
-__global__ void k_sel_gather(const int32_t *op, const int32_t *ip, int32_t n, const SelState *st, int32_t *above,
-                             uint32_t *n_above, int32_t *tie_flag, int32_t k)
+__global__ void k_sel_gather(KeySrc ks, int32_t n, const SelState *st, int32_t *above, uint32_t *n_above,
+                             int32_t *tie_flag, int32_t k)
 {
     const unsigned long long T = st->prefix;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long M = M_of(op, ip, (int32_t)v);
+        unsigned long long M = key_of(ks, (int32_t)v);
         tie_flag[v] = M == T ? 1 : 0;
         if (M > T) {
             uint32_t p = atomicAdd(n_above, 1u);
@@ -271,17 +280,16 @@ __global__ void k_sel_ties(const int32_t *tie_flag, const int32_t *tie_rank, int
 }
 
 // rank the (< k) vertices above T by (M desc, id asc); one block
-__global__ void k_sel_rank(const int32_t *op, const int32_t *ip, const int32_t *above, const uint32_t *n_above,
-                           int32_t *landmarks, int32_t k)
+__global__ void k_sel_rank(KeySrc ks, const int32_t *above, const uint32_t *n_above, int32_t *landmarks, int32_t k)
 {
     const uint32_t na = min(*n_above, (uint32_t)k);
     for (uint32_t i = threadIdx.x; i < na; i += blockDim.x) {
         int32_t a = above[i];
-        unsigned long long Ma = M_of(op, ip, a);
+        unsigned long long Ma = key_of(ks, a);
         uint32_t r = 0;
         for (uint32_t j = 0; j < na; ++j) {
             int32_t b = above[j];
-            unsigned long long Mb = M_of(op, ip, b);
+            unsigned long long Mb = key_of(ks, b);
             r += (Mb > Ma) || (Mb == Ma && b < a);
         }
         if (r < (uint32_t)k) landmarks[r] = a;
@@ -306,7 +314,15 @@ dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s)
         dbl_status st = read_status(ix, s);
         return st ? fail(ix, st, "landmark id out of range") : DBL_OK;
     }
-    cudaMemsetAsync(ix->landmarks, 0xff, sizeof(int32_t) * (size_t)k, s);  // -1
+    return select_top(ix, ix->out_ptr, ix->in_ptr, nullptr, n, k, ix->landmarks, s);
+}
+
+// out[0..k): the top min(k, n) vertices by key (descending), ties by id; -1 after.
+dbl_status select_top(dbl_index *ix, const int32_t *op, const int32_t *ip, const unsigned long long *keys, int32_t n,
+                      int32_t k, int32_t *out, cudaStream_t s)
+{
+    const KeySrc ks{op, ip, keys};
+    cudaMemsetAsync(out, 0xff, sizeof(int32_t) * (size_t)k, s);  // -1
     const int64_t take = k < n ? k : n;
     if (take == 0) return DBL_OK;
     SelState *sel = nullptr;
@@ -326,18 +342,18 @@ dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s)
     cudaStreamSynchronize(s);  // h_need is a stack value
     const unsigned grid = grid_for(n);
     for (int shift = 56; shift >= 0; shift -= 8) {
-        k_sel_hist<<<grid, kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, n, sel, shift);
+        k_sel_hist<<<grid, kBlock, 0, s>>>(ks, n, sel, shift);
         ++ix->launches;
         k_sel_pick<<<1, 32, 0, s>>>(sel, shift);
         ++ix->launches;
     }
-    k_sel_gather<<<grid, kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, n, sel, above, na, flag, k);
+    k_sel_gather<<<grid, kBlock, 0, s>>>(ks, n, sel, above, na, flag, k);
     ++ix->launches;
     st = exclusive_scan_i32(ix, flag, rank, n, s);
     if (!st) {
-        k_sel_rank<<<1, kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, above, na, ix->landmarks, k);
+        k_sel_rank<<<1, kBlock, 0, s>>>(ks, above, na, out, k);
         ++ix->launches;
-        k_sel_ties<<<grid, kBlock, 0, s>>>(flag, rank, n, sel, na, ix->landmarks, k);
+        k_sel_ties<<<grid, kBlock, 0, s>>>(flag, rank, n, sel, na, out, k);
         ++ix->launches;
     }
     free_buf(ix, sel, s);
@@ -424,6 +440,7 @@ __global__ void k_seed_leaves(const int32_t *bucket, const uint8_t *role, int32_
 // every vertex with a non-zero half joins the frontier in that direction
 __global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, DevGraph g, FrontierOut f)
 {
+    resolve_epoch(f);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += stride) {
         int64_t v = base + threadIdx.x;
@@ -446,8 +463,7 @@ __global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, Dev
 
 void launch_seed_frontier(dbl_index *ix, cudaStream_t s)
 {
-    ix->epoch += 1;
-    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, ix->epoch, ix->d_status};
+    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, 0, ix->d_status, ix->d_epoch, 1};
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     int64_t blocks = ((int64_t)ix->n + kBlock - 1) / kBlock;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, co
                                                    const uint32_t *ntasks_p, FrontierOut f,
                                                    unsigned long long *stats)
 {
+    resolve_epoch(f);
     expand_level<HS, TEAM>(g, rec, tasks, *ntasks_p, f, stats,
                            ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                            ((int64_t)gridDim.x * blockDim.x) >> 5);
@@ -54,6 +55,23 @@ static void launch_expand_team(dbl_index *ix, int cur, uint32_t ntasks, const Fr
     }
 }
 
+// Propagate over another record array with half width hs (used by the
+// coverage pass of the learned scorer): the frontier kernels read the
+// records and their width from the index, so swap them in for the call.
+dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s)
+{
+    uint64_t *rec0 = ix->rec;
+    const int32_t hs0 = ix->hs, rw0 = ix->rw;
+    ix->rec = rec;
+    ix->hs = hs;
+    ix->rw = 2 * hs;
+    dbl_status st = propagate(ix, s);
+    ix->rec = rec0;
+    ix->hs = hs0;
+    ix->rw = rw0;
+    return st;
+}
+
 // A device error during propagation (a frontier overflow, which the sizing
 // rules out) leaves labels short of the fixpoint: poison the index.
 static dbl_status propagate_error(dbl_index *ix, uint32_t code, cudaStream_t s)
@@ -81,10 +99,10 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
             ix->poisoned = true;
             return fail(ix, DBL_ERR_TIMEOUT, "propagate: level bound exceeded");
         }
-        ix->epoch += 1;
         const int nxt = cur ^ 1;
-        FrontierOut f{ix->front[nxt], ix->d_counts + kCntFront0 + nxt, ix->front_cap, ix->stamp, ix->epoch,
-                      ix->d_status};
+        // the seed level used base+1; level L fills base+1+L
+        FrontierOut f{ix->front[nxt], ix->d_counts + kCntFront0 + nxt, ix->front_cap, ix->stamp, 0,
+                      ix->d_status, ix->d_epoch, (unsigned long long)(1 + levels)};
         cudaMemsetAsync(ix->d_counts + kCntFront0 + nxt, 0, sizeof(uint32_t), s);
         tbegin(ix, DBL_KERNEL_PROPAGATE, s);
         switch (ix->hs) {
@@ -105,9 +123,14 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
     if (cur != 0) {
         cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     }
+    // every epoch of this propagation is used: move the base past them
+    k_epoch_advance<<<1, 1, 0, s>>>(ix->d_epoch, (unsigned long long)levels + 3);
+    ++ix->launches;
     atomic_add_host_stat(ix, 8, (uint64_t)levels, s);
     return DBL_OK;
 }
+
+__global__ void k_epoch_advance(unsigned long long *base, unsigned long long by) { *base += by; }
 
 // ---------------------------------------------------------------------------
 // Persistent form: one cooperative launch runs every level.  Level L reads
@@ -120,13 +143,15 @@ template <int HS, int TEAM>
 __global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0,
                                                                  uint64_t *f1, uint32_t *c3, int64_t cap,
                                                                  unsigned long long *stamp,
-                                                                 unsigned long long epoch0, uint32_t *status,
+                                                                 unsigned long long *epoch_base, uint32_t *status,
                                                                  unsigned long long *stats, GridBarrier bar,
                                                                  int64_t max_levels)
 {
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long epoch = epoch0;
+    // the seed level used base+1; level L fills base+2+L
+    const unsigned long long base = *(const volatile unsigned long long *)epoch_base;
+    unsigned long long epoch = base + 1;
     int64_t L = 0;
     for (;; ++L) {
         const uint32_t nt = ld_volatile_u32(c3 + L % 3);
@@ -144,6 +169,8 @@ __global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uin
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[8] += (unsigned long long)L;
         c3[L % 3] = 0;
+        // every block read the base at its start, long before this point
+        *epoch_base = base + (unsigned long long)L + 3;
     }
 }
 
@@ -160,14 +187,12 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
     uint32_t *c3 = ix->d_counts + kCntP0;
     int64_t cap = ix->front_cap;
     unsigned long long *stamp = ix->stamp;
-    unsigned long long epoch0 = ix->epoch;
+    unsigned long long *epoch_base = ix->d_epoch;
     uint32_t *status = ix->d_status;
     unsigned long long *stats = ix->d_stats;
     GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
     int64_t max_levels = (int64_t)ix->n + 2;
-    // the level count is unknown on the host: reserve every epoch the launch may use
-    ix->epoch += (unsigned long long)max_levels + 2;
-    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &stamp, &epoch0, &status, &stats, &bar, &max_levels};
+    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &stamp, &epoch_base, &status, &stats, &bar, &max_levels};
     dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_propagate_persistent<HS, TEAM>, grid, block, args, 0, s);
     ++ix->launches;

@@ -30,6 +30,16 @@ namespace dbl {
 __host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
 
 // ------------------------------------------------------------ label test
+// Each thread takes QPT queries (QPT = 4 for 32-byte records) and issues all
+// of their record loads before using any, so that many DRAM sectors are in
+// flight per warp; answers and codes are written coalesced, the deciding
+// rules are counted with warp ballots, and undecided pairs are compacted with
+// one atomic per warp.
+template <int HS>
+struct LabelQPT {
+    static constexpr int v = HS == 2 ? 4 : (HS == 4 ? 2 : 1);
+};
+
 template <int WD, int WB>
 __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const int32_t *qv, int64_t q,
                                                         const uint64_t *rec, int32_t n, uint8_t *ans,
@@ -38,66 +48,86 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
-    __shared__ unsigned int cnt[8];
-    if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
-    __syncthreads();
+    constexpr int QPT = LabelQPT<HS>::v;
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < q; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        bool undecided = false;
-        if (i < q) {
-            const int32_t u = __ldcs(qu + i), v = __ldcs(qv + i);
-            uint8_t a = 0, c = DBL_CODE_UNDECIDED;
-            if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
-                set_status(status, DBL_ERR_INVALID);
-            } else if (u == v) {
-                a = 1;
-                c = DBL_CODE_SELF;
-            } else {
-                uint64_t fu[HS], bu[HS], fv[HS], bv[HS];
-                load_half<HS>(rec + (size_t)u * RW, fu);
-                load_half<HS>(rec + (size_t)u * RW + HS, bu);
-                load_half<HS>(rec + (size_t)v * RW, fv);
-                load_half<HS>(rec + (size_t)v * RW + HS, bv);
-                uint64_t uv = 0, vu = 0, uu = 0, vv = 0, blf = 0;
+    unsigned int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // kept by lane 0
+    const int64_t tile = (int64_t)blockDim.x * QPT;
+    const int64_t stride = (int64_t)gridDim.x * tile;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < q; base += stride) {
+        int32_t u[QPT], v[QPT];
+        bool live[QPT];
 #pragma unroll
-                for (int w = 0; w < WD; ++w) {
-                    uv |= bu[w] & fv[w];
-                    vu |= bv[w] & fu[w];
-                    uu |= bu[w] & fu[w];
-                    vv |= bv[w] & fv[w];
-                }
-#pragma unroll
-                for (int w = WD; w < WD + WB; ++w) blf |= (fu[w] & ~fv[w]) | (bv[w] & ~bu[w]);
-                if (uv) {
-                    a = 1;
-                    c = DBL_CODE_DL;
-                } else if (blf) {
-                    c = DBL_CODE_BL;
-                } else if (vu) {
-                    c = DBL_CODE_THM1;
-                } else if (uu | vv) {
-                    c = DBL_CODE_THM2;
-                } else {
-                    undecided = true;
-                }
-            }
-            __stcs(ans + i, a);
-            if (code) __stcs(code + i, c);
-            if (c) atomicAdd(&cnt[c], 1u);
+        for (int j = 0; j < QPT; ++j) {
+            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            live[j] = i < q;
+            u[j] = live[j] ? __ldcs(qu + i) : 0;
+            v[j] = live[j] ? __ldcs(qv + i) : 0;
         }
-        const unsigned bal = __ballot_sync(kFull, undecided);
-        if (bal) {
-            uint32_t b0 = 0;
-            const int leader = __ffs(bal) - 1;
-            if (lane == leader) b0 = atomicAdd(n_und, (uint32_t)__popc(bal));
-            b0 = __shfl_sync(kFull, b0, leader);
-            if (undecided) und[b0 + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+        bool ok[QPT];
+        uint64_t fu[QPT][HS], bu[QPT][HS], fv[QPT][HS], bv[QPT][HS];
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            ok[j] = live[j] && (uint32_t)u[j] < (uint32_t)n && (uint32_t)v[j] < (uint32_t)n && u[j] != v[j];
+            const int32_t uu = ok[j] ? u[j] : 0, vv = ok[j] ? v[j] : 0;
+            load_half<HS>(rec + (size_t)uu * RW, fu[j]);
+            load_half<HS>(rec + (size_t)uu * RW + HS, bu[j]);
+            load_half<HS>(rec + (size_t)vv * RW, fv[j]);
+            load_half<HS>(rec + (size_t)vv * RW + HS, bv[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            uint8_t a = 0, c = DBL_CODE_UNDECIDED;
+            bool undecided = false;
+            if (live[j]) {
+                if ((uint32_t)u[j] >= (uint32_t)n || (uint32_t)v[j] >= (uint32_t)n) {
+                    set_status(status, DBL_ERR_INVALID);
+                } else if (u[j] == v[j]) {
+                    a = 1;
+                    c = DBL_CODE_SELF;
+                } else {
+                    uint64_t uv = 0, vu = 0, su = 0, sv = 0, blf = 0;
+#pragma unroll
+                    for (int w = 0; w < WD; ++w) {
+                        uv |= bu[j][w] & fv[j][w];
+                        vu |= bv[j][w] & fu[j][w];
+                        su |= bu[j][w] & fu[j][w];
+                        sv |= bv[j][w] & fv[j][w];
+                    }
+#pragma unroll
+                    for (int w = WD; w < WD + WB; ++w) blf |= (fu[j][w] & ~fv[j][w]) | (bv[j][w] & ~bu[j][w]);
+                    if (uv) {
+                        a = 1;
+                        c = DBL_CODE_DL;
+                    } else if (blf) {
+                        c = DBL_CODE_BL;
+                    } else if (vu) {
+                        c = DBL_CODE_THM1;
+                    } else if (su | sv) {
+                        c = DBL_CODE_THM2;
+                    } else {
+                        undecided = true;
+                    }
+                }
+                __stcs(ans + i, a);
+                if (code) __stcs(code + i, c);
+            }
+#pragma unroll
+            for (int r = 1; r < 6; ++r) counts[r] += __popc(__ballot_sync(kFull, live[j] && c == r));
+            const unsigned bal = __ballot_sync(kFull, undecided);
+            if (bal) {
+                uint32_t b0 = 0;
+                const int leader = __ffs(bal) - 1;
+                if (lane == leader) b0 = atomicAdd(n_und, (uint32_t)__popc(bal));
+                b0 = __shfl_sync(kFull, b0, leader);
+                if (undecided) und[b0 + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+            }
         }
     }
-    __syncthreads();
-    if (threadIdx.x < 8 && cnt[threadIdx.x]) atomicAdd(stats + threadIdx.x, (unsigned long long)cnt[threadIdx.x]);
+    if (lane == 0)
+#pragma unroll
+        for (int r = 1; r < 6; ++r)
+            if (counts[r]) atomicAdd(stats + r, (unsigned long long)counts[r]);
 }
 
 // ------------------------------------------------------------ search
@@ -503,34 +533,45 @@ static unsigned blocks_for(int64_t work)
     return (unsigned)b;
 }
 
-static SearchArgs search_args(dbl_index *ix, const int32_t *qu, const int32_t *qv, uint8_t *ans, uint8_t *code,
-                              uint32_t *n_claimed, uint32_t *overflow)
+static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv, uint8_t *ans,
+                              uint8_t *code, uint32_t *n_claimed, uint32_t *overflow)
 {
     SearchArgs a;
     a.g = dev_graph(ix);
     a.rec = ix->rec;
-    a.qtab = ix->qtab;
-    a.found = ix->found;
-    a.c = SearchCtx{ix->table, (unsigned long long)(ix->table_slots - 1), ix->claimed, n_claimed, overflow};
-    a.tasks = ix->stask;
-    a.task_cap = ix->stask_cap;
-    a.und = ix->und;
+    a.qtab = c->qtab;
+    a.found = c->found;
+    a.c = SearchCtx{c->table, (unsigned long long)(c->table_slots - 1), c->claimed, n_claimed, overflow};
+    a.tasks = c->stask;
+    a.task_cap = c->stask_cap;
+    a.und = c->und;
     a.qu = qu;
     a.qv = qv;
     a.ans = ans;
     a.code = code;
     a.stats = ix->d_stats;
-    a.lists[0] = ix->slot_list[0];
-    a.lists[1] = ix->slot_list[1];
-    a.list_cap = ix->table_slots;
+    a.lists[0] = c->slot_list[0];
+    a.lists[1] = c->slot_list[1];
+    a.list_cap = c->table_slots;
     return a;
 }
 
-template <int WD, int WB>
-static void launch_search_expand(dbl_index *ix, const SearchArgs &a, int64_t est, uint32_t sep, const SlotList &next,
-                                 cudaStream_t s)
+// Kernel timing brackets are kept for the index's own context only (they are
+// not thread-safe; explicit contexts may run on several host threads).
+static void qt_begin(dbl_index *ix, dbl_qctx *c, int kind, cudaStream_t s)
 {
-    uint32_t *nt = ix->d_counts + kCntTasks;
+    if (c == ix->qc) tbegin(ix, kind, s);
+}
+static void qt_end(dbl_index *ix, dbl_qctx *c, cudaStream_t s)
+{
+    if (c == ix->qc) tend(ix, s);
+}
+
+template <int WD, int WB>
+static void launch_search_expand(dbl_index *ix, dbl_qctx *c, const SearchArgs &a, int64_t est, uint32_t sep,
+                                 const SlotList &next, cudaStream_t s)
+{
+    uint32_t *nt = c->d_counts + kCntTasks;
     switch (ix->opt.team) {
     case 4: k_search_expand<WD, WB, 4><<<blocks_for(est * 4), kBlock, 0, s>>>(a, nt, sep, next); break;
     case 16:
@@ -541,121 +582,122 @@ static void launch_search_expand(dbl_index *ix, const SearchArgs &a, int64_t est
 }
 
 template <int WD, int WB>
-static dbl_status run_search_wave(dbl_index *ix, const int32_t *qu, const int32_t *qv, int64_t j0, int64_t j1,
-                                  uint8_t *ans, uint8_t *code, bool *overflowed, cudaStream_t s)
+static dbl_status run_search_wave(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv, int64_t j0,
+                                  int64_t j1, uint8_t *ans, uint8_t *code, bool *overflowed, cudaStream_t s)
 {
-    uint32_t *cnt = ix->d_counts;
-    uint32_t *h = ix->h_pinned;
-    const SearchArgs a = search_args(ix, qu, qv, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
+    uint32_t *cnt = c->d_counts;
+    uint32_t *h = c->h_pinned;
+    const SearchArgs a = search_args(ix, c, qu, qv, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
     cudaMemsetAsync(cnt + kCntSlots0, 0, sizeof(uint32_t) * 5, s);  // slots0, slots1, tasks, claimed, overflow
     // slot stamps are per wave (slots are cleared after each wave): level epochs 1, 2, ...
     uint32_t sep = 1;
-    SlotList lists[2] = {{ix->slot_list[0], cnt + kCntSlots0, ix->table_slots},
-                         {ix->slot_list[1], cnt + kCntSlots1, ix->table_slots}};
-    tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
+    SlotList lists[2] = {{c->slot_list[0], cnt + kCntSlots0, c->table_slots},
+                         {c->slot_list[1], cnt + kCntSlots1, c->table_slots}};
+    qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
     k_search_setup<WD, WB><<<blocks_for(j1 - j0), kBlock, 0, s>>>(a, j0, j1, sep, lists[0]);
     ++ix->launches;
-    tend(ix, s);
+    qt_end(ix, c, s);
     int cur = 0;
     int64_t levels = 0;
     const int64_t max_levels = (int64_t)ix->n + 2;
     for (;;) {
         cudaMemcpyAsync(h, cnt, sizeof(uint32_t) * kCntWords, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
-        if (e) return cuda_fail(ix, e, "search level");
+        if (e) return qfail(c, DBL_ERR_CUDA, std::string("search level: ") + cudaGetErrorString(e));
         if (h[kCntOverflow]) break;
         const uint32_t nslots = h[kCntSlots0 + cur];
         if (!nslots) break;
         if (++levels > max_levels) {
             ix->poisoned = true;
-            return fail(ix, DBL_ERR_TIMEOUT, "search: level bound exceeded");
+            return qfail(c, DBL_ERR_TIMEOUT, "search: level bound exceeded");
         }
         const int nxt = cur ^ 1;
         cudaMemsetAsync(cnt + kCntTasks, 0, sizeof(uint32_t), s);
         cudaMemsetAsync(cnt + kCntSlots0 + nxt, 0, sizeof(uint32_t), s);
-        tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
+        qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
         k_search_finalize<<<blocks_for(nslots), kBlock, 0, s>>>(a, lists[cur], cnt + kCntTasks);
         ++ix->launches;
-        tbegin(ix, DBL_KERNEL_SEARCH_EXPAND, s);
+        qt_begin(ix, c, DBL_KERNEL_SEARCH_EXPAND, s);
         ++sep;
         // tasks are at most nslots * (1 + maxdeg/kChunk); size the grid generously and let it stride
-        launch_search_expand<WD, WB>(ix, a, (int64_t)nslots * 2, sep, lists[nxt], s);
-        tend(ix, s);
+        launch_search_expand<WD, WB>(ix, c, a, (int64_t)nslots * 2, sep, lists[nxt], s);
+        qt_end(ix, c, s);
         cur = nxt;
     }
     *overflowed = h[kCntOverflow] != 0;
-    tbegin(ix, DBL_KERNEL_SEARCH_OTHER, s);
+    qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
     k_search_answer<<<blocks_for(j1 - j0), kBlock, 0, s>>>(a, j0, j1, *overflowed ? 0 : 1);
     ++ix->launches;
-    k_search_clear<<<blocks_for(ix->table_slots / 4), kBlock, 0, s>>>(a);
+    k_search_clear<<<blocks_for(c->table_slots / 4), kBlock, 0, s>>>(a);
     ++ix->launches;
-    tend(ix, s);
+    qt_end(ix, c, s);
     atomic_add_host_stat(ix, 14, 1, s);
     atomic_add_host_stat(ix, 8, (uint64_t)levels, s);
     cudaError_t e = cudaGetLastError();
-    return e ? cuda_fail(ix, e, "search wave") : DBL_OK;
+    return e ? qfail(c, DBL_ERR_CUDA, std::string("search wave: ") + cudaGetErrorString(e)) : DBL_OK;
 }
 
 template <int WD, int WB, int TEAM>
-static dbl_status launch_search_persistent(dbl_index *ix, const int32_t *qu, const int32_t *qv, uint8_t *ans,
-                                           uint8_t *code, cudaStream_t s)
+static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv,
+                                           uint8_t *ans, uint8_t *code, cudaStream_t s)
 {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search_persistent<WD, WB, TEAM>, kBlock, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
-    PersistState *ps = (PersistState *)ix->pstate;
+    PersistState *ps = (PersistState *)c->pstate;
     cudaMemsetAsync(ps, 0, sizeof(PersistState), s);
-    SearchArgs a = search_args(ix, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
-    const uint32_t *n_und = ix->d_counts + kCntUnd;
-    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
-    uint32_t *status = ix->d_status;
+    SearchArgs a = search_args(ix, c, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
+    const uint32_t *n_und = c->d_counts + kCntUnd;
+    GridBarrier bar{c->d_counts + kCntBarArrived, c->d_counts + kCntBarPhase};
+    uint32_t *status = c->d_status;
     int64_t max_levels = (int64_t)ix->n + 2;
     void *args[] = {&a, &ps, &n_und, &bar, &status, &max_levels};
     dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
-    tbegin(ix, DBL_KERNEL_SEARCH_EXPAND, s);
+    qt_begin(ix, c, DBL_KERNEL_SEARCH_EXPAND, s);
     cudaError_t e =
         cudaLaunchCooperativeKernel((const void *)k_search_persistent<WD, WB, TEAM>, grid, block, args, 0, s);
     ++ix->launches;
-    tend(ix, s);
-    return e ? cuda_fail(ix, e, "persistent search launch") : DBL_OK;
+    qt_end(ix, c, s);
+    return e ? qfail(c, DBL_ERR_CUDA, std::string("persistent search launch: ") + cudaGetErrorString(e)) : DBL_OK;
 }
 
 template <int WD, int WB>
-static dbl_status query_t(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
-                          cudaStream_t s)
+static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
+                          uint8_t *code, cudaStream_t s)
 {
-    dbl_status st = ensure_search_scratch(ix, q, s);
+    dbl_status st = ensure_search_scratch(c, q, s);
     if (st) return st;
-    uint32_t *cnt = ix->d_counts;
+    uint32_t *cnt = c->d_counts;
     cudaMemsetAsync(cnt + kCntUnd, 0, sizeof(uint32_t), s);
     int64_t blocks = (q + kBlock - 1) / kBlock;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
-    tbegin(ix, DBL_KERNEL_QUERY_LABEL, s);
-    k_query_label<WD, WB><<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, ix->und,
-                                                              cnt + kCntUnd, ix->d_status, ix->d_stats);
+    qt_begin(ix, c, DBL_KERNEL_QUERY_LABEL, s);
+    k_query_label<WD, WB><<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->und,
+                                                              cnt + kCntUnd, c->d_status, ix->d_stats);
     ++ix->launches;
-    tend(ix, s);
-    if (ix->opt.flags & DBL_FLAG_PERSISTENT) {
-        // the undecided count stays on the device; one launch runs every wave
+    qt_end(ix, c, s);
+    // one cooperative launch runs every wave, for the index's own context only
+    // (cooperative grids of concurrent contexts would compete for residency)
+    if ((ix->opt.flags & DBL_FLAG_PERSISTENT) && c == ix->qc) {
         switch (ix->opt.team) {
-        case 4: st = launch_search_persistent<WD, WB, 4>(ix, u, v, ans, code, s); break;
+        case 4: st = launch_search_persistent<WD, WB, 4>(ix, c, u, v, ans, code, s); break;
         case 16:
-        case 32: st = launch_search_persistent<WD, WB, 16>(ix, u, v, ans, code, s); break;
-        default: st = launch_search_persistent<WD, WB, 8>(ix, u, v, ans, code, s); break;
+        case 32: st = launch_search_persistent<WD, WB, 16>(ix, c, u, v, ans, code, s); break;
+        default: st = launch_search_persistent<WD, WB, 8>(ix, c, u, v, ans, code, s); break;
         }
-        return st;  // device errors (invalid ids, timeout) latch in the status word
+        return st;  // device errors (invalid ids, timeout) latch in the context's status word
     }
-    uint32_t *h = ix->h_pinned;
+    uint32_t *h = c->h_pinned;
     cudaMemcpyAsync(h, cnt + kCntUnd, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(h + 8, ix->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h + 8, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e) return cuda_fail(ix, e, "query label test");
+    if (e) return qfail(c, DBL_ERR_CUDA, std::string("query label test: ") + cudaGetErrorString(e));
     if (h[8]) {
-        cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);  // consumed; nothing was changed
-        return fail(ix, (dbl_status)h[8], "query: vertex id out of range");
+        cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), s);  // consumed; nothing was changed
+        return qfail(c, (dbl_status)h[8], "query: vertex id out of range");
     }
     const int64_t U = h[0];
     if (!U) return DBL_OK;
@@ -668,11 +710,11 @@ static dbl_status query_t(dbl_index *ix, const int32_t *u, const int32_t *v, int
         Range r = stack.back();
         stack.pop_back();
         bool over = false;
-        st = run_search_wave<WD, WB>(ix, u, v, r.j0, r.j1, ans, code, &over, s);
+        st = run_search_wave<WD, WB>(ix, c, u, v, r.j0, r.j1, ans, code, &over, s);
         if (st) return st;
         if (over) {
             const int64_t groups = (r.j1 - r.j0 + 63) / 64;
-            if (groups <= 1) return fail(ix, DBL_ERR_CAPACITY, "search: one group overflowed the state table");
+            if (groups <= 1) return qfail(c, DBL_ERR_CAPACITY, "search: one group overflowed the state table");
             const int64_t mid = r.j0 + (groups / 2) * 64;
             stack.push_back({mid, r.j1});
             stack.push_back({r.j0, mid});
@@ -681,22 +723,22 @@ static dbl_status query_t(dbl_index *ix, const int32_t *u, const int32_t *v, int
     return DBL_OK;
 }
 
-dbl_status query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans, uint8_t *code,
-                 cudaStream_t s)
+dbl_status query(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,
+                 uint8_t *code, cudaStream_t s)
 {
     if (q == 0) return DBL_OK;
     const int key = ix->wd * 16 + ix->wb;
     switch (key) {
-    case 1 * 16 + 1: return query_t<1, 1>(ix, u, v, q, ans, code, s);
-    case 2 * 16 + 1: return query_t<2, 1>(ix, u, v, q, ans, code, s);
-    case 1 * 16 + 2: return query_t<1, 2>(ix, u, v, q, ans, code, s);
-    case 2 * 16 + 2: return query_t<2, 2>(ix, u, v, q, ans, code, s);
-    case 4 * 16 + 1: return query_t<4, 1>(ix, u, v, q, ans, code, s);
-    case 1 * 16 + 4: return query_t<1, 4>(ix, u, v, q, ans, code, s);
-    case 2 * 16 + 4: return query_t<2, 4>(ix, u, v, q, ans, code, s);
-    case 4 * 16 + 2: return query_t<4, 2>(ix, u, v, q, ans, code, s);
-    case 4 * 16 + 4: return query_t<4, 4>(ix, u, v, q, ans, code, s);
-    default: return fail(ix, DBL_ERR_INVALID, "unsupported (k, kprime) combination");
+    case 1 * 16 + 1: return query_t<1, 1>(ix, c, u, v, q, ans, code, s);
+    case 2 * 16 + 1: return query_t<2, 1>(ix, c, u, v, q, ans, code, s);
+    case 1 * 16 + 2: return query_t<1, 2>(ix, c, u, v, q, ans, code, s);
+    case 2 * 16 + 2: return query_t<2, 2>(ix, c, u, v, q, ans, code, s);
+    case 4 * 16 + 1: return query_t<4, 1>(ix, c, u, v, q, ans, code, s);
+    case 1 * 16 + 4: return query_t<1, 4>(ix, c, u, v, q, ans, code, s);
+    case 2 * 16 + 4: return query_t<2, 4>(ix, c, u, v, q, ans, code, s);
+    case 4 * 16 + 2: return query_t<4, 2>(ix, c, u, v, q, ans, code, s);
+    case 4 * 16 + 4: return query_t<4, 4>(ix, c, u, v, q, ans, code, s);
+    default: return qfail(c, DBL_ERR_INVALID, "unsupported (k, kprime) combination");
     }
 }
 

@@ -1,0 +1,109 @@
+"""Learned landmark selection on top of the C ABI (orchestration only).
+
+The degree rule of the paper (Section 4.1) puts every landmark of an R-MAT or
+social graph into its giant strongly connected component, where one landmark
+already decides every pair routed through that component (Theorem 2's
+argument): the others add little to the DL test.  Here the first
+`base_slots` degree landmarks are kept and the remaining slots go to the
+vertices a network scores highest; the network is trained on how many of the
+sampled reachable pairs the kept landmarks leave undecided each vertex would
+decide (dbl_coverage).  The learned set is compared with the degree rule on
+held-out pairs and the degree rule is kept when the learned set is not better
+(the fallback).  Answers are exact for any landmark set.
+
+Every computation runs in the library's kernels (queries, coverage, features,
+tensor-core training, selection); this module only draws the random
+mini-batch indices (seeded) and moves tensors between calls.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import CODE_BFS_NEG, CODE_BFS_POS, CODE_DL, MLP, DBLIndex
+
+
+def train_scorer(ix: DBLIndex, qu, qv, base_slots: int, steps: int = 400, batch: int = 8192, lr: float = 0.01,
+                 momentum: float = 0.9, seed: int = 7):
+    """Train the scorer on the index's outcomes for the sampled pairs (qu, qv).
+
+    Returns (scores float32 [n], info)."""
+    import torch
+    t0 = time.perf_counter()
+    ans, _ = ix.query(qu, qv)                                     # outcomes of the plain index
+    count, target, kept = ix.coverage(qu, qv, reach=ans, base_slots=base_slots)
+    feats = ix.features()
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    gen = torch.Generator(device=feats.device)
+    gen.manual_seed(seed)
+    pos = torch.nonzero(count > 0).flatten().to(torch.int32)
+    n = ix.n
+    mlp = MLP(MLP.init_params(seed))
+    loss = torch.zeros(1, dtype=torch.float32, device=feats.device)
+    losses = []
+    half = batch // 2
+    for step in range(steps):
+        if pos.numel():
+            a = pos[torch.randint(0, pos.numel(), (half,), device=feats.device, generator=gen)]
+        else:
+            a = torch.randint(0, n, (half,), device=feats.device, generator=gen, dtype=torch.int32)
+        b = torch.randint(0, n, (batch - half,), device=feats.device, generator=gen, dtype=torch.int32)
+        idx = torch.cat([a, b]).to(torch.int32)
+        mlp.train_step(feats, target, idx, lr=lr, momentum=momentum, loss=loss)
+        if step % 50 == 0 or step == steps - 1:
+            losses.append(float(loss.item()))
+    scores = mlp.forward(feats)
+    torch.cuda.synchronize()
+    info = dict(pairs=int(qu.numel()), pairs_kept=kept, positive_vertices=int(pos.numel()), losses=losses,
+                data_s=t_data, train_s=time.perf_counter() - t0 - t_data)
+    mlp.close()
+    return scores, info
+
+
+def select_landmarks(ix: DBLIndex, scores, k: int, base_slots: int):
+    """First `base_slots` degree landmarks of ix, then the best-scored others."""
+    import torch
+    lm_deg = ix.selection()[0]
+    base = lm_deg[:base_slots]
+    sc = torch.nan_to_num(scores.clone(), nan=float("-inf"))
+    base_ok = base[base >= 0].long()
+    sc[base_ok] = float("-inf")
+    rest = ix.select_by_score(sc, k - base_slots)
+    return torch.cat([base, rest]).to(torch.int32)
+
+
+def decided(ix: DBLIndex, qu, qv) -> dict:
+    """How the index decides the pairs: counts of DL, search and other rules."""
+    _, code = ix.query(qu, qv)
+    c = code.long()
+    return dict(dl=int((c == CODE_DL).sum()), search=int(((c == CODE_BFS_POS) | (c == CODE_BFS_NEG)).sum()),
+                total=int(c.numel()))
+
+
+def learned_index(row_ptr, col, train_q, eval_q, k: int = 64, kprime: int = 64, base_slots: int | None = None,
+                  inserts=None, **kw):
+    """Build the plain index (after `inserts`, a list of (src, dst) batches),
+    train the scorer on the plain index's outcomes for train_q = (u, v), build
+    the learned index with the same leaves and insertions, and keep whichever
+    landmark set decides more of eval_q = (u, v) by the DL test (fallback to
+    the degree rule).  Returns (plain, chosen, info)."""
+    idx_kw = {a: b for a, b in kw.items() if a in ("flags", "team", "edge_capacity")}
+    train_kw = {a: b for a, b in kw.items() if a in ("steps", "batch", "lr", "momentum", "seed")}
+    plain = DBLIndex(row_ptr, col, k, kprime, **idx_kw)
+    for s, d in inserts or []:
+        plain.insert_edges(s, d)
+    if base_slots is None:
+        base_slots = max(1, k // 8)
+    scores, info = train_scorer(plain, train_q[0], train_q[1], base_slots, **train_kw)
+    lm = select_landmarks(plain, scores, k, base_slots)
+    _, lb, lr_ = plain.selection()
+    learned = DBLIndex(row_ptr, col, k, kprime, landmarks=lm, leaf_buckets=lb, leaf_roles=lr_, **idx_kw)
+    for s, d in inserts or []:
+        learned.insert_edges(s, d)
+    dp = decided(plain, *eval_q)
+    dlrn = decided(learned, *eval_q)
+    info.update(base_slots=base_slots, eval_plain=dp, eval_learned=dlrn,
+                fallback=not (dlrn["dl"] > dp["dl"] and dlrn["search"] <= dp["search"]))
+    return plain, (plain if info["fallback"] else learned), learned, info

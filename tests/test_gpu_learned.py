@@ -1,0 +1,175 @@
+"""Learned landmark scorer on the GPU vs its fp64 oracle (oracle/learned.py).
+
+Integer outputs (coverage counts, selections) must match exactly; bf16
+features within one bf16 rounding; network outputs and gradients within the
+error that bf16 operands with fp32 accumulation allow.
+"""
+import numpy as np
+import pytest
+import torch
+
+import dbl_inputs
+import oracle
+import paper_2101_09441_gb300 as dbl
+from oracle import learned as Lr
+from paper_2101_09441_gb300 import learned as L
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    dbl.build()
+
+
+def D(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return dbl_inputs.workload("tiny")
+
+
+def test_features_match_oracle(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    got = ix.features().float().cpu().numpy()
+    exp = Lr.features(tiny["row_ptr"], tiny["col"], ref.labels(), ref.landmarks)
+    assert np.allclose(got, exp, rtol=2 ** -7, atol=1e-6), np.abs(got - exp).max()
+
+
+def test_coverage_matches_oracle(tiny):
+    rp, col = tiny["row_ptr"], tiny["col"]
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    qu, qv = tiny["q_u"][:1200], tiny["q_v"][:1200]
+    ans, _ = ref.query(qu, qv)
+    # all reachable pairs (u != v), several passes of 256
+    keep = (ans == 1) & (qu != qv)
+    cnt, tgt, kept = ix.coverage(D(qu), D(qv), reach=D(keep.astype(np.uint8)), base_slots=0)
+    exp = Lr.coverage(rp, col, qu[keep], qv[keep])
+    assert kept == int(keep.sum())
+    assert np.array_equal(cnt.cpu().numpy(), exp)
+    t = tgt.cpu().numpy()
+    assert np.allclose(t, np.log1p(exp) / np.log1p(exp.max()), rtol=1e-6, atol=1e-6)
+    # pairs the first 8 landmark slots already decide are left out
+    dl_in, dl_out, _, _ = ref.labels()
+    mask = np.uint64(0xFF)
+    decided = ((dl_out[qu, 0] & dl_in[qv, 0] & mask) != 0)
+    keep2 = keep & ~decided
+    cnt2, _, kept2 = ix.coverage(D(qu), D(qv), reach=D(keep.astype(np.uint8)), base_slots=8)
+    assert kept2 == int(keep2.sum())
+    assert np.array_equal(cnt2.cpu().numpy(), Lr.coverage(rp, col, qu[keep2], qv[keep2]))
+
+
+def test_select_by_score_ties_by_id(tiny):
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    rng = np.random.default_rng(4)
+    sc = rng.integers(-50, 50, ix.n).astype(np.float32) / 4   # many ties, negatives
+    got = ix.select_by_score(D(sc), 100).cpu().numpy()
+    exp = np.lexsort((np.arange(ix.n), -sc))[:100]
+    assert np.array_equal(got, exp)
+
+
+def _quantised_params(seed):
+    p = dbl.MLP.init_params(seed)
+    p[2048:2176] = np.random.default_rng(seed).normal(0, 0.05, 128)     # non-zero biases
+    p[18560:18688] = np.random.default_rng(seed + 1).normal(0, 0.05, 128)
+    p[18816] = 0.1
+    return p
+
+
+def _split(p):
+    q = p.astype(np.float64)
+    return {"W1": q[0:2048].reshape(16, 128), "b1": q[2048:2176], "W2": q[2176:18560].reshape(128, 128),
+            "b2": q[18560:18688], "w3": q[18688:18816], "b3": np.array(q[18816])}
+
+
+def test_mlp_forward_matches_oracle():
+    p = _quantised_params(3)
+    m = dbl.MLP(p)
+    rng = np.random.default_rng(5)
+    X = rng.normal(0.5, 1.0, (1000, 16)).astype(np.float32)
+    Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    y = m.forward(Xb).cpu().numpy()
+    P = _split(p)
+    for k in ("W1", "W2"):
+        P[k] = bf16_round(P[k])
+    yo, _ = Lr.mlp_forward(bf16_round(X), P)
+    assert np.abs(y - yo).max() <= 2e-2 * max(1.0, np.abs(yo).max()), np.abs(y - yo).max()
+    # row gather gives the same rows
+    idx = torch.from_numpy(np.array([5, 999, 0, 5], np.int32)).cuda()
+    yi = m.forward(Xb, rows_idx=idx).cpu().numpy()
+    assert np.allclose(yi, y[[5, 999, 0, 5]], rtol=0, atol=0)
+
+
+def test_mlp_gradients_match_oracle():
+    p = _quantised_params(6)
+    m = dbl.MLP(p)
+    rng = np.random.default_rng(7)
+    R = 3000
+    X = rng.normal(0.5, 1.0, (R, 16)).astype(np.float32)
+    t = rng.normal(0, 1, R).astype(np.float32)
+    Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    g, loss = m.gradients(Xb, D(t))
+    g = g.cpu().numpy().astype(np.float64)
+    P = _split(p)
+    for k in ("W1", "W2"):
+        P[k] = bf16_round(P[k])
+    y, cache = Lr.mlp_forward(bf16_round(X), P)
+    go = Lr.mlp_backward(P, cache, y, t.astype(np.float64))
+    flat = np.concatenate([go["W1"].ravel(), go["b1"], go["W2"].ravel(), go["b2"], go["w3"], [go["b3"]]])
+    for name, a, b in (("W1", 0, 2048), ("b1", 2048, 2176), ("W2", 2176, 18560), ("b2", 18560, 18688),
+                       ("w3", 18688, 18816), ("b3", 18816, 18817)):
+        err = np.linalg.norm(g[a:b] - flat[a:b]) / max(np.linalg.norm(flat[a:b]), 1e-12)
+        assert err < 3e-2, (name, err)
+    assert abs(float(loss.item()) - Lr.mlp_loss(y, t)) <= 2e-2 * Lr.mlp_loss(y, t)
+
+
+def test_mlp_training_reduces_loss():
+    rng = np.random.default_rng(8)
+    R = 20000
+    X = rng.normal(0, 1, (R, 16)).astype(np.float32)
+    t = (np.maximum(X[:, 0], 0) + 0.5 * X[:, 3] * X[:, 4] > 0.3).astype(np.float32)
+    Xb = torch.from_numpy(X).to(torch.bfloat16).cuda()
+    td = D(t)
+    m = dbl.MLP(dbl.MLP.init_params(9))
+    _, l0 = m.gradients(Xb, td)
+    l0 = float(l0.item())
+    loss = torch.zeros(1, device="cuda")
+    for _ in range(300):
+        idx = torch.randint(0, R, (4096,), device="cuda", dtype=torch.int32)
+        m.train_step(Xb, td, idx, lr=0.05, momentum=0.9, loss=loss)
+    _, l1 = m.gradients(Xb, td)
+    assert float(l1.item()) < 0.5 * l0
+
+
+def test_learned_landmarks_exact_and_better_or_fallback(tiny):
+    """Learned landmarks (trained on the index after the 10k insertions) give
+    exact answers, and the chosen set decides at least as many held-out pairs
+    by the DL test as the degree rule (else the degree rule is kept)."""
+    rp, col = D(tiny["row_ptr"]), D(tiny["col"])
+    qu, qv = D(tiny["q_u"]), D(tiny["q_v"])
+    ins = [(D(tiny["ins_src"]), D(tiny["ins_dst"]))]
+    plain, chosen, learned, info = L.learned_index(rp, col, (qu[:50_000], qv[:50_000]), (qu[50_000:], qv[50_000:]),
+                                                   k=64, kprime=64, inserts=ins, steps=300)
+    print("learned scorer:", info)
+    assert all(np.isfinite(info["losses"]))
+    lm = learned.selection()[0].cpu().numpy()
+    assert len(set(lm[lm >= 0].tolist())) == int((lm >= 0).sum())          # distinct landmarks
+    # exact: answers equal the oracle's with the learned landmark set
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build(
+        lm, *[t.cpu().numpy() for t in plain.selection()[1:]])
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    a, c = learned.query(qu, qv)
+    ra, rc = ref.query(tiny["q_u"], tiny["q_v"], nthreads=8)
+    assert np.array_equal(a.cpu().numpy(), ra) and np.array_equal(c.cpu().numpy(), rc)
+    assert np.array_equal(a.cpu().numpy(), plain.query(qu, qv)[0].cpu().numpy())
+    dl_p, dl_c = L.decided(plain, qu[50_000:], qv[50_000:]), L.decided(chosen, qu[50_000:], qv[50_000:])
+    assert dl_c["dl"] >= dl_p["dl"]
