@@ -409,7 +409,8 @@ def bench_gpu(args):
     learned_t = run_form("learned_timing", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
     # fallback: keep the degree rule if the learned set decides fewer pairs by the labels
     dec_l = learned["decided_by"]
-    dec_p = (forms.get("graph") or forms.get("plain"))["decided_by"]
+    ref_form = forms.get("graph") or forms.get("plain") or forms.get("batched")
+    dec_p = ref_form["decided_by"] if ref_form else dec_l
     fallback = dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
     head = forms["graph"] if (fallback and "graph" in forms) else learned
     roof = roofline(learned_t, learned_t["ix"], args, w, I, batches)
