@@ -225,6 +225,24 @@ dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *
  * [10..15] zero. */
 dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
 
+/*
+ * Autotuner: time the sample insertion batch (src, dst, b) followed by the
+ * sample query batch (u, v, q; answers to ans) under each frontier schedule
+ * -- team widths 4, 8, 16, 32 (lanes sharing one frontier task) and
+ * level-by-level or persistent propagation -- each `trials` times from the
+ * same snapshot (slot 3 is overwritten), and keep the fastest in the index's
+ * options.  The index's labels and graph are restored afterwards.
+ * report (may be NULL) receives [8] mean ms per candidate (level-by-level
+ * teams 4..32, then persistent teams 4..32), [8] best team, [9] 1 if
+ * persistent, [10] best ms.  DBL_FLAG_ASYNC/TIMING are off during the trials
+ * and restored after.  Synchronous.
+ */
+dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, const int32_t *u,
+                        const int32_t *v, int64_t q, uint8_t *ans, int32_t trials, double *report, void *stream);
+/* Apply a frontier schedule directly (e.g. one cached from dbl_autotune):
+ * team width 4, 8, 16 or 32; persistent != 0 sets DBL_FLAG_PERSISTENT. */
+dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent);
+
 /* ---------------------------------------------------------------------------
  * Concurrent query batches.  A query context holds the scratch of one query
  * batch in flight (undecided list, search state); batches on different

@@ -33,7 +33,7 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_last_error",
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
-           "dbl_server_reset_stats", "dbl_server_destroy"]
+           "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule"]
 MLP_PARAMS = 18817
 
 
@@ -103,6 +103,8 @@ def lib():
             L.dbl_destroy.argtypes = [P, P]
             L.dbl_destroy.restype = None
             f32 = ctypes.c_float
+            L.dbl_autotune.argtypes = [P, P, P, i64, P, P, i64, P, i32, P, P]
+            L.dbl_set_schedule.argtypes = [P, i32, i32]
             L.dbl_qctx_create.argtypes = [P, P, P]
             L.dbl_qctx_destroy.argtypes = [P, P]
             L.dbl_qctx_destroy.restype = None
@@ -327,6 +329,37 @@ class DBLIndex:
         return dict(n=int(out[0]), k=int(out[1]), kprime=int(out[2]), edges_stored=int(out[3]),
                     edge_capacity=int(out[4]), m=int(out[5]), record_bytes=int(out[6]), flags=int(out[7]),
                     launches=int(out[8]), half_words=int(out[9]))
+
+    def autotune(self, src, dst, u, v, trials: int = 2, cache: str | None = None, stream=None) -> dict:
+        """dbl_autotune on a sample insertion batch and query batch; keeps the
+        fastest frontier schedule.  With `cache` (a JSON path), a result stored
+        for this graph's (n, m, k, kprime) is applied instead of re-measuring."""
+        import json
+        import torch
+        key = f"{self.n}:{self.m}:{self.k}:{self.kprime}"
+        if cache and os.path.exists(cache):
+            table = json.load(open(cache))
+            if key in table:
+                r = table[key]
+                self._apply_schedule(int(r["team"]), bool(r["persistent"]))
+                return dict(r, cached=True)
+        src, dst = self._pair(src, dst)
+        u, v = self._pair(u, v)
+        ans = torch.empty(u.numel(), dtype=torch.uint8, device=u.device)
+        rep = np.zeros(16, dtype=np.float64)
+        self._check(lib().dbl_autotune(self._h, _ptr(src), _ptr(dst), int(src.numel()), _ptr(u), _ptr(v),
+                                       int(u.numel()), _ptr(ans), int(trials), rep.ctypes.data, self._s(stream)))
+        out = {"team": int(rep[8]), "persistent": bool(rep[9]), "best_ms": float(rep[10]),
+               "level_ms": {t: float(rep[i]) for i, t in enumerate((4, 8, 16, 32))},
+               "persistent_ms": {t: float(rep[4 + i]) for i, t in enumerate((4, 8, 16, 32))}}
+        if cache:
+            table = json.load(open(cache)) if os.path.exists(cache) else {}
+            table[key] = out
+            json.dump(table, open(cache, "w"), indent=1)
+        return out
+
+    def _apply_schedule(self, team: int, persistent: bool):
+        self._check(lib().dbl_set_schedule(self._h, int(team), int(persistent)))
 
     # ------------------------------------------------------------------ learned scorer
     def features(self, stream=None):

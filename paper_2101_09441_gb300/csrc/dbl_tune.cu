@@ -1,0 +1,78 @@
+// Autotuner: picks the frontier schedule for this graph by measurement.
+//
+// Candidates are the team width (lanes that share one frontier task of up to
+// kChunk edges: 4, 8, 16 or 32) and whether frontier loops run as one
+// persistent cooperative launch or level by level.  Each candidate runs the
+// caller's sample insertion batch and query batch from the same snapshot
+// (slot 3), timed with CUDA events on the stream; the index is restored after
+// every trial, and the fastest candidate is kept in the index's options.
+#include <cstring>
+
+#include "dbl_internal.cuh"
+
+extern "C" dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent)
+{
+    if (!ix || (team != 4 && team != 8 && team != 16 && team != 32))
+        return dbl::fail(ix, DBL_ERR_INVALID, "set_schedule: team must be 4, 8, 16 or 32");
+    ix->opt.team = team;
+    ix->opt.flags = persistent ? (ix->opt.flags | DBL_FLAG_PERSISTENT) : (ix->opt.flags & ~DBL_FLAG_PERSISTENT);
+    return DBL_OK;
+}
+
+extern "C" dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, const int32_t *u,
+                                   const int32_t *v, int64_t q, uint8_t *ans, int32_t trials, double *report,
+                                   void *stream)
+{
+    if (!ix || b < 0 || q < 0 || (b > 0 && (!src || !dst)) || (q > 0 && (!u || !v || !ans)) || trials < 1)
+        return dbl::fail(ix, DBL_ERR_INVALID, "autotune: bad arguments");
+    if (ix->poisoned) return dbl::fail(ix, DBL_ERR_POISONED, "autotune: index poisoned");
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st = dbl_snapshot(ix, 3, stream);
+    if (st) return st;
+    const int teams[4] = {4, 8, 16, 32};
+    const int32_t flags0 = ix->opt.flags, team0 = ix->opt.team;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_team = team0, best_persistent = (flags0 & DBL_FLAG_PERSISTENT) ? 1 : 0;
+    for (int p = 0; p < 2 && !st; ++p) {
+        for (int t = 0; t < 4 && !st; ++t) {
+            ix->opt.team = teams[t];
+            ix->opt.flags = (flags0 & ~(DBL_FLAG_PERSISTENT | DBL_FLAG_ASYNC | DBL_FLAG_TIMING)) |
+                            (p ? DBL_FLAG_PERSISTENT : 0);
+            float total = 0;
+            for (int r = 0; r < trials + 1 && !st; ++r) {  // first run warms up
+                if ((st = dbl_restore(ix, 3, stream))) break;
+                cudaEventRecord(e0, s);
+                if (b && (st = dbl_insert_edges(ix, src, dst, b, stream))) break;
+                if (q && (st = dbl_query(ix, u, v, q, ans, nullptr, stream))) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r) total += ms;
+            }
+            const double avg = total / trials;
+            if (report) report[p * 4 + t] = avg;
+            if (!st && avg < best) {
+                best = avg;
+                best_team = teams[t];
+                best_persistent = p;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ix->opt.flags = (flags0 & ~DBL_FLAG_PERSISTENT) | (best_persistent ? DBL_FLAG_PERSISTENT : 0);
+    ix->opt.team = best_team;
+    dbl_status rs = dbl_restore(ix, 3, stream);
+    if (st) return st;
+    if (rs) return rs;
+    if (report) {
+        report[8] = best_team;
+        report[9] = best_persistent;
+        report[10] = best;
+    }
+    return dbl::read_status(ix, s);
+}
