@@ -70,7 +70,12 @@ enum {
 enum {
     DBL_FLAG_ASYNC = 1,      /* do not synchronise at the end of each call */
     DBL_FLAG_PERSISTENT = 2, /* run frontier loops in one persistent launch */
-    DBL_FLAG_TIMING = 4      /* bracket kernels with CUDA events (dbl_timings) */
+    DBL_FLAG_TIMING = 4,     /* bracket kernels with CUDA events (dbl_timings) */
+    DBL_FLAG_FINE_L2 = 8     /* at build, set the CUDA context's maximum L2 fetch
+                                granularity to 32 bytes (cudaLimitMaxL2FetchGranularity):
+                                label records are gathered 32 random bytes at a time.
+                                The limit is per context: it applies to every kernel
+                                of the process until changed. */
 };
 
 /* Kernel classes reported by dbl_timings. */
@@ -108,7 +113,9 @@ typedef struct {
     int32_t flags;         /* DBL_FLAG_* */
     int32_t bfs_words;     /* 64-query words per search wave (1..64); 0: 16 */
     int32_t team;          /* lanes per expansion task (4, 8, 16, 32); 0: 8 */
-    int32_t reserved[7];
+    int32_t query_unroll;  /* query pairs per thread in the label test (1, 2, 4);
+                              0: 4, 2 or 1 for 32-, 64- or 128-byte records */
+    int32_t reserved[6];
 } dbl_options;
 
 /* Fill *opt with the defaults above. */

@@ -22,7 +22,7 @@ DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAP
     DBL_ERR_POISONED = range(8)
 STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned"]
 CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
-FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING = 1, 2, 4
+FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2 = 1, 2, 4, 8
 KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "insert_append", "insert_seed",
                 "build_prep", "other"]
 
@@ -55,7 +55,7 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_voi
 class _Options(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p),
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
-                ("team", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _Graph(ctypes.Structure):
@@ -161,7 +161,7 @@ class DBLIndex:
 
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 8, stream=None,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, query_unroll: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -178,6 +178,7 @@ class DBLIndex:
         opt.edge_capacity = int(edge_capacity)
         opt.flags = int(flags)
         opt.team = int(team)
+        opt.query_unroll = int(query_unroll)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
 

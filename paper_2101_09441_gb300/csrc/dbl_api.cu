@@ -317,6 +317,9 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         if (!ix->opt.bfs_words) ix->opt.bfs_words = 16;
     }
     cudaGetDevice(&ix->device);
+    if (ix->opt.flags & DBL_FLAG_FINE_L2) {
+        if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32) != cudaSuccess) cudaGetLastError();
+    }
     ix->n = g->n;
     ix->m = g->m;
     ix->k = k;

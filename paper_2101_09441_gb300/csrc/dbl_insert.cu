@@ -16,6 +16,7 @@
 #include "dbl_frontier.cuh"
 #include "dbl_internal.cuh"
 #include "dbl_kernels.cuh"
+#include "dbl_persistent.cuh"
 
 namespace dbl {
 
@@ -143,11 +144,22 @@ __global__ void k_ins_commit(const int32_t *src, const int32_t *dst, int64_t b, 
 // Seeds of the repair: the skip test of Algorithm 3, then fwd(v) |= fwd(u),
 // bwd(u) |= bwd(v); changed endpoints start the frontier.
 template <int HS, int WD>
+__device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *dst, int64_t b, const DevGraph &g,
+                                           uint64_t *rec, const FrontierOut &f, unsigned long long *stats);
+
+template <int HS, int WD>
 __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const int32_t *dst, int64_t b, DevGraph g,
                                                      uint64_t *rec, FrontierOut f, unsigned long long *stats)
 {
     if (status_set(f.status)) return;
     resolve_epoch(f);
+    seed_edges<HS, WD>(src, dst, b, g, rec, f, stats);
+}
+
+template <int HS, int WD>
+__device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *dst, int64_t b, const DevGraph &g,
+                                           uint64_t *rec, const FrontierOut &f, unsigned long long *stats)
+{
     constexpr int RW = 2 * HS;
     unsigned long long skipped = 0, applied = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -196,6 +208,214 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
     warp_stat_add(stats, 11, applied);
 }
 
+// ---------------------------------------------------------------------------
+// Whole insertion batch in one cooperative launch (persistent form):
+//   validate | count | grow | write | seed | propagation level 0, 1, ...
+// with a grid barrier after each phase.  Counting takes each edge's slot
+// straight from the segment length (atomicAdd on len), so no commit pass is
+// needed; the one edge whose slot equals the old capacity grows the segment
+// (copying the old capacity's worth of entries; the batch's own entries are
+// written after the barrier).  A failed validation leaves every phase empty.
+struct InsArgs {
+    const int32_t *src, *dst;
+    int64_t b;
+    int32_t n;
+    int32_t *ovo, *ovi, *pool_out, *pool_in;
+    int64_t *pool_top;
+    int64_t pool_cap;
+    int32_t *slot_out, *slot_in;
+    DevGraph g;
+    uint64_t *rec, *f0, *f1;
+    uint32_t *c3;
+    int64_t cap;
+    unsigned long long *stamp, *epoch_base, *stats;
+    uint32_t *status;
+};
+
+template <int HS, int WD, int TEAM>
+__global__ void __launch_bounds__(kBlock) k_insert_persistent(InsArgs a, GridBarrier bar, int64_t max_levels)
+{
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    const int32_t n = a.n;
+    // P0: validate; zero the level counters
+    if (!ld_volatile_u32(a.status)) {
+        for (int64_t i = t0; i < a.b; i += nt)
+            if ((uint32_t)a.src[i] >= (uint32_t)n || (uint32_t)a.dst[i] >= (uint32_t)n)
+                set_status(a.status, DBL_ERR_INVALID);
+    }
+    if (leader) a.c3[0] = a.c3[1] = a.c3[2] = 0;
+    if (!grid_sync(bar, a.status) || ld_volatile_u32(a.status)) return;
+    // P1: slots from the live segment lengths
+    unsigned long long loops = 0;
+    for (int64_t i = t0; i < a.b; i += nt) {
+        const int32_t u = a.src[i], v = a.dst[i];
+        if (u == v) {
+            a.slot_out[i] = a.slot_in[i] = -1;
+            ++loops;
+            continue;
+        }
+        a.slot_out[i] = atomicAdd(a.ovo + n + u, 1);
+        a.slot_in[i] = atomicAdd(a.ovi + n + v, 1);
+    }
+    warp_stat_add(a.stats, 13, loops);
+    if (!grid_sync(bar, a.status)) return;
+    // P2: grow the segments that overflowed (one reservation per warp and direction)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.b; base += nt) {
+        const int64_t i = base + threadIdx.x;
+        for (int dir = 0; dir < 2; ++dir) {
+            int32_t *meta = dir ? a.ovi : a.ovo;
+            int32_t x = 0, old_cap = 0, nc = 0;
+            if (i < a.b) {
+                const int32_t s = dir ? a.slot_in[i] : a.slot_out[i];
+                x = dir ? a.dst[i] : a.src[i];
+                old_cap = meta[2 * n + x];
+                if (s >= 0 && s == old_cap) nc = grown_cap(meta[n + x]);
+            }
+            unsigned long long incl = (unsigned long long)nc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned long long total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) continue;
+            unsigned long long wbase = 0;
+            if (lane == 31) wbase = atomicAdd((unsigned long long *)(a.pool_top + dir), total);
+            wbase = __shfl_sync(kFull, wbase, 31);
+            if (!nc) continue;
+            const long long off = (long long)(wbase + incl - (unsigned long long)nc);
+            if (off + nc > a.pool_cap) {
+                set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
+                continue;
+            }
+            int32_t *pool = dir ? a.pool_in : a.pool_out;
+            const int32_t old = meta[x];
+            for (int32_t j = 0; j < old_cap; ++j) pool[off + j] = pool[old + j];
+            meta[x] = (int32_t)off;
+            meta[2 * n + x] = nc;
+        }
+    }
+    if (!grid_sync(bar, a.status)) return;
+    // P3: write the batch's ids into their slots
+    for (int64_t i = t0; i < a.b; i += nt) {
+        const int32_t so = a.slot_out[i];
+        if (so < 0) continue;
+        const int32_t u = a.src[i], v = a.dst[i], si = a.slot_in[i];
+        if (so < a.ovo[2 * n + u]) a.pool_out[(int64_t)a.ovo[u] + so] = v;
+        if (si < a.ovi[2 * n + v]) a.pool_in[(int64_t)a.ovi[v] + si] = u;
+    }
+    if (!grid_sync(bar, a.status)) return;
+    // P4: seeds (Algorithm 3's skip test, then the endpoint ORs) -> level-0 frontier
+    const unsigned long long base = *(const volatile unsigned long long *)a.epoch_base;
+    {
+        FrontierOut f{a.f0, a.c3, a.cap, a.stamp, base + 1, a.status};
+        seed_edges<HS, WD>(a.src, a.dst, a.b, a.g, a.rec, f, a.stats);
+    }
+    if (!grid_sync(bar, a.status)) return;
+    // P5: propagation levels, as in k_propagate_persistent
+    const int64_t warp0 = t0 >> 5, nwarps = nt >> 5;
+    unsigned long long epoch = base + 1;
+    int64_t L = 0;
+    for (;; ++L) {
+        const uint32_t ntk = ld_volatile_u32(a.c3 + L % 3);
+        if (ntk == 0 || ld_volatile_u32(a.status)) break;
+        if (L >= max_levels) {
+            set_status(a.status, DBL_ERR_TIMEOUT);
+            break;
+        }
+        ++epoch;
+        if (leader) a.c3[(L + 2) % 3] = 0;
+        FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, a.stamp, epoch, a.status};
+        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, f, a.stats, warp0, nwarps);
+        if (!grid_sync(bar, a.status)) break;
+    }
+    if (leader) {
+        a.stats[8] += (unsigned long long)L;
+        *a.epoch_base = base + (unsigned long long)L + 3;
+    }
+}
+
+template <int HS, int WD, int TEAM>
+static dbl_status launch_insert_persistent(dbl_index *ix, const InsArgs &args, cudaStream_t s)
+{
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_insert_persistent<HS, WD, TEAM>, kBlock, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    InsArgs a = args;
+    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
+    int64_t max_levels = (int64_t)ix->n + 2;
+    void *kargs[] = {&a, &bar, &max_levels};
+    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_insert_persistent<HS, WD, TEAM>, grid, block, kargs, 0, s);
+    ++ix->launches;
+    return e ? cuda_fail(ix, e, "persistent insert launch") : DBL_OK;
+}
+
+template <int HS, int WD>
+static dbl_status launch_insert_persistent_team(dbl_index *ix, const InsArgs &a, cudaStream_t s)
+{
+    switch (ix->opt.team) {
+    case 4: return launch_insert_persistent<HS, WD, 4>(ix, a, s);
+    case 16: return launch_insert_persistent<HS, WD, 16>(ix, a, s);
+    case 32: return launch_insert_persistent<HS, WD, 32>(ix, a, s);
+    default: return launch_insert_persistent<HS, WD, 8>(ix, a, s);
+    }
+}
+
+static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
+                                    int32_t *pos_in, cudaStream_t s)
+{
+    InsArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.b = b;
+    a.n = ix->n;
+    a.ovo = ix->ovo;
+    a.ovi = ix->ovi;
+    a.pool_out = ix->pool_out;
+    a.pool_in = ix->pool_in;
+    a.pool_top = ix->d_pool_top;
+    a.pool_cap = ix->pool_cap;
+    a.slot_out = pos_out;
+    a.slot_in = pos_in;
+    a.g = dev_graph(ix);
+    a.rec = ix->rec;
+    a.f0 = ix->front[0];
+    a.f1 = ix->front[1];
+    a.c3 = ix->d_counts + kCntP0;
+    a.cap = ix->front_cap;
+    a.stamp = ix->stamp;
+    a.epoch_base = ix->d_epoch;
+    a.stats = ix->d_stats;
+    a.status = ix->d_status;
+    tbegin(ix, DBL_KERNEL_PROPAGATE, s);
+    dbl_status st;
+    switch (ix->hs * 16 + ix->wd) {
+    case 2 * 16 + 1: st = launch_insert_persistent_team<2, 1>(ix, a, s); break;
+    case 4 * 16 + 1: st = launch_insert_persistent_team<4, 1>(ix, a, s); break;
+    case 4 * 16 + 2: st = launch_insert_persistent_team<4, 2>(ix, a, s); break;
+    case 8 * 16 + 1: st = launch_insert_persistent_team<8, 1>(ix, a, s); break;
+    case 8 * 16 + 2: st = launch_insert_persistent_team<8, 2>(ix, a, s); break;
+    case 8 * 16 + 4: st = launch_insert_persistent_team<8, 4>(ix, a, s); break;
+    default: st = fail(ix, DBL_ERR_INVALID, "insert: unsupported label width");
+    }
+    tend(ix, s);
+    if (st) return st;
+    ix->edges_stored += b;
+    atomic_add_host_stat(ix, 15, (uint64_t)b, s);
+    if (ix->opt.flags & DBL_FLAG_ASYNC) return DBL_OK;  // errors latch; dbl_sync reports them
+    dbl_status ds = read_status(ix, s);
+    if (ds == DBL_ERR_INVALID) {
+        ix->edges_stored -= b;  // the kernel changed nothing
+        return fail(ix, ds, "insert: vertex id out of range");
+    }
+    return ds;
+}
+
 static unsigned blocks_for(int64_t work, int64_t cap_mult = 16)
 {
     int64_t bl = (work + kBlock - 1) / kBlock;
@@ -229,6 +449,7 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     if (b == 0) return DBL_OK;
     if (ix->edges_stored + b > ix->edge_cap)
         return fail(ix, DBL_ERR_CAPACITY, "insert: edge capacity exhausted (dbl_options.edge_capacity)");
+    if (ix->opt.flags & DBL_FLAG_PERSISTENT) return insert_persistent(ix, src, dst, b, pos_out, pos_in, s);
     const int32_t n = ix->n;
     const unsigned grid = blocks_for(b);
     // 1. validate before anything changes

@@ -35,12 +35,7 @@ __host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (wo
 // flight per warp; answers and codes are written coalesced, the deciding
 // rules are counted with warp ballots, and undecided pairs are compacted with
 // one atomic per warp.
-template <int HS>
-struct LabelQPT {
-    static constexpr int v = HS == 2 ? 4 : (HS == 4 ? 2 : 1);
-};
-
-template <int WD, int WB>
+template <int WD, int WB, int QPT>
 __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const int32_t *qv, int64_t q,
                                                         const uint64_t *rec, int32_t n, uint8_t *ans,
                                                         uint8_t *code, int32_t *und, uint32_t *n_und,
@@ -48,7 +43,6 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
-    constexpr int QPT = LabelQPT<HS>::v;
     const int lane = threadIdx.x & 31;
     unsigned int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // kept by lane 0
     const int64_t tile = (int64_t)blockDim.x * QPT;
@@ -671,12 +665,16 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     if (st) return st;
     uint32_t *cnt = c->d_counts;
     cudaMemsetAsync(cnt + kCntUnd, 0, sizeof(uint32_t), s);
-    int64_t blocks = (q + kBlock - 1) / kBlock;
+    // pairs per thread: option, else 4 for 32-byte records, 2 for 64, 1 for 128
+    constexpr int HS = hs_of(WD + WB);
+    int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 2 ? 4 : (HS == 4 ? 2 : 1));
+    int64_t blocks = (q + (int64_t)kBlock * qpt - 1) / ((int64_t)kBlock * qpt);
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
     qt_begin(ix, c, DBL_KERNEL_QUERY_LABEL, s);
-    k_query_label<WD, WB><<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->und,
-                                                              cnt + kCntUnd, c->d_status, ix->d_stats);
+    auto kern = qpt >= 4 ? k_query_label<WD, WB, 4> : (qpt == 2 ? k_query_label<WD, WB, 2> : k_query_label<WD, WB, 1>);
+    kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->und, cnt + kCntUnd, c->d_status,
+                                             ix->d_stats);
     ++ix->launches;
     qt_end(ix, c, s);
     // one cooperative launch runs every wave, for the index's own context only
