@@ -109,7 +109,8 @@ typedef struct {
     dbl_free_fn free;   /* must be set iff alloc is set */
     void *ctx;
     int64_t edge_capacity; /* inserted edges the index can hold over its life;
-                              0: max(2^20, m/4) */
+                              0: max(2^20, m/4); at most 2^29 (larger values
+                              are clamped) */
     int32_t flags;         /* DBL_FLAG_* */
     int32_t bfs_words;     /* 64-query words per search wave (1..64); 0: 16 */
     int32_t team;          /* lanes per expansion task (4, 8, 16, 32); 0: 8 */
@@ -220,6 +221,17 @@ dbl_status dbl_sync(dbl_index *ix, void *stream);
  *  [15]    inserted edges stored
  */
 dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream);
+
+/*
+ * Phase trace of the index's last persistent launch (insertion or label
+ * propagation; recorded only when the index was built with DBL_FLAG_TIMING).
+ * out[0] = number of marks m (<= 63); out[1..m] = nanoseconds since the launch
+ * began (%globaltimer of block 0) at the start, after each grid barrier, and at
+ * the end.  An insertion launch's barriers follow its phases: validate,
+ * count + seed, grow + enqueue, write, then one per propagation level.
+ * Synchronises `stream`.  Diagnostic only: the paper has no counterpart.
+ */
+dbl_status dbl_phase_trace(dbl_index *ix, int64_t out[64], void *stream);
 
 /* With DBL_FLAG_TIMING: device time (ms, from CUDA events recorded on the
  * launching stream) and launch count per DBL_KERNEL_* class since the last

@@ -28,7 +28,7 @@ KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "in
 
 EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", "dbl_query_host",
            "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_snapshot", "dbl_restore", "dbl_sync",
-           "dbl_stats", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy", "dbl_insert_edges_noalloc",
+           "dbl_stats", "dbl_phase_trace", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy", "dbl_insert_edges_noalloc",
            "dbl_features", "dbl_coverage", "dbl_select_by_score", "dbl_mlp_create", "dbl_mlp_destroy",
            "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_last_error",
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
@@ -96,6 +96,7 @@ def lib():
             L.dbl_restore.argtypes = [P, ctypes.c_int, P]
             L.dbl_sync.argtypes = [P, P]
             L.dbl_stats.argtypes = [P, P, P]
+            L.dbl_phase_trace.argtypes = [P, P, P]
             L.dbl_info.argtypes = [P, P]
             L.dbl_timings.argtypes = [P, P, P, P]
             L.dbl_last_error.argtypes = [P]
@@ -316,6 +317,13 @@ class DBLIndex:
         out = np.zeros(16, dtype=np.uint64)
         self._check(lib().dbl_stats(self._h, out.ctypes.data, self._s(stream)))
         return out
+
+    def phase_trace(self, stream=None) -> list:
+        """Nanoseconds since the start of the last persistent launch at each of its
+        phase marks (start, every grid barrier, end); needs FLAG_TIMING."""
+        out = np.zeros(64, dtype=np.int64)
+        self._check(lib().dbl_phase_trace(self._h, out.ctypes.data, self._s(stream)))
+        return [int(x) for x in out[1:1 + int(out[0])]]
 
     def timings(self, stream=None) -> dict:
         """Per kernel class: (ms, launches) since the last call (needs FLAG_TIMING)."""

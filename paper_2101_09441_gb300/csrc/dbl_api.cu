@@ -329,6 +329,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     ix->hs = hs_for(ix->wd + ix->wb);
     ix->rw = 2 * ix->hs;
     ix->edge_cap = ix->opt.edge_capacity > 0 ? ix->opt.edge_capacity : std::max<int64_t>(1 << 20, g->m / 4);
+    if (ix->edge_cap > (1ll << 29)) ix->edge_cap = 1ll << 29;  // per-vertex slots then fit in 30 bits
     if (ix->edge_cap + g->m >= (1ll << 31)) ix->edge_cap = (1ll << 31) - 1 - g->m;
     ix->pool_cap = 4 * ix->edge_cap + 64;
     if (ix->pool_cap >= (1ll << 31)) ix->pool_cap = (1ll << 31) - 1;
@@ -353,7 +354,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->stamp, 16 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
         (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
-        (st = A((void **)&ix->d_epoch, 16)) ||
+        (st = A((void **)&ix->d_epoch, 16)) || (st = A((void **)&ix->d_trace, 8 * 64)) ||
         (st = A((void **)&ix->ins_cnt, 8 * n))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
@@ -367,6 +368,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     cudaMemsetAsync(ix->d_status, 0, 16, s);
     cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);
     cudaMemsetAsync(ix->d_epoch, 0, 16, s);
+    cudaMemsetAsync(ix->d_trace, 0, 8 * 64, s);
     cudaMemsetAsync(ix->ins_cnt, 0, 8 * n, s);
 
     tbegin(ix, DBL_KERNEL_BUILD_PREP, s);
@@ -674,6 +676,21 @@ dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *
     }
     cudaGetLastError();
     ix->tranges.clear();
+    return DBL_OK;
+}
+
+dbl_status dbl_phase_trace(dbl_index *ix, int64_t out[64], void *stream)
+{
+    if (!ix || !out) return fail(ix, DBL_ERR_INVALID, "phase_trace: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long h[64];
+    cudaError_t e = cudaMemcpyAsync(h, ix->d_trace, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(ix, e, "phase_trace");
+    const int64_t marks = h[0] < 64 ? (int64_t)h[0] : 63;
+    for (int i = 0; i < 64; ++i) out[i] = 0;
+    out[0] = marks;
+    for (int64_t i = 1; i <= marks; ++i) out[i] = (int64_t)(h[i] - h[1]);
     return DBL_OK;
 }
 

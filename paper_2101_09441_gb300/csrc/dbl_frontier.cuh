@@ -41,11 +41,10 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
     const int lane = threadIdx.x & 31;
     uint32_t nchunks = 0;
     if (want) {
+        // the degree loads and the stamp exchange are independent: one round trip
+        const int32_t d = deg_of(g, dir, x);
         unsigned long long *st = f.stamp + (size_t)dir * (size_t)g.n + x;
-        if (atomicExch(st, f.epoch) != f.epoch) {
-            int32_t d = deg_of(g, dir, x);
-            nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
-        }
+        if (atomicExch(st, f.epoch) != f.epoch) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     }
     uint32_t incl = nchunks;
 #pragma unroll
@@ -64,6 +63,92 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
         else set_status(f.status, DBL_ERR_CAPACITY);
     }
 }
+
+// Block-staged form of warp_enqueue.  Warps reserve room in a shared-memory
+// stage with a shared-memory CAS; stage_flush (every thread of the block)
+// then reserves the block's whole stage in the global frontier with one
+// atomicAdd, so a level costs one global reservation per block instead of one
+// per warp and iteration (all of them on the same word).  A warp whose tasks
+// do not fit in the stage reserves global slots itself.
+constexpr uint32_t kStage = 2048;
+
+struct Stage {
+    uint64_t *tasks;  // shared, kStage entries
+    uint32_t *n;      // shared, entries used
+};
+
+__device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
+                                              const Stage &st)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t nchunks = 0;
+    if (want) {
+        const int32_t d = deg_of(g, dir, x);
+        unsigned long long *sp = f.stamp + (size_t)dir * (size_t)g.n + x;
+        if (atomicExch(sp, f.epoch) != f.epoch) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
+    }
+    uint32_t incl = nchunks;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    uint32_t base = 0, global = 0;
+    if (lane == 31) {
+        uint32_t old = *(volatile uint32_t *)st.n;
+        for (;;) {  // ends: each failed CAS means another warp's reservation succeeded
+            if (old + total > kStage) {
+                global = 1;
+                break;
+            }
+            const uint32_t prev = atomicCAS(st.n, old, old + total);
+            if (prev == old) break;
+            old = prev;
+        }
+        base = global ? atomicAdd(f.count, total) : old;
+    }
+    base = __shfl_sync(kFull, base, 31);
+    global = __shfl_sync(kFull, global, 31);
+    uint32_t pos = base + incl - nchunks;
+    for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
+        const uint64_t t = make_task(x, c, dir);
+        if (!global) st.tasks[pos] = t;
+        else if ((int64_t)pos < f.cap) f.tasks[pos] = t;
+        else set_status(f.status, DBL_ERR_CAPACITY);
+    }
+}
+
+// Move the block's stage to the global frontier; every thread of the block
+// calls it.  Leaves the stage empty.
+__device__ __forceinline__ void stage_flush(const FrontierOut &f, const Stage &st)
+{
+    __shared__ uint32_t s_base;
+    __syncthreads();
+    const uint32_t cnt = *(volatile uint32_t *)st.n;
+    if (threadIdx.x == 0 && cnt) s_base = atomicAdd(f.count, cnt);
+    __syncthreads();
+    if (cnt) {
+        const uint32_t b = s_base;
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t pos = b + i;
+            if ((int64_t)pos < f.cap) f.tasks[pos] = st.tasks[i];
+            else set_status(f.status, DBL_ERR_CAPACITY);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *st.n = 0;
+    __syncthreads();
+}
+
+// Declares this block's stage (shared memory) and empties it; every thread calls it.
+#define DBL_BLOCK_STAGE(name)                                                                                         \
+    __shared__ uint64_t name##_tasks[::dbl::kStage];                                                                  \
+    __shared__ uint32_t name##_n;                                                                                     \
+    if (threadIdx.x == 0) name##_n = 0;                                                                               \
+    __syncthreads();                                                                                                  \
+    const ::dbl::Stage name{name##_tasks, &name##_n}
 
 // Same, for callers whose loop is not warp-uniform: uses the active mask.
 __device__ __forceinline__ void any_enqueue(int32_t x, int dir, const DevGraph &g, const FrontierOut &f)

@@ -156,11 +156,43 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
     seed_edges<HS, WD>(src, dst, b, g, rec, f, stats);
 }
 
+// One edge's seed: Algorithm 3's skip test on DL_out(u) and DL_in(v), then
+// fwd(v) |= fwd(u) and bwd(u) |= bwd(v).  All four half-records are loaded at
+// once (one memory round trip).  Returns true if the edge was applied;
+// want_f / want_b say whether fwd(v) / bwd(u) gained bits.
+template <int HS, int WD>
+__device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, bool &want_f, bool &want_b)
+{
+    constexpr int RW = 2 * HS;
+    uint64_t *fu = rec + (size_t)u * RW, *bu = fu + HS;
+    uint64_t *fv = rec + (size_t)v * RW, *bv = fv + HS;
+    uint64_t a[HS], c[HS], x[HS], y[HS];
+    load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
+    load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
+    load_half<HS>(fu, x);  // DL_in(u)  | BL_in(u)
+    load_half<HS>(bv, y);  // DL_out(v) | BL_out(v)
+    uint64_t inter = 0;
+#pragma unroll
+    for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
+    if (inter) return false;
+#pragma unroll
+    for (int w = 0; w < HS; ++w) {
+        if (x[w] & ~c[w]) {
+            unsigned long long old = atomicOr((unsigned long long *)(fv + w), x[w]);
+            want_f |= (x[w] & ~old) != 0;
+        }
+        if (y[w] & ~a[w]) {
+            unsigned long long old = atomicOr((unsigned long long *)(bu + w), y[w]);
+            want_b |= (y[w] & ~old) != 0;
+        }
+    }
+    return true;
+}
+
 template <int HS, int WD>
 __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *dst, int64_t b, const DevGraph &g,
                                            uint64_t *rec, const FrontierOut &f, unsigned long long *stats)
 {
-    constexpr int RW = 2 * HS;
     unsigned long long skipped = 0, applied = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < b; base += stride) {
@@ -171,34 +203,8 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
             u = src[i];
             v = dst[i];
             if (u != v) {
-                uint64_t *fu = rec + (size_t)u * RW, *bu = fu + HS;
-                uint64_t *fv = rec + (size_t)v * RW, *bv = fv + HS;
-                uint64_t a[HS], c[HS];
-                load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
-                load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
-                uint64_t inter = 0;
-#pragma unroll
-                for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
-                if (inter) {
-                    ++skipped;
-                } else {
-                    ++applied;
-                    uint64_t x[HS];
-                    load_half<HS>(fu, x);
-#pragma unroll
-                    for (int w = 0; w < HS; ++w)
-                        if (x[w] & ~c[w]) {
-                            unsigned long long old = atomicOr((unsigned long long *)(fv + w), x[w]);
-                            want_f |= (x[w] & ~old) != 0;
-                        }
-                    load_half<HS>(bv, x);
-#pragma unroll
-                    for (int w = 0; w < HS; ++w)
-                        if (x[w] & ~a[w]) {
-                            unsigned long long old = atomicOr((unsigned long long *)(bu + w), x[w]);
-                            want_b |= (x[w] & ~old) != 0;
-                        }
-                }
+                if (seed_one<HS, WD>(u, v, rec, want_f, want_b)) ++applied;
+                else ++skipped;
             }
         }
         warp_enqueue(want_f, v, 0, g, f);
@@ -209,13 +215,24 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
 }
 
 // ---------------------------------------------------------------------------
-// Whole insertion batch in one cooperative launch (persistent form):
-//   validate | count | grow | write | seed | propagation level 0, 1, ...
-// with a grid barrier after each phase.  Counting takes each edge's slot
-// straight from the segment length (atomicAdd on len), so no commit pass is
-// needed; the one edge whose slot equals the old capacity grows the segment
-// (copying the old capacity's worth of entries; the batch's own entries are
-// written after the barrier).  A failed validation leaves every phase empty.
+// Whole insertion batch in one cooperative launch (persistent form), with a
+// grid barrier after each phase:
+//   P0 validate
+//   P1 count + seed: each edge takes its slot straight from the live segment
+//      length (atomicAdd on len, so no commit pass is needed) and applies its
+//      seed (skip test, endpoint ORs); whether fwd(v) / bwd(u) gained bits is
+//      kept in bit 30 of the edge's slot words (slots are < 2^29)
+//   P2 grow + enqueue: the one edge whose slot equals the old capacity grows
+//      the segment (copying the old capacity's worth of entries; the batch's
+//      own entries are written after the barrier); the changed endpoints form
+//      the level-0 frontier, with chunk counts from the now final lengths
+//   P3 write the batch's ids into their slots
+//   P4 propagation levels, as in k_propagate_persistent.
+// Seeding before the appended edges are visible is sound: seeds read and OR
+// labels only, and the first level that walks adjacency runs after P3.  A
+// failed validation leaves every phase empty.
+constexpr int32_t kWantBit = 1 << 30;
+
 struct InsArgs {
     const int32_t *src, *dst;
     int64_t b;
@@ -233,12 +250,13 @@ struct InsArgs {
 };
 
 template <int HS, int WD, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_insert_persistent(InsArgs a, GridBarrier bar, int64_t max_levels)
+__device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, const Stage &st, int64_t max_levels)
 {
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const int lane = threadIdx.x & 31;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
+    const unsigned long long base = *(const volatile unsigned long long *)a.epoch_base;
     // P0: validate; zero the level counters
     if (!ld_volatile_u32(a.status)) {
         for (int64_t i = t0; i < a.b; i += nt)
@@ -246,75 +264,104 @@ __global__ void __launch_bounds__(kBlock) k_insert_persistent(InsArgs a, GridBar
                 set_status(a.status, DBL_ERR_INVALID);
     }
     if (leader) a.c3[0] = a.c3[1] = a.c3[2] = 0;
-    if (!grid_sync(bar, a.status) || ld_volatile_u32(a.status)) return;
-    // P1: slots from the live segment lengths
-    unsigned long long loops = 0;
-    for (int64_t i = t0; i < a.b; i += nt) {
-        const int32_t u = a.src[i], v = a.dst[i];
-        if (u == v) {
-            a.slot_out[i] = a.slot_in[i] = -1;
-            ++loops;
-            continue;
-        }
-        a.slot_out[i] = atomicAdd(a.ovo + n + u, 1);
-        a.slot_in[i] = atomicAdd(a.ovi + n + v, 1);
-    }
-    warp_stat_add(a.stats, 13, loops);
-    if (!grid_sync(bar, a.status)) return;
-    // P2: grow the segments that overflowed (one reservation per warp and direction)
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.b; base += nt) {
-        const int64_t i = base + threadIdx.x;
-        for (int dir = 0; dir < 2; ++dir) {
-            int32_t *meta = dir ? a.ovi : a.ovo;
-            int32_t x = 0, old_cap = 0, nc = 0;
-            if (i < a.b) {
-                const int32_t s = dir ? a.slot_in[i] : a.slot_out[i];
-                x = dir ? a.dst[i] : a.src[i];
-                old_cap = meta[2 * n + x];
-                if (s >= 0 && s == old_cap) nc = grown_cap(meta[n + x]);
-            }
-            unsigned long long incl = (unsigned long long)nc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const unsigned long long total = __shfl_sync(kFull, incl, 31);
-            if (total == 0) continue;
-            unsigned long long wbase = 0;
-            if (lane == 31) wbase = atomicAdd((unsigned long long *)(a.pool_top + dir), total);
-            wbase = __shfl_sync(kFull, wbase, 31);
-            if (!nc) continue;
-            const long long off = (long long)(wbase + incl - (unsigned long long)nc);
-            if (off + nc > a.pool_cap) {
-                set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
+    if (!gs.sync(a.status) || ld_volatile_u32(a.status)) return;
+    // P1: slots from the live segment lengths, and the seeds
+    {
+        unsigned long long loops = 0, skipped = 0, applied = 0;
+        for (int64_t i = t0; i < a.b; i += nt) {
+            const int32_t u = a.src[i], v = a.dst[i];
+            if (u == v) {
+                a.slot_out[i] = a.slot_in[i] = -1;
+                ++loops;
                 continue;
             }
-            int32_t *pool = dir ? a.pool_in : a.pool_out;
-            const int32_t old = meta[x];
-            for (int32_t j = 0; j < old_cap; ++j) pool[off + j] = pool[old + j];
-            meta[x] = (int32_t)off;
-            meta[2 * n + x] = nc;
+            const int32_t so = atomicAdd(a.ovo + n + u, 1);
+            const int32_t si = atomicAdd(a.ovi + n + v, 1);
+            bool want_f = false, want_b = false;
+            if (seed_one<HS, WD>(u, v, a.rec, want_f, want_b)) ++applied;
+            else ++skipped;
+            a.slot_out[i] = so | (want_b ? kWantBit : 0);
+            a.slot_in[i] = si | (want_f ? kWantBit : 0);
         }
+        warp_stat_add(a.stats, 13, loops);
+        warp_stat_add(a.stats, 12, skipped);
+        warp_stat_add(a.stats, 11, applied);
     }
-    if (!grid_sync(bar, a.status)) return;
+    if (!gs.sync(a.status)) return;
+    // P2: grow the segments that overflowed (one pool reservation per block and
+    // direction), and enqueue the seeds' changed endpoints
+    {
+        FrontierOut f{a.f0, a.c3, a.cap, a.stamp, base + 1, a.status};
+        __shared__ unsigned long long s_woff[32];  // per-warp growth, then its offset in the block's range
+        __shared__ unsigned long long s_gbase;
+        const int warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+        for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
+            const int64_t i = wbase + threadIdx.x;
+            bool want[2] = {false, false};
+            int32_t ends[2] = {0, 0};
+            for (int dir = 0; dir < 2; ++dir) {
+                int32_t *meta = dir ? a.ovi : a.ovo;
+                int32_t x = 0, old_cap = 0, nc = 0;
+                if (i < a.b) {
+                    const int32_t sw = dir ? a.slot_in[i] : a.slot_out[i];
+                    x = dir ? a.dst[i] : a.src[i];
+                    ends[dir] = x;
+                    if (sw >= 0) {
+                        want[dir] = (sw & kWantBit) != 0;
+                        old_cap = meta[2 * n + x];
+                        if ((sw & ~kWantBit) == old_cap) nc = grown_cap(meta[n + x]);
+                    }
+                }
+                unsigned long long incl = (unsigned long long)nc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned long long t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (lane == 31) s_woff[warp] = incl;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned long long run = 0;
+                    for (int w = 0; w < nwb; ++w) {
+                        const unsigned long long t = s_woff[w];
+                        s_woff[w] = run;
+                        run += t;
+                    }
+                    s_gbase = run ? atomicAdd((unsigned long long *)(a.pool_top + dir), run) : 0ull;
+                }
+                __syncthreads();
+                if (nc) {
+                    const long long off = (long long)(s_gbase + s_woff[warp] + incl - (unsigned long long)nc);
+                    if (off + nc > a.pool_cap) {
+                        set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
+                    } else {
+                        int32_t *pool = dir ? a.pool_in : a.pool_out;
+                        const int32_t old = meta[x];
+                        for (int32_t j = 0; j < old_cap; ++j) pool[off + j] = pool[old + j];
+                        meta[x] = (int32_t)off;
+                        meta[2 * n + x] = nc;
+                    }
+                }
+                __syncthreads();  // s_woff is reused by the next direction
+            }
+            // fwd(v) changed: v's out-edges (dir 0); bwd(u) changed: u's in-edges (dir 1)
+            stage_enqueue(want[1], ends[1], 0, a.g, f, st);
+            stage_enqueue(want[0], ends[0], 1, a.g, f, st);
+        }
+        stage_flush(f, st);
+    }
+    if (!gs.sync(a.status)) return;
     // P3: write the batch's ids into their slots
     for (int64_t i = t0; i < a.b; i += nt) {
-        const int32_t so = a.slot_out[i];
-        if (so < 0) continue;
-        const int32_t u = a.src[i], v = a.dst[i], si = a.slot_in[i];
+        const int32_t sw = a.slot_out[i];
+        if (sw < 0) continue;
+        const int32_t u = a.src[i], v = a.dst[i];
+        const int32_t so = sw & ~kWantBit, si = a.slot_in[i] & ~kWantBit;
         if (so < a.ovo[2 * n + u]) a.pool_out[(int64_t)a.ovo[u] + so] = v;
         if (si < a.ovi[2 * n + v]) a.pool_in[(int64_t)a.ovi[v] + si] = u;
     }
-    if (!grid_sync(bar, a.status)) return;
-    // P4: seeds (Algorithm 3's skip test, then the endpoint ORs) -> level-0 frontier
-    const unsigned long long base = *(const volatile unsigned long long *)a.epoch_base;
-    {
-        FrontierOut f{a.f0, a.c3, a.cap, a.stamp, base + 1, a.status};
-        seed_edges<HS, WD>(a.src, a.dst, a.b, a.g, a.rec, f, a.stats);
-    }
-    if (!grid_sync(bar, a.status)) return;
-    // P5: propagation levels, as in k_propagate_persistent
+    if (!gs.sync(a.status)) return;
+    // P4: propagation levels
     const int64_t warp0 = t0 >> 5, nwarps = nt >> 5;
     unsigned long long epoch = base + 1;
     int64_t L = 0;
@@ -328,8 +375,8 @@ __global__ void __launch_bounds__(kBlock) k_insert_persistent(InsArgs a, GridBar
         ++epoch;
         if (leader) a.c3[(L + 2) % 3] = 0;
         FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, a.stamp, epoch, a.status};
-        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, f, a.stats, warp0, nwarps);
-        if (!grid_sync(bar, a.status)) break;
+        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, f, a.stats, warp0, nwarps, st);
+        if (!gs.sync(a.status)) break;
     }
     if (leader) {
         a.stats[8] += (unsigned long long)L;
@@ -338,18 +385,28 @@ __global__ void __launch_bounds__(kBlock) k_insert_persistent(InsArgs a, GridBar
 }
 
 template <int HS, int WD, int TEAM>
+__global__ void __launch_bounds__(pblock_of(HS), 1) k_insert_persistent(InsArgs a, GridBarrier bar, int64_t max_levels)
+{
+    GridSync gs(bar);
+    DBL_BLOCK_STAGE(st);
+    insert_phases<HS, WD, TEAM>(a, gs, st, max_levels);
+    gs.leave();
+}
+
+template <int HS, int WD, int TEAM>
 static dbl_status launch_insert_persistent(dbl_index *ix, const InsArgs &args, cudaStream_t s)
 {
     static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_insert_persistent<HS, WD, TEAM>, kBlock, 0);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    if (blocks_per_sm < 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_insert_persistent<HS, WD, TEAM>, pblock_of(HS),
+                                                      0);
+    if (blocks_per_sm < 1) return fail(ix, DBL_ERR_CUDA, "persistent insert: kernel does not fit on an SM");
     InsArgs a = args;
-    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
+    GridBarrier bar = grid_barrier_at(ix->d_counts);
+    if (ix->opt.flags & DBL_FLAG_TIMING) bar.trace = ix->d_trace;
     int64_t max_levels = (int64_t)ix->n + 2;
     void *kargs[] = {&a, &bar, &max_levels};
-    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    dim3 grid((unsigned)num_sms()), block(pblock_of(HS));
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_insert_persistent<HS, WD, TEAM>, grid, block, kargs, 0, s);
     ++ix->launches;
     return e ? cuda_fail(ix, e, "persistent insert launch") : DBL_OK;

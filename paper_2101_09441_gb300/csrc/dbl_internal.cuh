@@ -169,6 +169,7 @@ struct dbl_index {
     // status, counters
     uint32_t *d_status = nullptr;
     unsigned long long *d_stats = nullptr;  // [16]
+    unsigned long long *d_trace = nullptr;  // [64] phase marks of the last persistent launch (DBL_FLAG_TIMING)
     uint32_t *h_pinned = nullptr;     // pinned host words for small readbacks
 
     // host-buffer staging (dbl_query_host / dbl_insert_edges_host)
@@ -229,8 +230,8 @@ enum {
     kCntOverflow = 7,   // search wave overflow flag
     kCntGrow = 8,       // (2 words) pool growth request, int64
     kCntP0 = 10,        // (3 words) persistent propagation level counts
-    kCntBarArrived = 13,  // grid barrier: blocks arrived
-    kCntBarPhase = 14,    // grid barrier: generation
+    kCntBarLeft = 13,   // grid barrier: blocks done with the launch
+    kCntBarCount = 14,  // (2 words, 8-byte aligned) grid barrier: arrivals, uint64
     kCntWords = 16
 };
 

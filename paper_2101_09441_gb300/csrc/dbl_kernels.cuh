@@ -16,10 +16,13 @@ __device__ __forceinline__ void warp_stat_add(unsigned long long *stats, int idx
 // One level of label propagation over `ntasks` tasks, processed by warps
 // [warp0, warp0 + nwarps*k) in steps of nwarps.  Every lane of a warp runs the
 // same number of iterations (warp_enqueue needs the whole warp).
+//
+// New tasks go through the block's stage (stage_enqueue); the stage is flushed
+// at the end, so every thread of the block must call this.
 template <int HS, int TEAM>
 __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
                                              uint32_t ntasks, const FrontierOut &f, unsigned long long *stats,
-                                             int64_t warp0, int64_t nwarps)
+                                             int64_t warp0, int64_t nwarps, const Stage &st)
 {
     constexpr int TPW = 32 / TEAM;
     constexpr int RW = 2 * HS;
@@ -71,11 +74,12 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                 }
                 want = changed;
             }
-            warp_enqueue(want, x, dir, g, f);
+            stage_enqueue(want, x, dir, g, f, st);
         }
     }
     warp_stat_add(stats, 9, ntask);
     warp_stat_add(stats, 10, relaxed);
+    stage_flush(f, st);
 }
 
 }  // namespace dbl

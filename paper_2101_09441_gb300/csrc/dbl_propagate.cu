@@ -24,10 +24,11 @@ __global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, co
                                                    const uint32_t *ntasks_p, FrontierOut f,
                                                    unsigned long long *stats)
 {
+    DBL_BLOCK_STAGE(st);
     resolve_epoch(f);
     expand_level<HS, TEAM>(g, rec, tasks, *ntasks_p, f, stats,
                            ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                           ((int64_t)gridDim.x * blockDim.x) >> 5);
+                           ((int64_t)gridDim.x * blockDim.x) >> 5, st);
 }
 
 template <int HS, int TEAM>
@@ -140,13 +141,13 @@ __global__ void k_epoch_advance(unsigned long long *base, unsigned long long by)
 // the same exit.  The level bound and the barrier's bounded wait turn any
 // runaway into DBL_ERR_TIMEOUT instead of a hang.
 template <int HS, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0,
-                                                                 uint64_t *f1, uint32_t *c3, int64_t cap,
-                                                                 unsigned long long *stamp,
-                                                                 unsigned long long *epoch_base, uint32_t *status,
-                                                                 unsigned long long *stats, GridBarrier bar,
-                                                                 int64_t max_levels)
+__global__ void __launch_bounds__(pblock_of(HS), 1)
+    k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0, uint64_t *f1, uint32_t *c3, int64_t cap,
+                           unsigned long long *stamp, unsigned long long *epoch_base, uint32_t *status,
+                           unsigned long long *stats, GridBarrier bar, int64_t max_levels)
 {
+    GridSync gs(bar);
+    DBL_BLOCK_STAGE(st);
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // the seed level used base+1; level L fills base+2+L
@@ -163,8 +164,8 @@ __global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uin
         ++epoch;
         if (blockIdx.x == 0 && threadIdx.x == 0) c3[(L + 2) % 3] = 0;
         FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, stamp, epoch, status};
-        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, f, stats, warp0, nwarps);
-        if (!grid_sync(bar, status)) break;
+        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, f, stats, warp0, nwarps, st);
+        if (!gs.sync(status)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[8] += (unsigned long long)L;
@@ -172,16 +173,16 @@ __global__ void __launch_bounds__(kBlock) k_propagate_persistent(DevGraph g, uin
         // every block read the base at its start, long before this point
         *epoch_base = base + (unsigned long long)L + 3;
     }
+    gs.leave();
 }
 
 template <int HS, int TEAM>
 static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
 {
     static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_propagate_persistent<HS, TEAM>, kBlock, 0);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    if (blocks_per_sm < 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_propagate_persistent<HS, TEAM>, pblock_of(HS), 0);
+    if (blocks_per_sm < 1) return fail(ix, DBL_ERR_CUDA, "persistent propagate: kernel does not fit on an SM");
     DevGraph g = dev_graph(ix);
     uint64_t *f0 = ix->front[0], *f1 = ix->front[1];
     uint32_t *c3 = ix->d_counts + kCntP0;
@@ -190,10 +191,11 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
     unsigned long long *epoch_base = ix->d_epoch;
     uint32_t *status = ix->d_status;
     unsigned long long *stats = ix->d_stats;
-    GridBarrier bar{ix->d_counts + kCntBarArrived, ix->d_counts + kCntBarPhase};
+    GridBarrier bar = grid_barrier_at(ix->d_counts);
+    if (ix->opt.flags & DBL_FLAG_TIMING) bar.trace = ix->d_trace;
     int64_t max_levels = (int64_t)ix->n + 2;
     void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &stamp, &epoch_base, &status, &stats, &bar, &max_levels};
-    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    dim3 grid((unsigned)num_sms()), block(pblock_of(HS));
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_propagate_persistent<HS, TEAM>, grid, block, args, 0, s);
     ++ix->launches;
     return e ? cuda_fail(ix, e, "persistent propagate launch") : DBL_OK;

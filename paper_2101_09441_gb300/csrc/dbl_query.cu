@@ -440,8 +440,8 @@ __global__ void k_search_clear(SearchArgs a) { search_clear(a); }
 // the phase counters; every decision is read by all blocks after a barrier.
 // Per level: finalize, barrier, expand, barrier.
 template <int WD, int WB, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_search_persistent(SearchArgs a, PersistState *ps, const uint32_t *n_und,
-                                                              GridBarrier bar, uint32_t *status, int64_t max_levels)
+__device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *ps, const uint32_t *n_und,
+                                             GridSync &gs, uint32_t *status, int64_t max_levels)
 {
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const uint32_t U = ld_volatile_u32(n_und);
@@ -466,14 +466,14 @@ __global__ void __launch_bounds__(kBlock) k_search_persistent(SearchArgs a, Pers
             ps->n_claimed = 0;
             ps->overflow = 0;
         }
-        if (!grid_sync(bar, status)) return;
+        if (!gs.sync(status)) return;
         const long long j0 = *(volatile long long *)&ps->range[0], j1 = *(volatile long long *)&ps->range[1];
         if (j0 < 0 || ld_volatile_u32(status)) break;
         ++waves;
         SlotList lists[2] = {{a.lists[0], &ps->list_count[0], a.list_cap}, {a.lists[1], &ps->list_count[1], a.list_cap}};
         uint32_t sep = 1;
         search_setup<WD, WB>(a, j0, j1, sep, lists[0]);
-        if (!grid_sync(bar, status)) return;
+        if (!gs.sync(status)) return;
         for (int64_t L = 0;; ++L) {
             const int cur = (int)(L & 1);
             if (!ld_volatile_u32(&ps->list_count[cur]) || ld_volatile_u32(&ps->overflow) || ld_volatile_u32(status))
@@ -484,19 +484,19 @@ __global__ void __launch_bounds__(kBlock) k_search_persistent(SearchArgs a, Pers
             }
             ++levels;
             search_finalize(a, lists[cur], &ps->task_count[cur]);
-            if (!grid_sync(bar, status)) return;
+            if (!gs.sync(status)) return;
             ++sep;
             if (leader) {
                 ps->list_count[cur] = 0;
                 ps->task_count[cur ^ 1] = 0;
             }
             search_expand<WD, WB, TEAM>(a, ld_volatile_u32(&ps->task_count[cur]), sep, lists[cur ^ 1]);
-            if (!grid_sync(bar, status)) return;
+            if (!gs.sync(status)) return;
         }
         const bool over = ld_volatile_u32(&ps->overflow) != 0;
         search_answer(a, j0, j1, !over);
         search_clear(a);
-        if (!grid_sync(bar, status)) return;
+        if (!gs.sync(status)) return;
         if (over && leader) {
             const long long groups = (j1 - j0 + 63) / 64;
             if (groups <= 1 || ps->top + 2 > 64) {
@@ -515,6 +515,16 @@ __global__ void __launch_bounds__(kBlock) k_search_persistent(SearchArgs a, Pers
         a.stats[8] += levels;
         a.stats[14] += waves;
     }
+}
+
+template <int WD, int WB, int TEAM>
+__global__ void __launch_bounds__(pblock_of(hs_of(WD + WB)), 1)
+    k_search_persistent(SearchArgs a, PersistState *ps, const uint32_t *n_und, GridBarrier bar, uint32_t *status,
+                        int64_t max_levels)
+{
+    GridSync gs(bar);
+    search_waves<WD, WB, TEAM>(a, ps, n_und, gs, status, max_levels);
+    gs.leave();
 }
 
 // ------------------------------------------------------------ host driver
@@ -635,20 +645,20 @@ template <int WD, int WB, int TEAM>
 static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv,
                                            uint8_t *ans, uint8_t *code, cudaStream_t s)
 {
+    constexpr int kPB = pblock_of(hs_of(WD + WB));
     static int blocks_per_sm = -1;
-    if (blocks_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search_persistent<WD, WB, TEAM>, kBlock, 0);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
+    if (blocks_per_sm < 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search_persistent<WD, WB, TEAM>, kPB, 0);
+    if (blocks_per_sm < 1) return qfail(c, DBL_ERR_CUDA, "persistent search: kernel does not fit on an SM");
     PersistState *ps = (PersistState *)c->pstate;
     cudaMemsetAsync(ps, 0, sizeof(PersistState), s);
     SearchArgs a = search_args(ix, c, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
     const uint32_t *n_und = c->d_counts + kCntUnd;
-    GridBarrier bar{c->d_counts + kCntBarArrived, c->d_counts + kCntBarPhase};
+    GridBarrier bar = grid_barrier_at(c->d_counts);
     uint32_t *status = c->d_status;
     int64_t max_levels = (int64_t)ix->n + 2;
     void *args[] = {&a, &ps, &n_und, &bar, &status, &max_levels};
-    dim3 grid((unsigned)(blocks_per_sm * num_sms())), block(kBlock);
+    dim3 grid((unsigned)num_sms()), block(kPB);
     qt_begin(ix, c, DBL_KERNEL_SEARCH_EXPAND, s);
     cudaError_t e =
         cudaLaunchCooperativeKernel((const void *)k_search_persistent<WD, WB, TEAM>, grid, block, args, 0, s);
