@@ -113,7 +113,9 @@ typedef struct {
                               are clamped) */
     int32_t flags;         /* DBL_FLAG_* */
     int32_t bfs_words;     /* 64-query words per search wave (1..64); 0: 16 */
-    int32_t team;          /* lanes per expansion task (4, 8, 16, 32); 0: 8 */
+    int32_t team;          /* lanes per expansion task (4, 8, 16, 32), or 1:
+                              one task per lane with the warp walking its
+                              tasks' edges 32 at a time; 0: 1 */
     int32_t query_unroll;  /* query pairs per thread in the label test (1, 2, 4);
                               0: 4, 2 or 1 for 32-, 64- or 128-byte records */
     int32_t reserved[6];
@@ -223,8 +225,9 @@ dbl_status dbl_sync(dbl_index *ix, void *stream);
 dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream);
 
 /*
- * Phase trace of the index's last persistent launch (insertion or label
- * propagation; recorded only when the index was built with DBL_FLAG_TIMING).
+ * Phase trace of the index's last persistent launch (insertion, label
+ * propagation, or the pruned search of a query batch on the index's own
+ * context; recorded only when the index was built with DBL_FLAG_TIMING).
  * out[0] = number of marks m (<= 63); out[1..m] = nanoseconds since the launch
  * began (%globaltimer of block 0) at the start, after each grid barrier, and at
  * the end.  An insertion launch's barriers follow its phases: validate,
@@ -247,19 +250,19 @@ dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
 /*
  * Autotuner: time the sample insertion batch (src, dst, b) followed by the
  * sample query batch (u, v, q; answers to ans) under each frontier schedule
- * -- team widths 4, 8, 16, 32 (lanes sharing one frontier task) and
+ * -- team widths 1, 4, 8, 16, 32 (dbl_options.team) and
  * level-by-level or persistent propagation -- each `trials` times from the
  * same snapshot (slot 3 is overwritten), and keep the fastest in the index's
  * options.  The index's labels and graph are restored afterwards.
- * report (may be NULL) receives [8] mean ms per candidate (level-by-level
- * teams 4..32, then persistent teams 4..32), [8] best team, [9] 1 if
- * persistent, [10] best ms.  DBL_FLAG_ASYNC/TIMING are off during the trials
+ * report (may be NULL, else 16 doubles) receives [0..9] mean ms per
+ * candidate (level-by-level teams 1, 4, 8, 16, 32, then persistent teams
+ * 1..32), [10] best team, [11] 1 if persistent, [12] best ms.  DBL_FLAG_ASYNC/TIMING are off during the trials
  * and restored after.  Synchronous.
  */
 dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, const int32_t *u,
                         const int32_t *v, int64_t q, uint8_t *ans, int32_t trials, double *report, void *stream);
 /* Apply a frontier schedule directly (e.g. one cached from dbl_autotune):
- * team width 4, 8, 16 or 32; persistent != 0 sets DBL_FLAG_PERSISTENT. */
+ * team width 1, 4, 8, 16 or 32; persistent != 0 sets DBL_FLAG_PERSISTENT. */
 dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent);
 
 /* ---------------------------------------------------------------------------

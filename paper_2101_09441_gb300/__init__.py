@@ -161,7 +161,7 @@ class DBLIndex:
     """
 
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
-                 leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 8, stream=None,
+                 leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
                  torch_allocator: bool = True, query_unroll: int = 0):
         import torch
         if not torch.cuda.is_available():
@@ -358,9 +358,10 @@ class DBLIndex:
         rep = np.zeros(16, dtype=np.float64)
         self._check(lib().dbl_autotune(self._h, _ptr(src), _ptr(dst), int(src.numel()), _ptr(u), _ptr(v),
                                        int(u.numel()), _ptr(ans), int(trials), rep.ctypes.data, self._s(stream)))
-        out = {"team": int(rep[8]), "persistent": bool(rep[9]), "best_ms": float(rep[10]),
-               "level_ms": {t: float(rep[i]) for i, t in enumerate((4, 8, 16, 32))},
-               "persistent_ms": {t: float(rep[4 + i]) for i, t in enumerate((4, 8, 16, 32))}}
+        teams = (1, 4, 8, 16, 32)
+        out = {"team": int(rep[10]), "persistent": bool(rep[11]), "best_ms": float(rep[12]),
+               "level_ms": {t: float(rep[i]) for i, t in enumerate(teams)},
+               "persistent_ms": {t: float(rep[5 + i]) for i, t in enumerate(teams)}}
         if cache:
             table = json.load(open(cache)) if os.path.exists(cache) else {}
             table[key] = out

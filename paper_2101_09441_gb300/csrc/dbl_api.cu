@@ -262,7 +262,7 @@ void dbl_default_options(dbl_options *opt)
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->bfs_words = 16;
-    opt->team = 8;
+    opt->team = 1;
 }
 
 static void destroy_impl(dbl_index *ix, cudaStream_t s)
@@ -305,15 +305,15 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     if (leaf_buckets && !leaf_roles) return fail(nullptr, DBL_ERR_INVALID, "leaf_roles required with leaf_buckets");
     if (opt && ((opt->alloc == nullptr) != (opt->free == nullptr)))
         return fail(nullptr, DBL_ERR_INVALID, "options: alloc and free must be set together");
-    if (opt && opt->team && opt->team != 4 && opt->team != 8 && opt->team != 16 && opt->team != 32)
-        return fail(nullptr, DBL_ERR_INVALID, "options: team must be 4, 8, 16 or 32");
+    if (opt && opt->team && opt->team != 1 && opt->team != 4 && opt->team != 8 && opt->team != 16 && opt->team != 32)
+        return fail(nullptr, DBL_ERR_INVALID, "options: team must be 1, 4, 8, 16 or 32");
     cudaStream_t s = (cudaStream_t)stream;
     dbl_index *ix = new (std::nothrow) dbl_index();
     if (!ix) return fail(nullptr, DBL_ERR_OOM, "host allocation");
     dbl_default_options(&ix->opt);
     if (opt) {
         ix->opt = *opt;
-        if (!ix->opt.team) ix->opt.team = 8;
+        if (!ix->opt.team) ix->opt.team = 1;
         if (!ix->opt.bfs_words) ix->opt.bfs_words = 16;
     }
     cudaGetDevice(&ix->device);

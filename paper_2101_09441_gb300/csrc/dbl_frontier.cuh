@@ -150,6 +150,97 @@ __device__ __forceinline__ void stage_flush(const FrontierOut &f, const Stage &s
     __syncthreads();                                                                                                  \
     const ::dbl::Stage name{name##_tasks, &name##_n}
 
+// Shared-memory append buffer of int32 items for one block: a push from any
+// lane (divergent code included) is a shared-memory atomic; istage_flush (every
+// thread of the block) moves the items to a global list with one reservation
+// per block.  Items that do not fit are appended to the global list directly.
+constexpr uint32_t kIStage = 2048;
+
+struct IStage {
+    int32_t *items;  // shared, kIStage entries
+    uint32_t *n;     // shared, pushes so far (may exceed kIStage)
+};
+
+struct IList {
+    int32_t *items;
+    uint32_t *count;
+    int64_t cap;
+    uint32_t *overflow;  // set when the list is full (may be null: cannot overflow)
+};
+
+__device__ __forceinline__ void istage_push(const IStage &st, int32_t item, const IList &dst)
+{
+    const uint32_t pos = atomicAdd(st.n, 1u);
+    if (pos < kIStage) {
+        st.items[pos] = item;
+        return;
+    }
+    const uint32_t g = atomicAdd(dst.count, 1u);
+    if ((int64_t)g < dst.cap) dst.items[g] = item;
+    else if (dst.overflow) atomicExch(dst.overflow, 1u);
+}
+
+__device__ __forceinline__ void istage_flush(const IStage &st, const IList &dst)
+{
+    __shared__ uint32_t s_base;
+    __syncthreads();
+    uint32_t cnt = *(volatile uint32_t *)st.n;
+    if (cnt > kIStage) cnt = kIStage;
+    if (threadIdx.x == 0 && cnt) s_base = atomicAdd(dst.count, cnt);
+    __syncthreads();
+    if (cnt) {
+        const uint32_t b = s_base;
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t pos = b + i;
+            if ((int64_t)pos < dst.cap) dst.items[pos] = st.items[i];
+            else if (dst.overflow) atomicExch(dst.overflow, 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *st.n = 0;
+    __syncthreads();
+}
+
+#define DBL_BLOCK_ISTAGE(name)                                                                                        \
+    __shared__ int32_t name##_items[::dbl::kIStage];                                                                  \
+    __shared__ uint32_t name##_n;                                                                                     \
+    if (threadIdx.x == 0) name##_n = 0;                                                                               \
+    __syncthreads();                                                                                                  \
+    const ::dbl::IStage name{name##_items, &name##_n}
+
+// Block-uniform reservation: every thread of the block calls it with its own
+// count and gets the start of its own range; the block's total is reserved in
+// *gcount with one atomicAdd.  *total receives the block's total.
+__device__ __forceinline__ uint32_t block_reserve(uint32_t mine, uint32_t *gcount, uint32_t *total)
+{
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_base, s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const uint32_t t = s_w[w];
+            s_w[w] = run;
+            run += t;
+        }
+        s_total = run;
+        s_base = run ? atomicAdd(gcount, run) : 0u;
+    }
+    __syncthreads();
+    const uint32_t r = s_base + s_w[warp] + incl - mine;
+    *total = s_total;
+    __syncthreads();
+    return r;
+}
+
 // Same, for callers whose loop is not warp-uniform: uses the active mask.
 __device__ __forceinline__ void any_enqueue(int32_t x, int dir, const DevGraph &g, const FrontierOut &f)
 {

@@ -416,6 +416,7 @@ template <int HS, int WD>
 static dbl_status launch_insert_persistent_team(dbl_index *ix, const InsArgs &a, cudaStream_t s)
 {
     switch (ix->opt.team) {
+    case 1: return launch_insert_persistent<HS, WD, 1>(ix, a, s);
     case 4: return launch_insert_persistent<HS, WD, 4>(ix, a, s);
     case 16: return launch_insert_persistent<HS, WD, 16>(ix, a, s);
     case 32: return launch_insert_persistent<HS, WD, 32>(ix, a, s);

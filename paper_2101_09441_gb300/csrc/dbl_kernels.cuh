@@ -13,6 +13,102 @@ __device__ __forceinline__ void warp_stat_add(unsigned long long *stats, int idx
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + idx, v);
 }
 
+// Owner lane of flat position e, given each lane's exclusive prefix `excl`
+// (non-decreasing over lanes, excl of lane 0 = 0): the largest lane k with
+// excl_k <= e.  Every lane of the warp must call it.
+__device__ __forceinline__ int flat_owner(uint32_t excl, uint32_t e)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+        const uint32_t v = __shfl_sync(kFull, excl, lo + step);
+        if (v <= e) lo += step;
+    }
+    return lo;
+}
+
+// Flattened level (TEAM == 1): each lane takes one task per round (task
+// w + nwarps*(32r + lane) for warp w, so a hub's consecutive chunks land in
+// different warps), and the warp walks the concatenation of its tasks' edges
+// 32 at a time; each edge's task data come from the owner lane by shuffles.
+// A round costs ceil(edges of the warp's tasks / 32) iterations, whatever the
+// mix of task sizes.
+template <int HS>
+__device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
+                                                  uint32_t ntasks, const FrontierOut &f,
+                                                  unsigned long long *stats, int64_t warp, int64_t nwarps,
+                                                  const Stage &st)
+{
+    constexpr int RW = 2 * HS;
+    const int lane = threadIdx.x & 31;
+    unsigned long long relaxed = 0, ntask = 0;
+    if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
+    for (int64_t r0 = 0; warp + nwarps * r0 < (int64_t)ntasks; r0 += 32) {  // warp-uniform
+        const int64_t t = warp + nwarps * (r0 + lane);
+        int32_t v = 0, b0 = 0, bd = 0, o0 = 0;
+        uint32_t lo = 0, cnt = 0;
+        int dir = 0;
+        uint64_t rv[HS];
+#pragma unroll
+        for (int i = 0; i < HS; ++i) rv[i] = 0;
+        if (t < (int64_t)ntasks) {
+            const uint64_t tk = __ldcg(tasks + t);
+            v = (int32_t)(uint32_t)tk;
+            const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
+            dir = (int)(tk >> 63);
+            const AdjRange r = adj_of(g, dir, v);
+            b0 = r.b0;
+            bd = r.bd;
+            o0 = r.o0;
+            const int32_t d = r.bd + r.od;
+            lo = chunk * (uint32_t)kChunk;
+            const int32_t hi = min(d, (int32_t)lo + kChunk);
+            cnt = hi > (int32_t)lo ? (uint32_t)(hi - (int32_t)lo) : 0u;
+            load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
+            ++ntask;
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t e = base + lane;
+            const int owner = flat_owner(excl, e);
+            const int odir = __shfl_sync(kFull, dir, owner);
+            const AdjRange orr{__shfl_sync(kFull, b0, owner), __shfl_sync(kFull, bd, owner),
+                               __shfl_sync(kFull, o0, owner), 0};
+            const uint32_t opos = __shfl_sync(kFull, lo, owner) + (e - __shfl_sync(kFull, excl, owner));
+            uint64_t orv[HS];
+#pragma unroll
+            for (int i = 0; i < HS; ++i) orv[i] = __shfl_sync(kFull, rv[i], owner);
+            bool want = false;
+            int32_t x = 0;
+            if (e < total) {
+                x = adj_at(g, odir, orr, (int32_t)opos);
+                ++relaxed;
+                uint64_t *px = rec + (size_t)x * RW + (odir ? HS : 0);
+                uint64_t rx[HS];
+                load_half<HS>(px, rx);
+#pragma unroll
+                for (int i = 0; i < HS; ++i) {
+                    if (orv[i] & ~rx[i]) {
+                        const unsigned long long old = atomicOr((unsigned long long *)(px + i), orv[i]);
+                        want |= (orv[i] & ~old) != 0;
+                    }
+                }
+            }
+            stage_enqueue(want, x, odir, g, f, st);
+        }
+    }
+    warp_stat_add(stats, 9, ntask);
+    warp_stat_add(stats, 10, relaxed);
+    stage_flush(f, st);
+}
+
 // One level of label propagation over `ntasks` tasks, processed by warps
 // [warp0, warp0 + nwarps*k) in steps of nwarps.  Every lane of a warp runs the
 // same number of iterations (warp_enqueue needs the whole warp).
@@ -24,62 +120,66 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                                              uint32_t ntasks, const FrontierOut &f, unsigned long long *stats,
                                              int64_t warp0, int64_t nwarps, const Stage &st)
 {
-    constexpr int TPW = 32 / TEAM;
-    constexpr int RW = 2 * HS;
-    const int lane = threadIdx.x & 31;
-    const int team = lane / TEAM, tl = lane % TEAM;
-    unsigned long long relaxed = 0, ntask = 0;
-    if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
-    for (int64_t wb = warp0 * TPW; wb < (int64_t)ntasks; wb += nwarps * TPW) {
-        const int64_t t = wb + team;
-        const bool has = t < (int64_t)ntasks;
-        int32_t v = 0, lo = 0, hi = 0;
-        int dir = 0;
-        AdjRange r{0, 0, 0, 0};
-        uint64_t rv[HS];
+    if constexpr (TEAM == 1) {
+        expand_level_flat<HS>(g, rec, tasks, ntasks, f, stats, warp0, nwarps, st);
+    } else {
+        constexpr int TPW = 32 / TEAM;
+        constexpr int RW = 2 * HS;
+        const int lane = threadIdx.x & 31;
+        const int team = lane / TEAM, tl = lane % TEAM;
+        unsigned long long relaxed = 0, ntask = 0;
+        if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
+        for (int64_t wb = warp0 * TPW; wb < (int64_t)ntasks; wb += nwarps * TPW) {
+            const int64_t t = wb + team;
+            const bool has = t < (int64_t)ntasks;
+            int32_t v = 0, lo = 0, hi = 0;
+            int dir = 0;
+            AdjRange r{0, 0, 0, 0};
+            uint64_t rv[HS];
 #pragma unroll
-        for (int i = 0; i < HS; ++i) rv[i] = 0;
-        if (has) {
-            const uint64_t tk = __ldcg(tasks + t);
-            v = (int32_t)(uint32_t)tk;
-            const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
-            dir = (int)(tk >> 63);
-            r = adj_of(g, dir, v);
-            const int32_t d = r.bd + r.od;
-            lo = (int32_t)chunk * kChunk;
-            hi = min(d, lo + kChunk);
-            load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
-            if (tl == 0) ++ntask;
-        }
-        int iters = has && hi > lo ? (hi - lo + TEAM - 1) / TEAM : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) iters = max(iters, __shfl_xor_sync(kFull, iters, o));
-        for (int it = 0; it < iters; ++it) {
-            const int32_t e = lo + it * TEAM + tl;
-            bool want = false;
-            int32_t x = 0;
-            if (has && e < hi) {
-                x = adj_at(g, dir, r, e);
-                ++relaxed;
-                uint64_t *px = rec + (size_t)x * RW + (dir ? HS : 0);
-                uint64_t rx[HS];
-                load_half<HS>(px, rx);
-                bool changed = false;
-#pragma unroll
-                for (int i = 0; i < HS; ++i) {
-                    if (rv[i] & ~rx[i]) {
-                        unsigned long long old = atomicOr((unsigned long long *)(px + i), rv[i]);
-                        changed |= (rv[i] & ~old) != 0;
-                    }
-                }
-                want = changed;
+            for (int i = 0; i < HS; ++i) rv[i] = 0;
+            if (has) {
+                const uint64_t tk = __ldcg(tasks + t);
+                v = (int32_t)(uint32_t)tk;
+                const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
+                dir = (int)(tk >> 63);
+                r = adj_of(g, dir, v);
+                const int32_t d = r.bd + r.od;
+                lo = (int32_t)chunk * kChunk;
+                hi = min(d, lo + kChunk);
+                load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
+                if (tl == 0) ++ntask;
             }
-            stage_enqueue(want, x, dir, g, f, st);
+            int iters = has && hi > lo ? (hi - lo + TEAM - 1) / TEAM : 0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) iters = max(iters, __shfl_xor_sync(kFull, iters, o));
+            for (int it = 0; it < iters; ++it) {
+                const int32_t e = lo + it * TEAM + tl;
+                bool want = false;
+                int32_t x = 0;
+                if (has && e < hi) {
+                    x = adj_at(g, dir, r, e);
+                    ++relaxed;
+                    uint64_t *px = rec + (size_t)x * RW + (dir ? HS : 0);
+                    uint64_t rx[HS];
+                    load_half<HS>(px, rx);
+                    bool changed = false;
+#pragma unroll
+                    for (int i = 0; i < HS; ++i) {
+                        if (rv[i] & ~rx[i]) {
+                            unsigned long long old = atomicOr((unsigned long long *)(px + i), rv[i]);
+                            changed |= (rv[i] & ~old) != 0;
+                        }
+                    }
+                    want = changed;
+                }
+                stage_enqueue(want, x, dir, g, f, st);
+            }
         }
+        warp_stat_add(stats, 9, ntask);
+        warp_stat_add(stats, 10, relaxed);
+        stage_flush(f, st);
     }
-    warp_stat_add(stats, 9, ntask);
-    warp_stat_add(stats, 10, relaxed);
-    stage_flush(f, st);
 }
 
 }  // namespace dbl

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, co
 template <int HS, int TEAM>
 static void launch_expand(dbl_index *ix, int cur, uint32_t ntasks, const FrontierOut &f, cudaStream_t s)
 {
-    constexpr int TPW = 32 / TEAM;
+    // tasks per warp at a time; the flattened form (TEAM 1) spreads about 8
+    // tasks over each warp so that a hub's chunks land in different warps
+    constexpr int TPW = TEAM == 1 ? 8 : 32 / TEAM;
     int64_t warps = ((int64_t)ntasks + TPW - 1) / TPW;
     int64_t blocks = (warps * 32 + kBlock - 1) / kBlock;
     int64_t cap = (int64_t)num_sms() * 8;
@@ -49,6 +51,7 @@ template <int HS>
 static void launch_expand_team(dbl_index *ix, int cur, uint32_t ntasks, const FrontierOut &f, cudaStream_t s)
 {
     switch (ix->opt.team) {
+    case 1: launch_expand<HS, 1>(ix, cur, ntasks, f, s); break;
     case 4: launch_expand<HS, 4>(ix, cur, ntasks, f, s); break;
     case 16: launch_expand<HS, 16>(ix, cur, ntasks, f, s); break;
     case 32: launch_expand<HS, 32>(ix, cur, ntasks, f, s); break;
@@ -205,6 +208,7 @@ template <int HS>
 static dbl_status launch_persistent_team(dbl_index *ix, cudaStream_t s)
 {
     switch (ix->opt.team) {
+    case 1: return launch_persistent<HS, 1>(ix, s);
     case 4: return launch_persistent<HS, 4>(ix, s);
     case 16: return launch_persistent<HS, 16>(ix, s);
     case 32: return launch_persistent<HS, 32>(ix, s);

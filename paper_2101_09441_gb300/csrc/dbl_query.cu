@@ -177,7 +177,13 @@ struct PersistState {
 
 constexpr int kMaxProbe = 2048;
 
-__device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsigned long long key)
+// Claimed slots go to the block's claim stage (cst), flushed to c.claimed.
+__device__ __forceinline__ IList claimed_list(const SearchCtx &c)
+{
+    return IList{c.claimed, c.n_claimed, (int64_t)c.slot_mask + 1, nullptr};  // each slot is claimed once per wave
+}
+
+__device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsigned long long key, const IStage &cst)
 {
     unsigned long long h = mix_key(key) & c.slot_mask;
     for (int p = 0; p < kMaxProbe; ++p) {
@@ -187,8 +193,7 @@ __device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsig
         if (k == kEmptyKey) {
             unsigned long long prev = atomicCAS(&s->key, kEmptyKey, key);
             if (prev == kEmptyKey) {
-                uint32_t pos = atomicAdd(c.n_claimed, 1u);
-                c.claimed[pos] = (int32_t)h;  // pos < slots: each slot is claimed once per wave
+                istage_push(cst, (int32_t)h, claimed_list(c));
                 return (int64_t)h;
             }
             if (prev == key) return (int64_t)h;
@@ -205,54 +210,96 @@ struct QT {
     static constexpr int W = 1 + WD + 2 * WB;
 };
 
+__device__ __forceinline__ IList slot_list_of(const SearchCtx &c, const SlotList &l)
+{
+    return IList{l.items, l.count, l.cap, c.overflow};
+}
+
+// Slots that gain pending bits join the next level's list (through the block's
+// list stage nst, flushed to `next`), once per level.
 __device__ __forceinline__ void mark_pending(const SearchCtx &c, int64_t slot, unsigned long long bits,
-                                             uint32_t epoch, const SlotList &next)
+                                             uint32_t epoch, const SlotList &next, const IStage &nst)
 {
     SearchSlot *s = c.table + slot;
     atomicOr(&s->pend, bits);
-    if (atomicExch(&s->stamp, epoch) != epoch) {
-        uint32_t pos = atomicAdd(next.count, 1u);
-        if ((int64_t)pos < next.cap) next.items[pos] = (int32_t)slot;
-        else atomicExch(c.overflow, 1u);
-    }
+    if (atomicExch(&s->stamp, epoch) != epoch) istage_push(nst, (int32_t)slot, slot_list_of(c, next));
 }
 
 // Wave setup: queries [j0, j1) of the undecided list (group j/64, bit j%64):
-// fill the query table, zero the groups' found words, and start every search
-// at its u (visited and pending there).
+// fill the query table, zero the groups' found words, and emit the first
+// level's tasks straight from each query's u: (u, g, chunk, bit j) for every
+// chunk of Suc(u).  u itself is not entered in the visited table; if a search
+// comes back to u it expands u once more, which adds nothing.  Each thread
+// takes kSetupQ queries per round with all their loads in flight; the task
+// list gets one reservation per block and round (the loop is block-uniform).
+constexpr int kSetupQ = 4;
+
 template <int WD, int WB>
-__device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, int64_t j1, uint32_t epoch,
-                                             const SlotList &first)
+__device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, int64_t j1, uint32_t *n_tasks)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
     constexpr int W = QT<WD, WB>::W;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     for (int64_t gq = (j0 >> 6) + t0; gq < ((j1 + 63) >> 6); gq += nt) a.found[gq] = 0;
-    for (int64_t j = j0 + t0; j < j1; j += nt) {
-        const int64_t i = a.und[j];
-        const int32_t u = a.qu[i], v = a.qv[i];
-        uint64_t *t = a.qtab + (size_t)j * W;
-        t[0] = (uint64_t)(uint32_t)u | ((uint64_t)(uint32_t)v << 32);
-        const uint64_t *ru = a.rec + (size_t)u * RW, *rv = a.rec + (size_t)v * RW;
+    const int64_t tile = (int64_t)blockDim.x * kSetupQ;
+    for (int64_t base = j0 + (int64_t)blockIdx.x * tile; base < j1; base += (int64_t)gridDim.x * tile) {
+        int64_t i[kSetupQ];
+        int32_t u[kSetupQ], v[kSetupQ];
+        uint32_t nch[kSetupQ], mine = 0;
 #pragma unroll
-        for (int w = 0; w < WD; ++w) t[1 + w] = ru[HS + w];              // DL_out(u)
-#pragma unroll
-        for (int w = 0; w < WB; ++w) {
-            t[1 + WD + w] = rv[WD + w];                                   // BL_in(v)
-            t[1 + WD + WB + w] = rv[HS + WD + w];                         // BL_out(v)
+        for (int k = 0; k < kSetupQ; ++k) {
+            const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+            i[k] = j < j1 ? a.und[j] : -1;
         }
-        const unsigned long long g = (unsigned long long)(j >> 6);
-        const unsigned long long bit = 1ull << (j & 63);
-        int64_t s = slot_find_or_insert(a.c, (g << 32) | (uint32_t)u);
-        if (s < 0) continue;
-        atomicOr(&a.c.table[s].visit, bit);
-        mark_pending(a.c, s, bit, epoch, first);
+#pragma unroll
+        for (int k = 0; k < kSetupQ; ++k) {
+            u[k] = i[k] >= 0 ? a.qu[i[k]] : 0;
+            v[k] = i[k] >= 0 ? a.qv[i[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kSetupQ; ++k) {
+            const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+            nch[k] = 0;
+            if (i[k] < 0) continue;
+            uint64_t *t = a.qtab + (size_t)j * W;
+            t[0] = (uint64_t)(uint32_t)u[k] | ((uint64_t)(uint32_t)v[k] << 32);
+            const uint64_t *ru = a.rec + (size_t)u[k] * RW, *rv = a.rec + (size_t)v[k] * RW;
+#pragma unroll
+            for (int w = 0; w < WD; ++w) t[1 + w] = ru[HS + w];  // DL_out(u)
+#pragma unroll
+            for (int w = 0; w < WB; ++w) {
+                t[1 + WD + w] = rv[WD + w];                       // BL_in(v)
+                t[1 + WD + WB + w] = rv[HS + WD + w];             // BL_out(v)
+            }
+            nch[k] = (uint32_t)((deg_of(a.g, 0, u[k]) + kChunk - 1) / kChunk);
+            mine += nch[k];
+        }
+        uint32_t total = 0;
+        uint32_t pos = block_reserve(mine, n_tasks, &total);
+        if (total == 0) continue;
+#pragma unroll
+        for (int k = 0; k < kSetupQ; ++k) {
+            const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+            for (uint32_t ch = 0; ch < nch[k]; ++ch, ++pos) {
+                if ((int64_t)pos >= a.task_cap) {
+                    atomicExch(a.c.overflow, 1u);
+                    break;
+                }
+                SearchTask tk;
+                tk.x = u[k];
+                tk.g = (uint32_t)(j >> 6);
+                tk.chunk = ch;
+                tk.pad = 0;
+                tk.mask = 1ull << (j & 63);
+                a.tasks[pos] = tk;
+            }
+        }
     }
 }
 
 // Slots listed for the next level -> tasks (x, g, chunk, mask) over Suc(x);
-// one task-list reservation per warp.
+// one task-list reservation per block (the loop is block-uniform).
 __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotList &cur, uint32_t *n_tasks)
 {
     const int64_t n = min((int64_t)ld_volatile_u32(cur.count), cur.cap);
@@ -272,18 +319,9 @@ __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotL
                 nch = (uint32_t)((deg_of(a.g, 0, x) + kChunk - 1) / kChunk);
             }
         }
-        uint32_t incl = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        uint32_t total = 0;
+        uint32_t pos = block_reserve(nch, n_tasks, &total);
         if (total == 0) continue;
-        uint32_t wbase = 0;
-        if (lane == 31) wbase = atomicAdd(n_tasks, total);
-        wbase = __shfl_sync(kFull, wbase, 31);
-        uint32_t pos = wbase + incl - nch;
         for (uint32_t ch = 0; ch < nch; ++ch, ++pos) {
             if ((int64_t)pos >= a.task_cap) {
                 atomicExch(a.c.overflow, 1u);
@@ -303,92 +341,181 @@ __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotL
 // One search level: for each task's edges x -> y and each live query j of the
 // task's mask, in Algorithm 2's order: y == v_j -> found; DL prune; BL prune;
 // otherwise y is visited for j, and bits new at y are pending for next level.
-template <int WD, int WB, int TEAM>
-__device__ __forceinline__ void search_expand(const SearchArgs &a, uint32_t n_tasks_in, uint32_t epoch,
-                                              const SlotList &next)
+// Tests of one edge x -> y against the live queries m of group g (Algorithm
+// 2's order), then the visit/pending update of (g, y).
+template <int WD, int WB>
+__device__ __forceinline__ void search_edge(const SearchArgs &a, int32_t y, uint32_t g, unsigned long long m,
+                                            uint32_t epoch, const SlotList &next, const IStage &cst,
+                                            const IStage &nst)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
     constexpr int W = QT<WD, WB>::W;
-    constexpr int TPW = 32 / TEAM;
+    const uint64_t *qg = a.qtab + (size_t)g * 64 * W;
+    uint64_t fy[HS], by[HS];
+    load_half<HS>(a.rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
+    load_half<HS>(a.rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
+    unsigned long long hits = 0, allowed = 0, rest = m;
+    while (rest) {
+        const int b = __ffsll((long long)rest) - 1;
+        rest &= rest - 1;
+        const uint64_t *qj = qg + (size_t)b * W;
+        const uint64_t uv = __ldg(qj);
+        const unsigned long long bit = 1ull << b;
+        if ((int32_t)(uint32_t)(uv >> 32) == y) {
+            hits |= bit;
+            continue;
+        }
+        uint64_t dl = 0, bl = 0;
+#pragma unroll
+        for (int w = 0; w < WD; ++w) dl |= __ldg(qj + 1 + w) & fy[w];
+        if (dl) continue;
+#pragma unroll
+        for (int w = 0; w < WB; ++w)
+            bl |= (fy[WD + w] & ~__ldg(qj + 1 + WD + w)) | (__ldg(qj + 1 + WD + WB + w) & ~by[WD + w]);
+        if (bl) continue;
+        allowed |= bit;
+    }
+    if (hits) atomicOr(a.found + g, hits);
+    if (allowed) {
+        const int64_t s = slot_find_or_insert(a.c, ((unsigned long long)g << 32) | (uint32_t)y, cst);
+        if (s < 0) return;
+        const unsigned long long old = atomicOr(&a.c.table[s].visit, allowed);
+        const unsigned long long nb = allowed & ~old;
+        if (nb) mark_pending(a.c, s, nb, epoch, next, nst);
+    }
+}
+
+// Flattened search level (TEAM == 1): one task per lane per round, the warp
+// walks the concatenation of its tasks' edges 32 at a time (see
+// expand_level_flat).
+template <int WD, int WB>
+__device__ __forceinline__ void search_expand_flat(const SearchArgs &a, uint32_t n_tasks_in, uint32_t epoch,
+                                                   const SlotList &next, const IStage &cst, const IStage &nst)
+{
     const int lane = threadIdx.x & 31;
-    const int team = lane / TEAM, tl = lane % TEAM;
     const int64_t ntasks = min((int64_t)n_tasks_in, a.task_cap);
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long relaxed = 0;
-    for (int64_t wb = warp0 * TPW; wb < ntasks; wb += nwarps * TPW) {
-        const int64_t t = wb + team;
-        if (t >= ntasks) continue;
-        const SearchTask tk = a.tasks[t];
-        const unsigned long long m = tk.mask & ~__ldcg(a.found + tk.g);
-        if (!m) continue;
-        const AdjRange r = adj_of(a.g, 0, tk.x);
-        const int32_t d = r.bd + r.od;
-        const int32_t lo = (int32_t)tk.chunk * kChunk;
-        const int32_t hi = min(d, lo + kChunk);
-        const uint64_t *qg = a.qtab + (size_t)tk.g * 64 * W;
-        for (int32_t e = lo + tl; e < hi; e += TEAM) {
-            const int32_t y = adj_at(a.g, 0, r, e);
-            ++relaxed;
-            uint64_t fy[HS], by[HS];
-            load_half<HS>(a.rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
-            load_half<HS>(a.rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
-            unsigned long long hits = 0, allowed = 0, rest = m;
-            while (rest) {
-                const int b = __ffsll((long long)rest) - 1;
-                rest &= rest - 1;
-                const uint64_t *qj = qg + (size_t)b * W;
-                const uint64_t uv = __ldg(qj);
-                const unsigned long long bit = 1ull << b;
-                if ((int32_t)(uint32_t)(uv >> 32) == y) {
-                    hits |= bit;
-                    continue;
-                }
-                uint64_t dl = 0, bl = 0;
-#pragma unroll
-                for (int w = 0; w < WD; ++w) dl |= __ldg(qj + 1 + w) & fy[w];
-                if (dl) continue;
-#pragma unroll
-                for (int w = 0; w < WB; ++w)
-                    bl |= (fy[WD + w] & ~__ldg(qj + 1 + WD + w)) | (__ldg(qj + 1 + WD + WB + w) & ~by[WD + w]);
-                if (bl) continue;
-                allowed |= bit;
+    for (int64_t r0 = 0; warp + nwarps * r0 < ntasks; r0 += 32) {  // warp-uniform
+        const int64_t t = warp + nwarps * (r0 + lane);
+        int32_t b0 = 0, bd = 0, o0 = 0;
+        uint32_t lo = 0, cnt = 0, g = 0;
+        unsigned long long m = 0;
+        if (t < ntasks) {
+            const SearchTask tk = a.tasks[t];
+            m = tk.mask & ~__ldcg(a.found + tk.g);
+            if (m) {
+                const AdjRange r = adj_of(a.g, 0, tk.x);
+                b0 = r.b0;
+                bd = r.bd;
+                o0 = r.o0;
+                g = tk.g;
+                const int32_t d = r.bd + r.od;
+                lo = tk.chunk * (uint32_t)kChunk;
+                const int32_t hi = min(d, (int32_t)lo + kChunk);
+                cnt = hi > (int32_t)lo ? (uint32_t)(hi - (int32_t)lo) : 0u;
             }
-            if (hits) atomicOr(a.found + tk.g, hits);
-            if (allowed) {
-                const int64_t s = slot_find_or_insert(a.c, ((unsigned long long)tk.g << 32) | (uint32_t)y);
-                if (s < 0) continue;
-                const unsigned long long old = atomicOr(&a.c.table[s].visit, allowed);
-                const unsigned long long nb = allowed & ~old;
-                if (nb) mark_pending(a.c, s, nb, epoch, next);
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t e = base + lane;
+            const int owner = flat_owner(excl, e);
+            const AdjRange orr{__shfl_sync(kFull, b0, owner), __shfl_sync(kFull, bd, owner),
+                               __shfl_sync(kFull, o0, owner), 0};
+            const uint32_t opos = __shfl_sync(kFull, lo, owner) + (e - __shfl_sync(kFull, excl, owner));
+            const uint32_t og = __shfl_sync(kFull, g, owner);
+            const unsigned long long om = __shfl_sync(kFull, m, owner);
+            if (e < total) {
+                ++relaxed;
+                search_edge<WD, WB>(a, adj_at(a.g, 0, orr, (int32_t)opos), og, om, epoch, next, cst, nst);
             }
         }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) relaxed += __shfl_xor_sync(kFull, relaxed, o);
     if (lane == 0 && relaxed) atomicAdd(a.stats + 10, relaxed);
+    istage_flush(cst, claimed_list(a.c));
+    istage_flush(nst, slot_list_of(a.c, next));
+}
+
+template <int WD, int WB, int TEAM>
+__device__ __forceinline__ void search_expand(const SearchArgs &a, uint32_t n_tasks_in, uint32_t epoch,
+                                              const SlotList &next, const IStage &cst, const IStage &nst)
+{
+    if constexpr (TEAM == 1) {
+        search_expand_flat<WD, WB>(a, n_tasks_in, epoch, next, cst, nst);
+    } else {
+        // TEAM lanes per task, 32/TEAM tasks per warp at a time
+        constexpr int TPW = 32 / TEAM;
+        const int lane = threadIdx.x & 31;
+        const int team = lane / TEAM, tl = lane % TEAM;
+        const int64_t ntasks = min((int64_t)n_tasks_in, a.task_cap);
+        const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        unsigned long long relaxed = 0;
+        for (int64_t wb = warp0 * TPW; wb < ntasks; wb += nwarps * TPW) {
+            const int64_t t = wb + team;
+            if (t >= ntasks) continue;
+            const SearchTask tk = a.tasks[t];
+            const unsigned long long m = tk.mask & ~__ldcg(a.found + tk.g);
+            if (!m) continue;
+            const AdjRange r = adj_of(a.g, 0, tk.x);
+            const int32_t d = r.bd + r.od;
+            const int32_t lo = (int32_t)tk.chunk * kChunk;
+            const int32_t hi = min(d, lo + kChunk);
+            for (int32_t e = lo + tl; e < hi; e += TEAM) {
+                ++relaxed;
+                search_edge<WD, WB>(a, adj_at(a.g, 0, r, e), tk.g, m, epoch, next, cst, nst);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) relaxed += __shfl_xor_sync(kFull, relaxed, o);
+        if (lane == 0 && relaxed) atomicAdd(a.stats + 10, relaxed);
+        istage_flush(cst, claimed_list(a.c));
+        istage_flush(nst, slot_list_of(a.c, next));
+    }
 }
 
 // Answers of queries [j0, j1): found -> true (bfs_pos); otherwise false
 // (bfs_neg) when the wave ran to exhaustion (final), else left for a rerun.
+// Four queries per thread and round, loads first.
 __device__ __forceinline__ void search_answer(const SearchArgs &a, int64_t j0, int64_t j1, bool final_wave)
 {
+    constexpr int Q = 4;
     __shared__ unsigned int cnt[2];
     if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const bool hit = (__ldcg(a.found + (j >> 6)) >> (j & 63)) & 1ull;
-        const int64_t i = a.und[j];
-        if (hit) {
-            a.ans[i] = 1;
-            if (a.code) a.code[i] = DBL_CODE_BFS_POS;
-            atomicAdd(&cnt[0], 1u);
-        } else if (final_wave) {
-            a.ans[i] = 0;
-            if (a.code) a.code[i] = DBL_CODE_BFS_NEG;
-            atomicAdd(&cnt[1], 1u);
+    const int64_t tile = (int64_t)blockDim.x * Q;
+    for (int64_t base = j0 + (int64_t)blockIdx.x * tile; base < j1; base += (int64_t)gridDim.x * tile) {
+        int64_t i[Q];
+        bool hit[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+            i[k] = j < j1 ? a.und[j] : -1;
+            hit[k] = j < j1 && ((__ldcg(a.found + (j >> 6)) >> (j & 63)) & 1ull);
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            if (i[k] < 0) continue;
+            if (hit[k]) {
+                a.ans[i[k]] = 1;
+                if (a.code) a.code[i[k]] = DBL_CODE_BFS_POS;
+                atomicAdd(&cnt[0], 1u);
+            } else if (final_wave) {
+                a.ans[i[k]] = 0;
+                if (a.code) a.code[i[k]] = DBL_CODE_BFS_NEG;
+                atomicAdd(&cnt[1], 1u);
+            }
         }
     }
     __syncthreads();
@@ -398,24 +525,36 @@ __device__ __forceinline__ void search_answer(const SearchArgs &a, int64_t j0, i
     }
 }
 
-// Return every slot claimed in the wave to empty.
+// Return every slot claimed in the wave to empty (four per thread and round).
 __device__ __forceinline__ void search_clear(const SearchArgs &a)
 {
-    const uint32_t n = ld_volatile_u32(a.c.n_claimed);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        SearchSlot *s = a.c.table + a.c.claimed[i];
-        s->key = kEmptyKey;
-        s->visit = 0;
-        s->pend = 0;
-        s->stamp = 0;
+    constexpr int Q = 4;
+    const int64_t n = ld_volatile_u32(a.c.n_claimed);
+    const int64_t tile = (int64_t)blockDim.x * Q;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        int32_t sl[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+            sl[k] = i < n ? a.c.claimed[i] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            if (sl[k] < 0) continue;
+            SearchSlot *s = a.c.table + sl[k];
+            s->key = kEmptyKey;
+            s->visit = 0;
+            s->pend = 0;
+            s->stamp = 0;
+        }
     }
 }
 
 // ------------------------------------------------------------ per-level kernels
 template <int WD, int WB>
-__global__ void k_search_setup(SearchArgs a, int64_t j0, int64_t j1, uint32_t epoch, SlotList first)
+__global__ void k_search_setup(SearchArgs a, int64_t j0, int64_t j1, uint32_t *n_tasks)
 {
-    search_setup<WD, WB>(a, j0, j1, epoch, first);
+    search_setup<WD, WB>(a, j0, j1, n_tasks);
 }
 
 __global__ void k_search_finalize(SearchArgs a, SlotList cur, uint32_t *n_tasks) { search_finalize(a, cur, n_tasks); }
@@ -424,7 +563,9 @@ template <int WD, int WB, int TEAM>
 __global__ void __launch_bounds__(kBlock) k_search_expand(SearchArgs a, const uint32_t *n_tasks, uint32_t epoch,
                                                           SlotList next)
 {
-    search_expand<WD, WB, TEAM>(a, ld_volatile_u32(n_tasks), epoch, next);
+    DBL_BLOCK_ISTAGE(cst);
+    DBL_BLOCK_ISTAGE(nst);
+    search_expand<WD, WB, TEAM>(a, ld_volatile_u32(n_tasks), epoch, next, cst, nst);
 }
 
 __global__ void k_search_answer(SearchArgs a, int64_t j0, int64_t j1, int final_wave)
@@ -441,7 +582,8 @@ __global__ void k_search_clear(SearchArgs a) { search_clear(a); }
 // Per level: finalize, barrier, expand, barrier.
 template <int WD, int WB, int TEAM>
 __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *ps, const uint32_t *n_und,
-                                             GridSync &gs, uint32_t *status, int64_t max_levels)
+                                             GridSync &gs, uint32_t *status, int64_t max_levels, const IStage &cst,
+                                             const IStage &nst)
 {
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const uint32_t U = ld_volatile_u32(n_und);
@@ -471,27 +613,26 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
         if (j0 < 0 || ld_volatile_u32(status)) break;
         ++waves;
         SlotList lists[2] = {{a.lists[0], &ps->list_count[0], a.list_cap}, {a.lists[1], &ps->list_count[1], a.list_cap}};
-        uint32_t sep = 1;
-        search_setup<WD, WB>(a, j0, j1, sep, lists[0]);
+        search_setup<WD, WB>(a, j0, j1, &ps->task_count[0]);
         if (!gs.sync(status)) return;
+        // level L: expand task list L%2 into slot list L%2 (slot stamps L+2),
+        // then turn that slot list into task list (L+1)%2
         for (int64_t L = 0;; ++L) {
             const int cur = (int)(L & 1);
-            if (!ld_volatile_u32(&ps->list_count[cur]) || ld_volatile_u32(&ps->overflow) || ld_volatile_u32(status))
-                break;
+            const uint32_t ntk = ld_volatile_u32(&ps->task_count[cur]);
+            if (!ntk || ld_volatile_u32(&ps->overflow) || ld_volatile_u32(status)) break;
             if (L >= max_levels) {
                 set_status(status, DBL_ERR_TIMEOUT);
                 break;
             }
             ++levels;
-            search_finalize(a, lists[cur], &ps->task_count[cur]);
+            if (leader) ps->task_count[cur ^ 1] = 0;
+            search_expand<WD, WB, TEAM>(a, ntk, (uint32_t)(L + 2), lists[cur], cst, nst);
             if (!gs.sync(status)) return;
-            ++sep;
-            if (leader) {
-                ps->list_count[cur] = 0;
-                ps->task_count[cur ^ 1] = 0;
-            }
-            search_expand<WD, WB, TEAM>(a, ld_volatile_u32(&ps->task_count[cur]), sep, lists[cur ^ 1]);
+            if (!ld_volatile_u32(&ps->list_count[cur]) || ld_volatile_u32(&ps->overflow)) break;
+            search_finalize(a, lists[cur], &ps->task_count[cur ^ 1]);
             if (!gs.sync(status)) return;
+            if (leader) ps->list_count[cur] = 0;  // written again two levels on, after a barrier
         }
         const bool over = ld_volatile_u32(&ps->overflow) != 0;
         search_answer(a, j0, j1, !over);
@@ -523,7 +664,9 @@ __global__ void __launch_bounds__(pblock_of(hs_of(WD + WB)), 1)
                         int64_t max_levels)
 {
     GridSync gs(bar);
-    search_waves<WD, WB, TEAM>(a, ps, n_und, gs, status, max_levels);
+    DBL_BLOCK_ISTAGE(cst);
+    DBL_BLOCK_ISTAGE(nst);
+    search_waves<WD, WB, TEAM>(a, ps, n_und, gs, status, max_levels, cst, nst);
     gs.leave();
 }
 
@@ -577,6 +720,7 @@ static void launch_search_expand(dbl_index *ix, dbl_qctx *c, const SearchArgs &a
 {
     uint32_t *nt = c->d_counts + kCntTasks;
     switch (ix->opt.team) {
+    case 1: k_search_expand<WD, WB, 1><<<blocks_for(est * 4), kBlock, 0, s>>>(a, nt, sep, next); break;
     case 4: k_search_expand<WD, WB, 4><<<blocks_for(est * 4), kBlock, 0, s>>>(a, nt, sep, next); break;
     case 16:
     case 32: k_search_expand<WD, WB, 16><<<blocks_for(est * 16), kBlock, 0, s>>>(a, nt, sep, next); break;
@@ -593,40 +737,38 @@ static dbl_status run_search_wave(dbl_index *ix, dbl_qctx *c, const int32_t *qu,
     uint32_t *h = c->h_pinned;
     const SearchArgs a = search_args(ix, c, qu, qv, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
     cudaMemsetAsync(cnt + kCntSlots0, 0, sizeof(uint32_t) * 5, s);  // slots0, slots1, tasks, claimed, overflow
-    // slot stamps are per wave (slots are cleared after each wave): level epochs 1, 2, ...
-    uint32_t sep = 1;
     SlotList lists[2] = {{c->slot_list[0], cnt + kCntSlots0, c->table_slots},
                          {c->slot_list[1], cnt + kCntSlots1, c->table_slots}};
     qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
-    k_search_setup<WD, WB><<<blocks_for(j1 - j0), kBlock, 0, s>>>(a, j0, j1, sep, lists[0]);
+    k_search_setup<WD, WB><<<blocks_for((j1 - j0 + kSetupQ - 1) / kSetupQ), kBlock, 0, s>>>(a, j0, j1, cnt + kCntTasks);
     ++ix->launches;
     qt_end(ix, c, s);
-    int cur = 0;
+    // level L: expand the task list into slot list L%2 (slot stamps L+2; slots
+    // are cleared after each wave), then turn that slot list into the next
+    // task list.  One host round trip per level reads the task count.
     int64_t levels = 0;
     const int64_t max_levels = (int64_t)ix->n + 2;
-    for (;;) {
+    for (int64_t L = 0;; ++L) {
         cudaMemcpyAsync(h, cnt, sizeof(uint32_t) * kCntWords, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e) return qfail(c, DBL_ERR_CUDA, std::string("search level: ") + cudaGetErrorString(e));
         if (h[kCntOverflow]) break;
-        const uint32_t nslots = h[kCntSlots0 + cur];
-        if (!nslots) break;
+        const uint32_t ntasks = h[kCntTasks];
+        if (!ntasks) break;
         if (++levels > max_levels) {
             ix->poisoned = true;
             return qfail(c, DBL_ERR_TIMEOUT, "search: level bound exceeded");
         }
-        const int nxt = cur ^ 1;
-        cudaMemsetAsync(cnt + kCntTasks, 0, sizeof(uint32_t), s);
-        cudaMemsetAsync(cnt + kCntSlots0 + nxt, 0, sizeof(uint32_t), s);
-        qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
-        k_search_finalize<<<blocks_for(nslots), kBlock, 0, s>>>(a, lists[cur], cnt + kCntTasks);
-        ++ix->launches;
+        const int cur = (int)(L & 1);
+        cudaMemsetAsync(cnt + kCntSlots0 + cur, 0, sizeof(uint32_t), s);
         qt_begin(ix, c, DBL_KERNEL_SEARCH_EXPAND, s);
-        ++sep;
-        // tasks are at most nslots * (1 + maxdeg/kChunk); size the grid generously and let it stride
-        launch_search_expand<WD, WB>(ix, c, a, (int64_t)nslots * 2, sep, lists[nxt], s);
+        launch_search_expand<WD, WB>(ix, c, a, (int64_t)ntasks, (uint32_t)(L + 2), lists[cur], s);
+        qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
+        cudaMemsetAsync(cnt + kCntTasks, 0, sizeof(uint32_t), s);
+        // the slot count is on the device: a fixed grid strides over it
+        k_search_finalize<<<(unsigned)(num_sms() * 8), kBlock, 0, s>>>(a, lists[cur], cnt + kCntTasks);
+        ++ix->launches;
         qt_end(ix, c, s);
-        cur = nxt;
     }
     *overflowed = h[kCntOverflow] != 0;
     qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
@@ -655,6 +797,7 @@ static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int
     SearchArgs a = search_args(ix, c, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
     const uint32_t *n_und = c->d_counts + kCntUnd;
     GridBarrier bar = grid_barrier_at(c->d_counts);
+    if ((ix->opt.flags & DBL_FLAG_TIMING) && c == ix->qc) bar.trace = ix->d_trace;
     uint32_t *status = c->d_status;
     int64_t max_levels = (int64_t)ix->n + 2;
     void *args[] = {&a, &ps, &n_und, &bar, &status, &max_levels};
@@ -691,6 +834,7 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     // (cooperative grids of concurrent contexts would compete for residency)
     if ((ix->opt.flags & DBL_FLAG_PERSISTENT) && c == ix->qc) {
         switch (ix->opt.team) {
+        case 1: st = launch_search_persistent<WD, WB, 1>(ix, c, u, v, ans, code, s); break;
         case 4: st = launch_search_persistent<WD, WB, 4>(ix, c, u, v, ans, code, s); break;
         case 16:
         case 32: st = launch_search_persistent<WD, WB, 16>(ix, c, u, v, ans, code, s); break;

@@ -1,7 +1,8 @@
 // Autotuner: picks the frontier schedule for this graph by measurement.
 //
 // Candidates are the team width (lanes that share one frontier task of up to
-// kChunk edges: 4, 8, 16 or 32) and whether frontier loops run as one
+// kChunk edges: 4, 8, 16 or 32; or 1: one task per lane, the warp walking the
+// concatenation of its tasks' edges) and whether frontier loops run as one
 // persistent cooperative launch or level by level.  Each candidate runs the
 // caller's sample insertion batch and query batch from the same snapshot
 // (slot 3), timed with CUDA events on the stream; the index is restored after
@@ -12,8 +13,8 @@
 
 extern "C" dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent)
 {
-    if (!ix || (team != 4 && team != 8 && team != 16 && team != 32))
-        return dbl::fail(ix, DBL_ERR_INVALID, "set_schedule: team must be 4, 8, 16 or 32");
+    if (!ix || (team != 1 && team != 4 && team != 8 && team != 16 && team != 32))
+        return dbl::fail(ix, DBL_ERR_INVALID, "set_schedule: team must be 1, 4, 8, 16 or 32");
     ix->opt.team = team;
     ix->opt.flags = persistent ? (ix->opt.flags | DBL_FLAG_PERSISTENT) : (ix->opt.flags & ~DBL_FLAG_PERSISTENT);
     return DBL_OK;
@@ -29,7 +30,8 @@ extern "C" dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int3
     cudaStream_t s = (cudaStream_t)stream;
     dbl_status st = dbl_snapshot(ix, 3, stream);
     if (st) return st;
-    const int teams[4] = {4, 8, 16, 32};
+    constexpr int kTeams = 5;
+    const int teams[kTeams] = {1, 4, 8, 16, 32};
     const int32_t flags0 = ix->opt.flags, team0 = ix->opt.team;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -37,7 +39,7 @@ extern "C" dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int3
     double best = 1e300;
     int best_team = team0, best_persistent = (flags0 & DBL_FLAG_PERSISTENT) ? 1 : 0;
     for (int p = 0; p < 2 && !st; ++p) {
-        for (int t = 0; t < 4 && !st; ++t) {
+        for (int t = 0; t < kTeams && !st; ++t) {
             ix->opt.team = teams[t];
             ix->opt.flags = (flags0 & ~(DBL_FLAG_PERSISTENT | DBL_FLAG_ASYNC | DBL_FLAG_TIMING)) |
                             (p ? DBL_FLAG_PERSISTENT : 0);
@@ -54,7 +56,7 @@ extern "C" dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int3
                 if (r) total += ms;
             }
             const double avg = total / trials;
-            if (report) report[p * 4 + t] = avg;
+            if (report) report[p * kTeams + t] = avg;
             if (!st && avg < best) {
                 best = avg;
                 best_team = teams[t];
@@ -70,9 +72,9 @@ extern "C" dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int3
     if (st) return st;
     if (rs) return rs;
     if (report) {
-        report[8] = best_team;
-        report[9] = best_persistent;
-        report[10] = best;
+        report[10] = best_team;
+        report[11] = best_persistent;
+        report[12] = best;
     }
     return dbl::read_status(ix, s);
 }

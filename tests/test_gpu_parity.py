@@ -128,7 +128,7 @@ def test_widths_random_selection(k, kprime):
     assert_queries(ix, ref, qu, qv, f"k={k} k'={kprime}")
 
 
-@pytest.mark.parametrize("team", [4, 8, 16, 32])
+@pytest.mark.parametrize("team", [1, 4, 8, 16, 32])
 def test_team_sizes(team, tiny):
     ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, team=team)
     ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
@@ -308,10 +308,11 @@ def test_torch_and_default_allocators_agree(tiny):
 # ---------------------------------------------------------------- persistent / async forms
 @pytest.mark.parametrize("flags", [dbl.FLAG_PERSISTENT, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
 @pytest.mark.parametrize("k", [64, 128])
-def test_persistent_forms_match_oracle(tiny, flags, k):
+@pytest.mark.parametrize("team", [1, 8])
+def test_persistent_forms_match_oracle(tiny, flags, k, team):
     """One cooperative launch per propagation and per query batch; with
     FLAG_ASYNC no call waits for the device."""
-    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), k, 64, flags=flags)
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), k, 64, flags=flags, team=team)
     ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], k, 64).build()
     ix.sync()
     assert_labels(ix, ref, "persistent build")
@@ -345,3 +346,28 @@ def test_async_invalid_batch_is_latched(tiny):
     ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
     ref.insert_edges(tiny["ins_src"][:500], tiny["ins_dst"][:500])
     assert_labels(ix, ref, "after the latched error was read")
+
+
+# ---------------------------------------------------------------- autotuner
+def test_autotune_restores_index_and_keeps_parity(tiny, tmp_path):
+    """dbl_autotune times every schedule from one snapshot and restores the
+    index: labels after tuning equal the labels before, the chosen schedule is
+    one of the candidates, a cached result is applied without re-measuring,
+    and the tuned index still matches the oracle."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    before = labels_np(ix)
+    cache = str(tmp_path / "sched.json")
+    out = ix.autotune(D(s[:1000]), D(d[:1000]), D(tiny["q_u"][:20000]), D(tiny["q_v"][:20000]), trials=1, cache=cache)
+    assert out["team"] in (1, 4, 8, 16, 32) and out["best_ms"] > 0
+    assert len(out["level_ms"]) == 5 and len(out["persistent_ms"]) == 5
+    for a, b in zip(labels_np(ix), before):
+        assert np.array_equal(a, b), "autotune changed the index"
+    again = ix.autotune(D(s[:1000]), D(d[:1000]), D(tiny["q_u"][:100]), D(tiny["q_v"][:100]), cache=cache)
+    assert again.get("cached") and again["team"] == out["team"]
+    ix.insert_edges(D(s), D(d))
+    ref.insert_edges(s, d)
+    ix.sync()
+    assert_labels(ix, ref, "after autotune")
+    assert_queries(ix, ref, tiny["q_u"][:20000], tiny["q_v"][:20000], "after autotune")

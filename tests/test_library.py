@@ -41,7 +41,7 @@ def test_default_options_and_errors_without_gpu(lib):
     import ctypes
     opt = dbl._Options()
     lib.dbl_default_options(ctypes.byref(opt))
-    assert opt.team == 8 and opt.bfs_words == 16 and opt.flags == 0
+    assert opt.team == 1 and opt.bfs_words == 16 and opt.flags == 0
     # invalid arguments are rejected before any device work
     h = ctypes.c_void_p()
     assert lib.dbl_build(None, None, 64, None, None, 64, None, None, ctypes.byref(h)) == dbl.DBL_ERR_INVALID
