@@ -344,6 +344,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     }
     std::memset(ix->h_pinned, 0, 64 * sizeof(uint32_t));
     ix->front_cap = 2 * ((int64_t)n + (int64_t)(m + ix->edge_cap) / kChunk + 64);
+    ix->wpd = ((int64_t)n + 31) / 32 + 1;  // + 1: never zero words
     if ((st = A((void **)&ix->out_ptr, 4 * (n + 1))) || (st = A((void **)&ix->out_col, 4 * m)) ||
         (st = A((void **)&ix->in_ptr, 4 * (n + 1))) || (st = A((void **)&ix->in_col, 4 * m)) ||
         (st = A((void **)&ix->ovo, 12 * n)) || (st = A((void **)&ix->ovi, 12 * n)) ||
@@ -351,10 +352,10 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
         (st = A((void **)&ix->rec, 8 * n * ix->rw)) || (st = A((void **)&ix->landmarks, 4 * (size_t)k)) ||
         (st = A((void **)&ix->leaf_bucket, 4 * n)) || (st = A((void **)&ix->leaf_role, n)) ||
-        (st = A((void **)&ix->stamp, 16 * n)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
+        (st = A((void **)&ix->mark, 16 * (size_t)ix->wpd)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
         (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
-        (st = A((void **)&ix->d_epoch, 16)) || (st = A((void **)&ix->d_trace, 8 * 64)) ||
+        (st = A((void **)&ix->d_trace, 8 * 64)) ||
         (st = A((void **)&ix->ins_cnt, 8 * n))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
@@ -363,11 +364,10 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     cudaMemsetAsync(ix->ovo, 0, 12 * n, s);
     cudaMemsetAsync(ix->ovi, 0, 12 * n, s);
     cudaMemsetAsync(ix->d_pool_top, 0, 16, s);
-    cudaMemsetAsync(ix->stamp, 0, 16 * n, s);
+    cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
     cudaMemsetAsync(ix->d_status, 0, 16, s);
     cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);
-    cudaMemsetAsync(ix->d_epoch, 0, 16, s);
     cudaMemsetAsync(ix->d_trace, 0, 8 * 64, s);
     cudaMemsetAsync(ix->ins_cnt, 0, 8 * n, s);
 
@@ -611,6 +611,9 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     cudaMemcpyAsync(ix->d_pool_top, sn.top.p, 16, cudaMemcpyDeviceToDevice, s);
     cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
+    // the frontier bitmaps are empty after every complete propagation; an
+    // aborted one (the index was poisoned) may have left bits behind
+    cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
     ix->edges_stored = sn.edges_stored;
     ix->poisoned = false;
     cudaError_t e = cudaGetLastError();

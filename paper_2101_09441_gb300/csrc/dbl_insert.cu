@@ -152,7 +152,6 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
                                                      uint64_t *rec, FrontierOut f, unsigned long long *stats)
 {
     if (status_set(f.status)) return;
-    resolve_epoch(f);
     seed_edges<HS, WD>(src, dst, b, g, rec, f, stats);
 }
 
@@ -245,7 +244,9 @@ struct InsArgs {
     uint64_t *rec, *f0, *f1;
     uint32_t *c3;
     int64_t cap;
-    unsigned long long *stamp, *epoch_base, *stats;
+    uint32_t *mark;  // frontier bitmaps, parity 0 then 1 (2 * wpd words each)
+    int64_t wpd;
+    unsigned long long *stats;
     uint32_t *status;
 };
 
@@ -256,7 +257,6 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
     const int lane = threadIdx.x & 31;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
-    const unsigned long long base = *(const volatile unsigned long long *)a.epoch_base;
     // P0: validate; zero the level counters
     if (!ld_volatile_u32(a.status)) {
         for (int64_t i = t0; i < a.b; i += nt)
@@ -291,7 +291,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
     // P2: grow the segments that overflowed (one pool reservation per block and
     // direction), and enqueue the seeds' changed endpoints
     {
-        FrontierOut f{a.f0, a.c3, a.cap, a.stamp, base + 1, a.status};
+        FrontierOut f{a.f0, a.c3, a.cap, a.mark, a.wpd, a.status};  // level-0 frontier: parity 0
         __shared__ unsigned long long s_woff[32];  // per-warp growth, then its offset in the block's range
         __shared__ unsigned long long s_gbase;
         const int warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
@@ -363,7 +363,6 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
     if (!gs.sync(a.status)) return;
     // P4: propagation levels
     const int64_t warp0 = t0 >> 5, nwarps = nt >> 5;
-    unsigned long long epoch = base + 1;
     int64_t L = 0;
     for (;; ++L) {
         const uint32_t ntk = ld_volatile_u32(a.c3 + L % 3);
@@ -372,16 +371,14 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             set_status(a.status, DBL_ERR_TIMEOUT);
             break;
         }
-        ++epoch;
         if (leader) a.c3[(L + 2) % 3] = 0;
-        FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, a.stamp, epoch, a.status};
-        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, f, a.stats, warp0, nwarps, st);
+        uint32_t *cur_mark = a.mark + (size_t)(L & 1) * 2 * (size_t)a.wpd;
+        uint32_t *nxt_mark = a.mark + (size_t)((L + 1) & 1) * 2 * (size_t)a.wpd;
+        FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, nxt_mark, a.wpd, a.status};
+        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, cur_mark, f, a.stats, warp0, nwarps, st);
         if (!gs.sync(a.status)) break;
     }
-    if (leader) {
-        a.stats[8] += (unsigned long long)L;
-        *a.epoch_base = base + (unsigned long long)L + 3;
-    }
+    if (leader) a.stats[8] += (unsigned long long)L;
 }
 
 template <int HS, int WD, int TEAM>
@@ -446,8 +443,8 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     a.f1 = ix->front[1];
     a.c3 = ix->d_counts + kCntP0;
     a.cap = ix->front_cap;
-    a.stamp = ix->stamp;
-    a.epoch_base = ix->d_epoch;
+    a.mark = ix->mark;
+    a.wpd = ix->wpd;
     a.stats = ix->d_stats;
     a.status = ix->d_status;
     tbegin(ix, DBL_KERNEL_PROPAGATE, s);
@@ -540,7 +537,7 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     ix->edges_stored += b;
     atomic_add_host_stat(ix, 15, (uint64_t)b, s);
     // 3. seed the repair frontier, then propagate to the fixpoint
-    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, 0, ix->d_status, ix->d_epoch, 1};
+    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, mark_of(ix, 0), ix->wpd, ix->d_status};
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     const DevGraph g = dev_graph(ix);
     tbegin(ix, DBL_KERNEL_INSERT_SEED, s);

@@ -152,11 +152,11 @@ struct dbl_index {
     uint8_t *leaf_role = nullptr;
 
     // frontier scratch
-    unsigned long long *stamp = nullptr;  // [2][n] enqueue epoch per direction
+    uint32_t *mark = nullptr;  // [2 parities][2 directions][wpd] frontier dedup bitmaps (see dbl_frontier.cuh)
+    int64_t wpd = 0;           // bitmap words per direction: ceil(n / 32)
     uint64_t *front[2] = {nullptr, nullptr};
     int64_t front_cap = 0;
     uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
-    unsigned long long *d_epoch = nullptr;  // device base of the frontier epochs (see dbl_frontier.cuh)
 
     // insertion scratch
     int32_t *ins_cnt = nullptr;       // [2][n] per-vertex batch counts
@@ -252,6 +252,12 @@ size_t persist_state_bytes();  // dbl_query.cu
 // bracket the launches between tbegin and tend (no-op without DBL_FLAG_TIMING)
 void tbegin(dbl_index *ix, int kind, cudaStream_t s);
 void tend(dbl_index *ix, cudaStream_t s);
+
+// Frontier dedup bitmaps of level parity p: [2 directions][wpd words].
+inline uint32_t *mark_of(const dbl_index *ix, int parity)
+{
+    return ix->mark + (size_t)parity * 2 * (size_t)ix->wpd;
+}
 
 inline DevGraph dev_graph(const dbl_index *ix)
 {

@@ -35,7 +35,7 @@ __device__ __forceinline__ int flat_owner(uint32_t excl, uint32_t e)
 // mix of task sizes.
 template <int HS>
 __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
-                                                  uint32_t ntasks, const FrontierOut &f,
+                                                  uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                                   unsigned long long *stats, int64_t warp, int64_t nwarps,
                                                   const Stage &st)
 {
@@ -56,6 +56,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
             v = (int32_t)(uint32_t)tk;
             const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
             dir = (int)(tk >> 63);
+            if (chunk == 0) mark_clear(cur_mark, f.wpd, dir, v);
             const AdjRange r = adj_of(g, dir, v);
             b0 = r.b0;
             bd = r.bd;
@@ -111,17 +112,19 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
 
 // One level of label propagation over `ntasks` tasks, processed by warps
 // [warp0, warp0 + nwarps*k) in steps of nwarps.  Every lane of a warp runs the
-// same number of iterations (warp_enqueue needs the whole warp).
+// same number of iterations (warp_enqueue needs the whole warp).  The tasks'
+// vertices are cleared from cur_mark, the bitmap their frontier was marked in.
 //
 // New tasks go through the block's stage (stage_enqueue); the stage is flushed
 // at the end, so every thread of the block must call this.
 template <int HS, int TEAM>
 __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
-                                             uint32_t ntasks, const FrontierOut &f, unsigned long long *stats,
-                                             int64_t warp0, int64_t nwarps, const Stage &st)
+                                             uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
+                                             unsigned long long *stats, int64_t warp0, int64_t nwarps,
+                                             const Stage &st)
 {
     if constexpr (TEAM == 1) {
-        expand_level_flat<HS>(g, rec, tasks, ntasks, f, stats, warp0, nwarps, st);
+        expand_level_flat<HS>(g, rec, tasks, ntasks, cur_mark, f, stats, warp0, nwarps, st);
     } else {
         constexpr int TPW = 32 / TEAM;
         constexpr int RW = 2 * HS;
@@ -143,6 +146,7 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                 v = (int32_t)(uint32_t)tk;
                 const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
                 dir = (int)(tk >> 63);
+                if (chunk == 0 && tl == 0) mark_clear(cur_mark, f.wpd, dir, v);
                 r = adj_of(g, dir, v);
                 const int32_t d = r.bd + r.od;
                 lo = (int32_t)chunk * kChunk;

@@ -156,7 +156,6 @@ __global__ void k_cov_filter(const int32_t *u, const int32_t *v, const uint8_t *
 __global__ void k_cov_seed(const int32_t *u, const int32_t *v, int64_t j0, int64_t j1, int32_t n, uint64_t *crec,
                            DevGraph g, FrontierOut f, uint32_t *status)
 {
-    resolve_epoch(f);
     for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < j1; j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = u[j], b = v[j];
         if ((uint32_t)a >= (uint32_t)n || (uint32_t)b >= (uint32_t)n) {
@@ -224,8 +223,7 @@ dbl_status coverage(dbl_index *ix, const int32_t *u_in, const int32_t *v_in, con
     for (int64_t j0 = 0; j0 < pairs && !st; j0 += kCovPairs) {
         const int64_t j1 = j0 + kCovPairs < pairs ? j0 + kCovPairs : pairs;
         cudaMemsetAsync(crec, 0, bytes, s);
-        FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, 0, ix->d_status,
-                      ix->d_epoch, 1};
+        FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, mark_of(ix, 0), ix->wpd, ix->d_status};
         cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
         k_cov_seed<<<(unsigned)((j1 - j0 + kBlock - 1) / kBlock), kBlock, 0, s>>>(u, v, j0, j1, ix->n, crec,
                                                                                    dev_graph(ix), f, ix->d_status);

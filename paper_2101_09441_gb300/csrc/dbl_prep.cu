@@ -440,7 +440,6 @@ __global__ void k_seed_leaves(const int32_t *bucket, const uint8_t *role, int32_
 // every vertex with a non-zero half joins the frontier in that direction
 __global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, DevGraph g, FrontierOut f)
 {
-    resolve_epoch(f);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += stride) {
         int64_t v = base + threadIdx.x;
@@ -463,7 +462,7 @@ __global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, Dev
 
 void launch_seed_frontier(dbl_index *ix, cudaStream_t s)
 {
-    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, ix->stamp, 0, ix->d_status, ix->d_epoch, 1};
+    FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, mark_of(ix, 0), ix->wpd, ix->d_status};
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     int64_t blocks = ((int64_t)ix->n + kBlock - 1) / kBlock;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;

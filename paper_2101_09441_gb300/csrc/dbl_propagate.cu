@@ -21,12 +21,11 @@ namespace dbl {
 
 template <int HS, int TEAM>
 __global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, const uint64_t *tasks,
-                                                   const uint32_t *ntasks_p, FrontierOut f,
+                                                   const uint32_t *ntasks_p, uint32_t *cur_mark, FrontierOut f,
                                                    unsigned long long *stats)
 {
     DBL_BLOCK_STAGE(st);
-    resolve_epoch(f);
-    expand_level<HS, TEAM>(g, rec, tasks, *ntasks_p, f, stats,
+    expand_level<HS, TEAM>(g, rec, tasks, *ntasks_p, cur_mark, f, stats,
                            ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                            ((int64_t)gridDim.x * blockDim.x) >> 5, st);
 }
@@ -43,7 +42,8 @@ static void launch_expand(dbl_index *ix, int cur, uint32_t ntasks, const Frontie
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_expand<HS, TEAM><<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), ix->rec, ix->front[cur],
-                                                           ix->d_counts + kCntFront0 + cur, f, ix->d_stats);
+                                                           ix->d_counts + kCntFront0 + cur, mark_of(ix, cur), f,
+                                                           ix->d_stats);
     ++ix->launches;
 }
 
@@ -104,9 +104,9 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
             return fail(ix, DBL_ERR_TIMEOUT, "propagate: level bound exceeded");
         }
         const int nxt = cur ^ 1;
-        // the seed level used base+1; level L fills base+1+L
-        FrontierOut f{ix->front[nxt], ix->d_counts + kCntFront0 + nxt, ix->front_cap, ix->stamp, 0,
-                      ix->d_status, ix->d_epoch, (unsigned long long)(1 + levels)};
+        // frontier buffer i is marked in bitmap parity i
+        FrontierOut f{ix->front[nxt], ix->d_counts + kCntFront0 + nxt, ix->front_cap, mark_of(ix, nxt), ix->wpd,
+                      ix->d_status};
         cudaMemsetAsync(ix->d_counts + kCntFront0 + nxt, 0, sizeof(uint32_t), s);
         tbegin(ix, DBL_KERNEL_PROPAGATE, s);
         switch (ix->hs) {
@@ -127,14 +127,10 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
     if (cur != 0) {
         cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     }
-    // every epoch of this propagation is used: move the base past them
-    k_epoch_advance<<<1, 1, 0, s>>>(ix->d_epoch, (unsigned long long)levels + 3);
-    ++ix->launches;
     atomic_add_host_stat(ix, 8, (uint64_t)levels, s);
     return DBL_OK;
 }
 
-__global__ void k_epoch_advance(unsigned long long *base, unsigned long long by) { *base += by; }
 
 // ---------------------------------------------------------------------------
 // Persistent form: one cooperative launch runs every level.  Level L reads
@@ -146,16 +142,13 @@ __global__ void k_epoch_advance(unsigned long long *base, unsigned long long by)
 template <int HS, int TEAM>
 __global__ void __launch_bounds__(pblock_of(HS), 1)
     k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0, uint64_t *f1, uint32_t *c3, int64_t cap,
-                           unsigned long long *stamp, unsigned long long *epoch_base, uint32_t *status,
-                           unsigned long long *stats, GridBarrier bar, int64_t max_levels)
+                           uint32_t *mark, int64_t wpd, uint32_t *status, unsigned long long *stats,
+                           GridBarrier bar, int64_t max_levels)
 {
     GridSync gs(bar);
     DBL_BLOCK_STAGE(st);
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the seed level used base+1; level L fills base+2+L
-    const unsigned long long base = *(const volatile unsigned long long *)epoch_base;
-    unsigned long long epoch = base + 1;
     int64_t L = 0;
     for (;; ++L) {
         const uint32_t nt = ld_volatile_u32(c3 + L % 3);
@@ -164,17 +157,16 @@ __global__ void __launch_bounds__(pblock_of(HS), 1)
             set_status(status, DBL_ERR_TIMEOUT);
             break;
         }
-        ++epoch;
         if (blockIdx.x == 0 && threadIdx.x == 0) c3[(L + 2) % 3] = 0;
-        FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, stamp, epoch, status};
-        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, f, stats, warp0, nwarps, st);
+        uint32_t *cur_mark = mark + (size_t)(L & 1) * 2 * (size_t)wpd;
+        uint32_t *nxt_mark = mark + (size_t)((L + 1) & 1) * 2 * (size_t)wpd;
+        FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, nxt_mark, wpd, status};
+        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, cur_mark, f, stats, warp0, nwarps, st);
         if (!gs.sync(status)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         stats[8] += (unsigned long long)L;
         c3[L % 3] = 0;
-        // every block read the base at its start, long before this point
-        *epoch_base = base + (unsigned long long)L + 3;
     }
     gs.leave();
 }
@@ -190,14 +182,14 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
     uint64_t *f0 = ix->front[0], *f1 = ix->front[1];
     uint32_t *c3 = ix->d_counts + kCntP0;
     int64_t cap = ix->front_cap;
-    unsigned long long *stamp = ix->stamp;
-    unsigned long long *epoch_base = ix->d_epoch;
+    uint32_t *mark = ix->mark;
+    int64_t wpd = ix->wpd;
     uint32_t *status = ix->d_status;
     unsigned long long *stats = ix->d_stats;
     GridBarrier bar = grid_barrier_at(ix->d_counts);
     if (ix->opt.flags & DBL_FLAG_TIMING) bar.trace = ix->d_trace;
     int64_t max_levels = (int64_t)ix->n + 2;
-    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &stamp, &epoch_base, &status, &stats, &bar, &max_levels};
+    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &mark, &wpd, &status, &stats, &bar, &max_levels};
     dim3 grid((unsigned)num_sms()), block(pblock_of(HS));
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_propagate_persistent<HS, TEAM>, grid, block, args, 0, s);
     ++ix->launches;
