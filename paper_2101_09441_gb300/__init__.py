@@ -371,6 +371,11 @@ class DBLIndex:
     def _apply_schedule(self, team: int, persistent: bool):
         self._check(lib().dbl_set_schedule(self._h, int(team), int(persistent)))
 
+    def set_schedule(self, team: int, persistent: bool):
+        """dbl_set_schedule: team width (1, 4, 8, 16, 32) and persistent or
+        level-by-level frontier loops."""
+        self._apply_schedule(team, persistent)
+
     # ------------------------------------------------------------------ learned scorer
     def features(self, stream=None):
         """dbl_features: bf16 [n, 16] (log1p-scaled per-vertex counts)."""
