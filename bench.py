@@ -292,6 +292,15 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     res = {"build_s": build_s}
     if build_t:
         res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
+    if flags & dbl.FLAG_PERSISTENT and not args.no_autotune:
+        # autotuned frontier schedule (sample: the first insertion batch and 1M
+        # queries); the persistent forms keep the fastest persistent candidate
+        a, b = batches[0]
+        nq = min(1_000_000, Q)
+        tune = ix.autotune(I.src[a:b], I.dst[a:b], I.qu[:nq], I.qv[:nq], trials=2)
+        team = min(tune["persistent_ms"], key=tune["persistent_ms"].get)
+        ix.set_schedule(team, persistent=True)
+        res["autotune"] = {"team": team, "persistent_ms": tune["persistent_ms"], "level_ms": tune["level_ms"]}
     use_graph = name in ("graph", "learned")
     step = make_step(ix, I, batches, events=not use_graph)
     for _ in range(args.warmup):
@@ -468,7 +477,8 @@ def main():
     ap.add_argument("--batch", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--kprime", type=int, default=64)
-    ap.add_argument("--team", type=int, default=8)
+    ap.add_argument("--team", type=int, default=0, help="frontier team width; 0: library default (1)")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the persistent forms")
     ap.add_argument("--forms", default="plain,batched,graph", help="comparison forms to time besides the headline")
     ap.add_argument("--train-queries", type=int, default=1_000_000)
     ap.add_argument("--train-steps", type=int, default=400)

@@ -117,7 +117,7 @@ typedef struct {
                               one task per lane with the warp walking its
                               tasks' edges 32 at a time; 0: 1 */
     int32_t query_unroll;  /* query pairs per thread in the label test (1, 2, 4);
-                              0: 4, 2 or 1 for 32-, 64- or 128-byte records */
+                              0: 2, or 1 for 128-byte records */
     int32_t reserved[6];
 } dbl_options;
 

@@ -30,11 +30,13 @@ namespace dbl {
 __host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
 
 // ------------------------------------------------------------ label test
-// Each thread takes QPT queries (QPT = 4 for 32-byte records) and issues all
+// Each thread takes QPT queries (default 2) and issues all
 // of their record loads before using any, so that many DRAM sectors are in
 // flight per warp; answers and codes are written coalesced, the deciding
-// rules are counted with warp ballots, and undecided pairs are compacted with
-// one atomic per warp.
+// rules are counted per thread, and undecided pairs are collected in a
+// shared-memory stage and appended to the undecided list with one atomic per
+// block (one per warp put ~10^5 atomics on a single word: a third of the
+// kernel's time).
 template <int WD, int WB, int QPT>
 __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const int32_t *qv, int64_t q,
                                                         const uint64_t *rec, int32_t n, uint8_t *ans,
@@ -44,7 +46,9 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
     const int lane = threadIdx.x & 31;
-    unsigned int counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // kept by lane 0
+    DBL_BLOCK_ISTAGE(ust);
+    const IList ulist{und, n_und, q, nullptr};
+    unsigned int counts[6] = {0, 0, 0, 0, 0, 0};  // per thread, by deciding rule (constant indices only)
     const int64_t tile = (int64_t)blockDim.x * QPT;
     const int64_t stride = (int64_t)gridDim.x * tile;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < q; base += stride) {
@@ -107,21 +111,16 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
                 if (code) __stcs(code + i, c);
             }
 #pragma unroll
-            for (int r = 1; r < 6; ++r) counts[r] += __popc(__ballot_sync(kFull, live[j] && c == r));
-            const unsigned bal = __ballot_sync(kFull, undecided);
-            if (bal) {
-                uint32_t b0 = 0;
-                const int leader = __ffs(bal) - 1;
-                if (lane == leader) b0 = atomicAdd(n_und, (uint32_t)__popc(bal));
-                b0 = __shfl_sync(kFull, b0, leader);
-                if (undecided) und[b0 + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
-            }
+            for (int r = 1; r < 6; ++r) counts[r] += (live[j] && c == r) ? 1u : 0u;
+            if (undecided) istage_push(ust, (int32_t)i, ulist);
         }
     }
-    if (lane == 0)
+    istage_flush(ust, ulist);
 #pragma unroll
-        for (int r = 1; r < 6; ++r)
-            if (counts[r]) atomicAdd(stats + r, (unsigned long long)counts[r]);
+    for (int r = 1; r < 6; ++r) {
+        const unsigned int t = __reduce_add_sync(kFull, counts[r]);
+        if (lane == 0 && t) atomicAdd(stats + r, (unsigned long long)t);
+    }
 }
 
 // ------------------------------------------------------------ search
@@ -818,9 +817,10 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     if (st) return st;
     uint32_t *cnt = c->d_counts;
     cudaMemsetAsync(cnt + kCntUnd, 0, sizeof(uint32_t), s);
-    // pairs per thread: option, else 4 for 32-byte records, 2 for 64, 1 for 128
+    // pairs per thread: option, else 2 (1 for 128-byte records); measured on
+    // 32-byte records, 2 beats 4 (more resident warps) and 1 (fewer loads in flight)
     constexpr int HS = hs_of(WD + WB);
-    int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 2 ? 4 : (HS == 4 ? 2 : 1));
+    int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 8 ? 1 : 2);
     int64_t blocks = (q + (int64_t)kBlock * qpt - 1) / ((int64_t)kBlock * qpt);
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
