@@ -352,8 +352,9 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
         (st = A((void **)&ix->rec, 8 * n * ix->rw)) || (st = A((void **)&ix->landmarks, 4 * (size_t)k)) ||
         (st = A((void **)&ix->leaf_bucket, 4 * n)) || (st = A((void **)&ix->leaf_role, n)) ||
-        (st = A((void **)&ix->mark, 16 * (size_t)ix->wpd)) || (st = A((void **)&ix->front[0], 8 * (size_t)ix->front_cap)) ||
-        (st = A((void **)&ix->front[1], 8 * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
+        (st = A((void **)&ix->mark, 16 * (size_t)ix->wpd)) ||
+        (st = A((void **)&ix->front[0], sizeof(FTask) * (size_t)ix->front_cap)) ||
+        (st = A((void **)&ix->front[1], sizeof(FTask) * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
         (st = A((void **)&ix->d_trace, 8 * 64)) ||
         (st = A((void **)&ix->ins_cnt, 8 * n))) {

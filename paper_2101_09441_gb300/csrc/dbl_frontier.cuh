@@ -17,7 +17,7 @@
 namespace dbl {
 
 struct FrontierOut {
-    uint64_t *tasks;
+    FTask *tasks;
     uint32_t *count;
     int64_t cap;
     uint32_t *mark;  // dedup bitmap of the frontier being filled: [2 directions][wpd words]
@@ -53,8 +53,10 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
 {
     const int lane = threadIdx.x & 31;
     uint32_t nchunks = 0;
+    AdjRange r{0, 0, 0, 0};
     if (want) {
-        const int32_t d = deg_of(g, dir, x);
+        r = adj_of(g, dir, x);
+        const int32_t d = r.bd + r.od;
         if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     }
     uint32_t incl = nchunks;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
     base = __shfl_sync(kFull, base, 31);
     uint32_t pos = base + incl - nchunks;
     for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
-        if ((int64_t)pos < f.cap) f.tasks[pos] = make_task(x, c, dir);
+        if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, make_ftask(x, dir, (int32_t)c, r));
         else set_status(f.status, DBL_ERR_CAPACITY);
     }
 }
@@ -81,11 +83,11 @@ __device__ __forceinline__ void warp_enqueue(bool want, int32_t x, int dir, cons
 // atomicAdd, so a level costs one global reservation per block instead of one
 // per warp and iteration (all of them on the same word).  A warp whose tasks
 // do not fit in the stage reserves global slots itself.
-constexpr uint32_t kStage = 2048;
+constexpr uint32_t kStage = 1024;  // 16 KB of tasks per block
 
 struct Stage {
-    uint64_t *tasks;  // shared, kStage entries
-    uint32_t *n;      // shared, entries used
+    FTask *tasks;  // shared, kStage entries
+    uint32_t *n;   // shared, entries used
 };
 
 __device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
@@ -93,8 +95,10 @@ __device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, con
 {
     const int lane = threadIdx.x & 31;
     uint32_t nchunks = 0;
+    AdjRange r{0, 0, 0, 0};
     if (want) {
-        const int32_t d = deg_of(g, dir, x);
+        r = adj_of(g, dir, x);
+        const int32_t d = r.bd + r.od;
         if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     }
     uint32_t incl = nchunks;
@@ -123,9 +127,9 @@ __device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, con
     global = __shfl_sync(kFull, global, 31);
     uint32_t pos = base + incl - nchunks;
     for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
-        const uint64_t t = make_task(x, c, dir);
+        const FTask t = make_ftask(x, dir, (int32_t)c, r);
         if (!global) st.tasks[pos] = t;
-        else if ((int64_t)pos < f.cap) f.tasks[pos] = t;
+        else if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, t);
         else set_status(f.status, DBL_ERR_CAPACITY);
     }
 }
@@ -143,7 +147,7 @@ __device__ __forceinline__ void stage_flush(const FrontierOut &f, const Stage &s
         const uint32_t b = s_base;
         for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
             const uint32_t pos = b + i;
-            if ((int64_t)pos < f.cap) f.tasks[pos] = st.tasks[i];
+            if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, st.tasks[i]);
             else set_status(f.status, DBL_ERR_CAPACITY);
         }
     }
@@ -154,7 +158,7 @@ __device__ __forceinline__ void stage_flush(const FrontierOut &f, const Stage &s
 
 // Declares this block's stage (shared memory) and empties it; every thread calls it.
 #define DBL_BLOCK_STAGE(name)                                                                                         \
-    __shared__ uint64_t name##_tasks[::dbl::kStage];                                                                  \
+    __shared__ ::dbl::FTask name##_tasks[::dbl::kStage];                                                              \
     __shared__ uint32_t name##_n;                                                                                     \
     if (threadIdx.x == 0) name##_n = 0;                                                                               \
     __syncthreads();                                                                                                  \
@@ -254,12 +258,13 @@ __device__ __forceinline__ uint32_t block_reserve(uint32_t mine, uint32_t *gcoun
 // Same, for callers whose loop is not warp-uniform: uses the active mask.
 __device__ __forceinline__ void any_enqueue(int32_t x, int dir, const DevGraph &g, const FrontierOut &f)
 {
-    const int32_t d = deg_of(g, dir, x);
+    const AdjRange r = adj_of(g, dir, x);
+    const int32_t d = r.bd + r.od;
     if (!mark_new(f, dir, x, d)) return;
     const uint32_t nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     uint32_t pos = atomicAdd(f.count, nchunks);
     for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
-        if ((int64_t)pos < f.cap) f.tasks[pos] = make_task(x, c, dir);
+        if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, make_ftask(x, dir, (int32_t)c, r));
         else set_status(f.status, DBL_ERR_CAPACITY);
     }
 }

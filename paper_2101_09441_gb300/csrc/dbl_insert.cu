@@ -221,11 +221,12 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
 //      length (atomicAdd on len, so no commit pass is needed) and applies its
 //      seed (skip test, endpoint ORs); whether fwd(v) / bwd(u) gained bits is
 //      kept in bit 30 of the edge's slot words (slots are < 2^29)
-//   P2 grow + enqueue: the one edge whose slot equals the old capacity grows
-//      the segment (copying the old capacity's worth of entries; the batch's
-//      own entries are written after the barrier); the changed endpoints form
-//      the level-0 frontier, with chunk counts from the now final lengths
-//   P3 write the batch's ids into their slots
+//   P2 grow: the one edge whose slot equals the old capacity grows the
+//      segment (copying the old capacity's worth of entries; the batch's own
+//      entries are written after the barrier)
+//   P3 write + enqueue: the batch's ids go into their slots, and the changed
+//      endpoints form the level-0 frontier (tasks resolved against the final
+//      segment offsets and lengths)
 //   P4 propagation levels, as in k_propagate_persistent.
 // Seeding before the appended edges are visible is sound: seeds read and OR
 // labels only, and the first level that walks adjacency runs after P3.  A
@@ -241,7 +242,8 @@ struct InsArgs {
     int64_t pool_cap;
     int32_t *slot_out, *slot_in;
     DevGraph g;
-    uint64_t *rec, *f0, *f1;
+    uint64_t *rec;
+    FTask *f0, *f1;
     uint32_t *c3;
     int64_t cap;
     uint32_t *mark;  // frontier bitmaps, parity 0 then 1 (2 * wpd words each)
@@ -288,77 +290,96 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         warp_stat_add(a.stats, 11, applied);
     }
     if (!gs.sync(a.status)) return;
-    // P2: grow the segments that overflowed (one pool reservation per block and
-    // direction), and enqueue the seeds' changed endpoints
+    // P2: grow the segments that overflowed; both directions' metadata are
+    // read in one round trip and the pool is reserved once per block for both
     {
-        FrontierOut f{a.f0, a.c3, a.cap, a.mark, a.wpd, a.status};  // level-0 frontier: parity 0
-        __shared__ unsigned long long s_woff[32];  // per-warp growth, then its offset in the block's range
-        __shared__ unsigned long long s_gbase;
+        __shared__ unsigned long long s_woff[2][32];  // per-warp growth, then its offset in the block's range
+        __shared__ unsigned long long s_gbase[2];
         const int warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
         for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
             const int64_t i = wbase + threadIdx.x;
-            bool want[2] = {false, false};
-            int32_t ends[2] = {0, 0};
-            for (int dir = 0; dir < 2; ++dir) {
-                int32_t *meta = dir ? a.ovi : a.ovo;
-                int32_t x = 0, old_cap = 0, nc = 0;
-                if (i < a.b) {
-                    const int32_t sw = dir ? a.slot_in[i] : a.slot_out[i];
-                    x = dir ? a.dst[i] : a.src[i];
-                    ends[dir] = x;
-                    if (sw >= 0) {
-                        want[dir] = (sw & kWantBit) != 0;
-                        old_cap = meta[2 * n + x];
-                        if ((sw & ~kWantBit) == old_cap) nc = grown_cap(meta[n + x]);
-                    }
+            int32_t x[2] = {0, 0}, old_cap[2] = {0, 0}, nc[2] = {0, 0};
+            if (i < a.b) {
+                const int32_t sw[2] = {a.slot_out[i], a.slot_in[i]};
+                x[0] = a.src[i];
+                x[1] = a.dst[i];
+#pragma unroll
+                for (int dir = 0; dir < 2; ++dir) {
+                    if (sw[dir] < 0) continue;
+                    const int32_t *meta = dir ? a.ovi : a.ovo;
+                    old_cap[dir] = meta[2 * n + x[dir]];
+                    const int32_t len = meta[n + x[dir]];
+                    if ((sw[dir] & ~kWantBit) == old_cap[dir]) nc[dir] = grown_cap(len);
                 }
-                unsigned long long incl = (unsigned long long)nc;
+            }
+            unsigned long long incl[2];
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                incl[dir] = (unsigned long long)nc[dir];
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    unsigned long long t = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += t;
+                    const unsigned long long t = __shfl_up_sync(kFull, incl[dir], o);
+                    if (lane >= o) incl[dir] += t;
                 }
-                if (lane == 31) s_woff[warp] = incl;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    unsigned long long run = 0;
-                    for (int w = 0; w < nwb; ++w) {
-                        const unsigned long long t = s_woff[w];
-                        s_woff[w] = run;
-                        run += t;
-                    }
-                    s_gbase = run ? atomicAdd((unsigned long long *)(a.pool_top + dir), run) : 0ull;
-                }
-                __syncthreads();
-                if (nc) {
-                    const long long off = (long long)(s_gbase + s_woff[warp] + incl - (unsigned long long)nc);
-                    if (off + nc > a.pool_cap) {
-                        set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
-                    } else {
-                        int32_t *pool = dir ? a.pool_in : a.pool_out;
-                        const int32_t old = meta[x];
-                        for (int32_t j = 0; j < old_cap; ++j) pool[off + j] = pool[old + j];
-                        meta[x] = (int32_t)off;
-                        meta[2 * n + x] = nc;
-                    }
-                }
-                __syncthreads();  // s_woff is reused by the next direction
+                if (lane == 31) s_woff[dir][warp] = incl[dir];
             }
-            // fwd(v) changed: v's out-edges (dir 0); bwd(u) changed: u's in-edges (dir 1)
-            stage_enqueue(want[1], ends[1], 0, a.g, f, st);
-            stage_enqueue(want[0], ends[0], 1, a.g, f, st);
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                const int dir = threadIdx.x;
+                unsigned long long run = 0;
+                for (int w = 0; w < nwb; ++w) {
+                    const unsigned long long t = s_woff[dir][w];
+                    s_woff[dir][w] = run;
+                    run += t;
+                }
+                s_gbase[dir] = run ? atomicAdd((unsigned long long *)(a.pool_top + dir), run) : 0ull;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                if (!nc[dir]) continue;
+                const long long off =
+                    (long long)(s_gbase[dir] + s_woff[dir][warp] + incl[dir] - (unsigned long long)nc[dir]);
+                if (off + nc[dir] > a.pool_cap) {
+                    set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
+                    continue;
+                }
+                int32_t *meta = dir ? a.ovi : a.ovo;
+                int32_t *pool = dir ? a.pool_in : a.pool_out;
+                const int32_t old = meta[x[dir]];
+                for (int32_t j = 0; j < old_cap[dir]; ++j) pool[off + j] = pool[old + j];
+                meta[x[dir]] = (int32_t)off;
+                meta[2 * n + x[dir]] = nc[dir];
+            }
+            __syncthreads();  // s_woff is reused by the next round
         }
-        stage_flush(f, st);
     }
     if (!gs.sync(a.status)) return;
-    // P3: write the batch's ids into their slots
-    for (int64_t i = t0; i < a.b; i += nt) {
-        const int32_t sw = a.slot_out[i];
-        if (sw < 0) continue;
-        const int32_t u = a.src[i], v = a.dst[i];
-        const int32_t so = sw & ~kWantBit, si = a.slot_in[i] & ~kWantBit;
-        if (so < a.ovo[2 * n + u]) a.pool_out[(int64_t)a.ovo[u] + so] = v;
-        if (si < a.ovi[2 * n + v]) a.pool_in[(int64_t)a.ovi[v] + si] = u;
+    // P3: write the batch's ids into their slots, and enqueue the seeds'
+    // changed endpoints (their tasks carry the final adjacency locations)
+    {
+        FrontierOut f{a.f0, a.c3, a.cap, a.mark, a.wpd, a.status};  // level-0 frontier: parity 0
+        for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
+            const int64_t i = wbase + threadIdx.x;
+            bool want_f = false, want_b = false;
+            int32_t u = 0, v = 0;
+            if (i < a.b) {
+                const int32_t so = a.slot_out[i], si = a.slot_in[i];
+                u = a.src[i];
+                v = a.dst[i];
+                if (so >= 0) {
+                    want_b = (so & kWantBit) != 0;
+                    want_f = (si & kWantBit) != 0;
+                    const int32_t po = so & ~kWantBit, pi = si & ~kWantBit;
+                    if (po < a.ovo[2 * n + u]) a.pool_out[(int64_t)a.ovo[u] + po] = v;
+                    if (pi < a.ovi[2 * n + v]) a.pool_in[(int64_t)a.ovi[v] + pi] = u;
+                }
+            }
+            // fwd(v) changed: v's out-edges (dir 0); bwd(u) changed: u's in-edges (dir 1)
+            stage_enqueue(want_f, v, 0, a.g, f, st);
+            stage_enqueue(want_b, u, 1, a.g, f, st);
+        }
+        stage_flush(f, st);
     }
     if (!gs.sync(a.status)) return;
     // P4: propagation levels

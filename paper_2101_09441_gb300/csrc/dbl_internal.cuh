@@ -86,10 +86,59 @@ __device__ __forceinline__ void load_half(const uint64_t *p, uint64_t (&w)[HS])
     }
 }
 
-// Propagation task: vertex, chunk of its edge list, direction.
-__device__ __forceinline__ uint64_t make_task(int32_t v, uint32_t chunk, int dir)
+// Propagation task (16 bytes): up to kChunk consecutive edges of v in one
+// direction, located when the task is made (the enqueuer has just read v's
+// adjacency metadata), so the consumer goes straight to the edge ids: ncol
+// edges of the base CSR from col0, then npool inserted edges from pool0.
+struct FTask {
+    int32_t v;
+    uint32_t meta;  // dir << 31 | (chunk == 0) << 30 | ncol << 8 | npool
+    int32_t col0;
+    int32_t pool0;
+};
+
+__device__ __forceinline__ FTask make_ftask(int32_t v, int dir, int32_t chunk, const AdjRange &r)
 {
-    return (uint64_t)(uint32_t)v | ((uint64_t)chunk << 32) | ((uint64_t)dir << 63);
+    const int32_t lo = chunk * kChunk, hi = min(r.bd + r.od, lo + kChunk);
+    const int32_t cend = min(hi, r.bd);
+    const int32_t ncol = cend > lo ? cend - lo : 0;
+    const int32_t pstart = max(lo, r.bd);
+    const int32_t npool = hi > pstart ? hi - pstart : 0;
+    FTask t;
+    t.v = v;
+    t.meta = ((uint32_t)dir << 31) | (chunk == 0 ? (1u << 30) : 0u) | ((uint32_t)ncol << 8) | (uint32_t)npool;
+    t.col0 = r.b0 + lo;
+    t.pool0 = r.o0 + (pstart - r.bd);
+    return t;
+}
+
+__device__ __forceinline__ int task_dir(const FTask &t) { return (int)(t.meta >> 31); }
+__device__ __forceinline__ bool task_first(const FTask &t) { return (t.meta >> 30) & 1u; }
+__device__ __forceinline__ int32_t task_ncol(const FTask &t) { return (int32_t)((t.meta >> 8) & 0x7fu); }
+__device__ __forceinline__ int32_t task_edges(const FTask &t) { return task_ncol(t) + (int32_t)(t.meta & 0x7fu); }
+
+// Edge e (0 <= e < task_edges) of a task, from its resolved location.
+__device__ __forceinline__ int32_t task_edge(const DevGraph &g, int dir, int32_t col0, int32_t ncol, int32_t pool0,
+                                            int32_t e)
+{
+    if (e < ncol) return __ldg((dir ? g.in_col : g.out_col) + col0 + e);
+    return __ldcg((dir ? g.pool_in : g.pool_out) + pool0 + (e - ncol));
+}
+
+__device__ __forceinline__ FTask load_ftask(const FTask *tasks, int64_t t)
+{
+    const int4 w = __ldcg(reinterpret_cast<const int4 *>(tasks) + t);
+    FTask r;
+    r.v = w.x;
+    r.meta = (uint32_t)w.y;
+    r.col0 = w.z;
+    r.pool0 = w.w;
+    return r;
+}
+
+__device__ __forceinline__ void store_ftask(FTask *tasks, int64_t t, const FTask &v)
+{
+    reinterpret_cast<int4 *>(tasks)[t] = make_int4(v.v, (int)v.meta, v.col0, v.pool0);
 }
 
 // Search task: (group, vertex) state slot, chunk, and the query bits to expand.
@@ -154,7 +203,7 @@ struct dbl_index {
     // frontier scratch
     uint32_t *mark = nullptr;  // [2 parities][2 directions][wpd] frontier dedup bitmaps (see dbl_frontier.cuh)
     int64_t wpd = 0;           // bitmap words per direction: ceil(n / 32)
-    uint64_t *front[2] = {nullptr, nullptr};
+    dbl::FTask *front[2] = {nullptr, nullptr};
     int64_t front_cap = 0;
     uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
 

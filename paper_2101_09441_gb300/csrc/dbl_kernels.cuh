@@ -34,7 +34,7 @@ __device__ __forceinline__ int flat_owner(uint32_t excl, uint32_t e)
 // A round costs ceil(edges of the warp's tasks / 32) iterations, whatever the
 // mix of task sizes.
 template <int HS>
-__device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
+__device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const FTask *tasks,
                                                   uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                                   unsigned long long *stats, int64_t warp, int64_t nwarps,
                                                   const Stage &st)
@@ -45,27 +45,21 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
     if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
     for (int64_t r0 = 0; warp + nwarps * r0 < (int64_t)ntasks; r0 += 32) {  // warp-uniform
         const int64_t t = warp + nwarps * (r0 + lane);
-        int32_t v = 0, b0 = 0, bd = 0, o0 = 0;
-        uint32_t lo = 0, cnt = 0;
+        int32_t col0 = 0, ncol = 0, pool0 = 0;
+        uint32_t cnt = 0;
         int dir = 0;
         uint64_t rv[HS];
 #pragma unroll
         for (int i = 0; i < HS; ++i) rv[i] = 0;
         if (t < (int64_t)ntasks) {
-            const uint64_t tk = __ldcg(tasks + t);
-            v = (int32_t)(uint32_t)tk;
-            const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
-            dir = (int)(tk >> 63);
-            if (chunk == 0) mark_clear(cur_mark, f.wpd, dir, v);
-            const AdjRange r = adj_of(g, dir, v);
-            b0 = r.b0;
-            bd = r.bd;
-            o0 = r.o0;
-            const int32_t d = r.bd + r.od;
-            lo = chunk * (uint32_t)kChunk;
-            const int32_t hi = min(d, (int32_t)lo + kChunk);
-            cnt = hi > (int32_t)lo ? (uint32_t)(hi - (int32_t)lo) : 0u;
-            load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
+            const FTask tk = load_ftask(tasks, t);
+            dir = task_dir(tk);
+            if (task_first(tk)) mark_clear(cur_mark, f.wpd, dir, tk.v);
+            col0 = tk.col0;
+            ncol = task_ncol(tk);
+            pool0 = tk.pool0;
+            cnt = (uint32_t)task_edges(tk);
+            load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
             ++ntask;
         }
         uint32_t incl = cnt;
@@ -80,16 +74,16 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
             const uint32_t e = base + lane;
             const int owner = flat_owner(excl, e);
             const int odir = __shfl_sync(kFull, dir, owner);
-            const AdjRange orr{__shfl_sync(kFull, b0, owner), __shfl_sync(kFull, bd, owner),
-                               __shfl_sync(kFull, o0, owner), 0};
-            const uint32_t opos = __shfl_sync(kFull, lo, owner) + (e - __shfl_sync(kFull, excl, owner));
+            const int32_t ocol0 = __shfl_sync(kFull, col0, owner), oncol = __shfl_sync(kFull, ncol, owner);
+            const int32_t opool0 = __shfl_sync(kFull, pool0, owner);
+            const int32_t oe = (int32_t)(e - __shfl_sync(kFull, excl, owner));
             uint64_t orv[HS];
 #pragma unroll
             for (int i = 0; i < HS; ++i) orv[i] = __shfl_sync(kFull, rv[i], owner);
             bool want = false;
             int32_t x = 0;
             if (e < total) {
-                x = adj_at(g, odir, orr, (int32_t)opos);
+                x = task_edge(g, odir, ocol0, oncol, opool0, oe);
                 ++relaxed;
                 uint64_t *px = rec + (size_t)x * RW + (odir ? HS : 0);
                 uint64_t rx[HS];
@@ -118,7 +112,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
 // New tasks go through the block's stage (stage_enqueue); the stage is flushed
 // at the end, so every thread of the block must call this.
 template <int HS, int TEAM>
-__device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const uint64_t *tasks,
+__device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const FTask *tasks,
                                              uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                              unsigned long long *stats, int64_t warp0, int64_t nwarps,
                                              const Stage &st)
@@ -135,34 +129,31 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
         for (int64_t wb = warp0 * TPW; wb < (int64_t)ntasks; wb += nwarps * TPW) {
             const int64_t t = wb + team;
             const bool has = t < (int64_t)ntasks;
-            int32_t v = 0, lo = 0, hi = 0;
+            int32_t col0 = 0, ncol = 0, pool0 = 0, cnt = 0;
             int dir = 0;
-            AdjRange r{0, 0, 0, 0};
             uint64_t rv[HS];
 #pragma unroll
             for (int i = 0; i < HS; ++i) rv[i] = 0;
             if (has) {
-                const uint64_t tk = __ldcg(tasks + t);
-                v = (int32_t)(uint32_t)tk;
-                const uint32_t chunk = (uint32_t)(tk >> 32) & 0x7fffffffu;
-                dir = (int)(tk >> 63);
-                if (chunk == 0 && tl == 0) mark_clear(cur_mark, f.wpd, dir, v);
-                r = adj_of(g, dir, v);
-                const int32_t d = r.bd + r.od;
-                lo = (int32_t)chunk * kChunk;
-                hi = min(d, lo + kChunk);
-                load_half<HS>(rec + (size_t)v * RW + (dir ? HS : 0), rv);
+                const FTask tk = load_ftask(tasks, t);
+                dir = task_dir(tk);
+                if (task_first(tk) && tl == 0) mark_clear(cur_mark, f.wpd, dir, tk.v);
+                col0 = tk.col0;
+                ncol = task_ncol(tk);
+                pool0 = tk.pool0;
+                cnt = task_edges(tk);
+                load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
                 if (tl == 0) ++ntask;
             }
-            int iters = has && hi > lo ? (hi - lo + TEAM - 1) / TEAM : 0;
+            int iters = (cnt + TEAM - 1) / TEAM;
 #pragma unroll
             for (int o = 16; o; o >>= 1) iters = max(iters, __shfl_xor_sync(kFull, iters, o));
             for (int it = 0; it < iters; ++it) {
-                const int32_t e = lo + it * TEAM + tl;
+                const int32_t e = it * TEAM + tl;
                 bool want = false;
                 int32_t x = 0;
-                if (has && e < hi) {
-                    x = adj_at(g, dir, r, e);
+                if (has && e < cnt) {
+                    x = task_edge(g, dir, col0, ncol, pool0, e);
                     ++relaxed;
                     uint64_t *px = rec + (size_t)x * RW + (dir ? HS : 0);
                     uint64_t rx[HS];

@@ -20,7 +20,7 @@
 namespace dbl {
 
 template <int HS, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, const uint64_t *tasks,
+__global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, const FTask *tasks,
                                                    const uint32_t *ntasks_p, uint32_t *cur_mark, FrontierOut f,
                                                    unsigned long long *stats)
 {
@@ -141,7 +141,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
 // runaway into DBL_ERR_TIMEOUT instead of a hang.
 template <int HS, int TEAM>
 __global__ void __launch_bounds__(pblock_of(HS), 1)
-    k_propagate_persistent(DevGraph g, uint64_t *rec, uint64_t *f0, uint64_t *f1, uint32_t *c3, int64_t cap,
+    k_propagate_persistent(DevGraph g, uint64_t *rec, FTask *f0, FTask *f1, uint32_t *c3, int64_t cap,
                            uint32_t *mark, int64_t wpd, uint32_t *status, unsigned long long *stats,
                            GridBarrier bar, int64_t max_levels)
 {
@@ -179,7 +179,7 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_propagate_persistent<HS, TEAM>, pblock_of(HS), 0);
     if (blocks_per_sm < 1) return fail(ix, DBL_ERR_CUDA, "persistent propagate: kernel does not fit on an SM");
     DevGraph g = dev_graph(ix);
-    uint64_t *f0 = ix->front[0], *f1 = ix->front[1];
+    FTask *f0 = ix->front[0], *f1 = ix->front[1];
     uint32_t *c3 = ix->d_counts + kCntP0;
     int64_t cap = ix->front_cap;
     uint32_t *mark = ix->mark;
