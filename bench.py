@@ -467,6 +467,146 @@ def bench_gpu(args):
         tdist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ serving
+def serve_requests(w, count, seed, q_off=0, e_off=0):
+    """`count` requests: 90% query batches, 10% insertion batches, sizes
+    floor(exp(U[0, ln 65537))) clamped to >= 1; queries and edges are taken in
+    order from the workload's streams (queries wrap around, edges do not)."""
+    rng = np.random.default_rng(seed)
+    Q, E = w["q_u"].shape[0], w["ins_src"].shape[0]
+    out = []
+    for _ in range(count):
+        size = max(1, int(np.exp(rng.uniform(0.0, np.log(65537.0)))))
+        if rng.random() < 0.1:
+            size = min(size, E - e_off)
+            if size <= 0:
+                continue
+            out.append((1, w["ins_src"][e_off:e_off + size], w["ins_dst"][e_off:e_off + size]))
+            e_off += size
+        else:
+            a = q_off % Q
+            size = min(size, Q - a)
+            out.append((0, w["q_u"][a:a + size], w["q_v"][a:a + size]))
+            q_off += size
+    return out, q_off, e_off
+
+
+def run_serving(srv, reqs, rate=None, seed=0):
+    """Submit the requests (Poisson arrivals at `rate` requests/s, or as fast
+    as the engine admits them), wait for all, and return the engine's report."""
+    import threading
+
+    import paper_2101_09441_gb300 as dbl
+    srv.reset_stats()
+    tickets = []
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    done = threading.Event()
+    errors = []
+
+    def waiter():
+        i = 0
+        while i < len(reqs):
+            if i < len(tickets):
+                try:
+                    srv.wait(tickets[i])
+                except Exception as e:  # noqa: BLE001 - reported below
+                    errors.append(str(e))
+                i += 1
+            else:
+                time.sleep(1e-5)
+        done.set()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for (kind, a, b), gap in zip(reqs, gaps):
+        t_next += gap
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            time.sleep(min(t_next - now, 1e-4))
+        while True:
+            try:
+                tickets.append(srv.submit(kind, a, b))
+                break
+            except dbl.DblError as e:
+                if e.status != dbl.DBL_ERR_BUSY:
+                    raise
+                time.sleep(1e-5)
+    done.wait()
+    wall = time.perf_counter() - t0
+    rep = srv.report()
+    rep["wall_s"] = wall
+    rep["requests_per_s"] = len(reqs) / wall
+    rep["pairs_per_s"] = rep["pairs"] / wall
+    rep["edges_per_s"] = rep["edges"] / wall
+    rep["errors"] = errors[:3]
+    return rep
+
+
+def bench_serve(args):
+    """Serving measurement: the learned index (k = 128, k' = 64) resident on
+    the device behind dbl_server; a closed-loop run gives the peak request
+    rate, then Poisson streams at 50% and 90% of it report p50/p99 latency and
+    sustained throughput.  One JSON line."""
+    import torch
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    from paper_2101_09441_gb300 import learned as L
+    dbl.build()
+    w = dbl_inputs.workload(args.serve_workload)
+    dev = torch.device("cuda", 0)
+    I = Inputs(w, dev)
+    E = int(w["ins_src"].shape[0])
+    k, kp = 128, 64
+    t0 = time.perf_counter()
+    plain = dbl.DBLIndex(I.rp, I.col, k, kp, edge_capacity=max(E, 1 << 20))
+    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], args.train_queries, w["seed"] + 300, False,
+                                w["ins_src"], w["ins_dst"])
+    base_slots = k // 8
+    scores, tinfo = L.train_scorer(plain, torch.from_numpy(tu).to(dev), torch.from_numpy(tv).to(dev), base_slots,
+                                   steps=args.train_steps)
+    lm = L.select_landmarks(plain, scores, k, base_slots)
+    _, lb, lr_ = plain.selection()
+    plain.close()
+    ix = dbl.DBLIndex(I.rp, I.col, k, kp, landmarks=lm, leaf_buckets=lb, leaf_roles=lr_,
+                      edge_capacity=max(2 * E, 1 << 20), flags=dbl.FLAG_PERSISTENT)
+    ix.sync()
+    ix.snapshot(0)
+    setup_s = time.perf_counter() - t0
+    n_req = args.serve_requests
+
+    def run(reqs, rate, seed):
+        # every run starts from the built index, so each one inserts new edges only
+        ix.restore(0)
+        ix.sync()
+        srv = dbl.Server(ix, slots=4)
+        try:
+            return run_serving(srv, reqs, rate, seed)
+        finally:
+            srv.close()
+
+    warm, _, _ = serve_requests(w, n_req // 4, 99)
+    run(warm, None, 0)
+    reqs, _, _ = serve_requests(w, n_req, 100)
+    peak = run(reqs, None, 0)
+    loads = {}
+    for i, frac in enumerate((0.5, 0.9)):
+        reqs, _, _ = serve_requests(w, n_req, 200 + i, q_off=(i + 1) * 3_000_000)
+        loads[str(frac)] = run(reqs, frac * peak["requests_per_s"], 300 + i)
+    ix.close()
+    line = {"metric": "serving: p50/p99 latency and sustained throughput under Poisson load", "impl": "dbl",
+            "workload": args.serve_workload, "n": int(w["n"]), "m": int(w["m"]), "k": k, "kprime": kp,
+            "landmarks": "learned", "mix": "90% query / 10% insertion requests, sizes floor(exp(U[0, ln 65537)))",
+            "requests_per_run": n_req, "setup_s": setup_s, "closed_loop_peak": peak, "poisson": loads,
+            "learned": {kk: v for kk, v in tinfo.items() if kk != "losses"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,11 +627,16 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="bracket one form's timed region with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--profile-form", default="learned_timing")
+    ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
+    ap.add_argument("--serve-workload", default="large", choices=["large", "social", "tiny"])
+    ap.add_argument("--serve-requests", type=int, default=1500)
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.serve:
+        bench_serve(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_gpu(args)
