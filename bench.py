@@ -44,8 +44,10 @@ UNIT = "ops/s (queries + inserted edges)"
 
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {}
-KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_kernels.cuh",
+# (The cooperative insertion kernel runs ~10x slower under ncu than alone, so no ncu
+# traffic is recorded for it.)
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_328_000 + 23_329_536, "cbf856f2ae44")}
+KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_insert.cu",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
 
 
@@ -345,9 +347,25 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     return res
 
 
-def roofline(form, ix, args, w, I, batches):
+def insertion_bytes(ix, w, I):
+    """Algorithmic bytes of appending and seeding one step's insertions (the
+    persistent insertion kernel does both before it propagates): per edge its
+    two ids (8 B), a read and a write of the segment word of each endpoint
+    (4 x 32 B), the two label records read by the skip test (2 x 32 B), the two
+    appended ids (2 x 32 B); applied edges also write back the two changed
+    halves (2 x 32 B).  Self-loops: the ids only."""
+    st = ix.stats()
+    E = int(w["ins_src"].shape[0])
+    loops = int((I.src == I.dst).sum().item())
+    applied = int(st[11]) / max(1, int(st[11]) + int(st[12])) * (E - loops)
+    return 8 * E + (E - loops) * (4 * 32 + 2 * 32 + 2 * 32) + applied * 2 * 32
+
+
+def roofline(form, ix, args, w, I, batches, persistent=True):
     """Achieved GB/s of the form's dominant kernel class (library CUDA events
-    over the timed region) against the measured HBM copy peak."""
+    over the timed region) against the measured HBM copy peak.  In the
+    persistent forms the `propagate` class is the insertion kernel (append,
+    seeds and repair in one launch per batch)."""
     import torch
     peaks, src = measured_peaks()
     Q = int(w["q_u"].shape[0])
@@ -356,9 +374,9 @@ def roofline(form, ix, args, w, I, batches):
     alg = {"query_label": args.steps * Q * (8 + 2 * rec + 2)}
     kern = form["kernels"]
     if "propagate" in kern:
-        alg["propagate"] = args.steps * changed_bytes(ix, w, batches, torch.diff(I.rp).long(),
-                                                      torch.bincount(I.col.long(), minlength=w["n"]), rec // 2,
-                                                      I.src, I.dst)
+        prop = changed_bytes(ix, w, batches, torch.diff(I.rp).long(), torch.bincount(I.col.long(), minlength=w["n"]),
+                             rec // 2, I.src, I.dst)
+        alg["propagate"] = args.steps * (prop + (insertion_bytes(ix, w, I) if persistent else 0))
     for k, v in kern.items():
         v["ms_per_launch"] = v["ms_total"] / v["launches"]
         if k in alg and v["ms_total"] > 0:
@@ -368,11 +386,16 @@ def roofline(form, ix, args, w, I, batches):
     dom = max(kern, key=lambda k: kern[k]["ms_total"])
     cand = dom if "achieved_gbs" in kern[dom] else max((k for k in kern if "achieved_gbs" in kern[k]),
                                                        key=lambda k: kern[k]["ms_total"])
-    ach = kern[cand]["achieved_gbs"]
-    traffic = NCU_TRAFFIC[cand][0] if cand in NCU_TRAFFIC and NCU_TRAFFIC[cand][1] == source_sha(cand) else None
-    return {"kernel": cand, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
-            "dominant_kernel_by_time": dom}
+    def obj(k):
+        ach = kern[k]["achieved_gbs"]
+        traffic = NCU_TRAFFIC[k][0] if k in NCU_TRAFFIC and NCU_TRAFFIC[k][1] == source_sha(k) else None
+        return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
+                "algorithmic_bytes_per_launch": kern[k]["algorithmic_bytes_per_launch"],
+                "ms_per_launch": kern[k]["ms_per_launch"]}
+    out = obj(cand)
+    out["dominant_kernel_by_time"] = dom
+    return out, (obj("query_label") if "achieved_gbs" in kern.get("query_label", {}) else None)
 
 
 def bench_gpu(args):
@@ -422,7 +445,7 @@ def bench_gpu(args):
     dec_p = ref_form["decided_by"] if ref_form else dec_l
     fallback = dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
     head = forms["graph"] if (fallback and "graph" in forms) else learned
-    roof = roofline(learned_t, learned_t["ix"], args, w, I, batches)
+    roof, roof_label = roofline(learned_t, learned_t["ix"], args, w, I, batches)
 
     # ---- end to end through the host-buffer C-ABI calls, headline index
     ix = learned["ix"]
@@ -453,6 +476,7 @@ def bench_gpu(args):
             "learned": {"fallback_to_degree_rule": bool(fallback), "train_s": train_s, "base_slots": base_slots,
                         **{k: v for k, v in tinfo.items() if k != "losses"}, "final_loss": tinfo["losses"][-1]},
             "roofline": roof,
+            "roofline_label_test": roof_label,
             "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
             "clocks": learned["clocks"],
