@@ -347,7 +347,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     ix->wpd = ((int64_t)n + 31) / 32 + 1;  // + 1: never zero words
     if ((st = A((void **)&ix->out_ptr, 4 * (n + 1))) || (st = A((void **)&ix->out_col, 4 * m)) ||
         (st = A((void **)&ix->in_ptr, 4 * (n + 1))) || (st = A((void **)&ix->in_col, 4 * m)) ||
-        (st = A((void **)&ix->ovo, 12 * n)) || (st = A((void **)&ix->ovi, 12 * n)) ||
+        (st = A((void **)&ix->vm, sizeof(VMeta) * n)) ||
         (st = A((void **)&ix->pool_out, 4 * (size_t)ix->pool_cap)) ||
         (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
         (st = A((void **)&ix->rec, 8 * n * ix->rw)) || (st = A((void **)&ix->landmarks, 4 * (size_t)k)) ||
@@ -362,8 +362,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         destroy_impl(ix, s);
         return fail(nullptr, st, msg);
     }
-    cudaMemsetAsync(ix->ovo, 0, 12 * n, s);
-    cudaMemsetAsync(ix->ovi, 0, 12 * n, s);
+    cudaMemsetAsync(ix->vm, 0, sizeof(VMeta) * n, s);
     cudaMemsetAsync(ix->d_pool_top, 0, 16, s);
     cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
@@ -580,15 +579,14 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     Snapshot &sn = ix->snaps[slot];
     dbl_status st;
-    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = 12 * (size_t)ix->n;
+    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
     if (!sn.rec.p) {
-        if ((st = alloc_buf(ix, &sn.rec.p, rec_b, s)) || (st = alloc_buf(ix, &sn.ovo.p, meta_b, s)) ||
-            (st = alloc_buf(ix, &sn.ovi.p, meta_b, s)) || (st = alloc_buf(ix, &sn.top.p, 16, s)))
+        if ((st = alloc_buf(ix, &sn.rec.p, rec_b, s)) || (st = alloc_buf(ix, &sn.vm.p, meta_b, s)) ||
+            (st = alloc_buf(ix, &sn.top.p, 16, s)))
             return st;
     }
     cudaMemcpyAsync(sn.rec.p, ix->rec, rec_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(sn.ovo.p, ix->ovo, meta_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(sn.ovi.p, ix->ovi, meta_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(sn.vm.p, ix->vm, meta_b, cudaMemcpyDeviceToDevice, s);
     // pool tops stay on the device, so that a restore is all device-to-device
     // copies (and can be captured in a CUDA graph)
     cudaMemcpyAsync(sn.top.p, ix->d_pool_top, 16, cudaMemcpyDeviceToDevice, s);
@@ -605,10 +603,9 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     if (slot < 0 || slot >= 4 || !ix->snaps[slot].valid) return fail(ix, DBL_ERR_INVALID, "no snapshot in that slot");
     cudaStream_t s = (cudaStream_t)stream;
     Snapshot &sn = ix->snaps[slot];
-    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = 12 * (size_t)ix->n;
+    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
     cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(ix->ovo, sn.ovo.p, meta_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(ix->ovi, sn.ovi.p, meta_b, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ix->vm, sn.vm.p, meta_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->d_pool_top, sn.top.p, 16, cudaMemcpyDeviceToDevice, s);
     cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);

@@ -63,9 +63,9 @@ __device__ __forceinline__ int32_t grown_cap(int32_t need)
 // New segments are reserved with one atomicAdd per warp (a warp-wide prefix
 // sum of the sizes) instead of one per vertex on the shared pool top.
 __global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *cnt_out,
-                           const int32_t *cnt_in, const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo,
-                           int32_t *ovi, int32_t *pool_out, int32_t *pool_in, int64_t *pool_top, int32_t n,
-                           int64_t pool_cap, uint32_t *status)
+                           const int32_t *cnt_in, const int32_t *pos_out, const int32_t *pos_in, VMeta *vm,
+                           int32_t *pool_out, int32_t *pool_in, int64_t *pool_top, int64_t pool_cap,
+                           uint32_t *status)
 {
     if (status_set(status)) return;
     const int lane = threadIdx.x & 31;
@@ -74,12 +74,13 @@ __global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, co
         const int64_t i = base + threadIdx.x;
         for (int dir = 0; dir < 2; ++dir) {
             int32_t x = 0, len = 0, nc = 0;
-            int32_t *meta = dir ? ovi : ovo;  // [off | len | cap]
+            VAdj a{0, 0u, 0, 0};
             if (i < b && (dir ? pos_in[i] : pos_out[i]) == 0) {
                 x = dir ? dst[i] : src[i];
-                len = meta[n + x];
+                a = load_vadj(vm, dir, x);
+                len = a.len;
                 const int32_t need = len + (dir ? cnt_in[x] : cnt_out[x]);
-                if (need > meta[2 * n + x]) nc = grown_cap(need);
+                if (need > va_cap(a.dc)) nc = grown_cap(need);
             }
             unsigned long long incl = (unsigned long long)nc;
 #pragma unroll
@@ -99,43 +100,42 @@ __global__ void k_ins_grow(const int32_t *src, const int32_t *dst, int64_t b, co
                 continue;
             }
             int32_t *pool = dir ? pool_in : pool_out;
-            const int32_t old = meta[x];
-            for (int32_t j = 0; j < len; ++j) pool[off + j] = pool[old + j];
-            meta[x] = (int32_t)off;
-            meta[2 * n + x] = nc;
+            for (int32_t j = 0; j < len; ++j) pool[off + j] = pool[a.off + j];
+            vm[x].d[dir].off = (int32_t)off;
+            vm[x].d[dir].dc = va_dc(va_deg(a.dc), nc);
         }
     }
 }
 
 __global__ void k_ins_write(const int32_t *src, const int32_t *dst, int64_t b, const int32_t *pos_out,
-                            const int32_t *pos_in, const int32_t *ovo, const int32_t *ovi, int32_t *pool_out,
-                            int32_t *pool_in, int32_t n, const uint32_t *status)
+                            const int32_t *pos_in, const VMeta *vm, int32_t *pool_out, int32_t *pool_in,
+                            const uint32_t *status)
 {
     if (status_set(status)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t po = pos_out[i];
         if (po < 0) continue;
-        const int32_t u = src[i], v = dst[i];
+        const int32_t u = src[i], v = dst[i], pi = pos_in[i];
+        const VAdj au = load_vadj(vm, 0, u), av = load_vadj(vm, 1, v);
         // a segment that could not grow (pool exhausted, status already set) is not written past its end
-        if (ovo[n + u] + po < ovo[2 * n + u]) pool_out[(int64_t)ovo[u] + ovo[n + u] + po] = v;
-        if (ovi[n + v] + pos_in[i] < ovi[2 * n + v]) pool_in[(int64_t)ovi[v] + ovi[n + v] + pos_in[i]] = u;
+        if (au.len + po < va_cap(au.dc)) pool_out[(int64_t)au.off + au.len + po] = v;
+        if (av.len + pi < va_cap(av.dc)) pool_in[(int64_t)av.off + av.len + pi] = u;
     }
 }
 
 __global__ void k_ins_commit(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
-                             const int32_t *pos_out, const int32_t *pos_in, int32_t *ovo, int32_t *ovi, int32_t n,
-                             const uint32_t *status)
+                             const int32_t *pos_out, const int32_t *pos_in, VMeta *vm, const uint32_t *status)
 {
     if (status_set(status)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
         if (pos_out[i] == 0) {
             const int32_t u = src[i];
-            ovo[n + u] += cnt_out[u];
+            vm[u].d[0].len += cnt_out[u];
             cnt_out[u] = 0;
         }
         if (pos_in[i] == 0) {
             const int32_t v = dst[i];
-            ovi[n + v] += cnt_in[v];
+            vm[v].d[1].len += cnt_in[v];
             cnt_in[v] = 0;
         }
     }
@@ -237,7 +237,8 @@ struct InsArgs {
     const int32_t *src, *dst;
     int64_t b;
     int32_t n;
-    int32_t *ovo, *ovi, *pool_out, *pool_in;
+    VMeta *vm;
+    int32_t *pool_out, *pool_in;
     int64_t *pool_top;
     int64_t pool_cap;
     int32_t *slot_out, *slot_in;
@@ -277,8 +278,8 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 ++loops;
                 continue;
             }
-            const int32_t so = atomicAdd(a.ovo + n + u, 1);
-            const int32_t si = atomicAdd(a.ovi + n + v, 1);
+            const int32_t so = atomicAdd(&a.vm[u].d[0].len, 1);
+            const int32_t si = atomicAdd(&a.vm[v].d[1].len, 1);
             bool want_f = false, want_b = false;
             if (seed_one<HS, WD>(u, v, a.rec, want_f, want_b)) ++applied;
             else ++skipped;
@@ -299,6 +300,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
             const int64_t i = wbase + threadIdx.x;
             int32_t x[2] = {0, 0}, old_cap[2] = {0, 0}, nc[2] = {0, 0};
+            VAdj ad[2] = {{0, 0u, 0, 0}, {0, 0u, 0, 0}};
             if (i < a.b) {
                 const int32_t sw[2] = {a.slot_out[i], a.slot_in[i]};
                 x[0] = a.src[i];
@@ -306,10 +308,9 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
 #pragma unroll
                 for (int dir = 0; dir < 2; ++dir) {
                     if (sw[dir] < 0) continue;
-                    const int32_t *meta = dir ? a.ovi : a.ovo;
-                    old_cap[dir] = meta[2 * n + x[dir]];
-                    const int32_t len = meta[n + x[dir]];
-                    if ((sw[dir] & ~kWantBit) == old_cap[dir]) nc[dir] = grown_cap(len);
+                    ad[dir] = load_vadj(a.vm, dir, x[dir]);  // len is final after the count phase
+                    old_cap[dir] = va_cap(ad[dir].dc);
+                    if ((sw[dir] & ~kWantBit) == old_cap[dir]) nc[dir] = grown_cap(ad[dir].len);
                 }
             }
             unsigned long long incl[2];
@@ -344,12 +345,10 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                     set_status(a.status, DBL_ERR_CAPACITY);  // cannot happen: the pool holds 4x the edge capacity
                     continue;
                 }
-                int32_t *meta = dir ? a.ovi : a.ovo;
                 int32_t *pool = dir ? a.pool_in : a.pool_out;
-                const int32_t old = meta[x[dir]];
-                for (int32_t j = 0; j < old_cap[dir]; ++j) pool[off + j] = pool[old + j];
-                meta[x[dir]] = (int32_t)off;
-                meta[2 * n + x[dir]] = nc[dir];
+                for (int32_t j = 0; j < old_cap[dir]; ++j) pool[off + j] = pool[ad[dir].off + j];
+                a.vm[x[dir]].d[dir].off = (int32_t)off;
+                a.vm[x[dir]].d[dir].dc = va_dc(va_deg(ad[dir].dc), nc[dir]);
             }
             __syncthreads();  // s_woff is reused by the next round
         }
@@ -371,8 +370,9 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                     want_b = (so & kWantBit) != 0;
                     want_f = (si & kWantBit) != 0;
                     const int32_t po = so & ~kWantBit, pi = si & ~kWantBit;
-                    if (po < a.ovo[2 * n + u]) a.pool_out[(int64_t)a.ovo[u] + po] = v;
-                    if (pi < a.ovi[2 * n + v]) a.pool_in[(int64_t)a.ovi[v] + pi] = u;
+                    const VAdj au = load_vadj(a.vm, 0, u), av = load_vadj(a.vm, 1, v);
+                    if (po < va_cap(au.dc)) a.pool_out[(int64_t)au.off + po] = v;
+                    if (pi < va_cap(av.dc)) a.pool_in[(int64_t)av.off + pi] = u;
                 }
             }
             // fwd(v) changed: v's out-edges (dir 0); bwd(u) changed: u's in-edges (dir 1)
@@ -450,8 +450,7 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     a.dst = dst;
     a.b = b;
     a.n = ix->n;
-    a.ovo = ix->ovo;
-    a.ovi = ix->ovi;
+    a.vm = ix->vm;
     a.pool_out = ix->pool_out;
     a.pool_in = ix->pool_in;
     a.pool_top = ix->d_pool_top;
@@ -546,14 +545,13 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
     k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status);
     ++ix->launches;
-    k_ins_grow<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out,
-                                       ix->pool_in, ix->d_pool_top, n, ix->pool_cap, ix->d_status);
+    k_ins_grow<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->vm, ix->pool_out,
+                                       ix->pool_in, ix->d_pool_top, ix->pool_cap, ix->d_status);
     ++ix->launches;
-    k_ins_write<<<grid, kBlock, 0, s>>>(src, dst, b, pos_out, pos_in, ix->ovo, ix->ovi, ix->pool_out, ix->pool_in, n,
+    k_ins_write<<<grid, kBlock, 0, s>>>(src, dst, b, pos_out, pos_in, ix->vm, ix->pool_out, ix->pool_in,
                                         ix->d_status);
     ++ix->launches;
-    k_ins_commit<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->ovo, ix->ovi, n,
-                                         ix->d_status);
+    k_ins_commit<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->vm, ix->d_status);
     ++ix->launches;
     ix->edges_stored += b;
     atomic_add_host_stat(ix, 15, (uint64_t)b, s);

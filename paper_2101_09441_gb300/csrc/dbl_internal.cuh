@@ -7,10 +7,14 @@
 //                               HS = next power of two >= k/64 + kprime/64, so a
 //                               half is 16, 32 or 64 bytes and, for k = kprime = 64,
 //                               a whole record is one 32-byte DRAM sector.
-//   out_ptr/out_col, in_ptr/in_col   base CSR of Suc and Pre (int32).
-//   ovo_*/ovi_*              inserted edges: per-vertex contiguous segments
-//                            (offset, length, capacity) in an edge pool, grown
-//                            by doubling.
+//   out_col, in_col          base CSR adjacency of Suc and Pre (int32); the
+//                            offsets out_ptr / in_ptr are kept for the build.
+//   vm      VMeta [n]        per-vertex adjacency metadata, one 32-byte sector:
+//                            per direction the base CSR range and the segment
+//                            of inserted edges (offset, length, capacity) in an
+//                            edge pool, grown by doubling.  Everything a
+//                            frontier or insertion step needs about a vertex's
+//                            adjacency is one sector.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,20 +35,53 @@ constexpr int kChunk = 64;     // edges per propagation / search task
 constexpr int kBlock = 256;    // threads per block for frontier kernels
 
 // ------------------------------------------------------------ device views
+// Adjacency of a vertex in one direction (dir 0 = Suc, 1 = Pre): base CSR
+// edges col[start, start + deg), inserted edges pool[off, off + len) in a
+// segment of capacity cap (0: none; else a power of two >= 4).  deg and
+// log2(cap) share one word, so a base degree must be below 2^kDegBits.
+struct VAdj {
+    int32_t start;
+    uint32_t dc;  // deg | log2(cap) << kDegBits
+    int32_t off;
+    int32_t len;
+};
+struct __align__(32) VMeta {
+    VAdj d[2];
+};
+constexpr int kDegBits = 27;
+
+__host__ __device__ __forceinline__ int32_t va_deg(uint32_t dc) { return (int32_t)(dc & ((1u << kDegBits) - 1u)); }
+__host__ __device__ __forceinline__ int32_t va_cap(uint32_t dc)
+{
+    const uint32_t e = dc >> kDegBits;
+    return e ? (int32_t)(1u << e) : 0;
+}
+__host__ __device__ __forceinline__ uint32_t va_dc(int32_t deg, int32_t cap)
+{
+    uint32_t e = 0;
+    while (cap > 1) {
+        cap >>= 1;
+        ++e;
+    }
+    return (uint32_t)deg | (e << kDegBits);
+}
+
 struct DevGraph {
     int32_t n;
-    const int32_t *out_ptr, *out_col;
-    const int32_t *in_ptr, *in_col;
-    const int32_t *ovo_off, *ovo_len, *pool_out;
-    const int32_t *ovi_off, *ovi_len, *pool_in;
+    VMeta *vm;
+    const int32_t *out_col, *in_col;
+    const int32_t *pool_out, *pool_in;
 };
 
-// degree of x in direction dir (0 = Suc, 1 = Pre), base + inserted
-__device__ __forceinline__ int32_t deg_of(const DevGraph &g, int dir, int32_t x)
+__device__ __forceinline__ VAdj load_vadj(const VMeta *vm, int dir, int32_t x)
 {
-    const int32_t *ptr = dir ? g.in_ptr : g.out_ptr;
-    const int32_t *ovl = dir ? g.ovi_len : g.ovo_len;
-    return __ldg(ptr + x + 1) - __ldg(ptr + x) + __ldcg(ovl + x);
+    const int4 w = __ldcg(reinterpret_cast<const int4 *>(vm + x) + dir);
+    VAdj a;
+    a.start = w.x;
+    a.dc = (uint32_t)w.y;
+    a.off = w.z;
+    a.len = w.w;
+    return a;
 }
 
 // Edge range of x: base part [b0, b0+bd) of col, then inserted part [o0, o0+od) of pool.
@@ -54,13 +91,15 @@ struct AdjRange {
 
 __device__ __forceinline__ AdjRange adj_of(const DevGraph &g, int dir, int32_t x)
 {
-    AdjRange r;
-    const int32_t *ptr = dir ? g.in_ptr : g.out_ptr;
-    r.b0 = __ldg(ptr + x);
-    r.bd = __ldg(ptr + x + 1) - r.b0;
-    r.o0 = __ldcg((dir ? g.ovi_off : g.ovo_off) + x);
-    r.od = __ldcg((dir ? g.ovi_len : g.ovo_len) + x);
-    return r;
+    const VAdj a = load_vadj(g.vm, dir, x);
+    return AdjRange{a.start, va_deg(a.dc), a.off, a.len};
+}
+
+// degree of x in direction dir, base + inserted
+__device__ __forceinline__ int32_t deg_of(const DevGraph &g, int dir, int32_t x)
+{
+    const AdjRange r = adj_of(g, dir, x);
+    return r.bd + r.od;
 }
 
 __device__ __forceinline__ int32_t adj_at(const DevGraph &g, int dir, const AdjRange &r, int32_t e)
@@ -169,7 +208,7 @@ struct Buf {
 
 struct Snapshot {
     bool valid = false;
-    Buf rec, ovo, ovi;  // labels; (off, len, cap) triples for both directions
+    Buf rec, vm;        // labels; per-vertex adjacency metadata
     Buf top;            // the two pool tops (device)
     int64_t edges_stored = 0;
 };
@@ -187,8 +226,7 @@ struct dbl_index {
 
     // graph
     int32_t *out_ptr = nullptr, *out_col = nullptr, *in_ptr = nullptr, *in_col = nullptr;
-    // inserted adjacency: [off | len | cap] blocks of n int32 each, per direction
-    int32_t *ovo = nullptr, *ovi = nullptr;
+    dbl::VMeta *vm = nullptr;  // [n] adjacency metadata incl. the inserted-edge segments
     int32_t *pool_out = nullptr, *pool_in = nullptr;
     int64_t pool_cap = 0, edge_cap = 0;
     int64_t edges_stored = 0;     // host mirror of inserted edges stored
@@ -312,15 +350,10 @@ inline DevGraph dev_graph(const dbl_index *ix)
 {
     DevGraph g;
     g.n = ix->n;
-    g.out_ptr = ix->out_ptr;
+    g.vm = ix->vm;
     g.out_col = ix->out_col;
-    g.in_ptr = ix->in_ptr;
     g.in_col = ix->in_col;
-    g.ovo_off = ix->ovo;
-    g.ovo_len = ix->ovo + ix->n;
     g.pool_out = ix->pool_out;
-    g.ovi_off = ix->ovi;
-    g.ovi_len = ix->ovi + ix->n;
     g.pool_in = ix->pool_in;
     return g;
 }

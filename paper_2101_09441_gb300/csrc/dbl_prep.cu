@@ -157,6 +157,20 @@ __global__ void k_scatter_in(const int32_t *row_ptr, const int32_t *col, int32_t
     }
 }
 
+// Per-vertex adjacency metadata from the two CSRs (no inserted edges yet).
+__global__ void k_fill_vmeta(const int32_t *out_ptr, const int32_t *in_ptr, int32_t n, VMeta *vm, uint32_t *status)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o0 = out_ptr[x], od = out_ptr[x + 1] - o0;
+        const int32_t i0 = in_ptr[x], id = in_ptr[x + 1] - i0;
+        if (od >= (1 << kDegBits) || id >= (1 << kDegBits)) set_status(status, DBL_ERR_INVALID);
+        VMeta v;
+        v.d[0] = VAdj{o0, va_dc(od, 0), 0, 0};
+        v.d[1] = VAdj{i0, va_dc(id, 0), 0, 0};
+        vm[x] = v;
+    }
+}
+
 static unsigned grid_for(int64_t work, int per_block = kBlock)
 {
     int64_t b = (work + per_block - 1) / per_block;
@@ -193,8 +207,13 @@ dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s)
     cudaMemcpyAsync(cnt, ix->in_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
     if (m) { k_scatter_in<<<grid_for((int64_t)n * 32), kBlock, 0, s>>>(ix->out_ptr, ix->out_col, n, cnt, ix->in_col); ++ix->launches; }
     free_buf(ix, cnt, s);
+    k_fill_vmeta<<<grid_for(n), kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, n, ix->vm, ix->d_status);
+    ++ix->launches;
     e = cudaGetLastError();
-    return e ? cuda_fail(ix, e, "prep_graph") : DBL_OK;
+    if (e) return cuda_fail(ix, e, "prep_graph");
+    st = read_status(ix, s);
+    if (st) return fail(ix, st, "a vertex has 2^27 or more base edges in one direction");
+    return DBL_OK;
 }
 
 // ------------------------------------------------------------ landmarks
