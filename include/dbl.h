@@ -230,8 +230,8 @@ dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream);
  * context; recorded only when the index was built with DBL_FLAG_TIMING).
  * out[0] = number of marks m (<= 63); out[1..m] = nanoseconds since the launch
  * began (%globaltimer of block 0) at the start, after each grid barrier, and at
- * the end.  An insertion launch's barriers follow its phases: validate,
- * count + seed, grow, write + enqueue, then one per propagation level.
+ * the end.  An insertion launch's barriers follow its phases: validate +
+ * count, seed + grow, write + enqueue, then one per propagation level.
  * Synchronises `stream`.  Diagnostic only: the paper has no counterpart.
  */
 dbl_status dbl_phase_trace(dbl_index *ix, int64_t out[64], void *stream);

@@ -216,21 +216,21 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
 // ---------------------------------------------------------------------------
 // Whole insertion batch in one cooperative launch (persistent form), with a
 // grid barrier after each phase:
-//   P0 validate
-//   P1 count + seed: each edge takes its slot straight from the live segment
-//      length (atomicAdd on len, so no commit pass is needed) and applies its
-//      seed (skip test, endpoint ORs); whether fwd(v) / bwd(u) gained bits is
-//      kept in bit 30 of the edge's slot words (slots are < 2^29)
-//   P2 grow: the one edge whose slot equals the old capacity grows the
-//      segment (copying the old capacity's worth of entries; the batch's own
-//      entries are written after the barrier)
+//   P1 validate + count: each edge takes its slot straight from the live
+//      segment length (atomicAdd on len, so no commit pass is needed); if an
+//      id is invalid the slots are given back and the launch ends
+//   P2 seed + grow: each edge applies its seed (skip test, endpoint ORs);
+//      whether fwd(v) / bwd(u) gained bits is kept in bit 30 of the edge's
+//      slot words (slots are < 2^29); the one edge whose slot equals the old
+//      capacity grows the segment (copying the old capacity's worth of
+//      entries; the batch's own entries are written after the barrier)
 //   P3 write + enqueue: the batch's ids go into their slots, and the changed
 //      endpoints form the level-0 frontier (tasks resolved against the final
 //      segment offsets and lengths)
 //   P4 propagation levels, as in k_propagate_persistent.
 // Seeding before the appended edges are visible is sound: seeds read and OR
 // labels only, and the first level that walks adjacency runs after P3.  A
-// failed validation leaves every phase empty.
+// failed validation leaves the index as it was.
 constexpr int32_t kWantBit = 1 << 30;
 
 struct InsArgs {
@@ -251,6 +251,7 @@ struct InsArgs {
     int64_t wpd;
     unsigned long long *stats;
     uint32_t *status;
+    uint32_t *bad;  // this batch has an invalid id (zero before the launch)
 };
 
 template <int HS, int WD, int TEAM>
@@ -260,43 +261,58 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
     const int lane = threadIdx.x & 31;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
     const int32_t n = a.n;
-    // P0: validate; zero the level counters
-    if (!ld_volatile_u32(a.status)) {
-        for (int64_t i = t0; i < a.b; i += nt)
-            if ((uint32_t)a.src[i] >= (uint32_t)n || (uint32_t)a.dst[i] >= (uint32_t)n)
-                set_status(a.status, DBL_ERR_INVALID);
-    }
-    if (leader) a.c3[0] = a.c3[1] = a.c3[2] = 0;
-    if (!gs.sync(a.status) || ld_volatile_u32(a.status)) return;
-    // P1: slots from the live segment lengths, and the seeds
+    // a status latched before this launch (asynchronous form) leaves every
+    // phase empty; no block writes the status word before the first barrier,
+    // so all blocks read the same value here
+    if (ld_volatile_u32(a.status)) return;
+    // P1: validate and count: each edge takes its slots from the live segment
+    // lengths (atomicAdd on len, so no commit pass is needed); an invalid id
+    // raises the batch's own flag, and then every slot taken is given back
+    // after the barrier and nothing else changes
     {
-        unsigned long long loops = 0, skipped = 0, applied = 0;
+        unsigned long long loops = 0;
         for (int64_t i = t0; i < a.b; i += nt) {
             const int32_t u = a.src[i], v = a.dst[i];
+            if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
+                atomicExch(a.bad, 1u);
+                a.slot_out[i] = a.slot_in[i] = -1;
+                continue;
+            }
             if (u == v) {
                 a.slot_out[i] = a.slot_in[i] = -1;
                 ++loops;
                 continue;
             }
-            const int32_t so = atomicAdd(&a.vm[u].d[0].len, 1);
-            const int32_t si = atomicAdd(&a.vm[v].d[1].len, 1);
-            bool want_f = false, want_b = false;
-            if (seed_one<HS, WD>(u, v, a.rec, want_f, want_b)) ++applied;
-            else ++skipped;
-            a.slot_out[i] = so | (want_b ? kWantBit : 0);
-            a.slot_in[i] = si | (want_f ? kWantBit : 0);
+            a.slot_out[i] = atomicAdd(&a.vm[u].d[0].len, 1);
+            a.slot_in[i] = atomicAdd(&a.vm[v].d[1].len, 1);
+        }
+        if (leader) a.c3[0] = a.c3[1] = a.c3[2] = 0;
+        if (!gs.sync(a.status)) return;
+        if (ld_volatile_u32(a.bad)) {
+            for (int64_t i = t0; i < a.b; i += nt) {
+                if (a.slot_out[i] < 0) continue;
+                atomicSub(&a.vm[a.src[i]].d[0].len, 1);
+                atomicSub(&a.vm[a.dst[i]].d[1].len, 1);
+            }
+            if (!gs.sync(a.status)) return;  // every block has read the flag
+            if (leader) {
+                *(volatile uint32_t *)a.bad = 0;
+                set_status(a.status, DBL_ERR_INVALID);
+            }
+            return;
         }
         warp_stat_add(a.stats, 13, loops);
-        warp_stat_add(a.stats, 12, skipped);
-        warp_stat_add(a.stats, 11, applied);
     }
-    if (!gs.sync(a.status)) return;
-    // P2: grow the segments that overflowed; both directions' metadata are
-    // read in one round trip and the pool is reserved once per block for both
+    // P2: seeds (Algorithm 3's skip test, then the endpoint ORs; whether
+    // fwd(v) / bwd(u) gained bits is kept in bit 30 of the edge's slot words,
+    // slots being < 2^29), and growth of the segments that overflowed: both
+    // directions' metadata are read in one round trip and the pool is reserved
+    // once per block for both
     {
         __shared__ unsigned long long s_woff[2][32];  // per-warp growth, then its offset in the block's range
         __shared__ unsigned long long s_gbase[2];
         const int warp = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+        unsigned long long skipped = 0, applied = 0;
         for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
             const int64_t i = wbase + threadIdx.x;
             int32_t x[2] = {0, 0}, old_cap[2] = {0, 0}, nc[2] = {0, 0};
@@ -305,12 +321,19 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 const int32_t sw[2] = {a.slot_out[i], a.slot_in[i]};
                 x[0] = a.src[i];
                 x[1] = a.dst[i];
+                if (sw[0] >= 0) {
+                    bool want_f = false, want_b = false;
+                    if (seed_one<HS, WD>(x[0], x[1], a.rec, want_f, want_b)) ++applied;
+                    else ++skipped;
+                    if (want_b) a.slot_out[i] = sw[0] | kWantBit;
+                    if (want_f) a.slot_in[i] = sw[1] | kWantBit;
+                }
 #pragma unroll
                 for (int dir = 0; dir < 2; ++dir) {
                     if (sw[dir] < 0) continue;
                     ad[dir] = load_vadj(a.vm, dir, x[dir]);  // len is final after the count phase
                     old_cap[dir] = va_cap(ad[dir].dc);
-                    if ((sw[dir] & ~kWantBit) == old_cap[dir]) nc[dir] = grown_cap(ad[dir].len);
+                    if (sw[dir] == old_cap[dir]) nc[dir] = grown_cap(ad[dir].len);
                 }
             }
             unsigned long long incl[2];
@@ -352,6 +375,8 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             }
             __syncthreads();  // s_woff is reused by the next round
         }
+        warp_stat_add(a.stats, 12, skipped);
+        warp_stat_add(a.stats, 11, applied);
     }
     if (!gs.sync(a.status)) return;
     // P3: write the batch's ids into their slots, and enqueue the seeds'
@@ -467,6 +492,7 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     a.wpd = ix->wpd;
     a.stats = ix->d_stats;
     a.status = ix->d_status;
+    a.bad = ix->d_counts + kCntBad;
     tbegin(ix, DBL_KERNEL_PROPAGATE, s);
     dbl_status st;
     switch (ix->hs * 16 + ix->wd) {

@@ -315,7 +315,7 @@ enum {
     kCntTasks = 5,      // search tasks
     kCntClaimed = 6,    // claimed slots
     kCntOverflow = 7,   // search wave overflow flag
-    kCntGrow = 8,       // (2 words) pool growth request, int64
+    kCntBad = 8,        // the persistent insertion's invalid-id flag (zero between launches)
     kCntP0 = 10,        // (3 words) persistent propagation level counts
     kCntBarLeft = 13,   // grid barrier: blocks done with the launch
     kCntBarCount = 14,  // (2 words, 8-byte aligned) grid barrier: arrivals, uint64
