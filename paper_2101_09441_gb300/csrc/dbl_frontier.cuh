@@ -90,25 +90,21 @@ struct Stage {
     uint32_t *n;   // shared, entries used
 };
 
-__device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
-                                              const Stage &st)
+// Reserve room for `cnt` items per lane (warp-collective): in the block's
+// stage if they fit, else straight in the global frontier.  Returns the
+// lane's first position and whether it is global.
+__device__ __forceinline__ uint32_t stage_reserve(uint32_t cnt, const FrontierOut &f, const Stage &st, bool &global_out)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t nchunks = 0;
-    AdjRange r{0, 0, 0, 0};
-    if (want) {
-        r = adj_of(g, dir, x);
-        const int32_t d = r.bd + r.od;
-        if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
-    }
-    uint32_t incl = nchunks;
+    uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t t = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += t;
     }
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
+    global_out = false;
+    if (total == 0) return 0;
     uint32_t base = 0, global = 0;
     if (lane == 31) {
         uint32_t old = *(volatile uint32_t *)st.n;
@@ -124,14 +120,48 @@ __device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, con
         base = global ? atomicAdd(f.count, total) : old;
     }
     base = __shfl_sync(kFull, base, 31);
-    global = __shfl_sync(kFull, global, 31);
-    uint32_t pos = base + incl - nchunks;
-    for (uint32_t c = 0; c < nchunks; ++c, ++pos) {
-        const FTask t = make_ftask(x, dir, (int32_t)c, r);
-        if (!global) st.tasks[pos] = t;
-        else if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, t);
-        else set_status(f.status, DBL_ERR_CAPACITY);
+    global_out = __shfl_sync(kFull, global, 31) != 0;
+    return base + incl - cnt;
+}
+
+__device__ __forceinline__ void stage_write(bool global, uint32_t pos, const FTask &t, const FrontierOut &f,
+                                            const Stage &st)
+{
+    if (!global) st.tasks[pos] = t;
+    else if ((int64_t)pos < f.cap) store_ftask(f.tasks, pos, t);
+    else set_status(f.status, DBL_ERR_CAPACITY);
+}
+
+// The chunks of x (already marked) into the stage; warp-collective.
+__device__ __forceinline__ void stage_put(uint32_t nchunks, int32_t x, int dir, const AdjRange &r,
+                                          const FrontierOut &f, const Stage &st)
+{
+    bool global;
+    uint32_t pos = stage_reserve(nchunks, f, st, global);
+    for (uint32_t c = 0; c < nchunks; ++c, ++pos) stage_write(global, pos, make_ftask(x, dir, (int32_t)c, r), f, st);
+}
+
+// One ready task per lane (has) into the stage; warp-collective.
+__device__ __forceinline__ void stage_put_task(bool has, const FTask &t, const FrontierOut &f, const Stage &st)
+{
+    bool global;
+    const uint32_t pos = stage_reserve(has ? 1u : 0u, f, st, global);
+    if (has) stage_write(global, pos, t, f, st);
+}
+
+// Mark x in the frontier being filled and, if it is new there, stage its
+// chunks; warp-collective (lanes with want == false pass through).
+__device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
+                                              const Stage &st)
+{
+    uint32_t nchunks = 0;
+    AdjRange r{0, 0, 0, 0};
+    if (want) {
+        r = adj_of(g, dir, x);
+        const int32_t d = r.bd + r.od;
+        if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     }
+    stage_put(nchunks, x, dir, r, f, st);
 }
 
 // Move the block's stage to the global frontier; every thread of the block

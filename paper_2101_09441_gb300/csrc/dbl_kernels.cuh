@@ -27,77 +27,144 @@ __device__ __forceinline__ int flat_owner(uint32_t excl, uint32_t e)
     return lo;
 }
 
+// Local continuation: a vertex that a warp's pushes change, and whose edges
+// fit in one task, goes to the warp's own list (shared memory) instead of the
+// next level's frontier, and the warp processes its list in further rounds of
+// the same level (up to kLocalRounds), so chains of small vertices advance
+// several hops per grid barrier.  The vertex is marked in the next level's
+// bitmap as usual; the warp clears the bit before it reads the vertex's
+// record, with a fence in between: a push that lands after the read then finds
+// the bit clear and enqueues the vertex again (its atomicOr has returned
+// before it marks), so no bit is lost.  What is left in a list after the last
+// local round goes to the next level.
+constexpr int kLocal = 32;
+constexpr int kLocalRounds = 8;
+
+__device__ __forceinline__ void enqueue_local(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
+                                              const Stage &st, FTask *wl, int &wl_n)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t nchunks = 0;
+    AdjRange r{0, 0, 0, 0};
+    if (want) {
+        r = adj_of(g, dir, x);
+        const int32_t d = r.bd + r.od;
+        if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
+    }
+    const bool loc = nchunks == 1;
+    const unsigned bl = __ballot_sync(kFull, loc);
+    const int rank = __popc(bl & ((1u << lane) - 1u));
+    const bool to_local = loc && wl_n + rank < kLocal;
+    if (to_local) wl[wl_n + rank] = make_ftask(x, dir, 0, r);
+    wl_n = min(kLocal, wl_n + __popc(bl));
+    stage_put(to_local ? 0u : nchunks, x, dir, r, f, st);
+}
+
+// One round of the flattened level: lane-held tasks (has, tk); their
+// vertices' bits are cleared in clear_mark (fence after the clear when the
+// bitmap is the one being filled: local tasks).
+template <int HS>
+__device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, bool has, const FTask &tk,
+                                           uint32_t *clear_mark, bool local, const FrontierOut &f, const Stage &st,
+                                           FTask *wl, int &wl_n, unsigned long long &relaxed,
+                                           unsigned long long &ntask)
+{
+    constexpr int RW = 2 * HS;
+    const int lane = threadIdx.x & 31;
+    int32_t col0 = 0, ncol = 0, pool0 = 0;
+    uint32_t cnt = 0;
+    int dir = 0;
+    uint64_t rv[HS];
+#pragma unroll
+    for (int i = 0; i < HS; ++i) rv[i] = 0;
+    if (has) {
+        dir = task_dir(tk);
+        if (task_first(tk)) {
+            mark_clear(clear_mark, f.wpd, dir, tk.v);
+            if (local) __threadfence();
+        }
+        col0 = tk.col0;
+        ncol = task_ncol(tk);
+        pool0 = tk.pool0;
+        cnt = (uint32_t)task_edges(tk);
+        load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
+        ++ntask;
+    }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += x;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t e = base + lane;
+        const int owner = flat_owner(excl, e);
+        const int odir = __shfl_sync(kFull, dir, owner);
+        const int32_t ocol0 = __shfl_sync(kFull, col0, owner), oncol = __shfl_sync(kFull, ncol, owner);
+        const int32_t opool0 = __shfl_sync(kFull, pool0, owner);
+        const int32_t oe = (int32_t)(e - __shfl_sync(kFull, excl, owner));
+        uint64_t orv[HS];
+#pragma unroll
+        for (int i = 0; i < HS; ++i) orv[i] = __shfl_sync(kFull, rv[i], owner);
+        bool want = false;
+        int32_t x = 0;
+        if (e < total) {
+            x = task_edge(g, odir, ocol0, oncol, opool0, oe);
+            ++relaxed;
+            uint64_t *px = rec + (size_t)x * RW + (odir ? HS : 0);
+            uint64_t rx[HS];
+            load_half<HS>(px, rx);
+#pragma unroll
+            for (int i = 0; i < HS; ++i) {
+                if (orv[i] & ~rx[i]) {
+                    const unsigned long long old = atomicOr((unsigned long long *)(px + i), orv[i]);
+                    want |= (orv[i] & ~old) != 0;
+                }
+            }
+        }
+        enqueue_local(want, x, odir, g, f, st, wl, wl_n);
+    }
+}
+
 // Flattened level (TEAM == 1): each lane takes one task per round (task
 // w + nwarps*(32r + lane) for warp w, so a hub's consecutive chunks land in
 // different warps), and the warp walks the concatenation of its tasks' edges
 // 32 at a time; each edge's task data come from the owner lane by shuffles.
 // A round costs ceil(edges of the warp's tasks / 32) iterations, whatever the
-// mix of task sizes.
+// mix of task sizes.  Then the warp's local rounds (above).
 template <int HS>
 __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const FTask *tasks,
                                                   uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                                   unsigned long long *stats, int64_t warp, int64_t nwarps,
                                                   const Stage &st)
 {
-    constexpr int RW = 2 * HS;
+    __shared__ FTask s_wl[32 * kLocal];
     const int lane = threadIdx.x & 31;
+    FTask *wl = s_wl + (threadIdx.x >> 5) * kLocal;
+    int wl_n = 0;  // warp-uniform
     unsigned long long relaxed = 0, ntask = 0;
     if ((int64_t)ntasks > f.cap) ntasks = (uint32_t)f.cap;  // both frontier buffers have the same capacity
     for (int64_t r0 = 0; warp + nwarps * r0 < (int64_t)ntasks; r0 += 32) {  // warp-uniform
         const int64_t t = warp + nwarps * (r0 + lane);
-        int32_t col0 = 0, ncol = 0, pool0 = 0;
-        uint32_t cnt = 0;
-        int dir = 0;
-        uint64_t rv[HS];
-#pragma unroll
-        for (int i = 0; i < HS; ++i) rv[i] = 0;
-        if (t < (int64_t)ntasks) {
-            const FTask tk = load_ftask(tasks, t);
-            dir = task_dir(tk);
-            if (task_first(tk)) mark_clear(cur_mark, f.wpd, dir, tk.v);
-            col0 = tk.col0;
-            ncol = task_ncol(tk);
-            pool0 = tk.pool0;
-            cnt = (uint32_t)task_edges(tk);
-            load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
-            ++ntask;
-        }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += x;
-        }
-        const uint32_t excl = incl - cnt;
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t e = base + lane;
-            const int owner = flat_owner(excl, e);
-            const int odir = __shfl_sync(kFull, dir, owner);
-            const int32_t ocol0 = __shfl_sync(kFull, col0, owner), oncol = __shfl_sync(kFull, ncol, owner);
-            const int32_t opool0 = __shfl_sync(kFull, pool0, owner);
-            const int32_t oe = (int32_t)(e - __shfl_sync(kFull, excl, owner));
-            uint64_t orv[HS];
-#pragma unroll
-            for (int i = 0; i < HS; ++i) orv[i] = __shfl_sync(kFull, rv[i], owner);
-            bool want = false;
-            int32_t x = 0;
-            if (e < total) {
-                x = task_edge(g, odir, ocol0, oncol, opool0, oe);
-                ++relaxed;
-                uint64_t *px = rec + (size_t)x * RW + (odir ? HS : 0);
-                uint64_t rx[HS];
-                load_half<HS>(px, rx);
-#pragma unroll
-                for (int i = 0; i < HS; ++i) {
-                    if (orv[i] & ~rx[i]) {
-                        const unsigned long long old = atomicOr((unsigned long long *)(px + i), orv[i]);
-                        want |= (orv[i] & ~old) != 0;
-                    }
-                }
-            }
-            stage_enqueue(want, x, odir, g, f, st);
-        }
+        const bool has = t < (int64_t)ntasks;
+        const FTask tk = has ? load_ftask(tasks, t) : FTask{0, 0u, 0, 0};
+        flat_round<HS>(g, rec, has, tk, cur_mark, false, f, st, wl, wl_n, relaxed, ntask);
+    }
+    for (int lr = 0; lr < kLocalRounds && wl_n > 0; ++lr) {
+        __syncwarp();
+        const bool has = lane < wl_n;
+        const FTask tk = has ? wl[lane] : FTask{0, 0u, 0, 0};
+        __syncwarp();
+        wl_n = 0;
+        flat_round<HS>(g, rec, has, tk, f.mark, true, f, st, wl, wl_n, relaxed, ntask);
+    }
+    __syncwarp();
+    {
+        const bool has = lane < wl_n;  // left for the next level (already marked there)
+        const FTask tk = has ? wl[lane] : FTask{0, 0u, 0, 0};
+        stage_put_task(has, tk, f, st);
     }
     warp_stat_add(stats, 9, ntask);
     warp_stat_add(stats, 10, relaxed);
