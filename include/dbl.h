@@ -254,7 +254,7 @@ dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
  * level-by-level or persistent propagation -- each `trials` times from the
  * same snapshot (slot 3 is overwritten), and keep the fastest in the index's
  * options.  The index's labels and graph are restored afterwards.
- * report (may be NULL, else 16 doubles) receives [0..9] mean ms per
+ * report (may be NULL, else 16 doubles) receives [0..9] the fastest trial's ms per
  * candidate (level-by-level teams 1, 4, 8, 16, 32, then persistent teams
  * 1..32), [10] best team, [11] 1 if persistent, [12] best ms.  DBL_FLAG_ASYNC/TIMING are off during the trials
  * and restored after.  Synchronous.

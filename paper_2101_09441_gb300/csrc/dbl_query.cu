@@ -33,21 +33,21 @@ __host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (wo
 // Each thread takes QPT queries (default 2) and issues all
 // of their record loads before using any, so that many DRAM sectors are in
 // flight per warp; answers and codes are written coalesced, the deciding
-// rules are counted per thread, and undecided pairs are collected in a
-// shared-memory stage and appended to the undecided list with one atomic per
-// block (one per warp put ~10^5 atomics on a single word: a third of the
-// kernel's time).
+// rules are counted per thread.  An undecided pair gets the answer byte
+// kAnsUndecided; the search compacts those from the answer array itself
+// (compact_undecided), so the label test writes nothing else (appending to an
+// undecided list here, one atomic per warp, took a third of the kernel's time;
+// one per block through a shared-memory stage still took a tenth).
+constexpr uint8_t kAnsUndecided = 2;
+
 template <int WD, int WB, int QPT>
 __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const int32_t *qv, int64_t q,
                                                         const uint64_t *rec, int32_t n, uint8_t *ans,
-                                                        uint8_t *code, int32_t *und, uint32_t *n_und,
-                                                        uint32_t *status, unsigned long long *stats)
+                                                        uint8_t *code, uint32_t *status, unsigned long long *stats)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
     const int lane = threadIdx.x & 31;
-    DBL_BLOCK_ISTAGE(ust);
-    const IList ulist{und, n_und, q, nullptr};
     unsigned int counts[6] = {0, 0, 0, 0, 0, 0};  // per thread, by deciding rule (constant indices only)
     const int64_t tile = (int64_t)blockDim.x * QPT;
     const int64_t stride = (int64_t)gridDim.x * tile;
@@ -76,7 +76,6 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
         for (int j = 0; j < QPT; ++j) {
             const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
             uint8_t a = 0, c = DBL_CODE_UNDECIDED;
-            bool undecided = false;
             if (live[j]) {
                 if ((uint32_t)u[j] >= (uint32_t)n || (uint32_t)v[j] >= (uint32_t)n) {
                     set_status(status, DBL_ERR_INVALID);
@@ -104,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
                     } else if (su | sv) {
                         c = DBL_CODE_THM2;
                     } else {
-                        undecided = true;
+                        a = kAnsUndecided;
                     }
                 }
                 __stcs(ans + i, a);
@@ -112,15 +111,69 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
             }
 #pragma unroll
             for (int r = 1; r < 6; ++r) counts[r] += (live[j] && c == r) ? 1u : 0u;
-            if (undecided) istage_push(ust, (int32_t)i, ulist);
         }
     }
-    istage_flush(ust, ulist);
 #pragma unroll
     for (int r = 1; r < 6; ++r) {
         const unsigned int t = __reduce_add_sync(kFull, counts[r]);
         if (lane == 0 && t) atomicAdd(stats + r, (unsigned long long)t);
     }
+}
+
+// The undecided pairs of a batch, from the answer array: und[] gets their
+// indices (in no particular order) and *n_und their number.  The aligned
+// middle of the array is read 16 bytes at a time, two words per thread and
+// round (bytes compared four at a time), and each round's hits are written
+// after one block-level reservation (the loop is block-uniform); the few
+// bytes before the first and after the last aligned word are checked by
+// block 0.
+__device__ __forceinline__ uint32_t undecided_bits(uint32_t w)
+{
+    const uint32_t m = __vcmpeq4(w, 0x01010101u * kAnsUndecided);  // 0xff per matching byte
+    return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
+}
+
+__device__ __forceinline__ void compact_undecided(const uint8_t *ans, int64_t q, int32_t *und, uint32_t *n_und)
+{
+    constexpr int K = 2;  // 16-byte words per thread and round
+    int64_t head = (int64_t)((16u - ((uint32_t)(uintptr_t)ans & 15u)) & 15u);
+    if (head > q) head = q;
+    const int64_t nw = (q - head) / 16;
+    const int64_t tail0 = head + nw * 16;
+    const uint4 *wp = reinterpret_cast<const uint4 *>(ans + head);
+    const int64_t tile = (int64_t)blockDim.x * K;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < nw; base += (int64_t)gridDim.x * tile) {
+        uint32_t hits = 0;  // bit 16k + b: byte b of the thread's word k
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t wi = base + (int64_t)k * blockDim.x + threadIdx.x;
+            if (wi < nw) {
+                const uint4 w = __ldcg(wp + wi);
+                hits |= (undecided_bits(w.x) | (undecided_bits(w.y) << 4) | (undecided_bits(w.z) << 8) |
+                         (undecided_bits(w.w) << 12)) << (16 * k);
+            }
+        }
+        uint32_t total = 0;
+        uint32_t pos = block_reserve((uint32_t)__popc(hits), n_und, &total);
+        while (hits) {
+            const int bit = __ffs(hits) - 1;
+            hits &= hits - 1;
+            const int64_t wi = base + (int64_t)(bit >> 4) * blockDim.x + threadIdx.x;
+            und[pos++] = (int32_t)(head + wi * 16 + (bit & 15));
+        }
+    }
+    if (blockIdx.x == 0) {
+        const int64_t extra = head + (q - tail0);  // fewer than 32
+        if ((int64_t)threadIdx.x < extra) {
+            const int64_t i = threadIdx.x < head ? (int64_t)threadIdx.x : tail0 + (threadIdx.x - head);
+            if (ans[i] == kAnsUndecided) und[atomicAdd(n_und, 1u)] = (int32_t)i;
+        }
+    }
+}
+
+__global__ void k_compact_undecided(const uint8_t *ans, int64_t q, int32_t *und, uint32_t *n_und)
+{
+    compact_undecided(ans, q, und, n_und);
 }
 
 // ------------------------------------------------------------ search
@@ -154,7 +207,9 @@ struct SearchArgs {
     SearchCtx c;
     SearchTask *tasks;
     int64_t task_cap;
-    const int32_t *und;
+    int32_t *und;
+    uint32_t *n_und;
+    int64_t q;
     const int32_t *qu, *qv;
     uint8_t *ans, *code;
     unsigned long long *stats;
@@ -585,6 +640,8 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
                                              const IStage &nst)
 {
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    compact_undecided(a.ans, a.q, a.und, a.n_und);
+    if (!gs.sync(status)) return;
     const uint32_t U = ld_volatile_u32(n_und);
     if (U == 0) return;
     if (leader) {
@@ -679,8 +736,8 @@ static unsigned blocks_for(int64_t work)
     return (unsigned)b;
 }
 
-static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv, uint8_t *ans,
-                              uint8_t *code, uint32_t *n_claimed, uint32_t *overflow)
+static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv, int64_t q,
+                              uint8_t *ans, uint8_t *code, uint32_t *n_claimed, uint32_t *overflow)
 {
     SearchArgs a;
     a.g = dev_graph(ix);
@@ -691,6 +748,8 @@ static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, con
     a.tasks = c->stask;
     a.task_cap = c->stask_cap;
     a.und = c->und;
+    a.n_und = c->d_counts + kCntUnd;
+    a.q = q;
     a.qu = qu;
     a.qv = qv;
     a.ans = ans;
@@ -734,7 +793,7 @@ static dbl_status run_search_wave(dbl_index *ix, dbl_qctx *c, const int32_t *qu,
 {
     uint32_t *cnt = c->d_counts;
     uint32_t *h = c->h_pinned;
-    const SearchArgs a = search_args(ix, c, qu, qv, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
+    const SearchArgs a = search_args(ix, c, qu, qv, 0, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
     cudaMemsetAsync(cnt + kCntSlots0, 0, sizeof(uint32_t) * 5, s);  // slots0, slots1, tasks, claimed, overflow
     SlotList lists[2] = {{c->slot_list[0], cnt + kCntSlots0, c->table_slots},
                          {c->slot_list[1], cnt + kCntSlots1, c->table_slots}};
@@ -784,7 +843,7 @@ static dbl_status run_search_wave(dbl_index *ix, dbl_qctx *c, const int32_t *qu,
 
 template <int WD, int WB, int TEAM>
 static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv,
-                                           uint8_t *ans, uint8_t *code, cudaStream_t s)
+                                           int64_t q, uint8_t *ans, uint8_t *code, cudaStream_t s)
 {
     constexpr int kPB = pblock_of(hs_of(WD + WB));
     static int blocks_per_sm = -1;
@@ -793,7 +852,7 @@ static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int
     if (blocks_per_sm < 1) return qfail(c, DBL_ERR_CUDA, "persistent search: kernel does not fit on an SM");
     PersistState *ps = (PersistState *)c->pstate;
     cudaMemsetAsync(ps, 0, sizeof(PersistState), s);
-    SearchArgs a = search_args(ix, c, qu, qv, ans, code, &ps->n_claimed, &ps->overflow);
+    SearchArgs a = search_args(ix, c, qu, qv, q, ans, code, &ps->n_claimed, &ps->overflow);
     const uint32_t *n_und = c->d_counts + kCntUnd;
     GridBarrier bar = grid_barrier_at(c->d_counts);
     if ((ix->opt.flags & DBL_FLAG_TIMING) && c == ix->qc) bar.trace = ix->d_trace;
@@ -826,22 +885,25 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     if (blocks < 1) blocks = 1;
     qt_begin(ix, c, DBL_KERNEL_QUERY_LABEL, s);
     auto kern = qpt >= 4 ? k_query_label<WD, WB, 4> : (qpt == 2 ? k_query_label<WD, WB, 2> : k_query_label<WD, WB, 1>);
-    kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->und, cnt + kCntUnd, c->d_status,
-                                             ix->d_stats);
+    kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->d_status, ix->d_stats);
     ++ix->launches;
     qt_end(ix, c, s);
     // one cooperative launch runs every wave, for the index's own context only
     // (cooperative grids of concurrent contexts would compete for residency)
     if ((ix->opt.flags & DBL_FLAG_PERSISTENT) && c == ix->qc) {
         switch (ix->opt.team) {
-        case 1: st = launch_search_persistent<WD, WB, 1>(ix, c, u, v, ans, code, s); break;
-        case 4: st = launch_search_persistent<WD, WB, 4>(ix, c, u, v, ans, code, s); break;
+        case 1: st = launch_search_persistent<WD, WB, 1>(ix, c, u, v, q, ans, code, s); break;
+        case 4: st = launch_search_persistent<WD, WB, 4>(ix, c, u, v, q, ans, code, s); break;
         case 16:
-        case 32: st = launch_search_persistent<WD, WB, 16>(ix, c, u, v, ans, code, s); break;
-        default: st = launch_search_persistent<WD, WB, 8>(ix, c, u, v, ans, code, s); break;
+        case 32: st = launch_search_persistent<WD, WB, 16>(ix, c, u, v, q, ans, code, s); break;
+        default: st = launch_search_persistent<WD, WB, 8>(ix, c, u, v, q, ans, code, s); break;
         }
         return st;  // device errors (invalid ids, timeout) latch in the context's status word
     }
+    qt_begin(ix, c, DBL_KERNEL_SEARCH_OTHER, s);
+    k_compact_undecided<<<blocks_for((q + 31) / 32), kBlock, 0, s>>>(ans, q, c->und, cnt + kCntUnd);
+    ++ix->launches;
+    qt_end(ix, c, s);
     uint32_t *h = c->h_pinned;
     cudaMemcpyAsync(h, cnt + kCntUnd, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h + 8, c->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
