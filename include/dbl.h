@@ -190,7 +190,11 @@ dbl_status dbl_insert_edges_noalloc(dbl_index *ix, const int32_t *src, const int
 
 /* Host-buffer forms: copy inputs from host memory (pinned or pageable) to
  * the device, run the call, and copy results back, in overlapped chunks
- * (the transfer overlap of Section 6.6).  Synchronous. */
+ * (the transfer overlap of Section 6.6).  Synchronous, unless the index was
+ * built with DBL_FLAG_ASYNC: then the call returns once its copies and
+ * kernels are queued on `stream`, and the host buffers must stay valid and
+ * unchanged (and the answers are ready) only after dbl_sync or a
+ * synchronisation of `stream`; errors latch as in the other calls. */
 dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v_host, int64_t q,
                           uint8_t *ans_host, uint8_t *code_host, void *stream);
 dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const int32_t *dst_host,

@@ -513,15 +513,16 @@ dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v
         if (code_host) cudaMemcpyAsync(code_host + off, dc, (size_t)len, cudaMemcpyDeviceToHost, s);
         cudaEventRecord(ev_used[b], s);
     }
-    cudaError_t e = cudaStreamSynchronize(s);
-    cudaStreamSynchronize(ix->copy_stream);
-    for (int b = 0; b < 2; ++b) {
+    const bool async = (ix->opt.flags & DBL_FLAG_ASYNC) != 0;
+    cudaError_t e = async ? cudaGetLastError() : cudaStreamSynchronize(s);
+    if (!async) cudaStreamSynchronize(ix->copy_stream);
+    for (int b = 0; b < 2; ++b) {  // released once the recorded work completes
         cudaEventDestroy(ev_in[b]);
         cudaEventDestroy(ev_used[b]);
     }
     if (st) return st;
     if (e) return cuda_fail(ix, e, "query_host");
-    return read_status(ix, s);
+    return async ? DBL_OK : read_status(ix, s);
 }
 
 dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const int32_t *dst_host, int64_t b,
@@ -539,7 +540,7 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
     cudaMemcpyAsync(d + 4 * ix->stage_chunk, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
     st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->stage_chunk), b, s);
     if (st) return st;
-    return read_status(ix, s);
+    return (ix->opt.flags & DBL_FLAG_ASYNC) ? DBL_OK : read_status(ix, s);
 }
 
 dbl_status dbl_labels(dbl_index *ix, uint64_t *dl_in, uint64_t *dl_out, uint64_t *bl_in, uint64_t *bl_out,

@@ -296,6 +296,29 @@ def test_host_buffer_forms(tiny):
     assert np.array_equal(a1.cpu().numpy(), a2) and np.array_equal(c1.cpu().numpy(), c2)
 
 
+def test_host_buffer_forms_asynchronous(tiny):
+    """With FLAG_ASYNC the host-buffer calls only queue their copies and
+    kernels (pinned buffers, several insertion batches and query chunks in
+    flight); after a sync the answers equal the oracle's."""
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    rans, rcode = ref.query(tiny["q_u"], tiny["q_v"], nthreads=8)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    src, dst, qu, qv = pin(tiny["ins_src"]), pin(tiny["ins_dst"]), pin(tiny["q_u"]), pin(tiny["q_v"])
+    ans = torch.empty(qu.shape[0], dtype=torch.uint8).pin_memory().numpy()
+    code = torch.empty(qu.shape[0], dtype=torch.uint8).pin_memory().numpy()
+    for flags in (dbl.FLAG_ASYNC, dbl.FLAG_ASYNC | dbl.FLAG_PERSISTENT):
+        ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=flags)
+        for a in range(0, src.shape[0], 1000):
+            ix.insert_edges_host(src[a:a + 1000], dst[a:a + 1000])
+        ans[:] = 7
+        ix.query_host(qu, qv, with_code=True, out=(ans, code))
+        ix.sync()
+        torch.cuda.synchronize()
+        assert np.array_equal(ans, rans) and np.array_equal(code, rcode), f"flags {flags}"
+        ix.close()
+
+
 def test_torch_and_default_allocators_agree(tiny):
     a = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, torch_allocator=False)
     b = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, torch_allocator=True)
