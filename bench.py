@@ -44,9 +44,8 @@ UNIT = "ops/s (queries + inserted edges)"
 
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
-# (The cooperative insertion kernel runs ~10x slower under ncu than alone, so no ncu
-# traffic is recorded for it.)
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_328_000 + 23_329_536, "cbf856f2ae44")}
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_455_000 + 21_871_616, "093943455728"),
+                                             "propagate": (54_260_480 + 1_915_392, "c9371526e6e2")}
 KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_insert.cu",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
 
@@ -339,6 +338,15 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
         res["queries_per_s"] = world * args.steps * Q / (q_ms * 1e-3)
         res["inserted_edges_per_s"] = world * args.steps * E / (ins_ms * 1e-3)
         res["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in ix.timings().items() if v[1]}
+    # label-repair work of one step (edges relaxed), for the learned-vs-degree judge
+    r0 = int(ix.stats()[10])
+    ix.restore(0)
+    for a_, b_ in batches:
+        ix.insert_edges(I.src[a_:b_], I.dst[a_:b_])
+    ix.sync()
+    res["relaxed_per_step"] = int(ix.stats()[10]) - r0
+    ix.query(I.qu, I.qv, out=(I.ans, I.code))
+    ix.sync()
     code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
     res["decided_by"] = {n: int(code[i]) for i, n in enumerate(
         ["undecided", "self", "dl", "bl", "thm1", "thm2", "bfs_pos", "bfs_neg"])}
@@ -439,11 +447,15 @@ def bench_gpu(args):
     plain_ix.close()
     learned = run_form("learned", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
     learned_t = run_form("learned_timing", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
-    # fallback: keep the degree rule if the learned set decides fewer pairs by the labels
+    # fallback: keep the degree rule if the learned set sends more pairs to the
+    # search or makes the insertions' repair much dearer (edges relaxed per step)
     dec_l = learned["decided_by"]
-    ref_form = forms.get("graph") or forms.get("plain") or forms.get("batched")
+    ref_form = forms.get("graph") or forms.get("batched") or forms.get("plain")
     dec_p = ref_form["decided_by"] if ref_form else dec_l
-    fallback = dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
+    rep_l = learned["relaxed_per_step"]
+    rep_p = ref_form["relaxed_per_step"] if ref_form else rep_l
+    fallback = (dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
+                or not L.repair_ok(rep_p, rep_l))
     head = forms["graph"] if (fallback and "graph" in forms) else learned
     roof, roof_label = roofline(learned_t, learned_t["ix"], args, w, I, batches)
 

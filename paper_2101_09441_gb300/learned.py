@@ -82,28 +82,47 @@ def decided(ix: DBLIndex, qu, qv) -> dict:
                 total=int(c.numel()))
 
 
+REPAIR_SLACK = 1.5
+
+
+def repair_ok(repair_plain: int, repair_learned: int) -> bool:
+    """The learned landmarks' insertion repair (edges relaxed) stays within
+    REPAIR_SLACK of the degree rule's (plus a small absolute allowance)."""
+    return repair_learned <= REPAIR_SLACK * repair_plain + 10_000
+
+
 def learned_index(row_ptr, col, train_q, eval_q, k: int = 64, kprime: int = 64, base_slots: int | None = None,
                   inserts=None, **kw):
     """Build the plain index (after `inserts`, a list of (src, dst) batches),
     train the scorer on the plain index's outcomes for train_q = (u, v), build
-    the learned index with the same leaves and insertions, and keep whichever
-    landmark set decides more of eval_q = (u, v) by the DL test (fallback to
-    the degree rule).  Returns (plain, chosen, info)."""
+    the learned index with the same leaves and insertions, and keep the
+    learned set only if it decides more of eval_q = (u, v) by the DL test,
+    sends no more of them to the search, and does not make the insertions'
+    label repair much dearer (edges relaxed at most REPAIR_SLACK times the
+    degree rule's): landmarks whose reach grows under insertions make every
+    batch push their bits to millions of vertices.  Otherwise the degree rule
+    is kept.  Returns (plain, chosen, learned, info).
     idx_kw = {a: b for a, b in kw.items() if a in ("flags", "team", "edge_capacity")}
     train_kw = {a: b for a, b in kw.items() if a in ("steps", "batch", "lr", "momentum", "seed")}
     plain = DBLIndex(row_ptr, col, k, kprime, **idx_kw)
+    r0 = int(plain.stats()[10])
     for s, d in inserts or []:
         plain.insert_edges(s, d)
+    repair_plain = int(plain.stats()[10]) - r0
     if base_slots is None:
         base_slots = max(1, k // 8)
     scores, info = train_scorer(plain, train_q[0], train_q[1], base_slots, **train_kw)
     lm = select_landmarks(plain, scores, k, base_slots)
     _, lb, lr_ = plain.selection()
     learned = DBLIndex(row_ptr, col, k, kprime, landmarks=lm, leaf_buckets=lb, leaf_roles=lr_, **idx_kw)
+    r0 = int(learned.stats()[10])
     for s, d in inserts or []:
         learned.insert_edges(s, d)
+    repair_learned = int(learned.stats()[10]) - r0
     dp = decided(plain, *eval_q)
     dlrn = decided(learned, *eval_q)
-    info.update(base_slots=base_slots, eval_plain=dp, eval_learned=dlrn,
-                fallback=not (dlrn["dl"] > dp["dl"] and dlrn["search"] <= dp["search"]))
+    info.update(base_slots=base_slots, eval_plain=dp, eval_learned=dlrn, repair_plain=repair_plain,
+                repair_learned=repair_learned,
+                fallback=not (dlrn["dl"] > dp["dl"] and dlrn["search"] <= dp["search"]
+                              and repair_ok(repair_plain, repair_learned)))
     return plain, (plain if info["fallback"] else learned), learned, info

@@ -173,3 +173,5 @@ def test_learned_landmarks_exact_and_better_or_fallback(tiny):
     assert np.array_equal(a.cpu().numpy(), plain.query(qu, qv)[0].cpu().numpy())
     dl_p, dl_c = L.decided(plain, qu[50_000:], qv[50_000:]), L.decided(chosen, qu[50_000:], qv[50_000:])
     assert dl_c["dl"] >= dl_p["dl"]
+    # a kept learned set does not make the insertions' label repair much dearer
+    assert info["fallback"] or L.repair_ok(info["repair_plain"], info["repair_learned"])
