@@ -101,7 +101,7 @@ def learned_index(row_ptr, col, train_q, eval_q, k: int = 64, kprime: int = 64, 
     label repair much dearer (edges relaxed at most REPAIR_SLACK times the
     degree rule's): landmarks whose reach grows under insertions make every
     batch push their bits to millions of vertices.  Otherwise the degree rule
-    is kept.  Returns (plain, chosen, learned, info).
+    is kept.  Returns (plain, chosen, learned, info)."""
     idx_kw = {a: b for a, b in kw.items() if a in ("flags", "team", "edge_capacity")}
     train_kw = {a: b for a, b in kw.items() if a in ("steps", "batch", "lr", "momentum", "seed")}
     plain = DBLIndex(row_ptr, col, k, kprime, **idx_kw)
