@@ -294,11 +294,12 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     if build_t:
         res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
     if flags & dbl.FLAG_PERSISTENT and not args.no_autotune:
-        # autotuned frontier schedule (sample: the first three insertion batches
-        # and 1M queries); the persistent forms keep the fastest persistent candidate
-        a, b = batches[0][0], batches[min(2, len(batches) - 1)][1]
+        # autotuned frontier schedule (sample: the step's insertions as one batch
+        # and 1M queries; a few batches of the first hundred thousand edges do not
+        # separate the candidates); the persistent forms keep the fastest
+        # persistent candidate
         nq = min(1_000_000, Q)
-        tune = ix.autotune(I.src[a:b], I.dst[a:b], I.qu[:nq], I.qv[:nq], trials=4)
+        tune = ix.autotune(I.src, I.dst, I.qu[:nq], I.qv[:nq], trials=4)
         team = min(tune["persistent_ms"], key=tune["persistent_ms"].get)
         ix.set_schedule(team, persistent=True)
         res["autotune"] = {"team": team, "persistent_ms": tune["persistent_ms"], "level_ms": tune["level_ms"]}
