@@ -277,6 +277,8 @@ static void destroy_impl(dbl_index *ix, cudaStream_t s)
     ix->owned.clear();
     if (ix->h_pinned) cudaFreeHost(ix->h_pinned);
     if (ix->copy_stream) cudaStreamDestroy(ix->copy_stream);
+    for (auto &e : ix->ev_stage_used)
+        if (e) cudaEventDestroy(e);
     for (auto &r : ix->tranges) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -468,6 +470,11 @@ static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
         cudaError_t e = cudaStreamCreateWithFlags(&ix->copy_stream, cudaStreamNonBlocking);
         if (e) return cuda_fail(ix, e, "copy stream");
     }
+    for (auto &e : ix->ev_stage_used) {
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return cuda_fail(ix, cudaGetLastError(), "stage events");
+        // (re)allocated buffers: the first uploads wait for everything queued so far
+        cudaEventRecord(e, s);
+    }
     ix->stage_chunk = chunk;
     return DBL_OK;
 }
@@ -480,21 +487,22 @@ dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v
         return fail(ix, DBL_ERR_INVALID, "query_host: bad batch");
     if (q == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t chunk = std::min<int64_t>(q, 1 << 22);
+    // large chunks: each chunk is one label test and one search (whose cost
+    // has a fixed part); the upload of the first chunk overlaps earlier work
+    const int64_t chunk = std::min<int64_t>(q, 1 << 24);
     dbl_status st = ensure_stage(ix, chunk, s);
     if (st) return st;
     const int64_t nch = (q + chunk - 1) / chunk;
-    cudaEvent_t ev_in[2], ev_used[2];
-    for (int b = 0; b < 2; ++b) {
-        cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&ev_used[b], cudaEventDisableTiming);
-        cudaEventRecord(ev_used[b], s);
-    }
+    // A chunk's upload waits only until the buffer's previous query chunk is done
+    // with it (ev_stage_used, kept across calls), not for everything queued on the
+    // stream: uploads overlap earlier work such as insertions.
+    cudaEvent_t ev_in[2];
+    for (int b = 0; b < 2; ++b) cudaEventCreateWithFlags(&ev_in[b], cudaEventDisableTiming);
     auto stage_in = [&](int64_t c) {
         const int b = (int)(c & 1);
         const int64_t off = c * chunk, len = std::min(chunk, q - off);
         char *d = (char *)ix->dstage[b];
-        cudaStreamWaitEvent(ix->copy_stream, ev_used[b], 0);
+        cudaStreamWaitEvent(ix->copy_stream, ix->ev_stage_used[b], 0);
         cudaMemcpyAsync(d, u_host + off, 4 * (size_t)len, cudaMemcpyHostToDevice, ix->copy_stream);
         cudaMemcpyAsync(d + 4 * chunk, v_host + off, 4 * (size_t)len, cudaMemcpyHostToDevice, ix->copy_stream);
         cudaEventRecord(ev_in[b], ix->copy_stream);
@@ -511,15 +519,12 @@ dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v
         if (st) break;
         cudaMemcpyAsync(ans_host + off, da, (size_t)len, cudaMemcpyDeviceToHost, s);
         if (code_host) cudaMemcpyAsync(code_host + off, dc, (size_t)len, cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(ev_used[b], s);
+        cudaEventRecord(ix->ev_stage_used[b], s);
     }
     const bool async = (ix->opt.flags & DBL_FLAG_ASYNC) != 0;
     cudaError_t e = async ? cudaGetLastError() : cudaStreamSynchronize(s);
     if (!async) cudaStreamSynchronize(ix->copy_stream);
-    for (int b = 0; b < 2; ++b) {  // released once the recorded work completes
-        cudaEventDestroy(ev_in[b]);
-        cudaEventDestroy(ev_used[b]);
-    }
+    for (int b = 0; b < 2; ++b) cudaEventDestroy(ev_in[b]);  // released once the recorded work completes
     if (st) return st;
     if (e) return cuda_fail(ix, e, "query_host");
     return async ? DBL_OK : read_status(ix, s);
@@ -533,12 +538,18 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
         return fail(ix, DBL_ERR_INVALID, "insert_host: bad batch");
     if (b == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    dbl_status st = ensure_stage(ix, std::max<int64_t>(b, 1 << 16), s);
-    if (st) return st;
-    char *d = (char *)ix->dstage[0];
+    if (b > ix->istage_cap) {
+        free_buf(ix, ix->istage, s);
+        ix->istage = nullptr;
+        const int64_t cap = std::max<int64_t>(b, 1 << 16);
+        dbl_status st = alloc_buf(ix, &ix->istage, 8 * (size_t)cap, s);
+        if (st) return st;
+        ix->istage_cap = cap;
+    }
+    char *d = (char *)ix->istage;
     cudaMemcpyAsync(d, src_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(d + 4 * ix->stage_chunk, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
-    st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->stage_chunk), b, s);
+    cudaMemcpyAsync(d + 4 * ix->istage_cap, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
+    dbl_status st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->istage_cap), b, s);
     if (st) return st;
     return (ix->opt.flags & DBL_FLAG_ASYNC) ? DBL_OK : read_status(ix, s);
 }

@@ -260,8 +260,11 @@ struct dbl_index {
     uint32_t *h_pinned = nullptr;     // pinned host words for small readbacks
 
     // host-buffer staging (dbl_query_host / dbl_insert_edges_host)
-    void *dstage[2] = {nullptr, nullptr};
+    void *dstage[2] = {nullptr, nullptr};  // query host form: double-buffered chunks
     int64_t stage_chunk = 0;
+    cudaEvent_t ev_stage_used[2] = {nullptr, nullptr};  // recorded when a query chunk is done with its buffer
+    void *istage = nullptr;                // insertion host form: its own buffer, so query
+    int64_t istage_cap = 0;                //   uploads can overlap insertions
     cudaStream_t copy_stream = nullptr;
 
     // DBL_FLAG_TIMING: event pairs per kernel class, harvested by dbl_timings
