@@ -394,3 +394,25 @@ def test_autotune_restores_index_and_keeps_parity(tiny, tmp_path):
     ix.sync()
     assert_labels(ix, ref, "after autotune")
     assert_queries(ix, ref, tiny["q_u"][:20000], tiny["q_v"][:20000], "after autotune")
+
+
+def test_phase_trace_and_schedule(tiny):
+    """dbl_phase_trace after a persistent insertion: start, one mark per grid
+    barrier (validate + count, seed + grow, write + enqueue, each level) and
+    the end, non-decreasing; dbl_set_schedule switches team width and
+    persistence without changing results."""
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=dbl.FLAG_TIMING | dbl.FLAG_PERSISTENT)
+    ix.insert_edges(D(s[:1000]), D(d[:1000]))
+    tr = ix.phase_trace()
+    assert len(tr) >= 5 and tr[0] == 0 and all(b >= a for a, b in zip(tr, tr[1:])), tr
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ref.insert_edges(s[:1000], d[:1000])
+    for team, persistent in ((8, False), (32, True), (1, True)):
+        ix.set_schedule(team, persistent)
+    ix.insert_edges(D(s[1000:]), D(d[1000:]))
+    ref.insert_edges(s[1000:], d[1000:])
+    ix.sync()
+    assert_labels(ix, ref, "after set_schedule")
+    with pytest.raises(dbl.DblError):
+        ix.set_schedule(3, True)

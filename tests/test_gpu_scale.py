@@ -205,3 +205,52 @@ def test_batched_config_uneven_batches(social):
     rans, rcode = ref.query(w["q_u"], w["q_v"], nthreads=THREADS)
     assert_same_answers(ans, code, rans, rcode, "k=128, uneven query batches")
     ix.close()
+
+
+def _merged_csr(rp, col, src, dst, n):
+    """CSR of the base graph plus the inserted edges, on the device (rows sorted)."""
+    deg = torch.diff(rp.long())
+    s_all = torch.cat([torch.repeat_interleave(torch.arange(n, device=rp.device), deg), src.long()])
+    d_all = torch.cat([col.long(), dst.long()])
+    order = torch.argsort(s_all * n + d_all)
+    s_all, d_all = s_all[order], d_all[order]
+    rp2 = torch.zeros(n + 1, dtype=torch.int64, device=rp.device)
+    rp2[1:] = torch.cumsum(torch.bincount(s_all, minlength=n), 0)
+    return rp2.to(torch.int32), d_all.to(torch.int32)
+
+
+def test_large_graph_incremental_equals_rebuild():
+    """n = 2^24, m = 2^28 (the learned and serving workloads), k = 128,
+    k' = 64: properties that hold at any size, checked without the oracle.
+    (1) Labels after 1M insertions in batches of 100k through the persistent
+    kernels equal the labels built from scratch on the final graph with the
+    same landmark and leaf sets (the least fixpoint is unique).  (2) Every
+    query whose v is the end of a forward walk from u (reachable by
+    construction) is answered true, and the searches agree with the labels'
+    verdicts on the rest (both indices answer identically)."""
+    dbl.build()
+    dbl_inputs.build()
+    w = dbl_inputs.workload("large")
+    n = int(w["n"])
+    rp, col = D(w["row_ptr"]), D(w["col"])
+    src, dst = D(w["ins_src"]), D(w["ins_dst"])
+    E = int(src.numel())
+    inc = dbl.DBLIndex(rp, col, 128, 64, edge_capacity=E, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC)
+    for a in range(0, E, 100_000):
+        inc.insert_edges(src[a:a + 100_000], dst[a:a + 100_000])
+    inc.sync()
+    lm, lb, lr = inc.selection()
+    rp2, col2 = _merged_csr(rp, col, src, dst, n)
+    del rp, col
+    torch.cuda.empty_cache()
+    full = dbl.DBLIndex(rp2, col2, 128, 64, landmarks=lm, leaf_buckets=lb, leaf_roles=lr)
+    for a, b, name in zip(inc.labels(), full.labels(), ("dl_in", "dl_out", "bl_in", "bl_out")):
+        assert torch.equal(a, b), f"large graph: {name} differs between incremental repair and rebuild"
+    qu, qv = D(w["q_u"]), D(w["q_v"])
+    a1, c1 = inc.query(qu, qv)
+    inc.sync()
+    a2, c2 = full.query(qu, qv)
+    assert torch.equal(a1, a2) and torch.equal(c1, c2)
+    assert bool((a1[1::2] == 1).all()), "a walk descendant was answered unreachable"
+    inc.close()
+    full.close()
