@@ -293,6 +293,7 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     res = {"build_s": build_s}
     if build_t:
         res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
+        res["build_algorithmic_bytes"] = build_bytes(ix, I, ix.info()["record_bytes"] // 2)
     if flags & dbl.FLAG_PERSISTENT and not args.no_autotune:
         # autotuned frontier schedule (sample: the step's insertions as one batch
         # and 1M queries; a few batches of the first hundred thousand edges do not
@@ -356,6 +357,21 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     return res
 
 
+def build_bytes(ix, I, rec_half_bytes):
+    """Algorithmic bytes of the label build (Algorithm 1 as one fixpoint):
+    per direction, every vertex whose final half-record is non-zero pushes it
+    once: offsets (8 B) + adjacency (4 B/edge) + neighbour record sectors
+    (32 B/edge) + its own half-record."""
+    import torch
+    dl_in, dl_out, bl_in, bl_out = ix.labels()
+    fwd = (dl_in != 0).any(1) | (bl_in != 0).any(1)
+    bwd = (dl_out != 0).any(1) | (bl_out != 0).any(1)
+    deg_out = torch.diff(I.rp).long()
+    deg_in = torch.bincount(I.col.long(), minlength=deg_out.numel())
+    return float((8 + 36 * deg_out[fwd].double() + rec_half_bytes).sum() +
+                 (8 + 36 * deg_in[bwd].double() + rec_half_bytes).sum())
+
+
 def insertion_bytes(ix, w, I):
     """Algorithmic bytes of appending and seeding one step's insertions (the
     persistent insertion kernel does both before it propagates): per edge its
@@ -368,6 +384,19 @@ def insertion_bytes(ix, w, I):
     loops = int((I.src == I.dst).sum().item())
     applied = int(st[11]) / max(1, int(st[11]) + int(st[12])) * (E - loops)
     return 8 * E + (E - loops) * (4 * 32 + 2 * 32 + 2 * 32) + applied * 2 * 32
+
+
+def build_roofline(form):
+    """Achieved GB/s of the label build's propagation (CUDA events at build)."""
+    peaks, src = measured_peaks()
+    ms = form.get("build_kernel_ms", {}).get("propagate")
+    alg = form.get("build_algorithmic_bytes")
+    if not ms or not alg:
+        return None
+    ach = alg / (ms * 1e-3) / 1e9
+    return {"kernel": "propagate (label build)", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs of {src}",
+            "algorithmic_bytes": alg, "ms": ms}
 
 
 def roofline(form, ix, args, w, I, batches, persistent=True):
@@ -490,6 +519,7 @@ def bench_gpu(args):
                         **{k: v for k, v in tinfo.items() if k != "losses"}, "final_loss": tinfo["losses"][-1]},
             "roofline": roof,
             "roofline_label_test": roof_label,
+            "roofline_build": build_roofline(learned_t),
             "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
             "clocks": learned["clocks"],

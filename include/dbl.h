@@ -118,7 +118,11 @@ typedef struct {
                               tasks' edges 32 at a time; 0: 1 */
     int32_t query_unroll;  /* query pairs per thread in the label test (1, 2, 4);
                               0: 2, or 1 for 128-byte records */
-    int32_t reserved[6];
+    int32_t search_first_log2; /* a search wave first hashes its states into
+                              the first 2^x slots of its table (clamped to the
+                              table); a lone 64-query group that overflows them
+                              is rerun over the whole table; 0: 22 */
+    int32_t reserved[5];
 } dbl_options;
 
 /* Fill *opt with the defaults above. */

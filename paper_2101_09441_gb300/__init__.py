@@ -55,7 +55,8 @@ _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_voi
 class _Options(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p),
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
-                ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class _Graph(ctypes.Structure):
@@ -162,7 +163,7 @@ class DBLIndex:
 
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
-                 torch_allocator: bool = True, query_unroll: int = 0):
+                 torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -180,6 +181,7 @@ class DBLIndex:
         opt.flags = int(flags)
         opt.team = int(team)
         opt.query_unroll = int(query_unroll)
+        opt.search_first_log2 = int(search_first_log2)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
 

@@ -215,6 +215,7 @@ struct SearchArgs {
     unsigned long long *stats;
     int32_t *lists[2];
     int64_t list_cap;
+    unsigned long long first_mask;  // slot mask of a wave's first attempt (kFirstSlots)
 };
 
 // Device-side state of the persistent search.
@@ -225,9 +226,16 @@ struct PersistState {
     uint32_t overflow;
     int32_t top;
     int32_t pad;
-    long long range[2];
-    long long stack[64][2];
+    long long range[3];      // j0, j1, whole table (see kFirstSlots)
+    long long stack[64][3];
 };
+
+// A wave first hashes its (group, vertex) states into the first kFirstSlots
+// slots of the table (128 MB of slots: the pages stay in the address
+// translation caches; dbl_options.search_first_log2 changes it); a single
+// group that overflows them is rerun over the whole table, which always holds
+// one group.
+constexpr int64_t kFirstSlots = 1ll << 22;
 
 constexpr int kMaxProbe = 2048;
 
@@ -648,6 +656,7 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
         ps->top = 1;
         ps->stack[0][0] = 0;
         ps->stack[0][1] = U;
+        ps->stack[0][2] = 0;
     }
     unsigned long long levels = 0, waves = 0;
     for (;;) {
@@ -656,6 +665,7 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
                 --ps->top;
                 ps->range[0] = ps->stack[ps->top][0];
                 ps->range[1] = ps->stack[ps->top][1];
+                ps->range[2] = ps->stack[ps->top][2];
             } else {
                 ps->range[0] = ps->range[1] = -1;
             }
@@ -667,9 +677,12 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
         if (!gs.sync(status)) return;
         const long long j0 = *(volatile long long *)&ps->range[0], j1 = *(volatile long long *)&ps->range[1];
         if (j0 < 0 || ld_volatile_u32(status)) break;
+        const bool whole = *(volatile long long *)&ps->range[2] != 0;
+        SearchArgs aw = a;
+        if (!whole) aw.c.slot_mask = a.first_mask;
         ++waves;
         SlotList lists[2] = {{a.lists[0], &ps->list_count[0], a.list_cap}, {a.lists[1], &ps->list_count[1], a.list_cap}};
-        search_setup<WD, WB>(a, j0, j1, &ps->task_count[0]);
+        search_setup<WD, WB>(aw, j0, j1, &ps->task_count[0]);
         if (!gs.sync(status)) return;
         // level L: expand task list L%2 into slot list L%2 (slot stamps L+2),
         // then turn that slot list into task list (L+1)%2
@@ -683,27 +696,34 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
             }
             ++levels;
             if (leader) ps->task_count[cur ^ 1] = 0;
-            search_expand<WD, WB, TEAM>(a, ntk, (uint32_t)(L + 2), lists[cur], cst, nst);
+            search_expand<WD, WB, TEAM>(aw, ntk, (uint32_t)(L + 2), lists[cur], cst, nst);
             if (!gs.sync(status)) return;
             if (!ld_volatile_u32(&ps->list_count[cur]) || ld_volatile_u32(&ps->overflow)) break;
-            search_finalize(a, lists[cur], &ps->task_count[cur ^ 1]);
+            search_finalize(aw, lists[cur], &ps->task_count[cur ^ 1]);
             if (!gs.sync(status)) return;
             if (leader) ps->list_count[cur] = 0;  // written again two levels on, after a barrier
         }
         const bool over = ld_volatile_u32(&ps->overflow) != 0;
-        search_answer(a, j0, j1, !over);
-        search_clear(a);
+        search_answer(aw, j0, j1, !over);
+        search_clear(aw);
         if (!gs.sync(status)) return;
         if (over && leader) {
             const long long groups = (j1 - j0 + 63) / 64;
-            if (groups <= 1 || ps->top + 2 > 64) {
+            if (groups <= 1 && !whole && ps->top < 64) {
+                ps->stack[ps->top][0] = j0;  // rerun over the whole table
+                ps->stack[ps->top][1] = j1;
+                ps->stack[ps->top][2] = 1;
+                ps->top += 1;
+            } else if (groups <= 1 || ps->top + 2 > 64) {
                 set_status(status, DBL_ERR_CAPACITY);
             } else {
                 const long long mid = j0 + (groups / 2) * 64;
                 ps->stack[ps->top][0] = mid;
                 ps->stack[ps->top][1] = j1;
+                ps->stack[ps->top][2] = whole ? 1 : 0;
                 ps->stack[ps->top + 1][0] = j0;
                 ps->stack[ps->top + 1][1] = mid;
+                ps->stack[ps->top + 1][2] = whole ? 1 : 0;
                 ps->top += 2;
             }
         }
@@ -758,6 +778,8 @@ static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, con
     a.lists[0] = c->slot_list[0];
     a.lists[1] = c->slot_list[1];
     a.list_cap = c->table_slots;
+    const int64_t first = ix->opt.search_first_log2 > 0 ? (1ll << std::min(ix->opt.search_first_log2, 40)) : kFirstSlots;
+    a.first_mask = (unsigned long long)(std::min<int64_t>(c->table_slots, first) - 1);
     return a;
 }
 
@@ -789,11 +811,13 @@ static void launch_search_expand(dbl_index *ix, dbl_qctx *c, const SearchArgs &a
 
 template <int WD, int WB>
 static dbl_status run_search_wave(dbl_index *ix, dbl_qctx *c, const int32_t *qu, const int32_t *qv, int64_t j0,
-                                  int64_t j1, uint8_t *ans, uint8_t *code, bool *overflowed, cudaStream_t s)
+                                  int64_t j1, bool whole, uint8_t *ans, uint8_t *code, bool *overflowed,
+                                  cudaStream_t s)
 {
     uint32_t *cnt = c->d_counts;
     uint32_t *h = c->h_pinned;
-    const SearchArgs a = search_args(ix, c, qu, qv, 0, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
+    SearchArgs a = search_args(ix, c, qu, qv, 0, ans, code, cnt + kCntClaimed, cnt + kCntOverflow);
+    if (!whole) a.c.slot_mask = a.first_mask;
     cudaMemsetAsync(cnt + kCntSlots0, 0, sizeof(uint32_t) * 5, s);  // slots0, slots1, tasks, claimed, overflow
     SlotList lists[2] = {{c->slot_list[0], cnt + kCntSlots0, c->table_slots},
                          {c->slot_list[1], cnt + kCntSlots1, c->table_slots}};
@@ -916,22 +940,28 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     const int64_t U = h[0];
     if (!U) return DBL_OK;
     // waves: all groups at once; on overflow rerun the unanswered in halves
+    // (a lone group that overflows the first kFirstSlots slots reruns over the whole table)
     struct Range {
         int64_t j0, j1;
+        bool whole;
     };
-    std::vector<Range> stack{{0, U}};
+    std::vector<Range> stack{{0, U, false}};
     while (!stack.empty()) {
         Range r = stack.back();
         stack.pop_back();
         bool over = false;
-        st = run_search_wave<WD, WB>(ix, c, u, v, r.j0, r.j1, ans, code, &over, s);
+        st = run_search_wave<WD, WB>(ix, c, u, v, r.j0, r.j1, r.whole, ans, code, &over, s);
         if (st) return st;
         if (over) {
             const int64_t groups = (r.j1 - r.j0 + 63) / 64;
+            if (groups <= 1 && !r.whole) {
+                stack.push_back({r.j0, r.j1, true});
+                continue;
+            }
             if (groups <= 1) return qfail(c, DBL_ERR_CAPACITY, "search: one group overflowed the state table");
             const int64_t mid = r.j0 + (groups / 2) * 64;
-            stack.push_back({mid, r.j1});
-            stack.push_back({r.j0, mid});
+            stack.push_back({mid, r.j1, r.whole});
+            stack.push_back({r.j0, mid, r.whole});
         }
     }
     return DBL_OK;

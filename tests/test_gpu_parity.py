@@ -416,3 +416,19 @@ def test_phase_trace_and_schedule(tiny):
     assert_labels(ix, ref, "after set_schedule")
     with pytest.raises(dbl.DblError):
         ix.set_schedule(3, True)
+
+
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT])
+def test_search_overflow_reruns(tiny, flags):
+    """A tiny first-attempt slice of the search table (2^6 slots) makes the
+    waves overflow: they split in halves and lone groups rerun over the whole
+    table; every answer and code still equals the oracle's."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=flags, search_first_log2=6)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ix.insert_edges(D(tiny["ins_src"]), D(tiny["ins_dst"]))
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    ix.sync()
+    w0 = int(ix.stats()[14])
+    assert_queries(ix, ref, tiny["q_u"], tiny["q_v"], f"first slice 2^6, flags {flags}")
+    ix.sync()
+    assert int(ix.stats()[14]) - w0 > 1, "expected several search waves"
