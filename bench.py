@@ -44,7 +44,7 @@ UNIT = "ops/s (queries + inserted edges)"
 
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_455_000 + 21_871_616, "093943455728"),
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_413_000 + 21_857_792, "133eba2d8343"),
                                              "propagate": (54_260_480 + 1_915_392, "c9371526e6e2")}
 KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_insert.cu",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}

@@ -151,17 +151,22 @@ __device__ __forceinline__ void stage_put_task(bool has, const FTask &t, const F
 
 // Mark x in the frontier being filled and, if it is new there, stage its
 // chunks; warp-collective (lanes with want == false pass through).
-__device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
-                                              const Stage &st)
+// stage_enqueue with x's adjacency already loaded (r is read only if want).
+__device__ __forceinline__ void stage_enqueue_at(bool want, int32_t x, int dir, const AdjRange &r,
+                                                 const FrontierOut &f, const Stage &st)
 {
     uint32_t nchunks = 0;
-    AdjRange r{0, 0, 0, 0};
     if (want) {
-        r = adj_of(g, dir, x);
         const int32_t d = r.bd + r.od;
         if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
     }
     stage_put(nchunks, x, dir, r, f, st);
+}
+
+__device__ __forceinline__ void stage_enqueue(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
+                                              const Stage &st)
+{
+    stage_enqueue_at(want, x, dir, want ? adj_of(g, dir, x) : AdjRange{0, 0, 0, 0}, f, st);
 }
 
 // Move the block's stage to the global frontier; every thread of the block

@@ -158,7 +158,11 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
 // One edge's seed: Algorithm 3's skip test on DL_out(u) and DL_in(v), then
 // fwd(v) |= fwd(u) and bwd(u) |= bwd(v).  All four half-records are loaded at
 // once (one memory round trip).  Returns true if the edge was applied;
-// want_f / want_b say whether fwd(v) / bwd(u) gained bits.
+// want_f / want_b say whether fwd(v) / bwd(u) gained bits.  That is decided
+// from the values loaded before the ORs, which are then fire-and-forget: the
+// first OR that adds a bit to a word was issued by a thread whose load did not
+// see that bit, and a load that misses bits the OR brings means the word
+// grows.  Callers read the frontier only after a grid barrier or a launch.
 template <int HS, int WD>
 __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, bool &want_f, bool &want_b)
 {
@@ -177,12 +181,12 @@ __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, bo
 #pragma unroll
     for (int w = 0; w < HS; ++w) {
         if (x[w] & ~c[w]) {
-            unsigned long long old = atomicOr((unsigned long long *)(fv + w), x[w]);
-            want_f |= (x[w] & ~old) != 0;
+            atomicOr((unsigned long long *)(fv + w), x[w]);
+            want_f = true;
         }
         if (y[w] & ~a[w]) {
-            unsigned long long old = atomicOr((unsigned long long *)(bu + w), y[w]);
-            want_b |= (y[w] & ~old) != 0;
+            atomicOr((unsigned long long *)(bu + w), y[w]);
+            want_b = true;
         }
     }
     return true;
@@ -321,6 +325,15 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 const int32_t sw[2] = {a.slot_out[i], a.slot_in[i]};
                 x[0] = a.src[i];
                 x[1] = a.dst[i];
+                // with 16-byte halves the segment metadata is loaded before the
+                // seed's records, in the same round trip (len is final after the
+                // count phase); wider records leave no registers for that
+                constexpr bool kEarly = HS <= 2;
+                if (kEarly) {
+#pragma unroll
+                    for (int dir = 0; dir < 2; ++dir)
+                        if (sw[dir] >= 0) ad[dir] = load_vadj(a.vm, dir, x[dir]);
+                }
                 if (sw[0] >= 0) {
                     bool want_f = false, want_b = false;
                     if (seed_one<HS, WD>(x[0], x[1], a.rec, want_f, want_b)) ++applied;
@@ -331,7 +344,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
 #pragma unroll
                 for (int dir = 0; dir < 2; ++dir) {
                     if (sw[dir] < 0) continue;
-                    ad[dir] = load_vadj(a.vm, dir, x[dir]);  // len is final after the count phase
+                    if (!kEarly) ad[dir] = load_vadj(a.vm, dir, x[dir]);
                     old_cap[dir] = va_cap(ad[dir].dc);
                     if (sw[dir] == old_cap[dir]) nc[dir] = grown_cap(ad[dir].len);
                 }
@@ -387,6 +400,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             const int64_t i = wbase + threadIdx.x;
             bool want_f = false, want_b = false;
             int32_t u = 0, v = 0;
+            VAdj eu{0, 0u, 0, 0}, ev{0, 0u, 0, 0};  // adjacency of the tasks to enqueue
             if (i < a.b) {
                 const int32_t so = a.slot_out[i], si = a.slot_in[i];
                 u = a.src[i];
@@ -395,14 +409,17 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                     want_b = (so & kWantBit) != 0;
                     want_f = (si & kWantBit) != 0;
                     const int32_t po = so & ~kWantBit, pi = si & ~kWantBit;
+                    // both halves of each endpoint's metadata sector in one round trip
                     const VAdj au = load_vadj(a.vm, 0, u), av = load_vadj(a.vm, 1, v);
+                    if (want_f) ev = load_vadj(a.vm, 0, v);
+                    if (want_b) eu = load_vadj(a.vm, 1, u);
                     if (po < va_cap(au.dc)) a.pool_out[(int64_t)au.off + po] = v;
                     if (pi < va_cap(av.dc)) a.pool_in[(int64_t)av.off + pi] = u;
                 }
             }
             // fwd(v) changed: v's out-edges (dir 0); bwd(u) changed: u's in-edges (dir 1)
-            stage_enqueue(want_f, v, 0, a.g, f, st);
-            stage_enqueue(want_b, u, 1, a.g, f, st);
+            stage_enqueue_at(want_f, v, 0, AdjRange{ev.start, va_deg(ev.dc), ev.off, ev.len}, f, st);
+            stage_enqueue_at(want_b, u, 1, AdjRange{eu.start, va_deg(eu.dc), eu.off, eu.len}, f, st);
         }
         stage_flush(f, st);
     }
