@@ -367,9 +367,14 @@ dbl_status dbl_select_by_score(dbl_index *ix, const float *scores, int32_t k, in
  * Weights are kept in fp32 with bf16 copies for the tensor-core kernels. */
 dbl_status dbl_mlp_create(const float *params_host, dbl_mlp **out, void *stream);
 void dbl_mlp_destroy(dbl_mlp *m, void *stream);
-/* Copy the current fp32 parameters to params_host[DBL_MLP_PARAMS]. */
+/* Copy the current fp32 parameters to params_host[DBL_MLP_PARAMS]
+ * (synchronises `stream`; reports errors as dbl_mlp_sync does). */
 dbl_status dbl_mlp_params(dbl_mlp *m, float *params_host, void *stream);
-/* y[r] = network(X[rows_idx ? rows_idx[r] : r]) for r < rows; X bf16 [.][16]. */
+/* y[r] = network(X[rows_idx ? rows_idx[r] : r]) for r < rows; X bf16 [.][16].
+ * Runs on the tcgen05 tensor cores in 128-row tiles; without rows_idx and
+ * with X 16-byte aligned the tiles arrive by TMA tensor copies (a tensor map
+ * the driver refuses is DBL_ERR_CUDA).  The forward, gradient and training
+ * calls are asynchronous; dbl_mlp_sync reports their errors. */
 dbl_status dbl_mlp_forward(dbl_mlp *m, const uint16_t *X, const int32_t *rows_idx, int64_t rows, float *y,
                            void *stream);
 /* Gradients (device fp32 [DBL_MLP_PARAMS]) and loss (device fp32, may be
@@ -379,6 +384,9 @@ dbl_status dbl_mlp_gradients(dbl_mlp *m, const uint16_t *X, const float *target,
 /* One SGD-with-momentum step on the rows: v = momentum*v + grad; p -= lr*v. */
 dbl_status dbl_mlp_train_step(dbl_mlp *m, const uint16_t *X, const float *target, const int32_t *rows_idx,
                               int64_t rows, float lr, float momentum, float *loss, void *stream);
+/* Wait for `stream`; DBL_ERR_TIMEOUT if a tensor-core kernel of this network
+ * gave up a bounded wait since it was created (its outputs are invalid). */
+dbl_status dbl_mlp_sync(dbl_mlp *m, void *stream);
 const char *dbl_mlp_last_error(const dbl_mlp *m);
 
 /* Message of the last error on this index (or of the last failed build when

@@ -30,7 +30,7 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_snapshot", "dbl_restore", "dbl_sync",
            "dbl_stats", "dbl_phase_trace", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy", "dbl_insert_edges_noalloc",
            "dbl_features", "dbl_coverage", "dbl_select_by_score", "dbl_mlp_create", "dbl_mlp_destroy",
-           "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_last_error",
+           "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_sync", "dbl_mlp_last_error",
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
            "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule"]
@@ -133,6 +133,7 @@ def lib():
             L.dbl_mlp_forward.argtypes = [P, P, P, i64, P, P]
             L.dbl_mlp_gradients.argtypes = [P, P, P, P, i64, P, P, P]
             L.dbl_mlp_train_step.argtypes = [P, P, P, P, i64, f32, f32, P, P]
+            L.dbl_mlp_sync.argtypes = [P, P]
             L.dbl_mlp_last_error.argtypes = [P]
             L.dbl_mlp_last_error.restype = ctypes.c_char_p
             for name in EXPORTS:
@@ -565,6 +566,7 @@ class MLP:
         y = torch.empty(R, dtype=torch.float32, device=X.device)
         self._check(lib().dbl_mlp_forward(self._h, _ptr(X), _ptr(rows_idx), R, _ptr(y),
                                           _stream_handle(stream or self._stream)))
+        self.sync(stream)
         return y
 
     def gradients(self, X, target, rows_idx=None, stream=None):
@@ -574,7 +576,13 @@ class MLP:
         loss = torch.empty(1, dtype=torch.float32, device=X.device)
         self._check(lib().dbl_mlp_gradients(self._h, _ptr(X), _ptr(target), _ptr(rows_idx), R, _ptr(g), _ptr(loss),
                                             _stream_handle(stream or self._stream)))
+        self.sync(stream)
         return g, loss
+
+    def sync(self, stream=None):
+        """dbl_mlp_sync: wait for the stream and raise if a tensor-core kernel
+        gave up a bounded wait."""
+        self._check(lib().dbl_mlp_sync(self._h, _stream_handle(stream or self._stream)))
 
     def train_step(self, X, target, rows_idx=None, lr: float = 0.05, momentum: float = 0.9, loss=None,
                    stream=None):

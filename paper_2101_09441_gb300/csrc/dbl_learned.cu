@@ -9,18 +9,21 @@
 //   coverage   count[c] = #{j : u_j reaches c, c reaches v_j} for sampled pairs,
 //              256 pairs per pass as bits of a 4-word record, propagated with the
 //              same frontier kernels as the labels
-//   MLP        bf16 operands, fp32 accumulate, mma.sync m16n8k16 tensor-core
-//              tiles; a fused forward (both hidden layers stay in registers)
-//              and a backward of three GEMMs with split-K reductions
+//   MLP        bf16 operands, fp32 accumulate on the 5th-generation tensor
+//              cores (tcgen05.mma, accumulators in TMEM, read back with
+//              tcgen05.ld): a fused forward over 128-row tiles fed by TMA, and
+//              a backward of three 128 x 128-tile GEMMs with split-K reductions
 //   selection  top-k by score with the landmark radix select
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
 #include "dbl_frontier.cuh"
 #include "dbl_internal.cuh"
+#include "dbl_tc.cuh"
 #include "dbl_kernels.cuh"
 
 namespace dbl {
@@ -243,27 +246,15 @@ dbl_status coverage(dbl_index *ix, const int32_t *u_in, const int32_t *v_in, con
     return e ? cuda_fail(ix, e, "coverage") : DBL_OK;
 }
 
-// ------------------------------------------------------------ tensor-core tiles
+// ------------------------------------------------------------ tensor-core kernels
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// D = A(16x16, row) * B(16x8, col) + C, bf16 inputs, fp32 accumulate.
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 constexpr int kH = 128;       // hidden width
 constexpr int kF = 16;        // features
-constexpr int kW1Pitch = kF + 8;    // smem pitch (bf16) of W1t rows: [out][in]
-constexpr int kW2Pitch = kH + 8;    // smem pitch (bf16) of W2t rows: [out][in]
 
 // Parameter offsets in the flat fp32 vector (18,817 values).
 constexpr int kOffW1 = 0;                     // [16][128]  (in x out)
@@ -274,203 +265,347 @@ constexpr int kOffW3 = kOffB2 + kH;           // [128]
 constexpr int kOffB3 = kOffW3 + kH;           // [1]
 constexpr int kNumParams = kOffB3 + 1;
 
+// Position of element (row, k) in a [K / 8][rows][8] operand tile (the
+// K-block layout of dbl_tc.cuh).
+__host__ __device__ constexpr int kblk(int row, int k, int rows) { return (k >> 3) * rows * 8 + row * 8 + (k & 7); }
+
 struct MlpDev {
-    const bf16 *W1t;      // [128][16]  out-major (B operand of layer 1)
-    const bf16 *W2t;      // [128][128] out-major (B operand of layer 2)
+    const bf16 *W1c;      // layer-1 B operand, N = 128 (out) x K = 16 (in), K-block layout
+    const bf16 *W2c;      // layer-2 B operand, N = 128 (out) x K = 128 (in), K-block layout
     const float *p;       // fp32 parameters (biases, w3, b3)
 };
 
-// Fused forward: each warp takes 16 rows; both hidden layers stay in
-// registers (the accumulator fragment of two n8 tiles is exactly the A
-// fragment of the next k16 step).  Optionally stores H1, H2 (bf16) for the
-// backward pass.  rows_idx (optional) gathers the input rows.
-__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, const bf16 *X, const int32_t *rows_idx, int64_t R,
-                                                     float *y, bf16 *H1out, bf16 *H2out)
+constexpr int kTileR = 128;                 // rows per tile: the MMA's M
+constexpr uint32_t kWaitLimit = 1u << 22;   // polls of an mbarrier before a kernel gives up
+
+// Shared memory of the forward kernel (operand tiles first, 4 KB aligned).
+// The block requests more than it uses: at most two blocks (2 x 256 TMEM
+// columns) then share an SM, and every address a tile descriptor can reach,
+// even with its two byte offsets exchanged (rows 15 x 2 KB apart), stays
+// inside the block's allocation.
+struct FwdSmem {
+    bf16 x[2][kTileR * kF];
+    bf16 w1[kH * kF];
+    bf16 h1[kTileR * kH];
+    bf16 w2[kH * kH];
+    float b1[kH], b2[kH], w3[kH];
+    uint64_t bar_w, bar_x[2], bar_mma;
+    uint32_t tmem;
+};
+constexpr int kFwdSmemBytes = 112 * 1024;
+static_assert(sizeof(FwdSmem) + 1024 <= kFwdSmemBytes, "forward shared memory");
+static_assert(offsetof(FwdSmem, w2) + 7 * 4096 + 15 * 2048 + 256 <= kFwdSmemBytes, "descriptor reach");
+
+// Fused forward on the 5th-generation tensor cores.  A block owns 128-row
+// tiles: X (128 x 16 bf16) arrives by a TMA tensor copy (or by the threads
+// when rows are gathered), layer 1 is one 128 x 128 x 16 MMA into TMEM columns
+// [0, 128), the epilogue adds b1, applies ReLU and writes H1 as bf16 back to
+// shared memory, layer 2 is eight 128 x 128 x 16 MMAs into columns [128, 256),
+// and its epilogue adds b2, applies ReLU, rounds H2 to bf16 and takes the dot
+// product with w3.  Thread t owns row t of the tile (TMEM lane t).  The next
+// tile's X copy is in flight during the current tile.  Every wait is bounded:
+// on a timeout the block raises *err, waits (bounded) for its copies and MMAs,
+// frees its TMEM and returns.
+__global__ void __launch_bounds__(kTileR, 1)
+    k_mlp_forward(const __grid_constant__ CUtensorMap xmap, int use_tma, MlpDev m, const bf16 *X,
+                  const int32_t *rows_idx, int64_t R, float *y, bf16 *H1out, bf16 *H2out, uint32_t *err)
 {
-    __shared__ __align__(16) bf16 w1s[kH * kW1Pitch];
-    __shared__ __align__(16) bf16 w2s[kH * kW2Pitch];
-    __shared__ float b1s[kH], b2s[kH], w3s[kH];
-    for (int i = threadIdx.x; i < kH * kF; i += blockDim.x) w1s[(i / kF) * kW1Pitch + i % kF] = m.W1t[i];
-    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) w2s[(i / kH) * kW2Pitch + i % kH] = m.W2t[i];
-    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
-        b1s[i] = m.p[kOffB1 + i];
-        b2s[i] = m.p[kOffB2 + i];
-        w3s[i] = m.p[kOffW3 + i];
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    FwdSmem &S = *reinterpret_cast<FwdSmem *>(dsm);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        tc::mbar_init(&S.bar_w, 1);
+        tc::mbar_init(&S.bar_x[0], 1);
+        tc::mbar_init(&S.bar_x[1], 1);
+        tc::mbar_init(&S.bar_mma, 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 256);
+    for (int i = tid; i < kH; i += blockDim.x) {
+        S.b1[i] = m.p[kOffB1 + i];
+        S.b2[i] = m.p[kOffB2 + i];
+        S.w3[i] = m.p[kOffW3 + i];
     }
     const float b3 = m.p[kOffB3];
+    tc::tc_fence_before();
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r0 = warp * 16; r0 < R; r0 += nwarp * 16) {
-        const int64_t ra = r0 + g, rb = r0 + g + 8;
-        const int64_t xa = ra < R ? (rows_idx ? rows_idx[ra] : ra) : -1;
-        const int64_t xb = rb < R ? (rows_idx ? rows_idx[rb] : rb) : -1;
-        uint32_t a[4];
-        const uint32_t *Xa = reinterpret_cast<const uint32_t *>(X + (xa >= 0 ? xa : 0) * kF);
-        const uint32_t *Xb = reinterpret_cast<const uint32_t *>(X + (xb >= 0 ? xb : 0) * kF);
-        a[0] = xa >= 0 ? Xa[t] : 0u;        // row g,   cols 2t..2t+1
-        a[1] = xb >= 0 ? Xb[t] : 0u;        // row g+8, cols 2t..2t+1
-        a[2] = xa >= 0 ? Xa[t + 4] : 0u;    // row g,   cols 2t+8..
-        a[3] = xb >= 0 ? Xb[t + 4] : 0u;    // row g+8, cols 2t+8..
-        // layer 1 -> H1 as layer-2 A fragments
-        uint32_t h1[8][4];
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int64_t ntiles = (R + kTileR - 1) / kTileR;
+    bool x_pending[2] = {false, false};  // a tensor copy into x[b] not yet waited for
+    if (tid == 0) {
+        tc::mbar_expect_tx(&S.bar_w, (uint32_t)(sizeof(S.w1) + sizeof(S.w2)));
+        tc::bulk_g2s(S.w1, m.W1c, (uint32_t)sizeof(S.w1), &S.bar_w);
+        tc::bulk_g2s(S.w2, m.W2c, (uint32_t)sizeof(S.w2), &S.bar_w);
+    }
+    if (use_tma && (int64_t)blockIdx.x < ntiles) {
+        if (tid == 0) {
+            tc::mbar_expect_tx(&S.bar_x[0], (uint32_t)sizeof(S.x[0]));
+            tc::tma_load_3d(S.x[0], &xmap, 0, (int32_t)(blockIdx.x * kTileR), 0, &S.bar_x[0]);
+        }
+        x_pending[0] = true;
+    }
+    bool ok = __syncthreads_and(tc::mbar_wait(&S.bar_w, 0, kWaitLimit));
+    uint32_t px[2] = {0, 0}, pm = 0;
+    bool mma_pending = false;
+    const uint32_t id = tc::idesc_bf16(kTileR, kH);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int64_t r = tile * kTileR + tid;
+        if (use_tma) {
+            ok = tc::mbar_wait(&S.bar_x[buf], px[buf], kWaitLimit);
+            if (ok) {
+                px[buf] ^= 1;
+                x_pending[buf] = false;
+            }
+        } else {
+            uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+            if (r < R) {
+                const int64_t src = rows_idx ? (int64_t)rows_idx[r] : r;
+                const uint4 *xp = reinterpret_cast<const uint4 *>(X + src * kF);
+                lo = xp[0];
+                hi = xp[1];
+            }
+            uint4 *xs = reinterpret_cast<uint4 *>(S.x[buf]);
+            xs[tid] = lo;           // K block 0
+            xs[kTileR + tid] = hi;  // K block 1
+            tc::fence_async_smem();
+        }
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        // layer 1; the next tile's X goes into the other buffer, whose last
+        // reader (the previous tile's layer-1 MMA) has completed
+        const int64_t nxt = tile + gridDim.x;
+        if (use_tma && nxt < ntiles) x_pending[buf ^ 1] = true;
+        if (tid == 0) {
+            if (use_tma && nxt < ntiles) {
+                tc::mbar_expect_tx(&S.bar_x[buf ^ 1], (uint32_t)sizeof(S.x[0]));
+                tc::tma_load_3d(S.x[buf ^ 1], &xmap, 0, (int32_t)(nxt * kTileR), 0, &S.bar_x[buf ^ 1]);
+            }
+            tc::tc_fence_after();
+            tc::mma_bf16(tmem, tc::smem_desc(S.x[buf], kTileR * 16, 128), tc::smem_desc(S.w1, kH * 16, 128), id, 0u);
+            tc::mma_commit(&S.bar_mma);
+        }
+        mma_pending = true;
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar_mma, pm, kWaitLimit));
+        if (!ok) break;
+        pm ^= 1;
+        mma_pending = false;
+        tc::tc_fence_after();
+        uint4 *h1 = reinterpret_cast<uint4 *>(S.h1);
+#pragma unroll 1
+        for (int c = 0; c < kH / 16; ++c) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), v);
+            uint32_t pk[8];
 #pragma unroll
-        for (int nt = 0; nt < 16; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const bf16 *wb = w1s + (nt * 8 + g) * kW1Pitch;
-            mma_bf16(c, a, *reinterpret_cast<const uint32_t *>(wb + 2 * t),
-                     *reinterpret_cast<const uint32_t *>(wb + 2 * t + 8));
-            const int col = nt * 8 + 2 * t;
-            const float z0 = fmaxf(c[0] + b1s[col], 0.f), z1 = fmaxf(c[1] + b1s[col + 1], 0.f);
-            const float z2 = fmaxf(c[2] + b1s[col], 0.f), z3 = fmaxf(c[3] + b1s[col + 1], 0.f);
-            const int kt = nt >> 1;
-            if ((nt & 1) == 0) {
-                h1[kt][0] = pack_bf16(z0, z1);
-                h1[kt][1] = pack_bf16(z2, z3);
-            } else {
-                h1[kt][2] = pack_bf16(z0, z1);
-                h1[kt][3] = pack_bf16(z2, z3);
+            for (int j = 0; j < 8; ++j) {
+                const int col = c * 16 + 2 * j;
+                pk[j] = pack_bf16(fmaxf(v[2 * j] + S.b1[col], 0.f), fmaxf(v[2 * j + 1] + S.b1[col + 1], 0.f));
+            }
+            const uint4 q0 = make_uint4(pk[0], pk[1], pk[2], pk[3]), q1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            h1[(2 * c) * kTileR + tid] = q0;
+            h1[(2 * c + 1) * kTileR + tid] = q1;
+            if (H1out && r < R) {
+                uint4 *g = reinterpret_cast<uint4 *>(H1out + r * kH + c * 16);
+                g[0] = q0;
+                g[1] = q1;
             }
         }
-        if (H1out) {
+        tc::fence_async_smem();
+        tc::tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after();
 #pragma unroll
-            for (int kt = 0; kt < 8; ++kt) {
-                const int col = kt * 16 + 2 * t;
-                if (ra < R) {
-                    *reinterpret_cast<uint32_t *>(H1out + ra * kH + col) = h1[kt][0];
-                    *reinterpret_cast<uint32_t *>(H1out + ra * kH + col + 8) = h1[kt][2];
-                }
-                if (rb < R) {
-                    *reinterpret_cast<uint32_t *>(H1out + rb * kH + col) = h1[kt][1];
-                    *reinterpret_cast<uint32_t *>(H1out + rb * kH + col + 8) = h1[kt][3];
-                }
+            for (int k = 0; k < kH / 16; ++k)
+                tc::mma_bf16(tmem + kH, tc::smem_desc(S.h1 + k * 2 * kTileR * 8, kTileR * 16, 128),
+                             tc::smem_desc(S.w2 + k * 2 * kH * 8, kH * 16, 128), id, k > 0 ? 1u : 0u);
+            tc::mma_commit(&S.bar_mma);
+        }
+        mma_pending = true;
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar_mma, pm, kWaitLimit));
+        if (!ok) break;
+        pm ^= 1;
+        mma_pending = false;
+        tc::tc_fence_after();
+        float acc = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < kH / 16; ++c) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)(kH + c * 16), v);
+            uint32_t pk[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = c * 16 + 2 * j;
+                // H2 is rounded to bf16 (the stored activation); the output uses the same rounded values
+                const __nv_bfloat162 h =
+                    __floats2bfloat162_rn(fmaxf(v[2 * j] + S.b2[col], 0.f), fmaxf(v[2 * j + 1] + S.b2[col + 1], 0.f));
+                acc += __bfloat162float(h.x) * S.w3[col] + __bfloat162float(h.y) * S.w3[col + 1];
+                pk[j] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            if (H2out && r < R) {
+                uint4 *g = reinterpret_cast<uint4 *>(H2out + r * kH + c * 16);
+                g[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                g[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
-        // layer 2 and the output dot product
-        float ya = 0.f, yb = 0.f;
-#pragma unroll 4
-        for (int nt = 0; nt < 16; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const bf16 *wb = w2s + (nt * 8 + g) * kW2Pitch;
+        if (r < R) y[r] = acc + b3;
+        tc::tc_fence_before();
+        __syncthreads();  // TMEM and H1 are rewritten by the next tile
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1u);
+        // bounded waits for what this block still has in flight
+        if (mma_pending) tc::mbar_wait(&S.bar_mma, pm, kWaitLimit);
+        for (int b = 0; b < 2; ++b)
+            if (x_pending[b]) tc::mbar_wait(&S.bar_x[b], px[b], kWaitLimit);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// C = A * B on the tensor cores, 128 x 128 output tiles, K in stages of 64.
+// A(m, k) = A[m*sAm + k*sAk], B(k, n) = B[k*sBk + n*sBn] (bf16, any strides;
+// rows beyond M or N and K beyond the block's range are zero).  The threads
+// stage both operands into the K-block layout, one thread issues the four
+// K = 16 MMAs of a stage into the TMEM accumulator, and the epilogue (thread t
+// = output row t) either atomically adds into fp32 C (grid.z splits K: weight
+// gradients) or writes bf16 C * [mask > 0] (grid.z = 1).
+enum { kEpiAtomic = 0, kEpiMaskBf16 = 1 };
+constexpr int kGT = 128, kGKs = 64;
+
+struct GemmSmem {
+    bf16 a[kGT * kGKs];
+    bf16 b[kGT * kGKs];
+    uint64_t bar;
+    uint32_t tmem;
+};
+// at most three blocks (3 x 128 TMEM columns) per SM; descriptor reach as in FwdSmem
+constexpr int kGemmSmemBytes = 64 * 1024;
+static_assert(sizeof(GemmSmem) + 1024 <= kGemmSmemBytes, "gemm shared memory");
+static_assert(offsetof(GemmSmem, b) + 3 * 4096 + 15 * 2048 + 256 <= kGemmSmemBytes, "descriptor reach");
+
+// One operand row (index `row` of the tile) for K positions [k0, k0 + 64):
+// element (row, k) = P[row_off + k * sk]; lanes beyond `limit` are zero.
+__device__ __forceinline__ void stage_row(bf16 *tile, int row, const bf16 *P, int64_t row_off, int64_t sk, bool valid,
+                                          int64_t k0, int64_t k_end)
+{
+    uint4 *t = reinterpret_cast<uint4 *>(tile);
+    const unsigned short *q = reinterpret_cast<const unsigned short *>(P);
+#pragma unroll 1
+    for (int kb = 0; kb < kGKs / 8; ++kb) {
+        uint32_t w[4];
 #pragma unroll
-            for (int kt = 0; kt < 8; ++kt)
-                mma_bf16(c, h1[kt], *reinterpret_cast<const uint32_t *>(wb + kt * 16 + 2 * t),
-                         *reinterpret_cast<const uint32_t *>(wb + kt * 16 + 2 * t + 8));
-            const int col = nt * 8 + 2 * t;
-            // H2 is rounded to bf16 (the stored activation); the output uses the same rounded values
-            const __nv_bfloat162 ha = __floats2bfloat162_rn(fmaxf(c[0] + b2s[col], 0.f), fmaxf(c[1] + b2s[col + 1], 0.f));
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(fmaxf(c[2] + b2s[col], 0.f), fmaxf(c[3] + b2s[col + 1], 0.f));
-            ya += __bfloat162float(ha.x) * w3s[col] + __bfloat162float(ha.y) * w3s[col + 1];
-            yb += __bfloat162float(hb.x) * w3s[col] + __bfloat162float(hb.y) * w3s[col + 1];
-            if (H2out) {
-                if (ra < R) *reinterpret_cast<__nv_bfloat162 *>(H2out + ra * kH + col) = ha;
-                if (rb < R) *reinterpret_cast<__nv_bfloat162 *>(H2out + rb * kH + col) = hb;
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int64_t k = k0 + kb * 8 + 2 * j;
+            const uint32_t lo = (valid && k < k_end) ? q[row_off + k * sk] : 0u;
+            const uint32_t hi = (valid && k + 1 < k_end) ? q[row_off + (k + 1) * sk] : 0u;
+            w[j] = lo | (hi << 16);
         }
-        ya += __shfl_xor_sync(kFull, ya, 1);
-        ya += __shfl_xor_sync(kFull, ya, 2);
-        yb += __shfl_xor_sync(kFull, yb, 1);
-        yb += __shfl_xor_sync(kFull, yb, 2);
-        if (t == 0) {
-            if (ra < R) y[ra] = ya + b3;
-            if (rb < R) y[rb] = yb + b3;
-        }
+        t[kb * kGT + row] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
-// Generic C = A * B on tensor cores, 64x64 tiles, BK = 32, 4 warps (32x32 each).
-// A(m, k) = A[m*sAm + k*sAk], B(k, n) = B[k*sBk + n*sBn] (bf16, any strides).
-// grid.z splits K; the epilogue either atomically adds into fp32 C (split-K
-// reductions of weight gradients) or writes bf16 C * [mask > 0] and adds the
-// column sums of that product into colsum (fp32).
-enum { kEpiAtomic = 0, kEpiMaskBf16 = 1 };
-constexpr int kGM = 64, kGN = 64, kGK = 32, kGPitch = kGK + 8;
-
 template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm(int64_t M, int64_t N, int64_t K, const bf16 *A, int64_t sAm, int64_t sAk,
-                                              const bf16 *B, int64_t sBk, int64_t sBn, float *C, int64_t ldc,
-                                              const bf16 *mask, bf16 *outb, float *colsum, int64_t kchunk)
+__global__ void __launch_bounds__(kGT, 1)
+    k_gemm(int64_t M, int64_t N, int64_t K, const bf16 *A, int64_t sAm, int64_t sAk, const bf16 *B, int64_t sBk,
+           int64_t sBn, float *C, int64_t ldc, const bf16 *mask, bf16 *outb, int64_t kchunk, uint32_t *err)
 {
-    __shared__ __align__(16) bf16 As[kGM * kGPitch];
-    __shared__ __align__(16) bf16 Bs[kGN * kGPitch];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int64_t m0 = (int64_t)blockIdx.y * kGM, n0 = (int64_t)blockIdx.x * kGN;
-    const int64_t k_begin = (int64_t)blockIdx.z * kchunk, k_end = min(K, k_begin + kchunk);
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const bf16 zero = __float2bfloat16_rn(0.f);
-    for (int64_t k0 = k_begin; k0 < k_end; k0 += kGK) {
-        for (int i = threadIdx.x; i < kGM * kGK; i += blockDim.x) {
-            const int r = i / kGK, c = i % kGK;
-            const int64_t gm = m0 + r, gk = k0 + c;
-            As[r * kGPitch + c] = (gm < M && gk < k_end) ? A[gm * sAm + gk * sAk] : zero;
-            const int64_t gn = n0 + r;
-            Bs[r * kGPitch + c] = (gn < N && gk < k_end) ? B[gk * sBk + gn * sBn] : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kGK; kk += 16) {
-            uint32_t a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const bf16 *p = As + (wm + mt * 16 + g) * kGPitch + kk + 2 * t;
-                a[mt][0] = *reinterpret_cast<const uint32_t *>(p);
-                a[mt][1] = *reinterpret_cast<const uint32_t *>(p + 8 * kGPitch);
-                a[mt][2] = *reinterpret_cast<const uint32_t *>(p + 8);
-                a[mt][3] = *reinterpret_cast<const uint32_t *>(p + 8 * kGPitch + 8);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const bf16 *p = Bs + (wn + nt * 8 + g) * kGPitch + kk + 2 * t;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(p);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(p + 8);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], a[mt], b0, b1);
-            }
-        }
-        __syncthreads();
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    GemmSmem &S = *reinterpret_cast<GemmSmem *>(dsm);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        tc::mbar_init(&S.bar, 1);
+        tc::mbar_init_fence();
     }
+    if (warp == 0) tc::tmem_alloc(&S.tmem, kGT);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const int64_t m0 = (int64_t)blockIdx.y * kGT, n0 = (int64_t)blockIdx.x * kGT;
+    const int64_t k_begin = (int64_t)blockIdx.z * kchunk, k_end = min(K, k_begin + kchunk);
+    const uint32_t id = tc::idesc_bf16(kGT, kGT);
+    const int64_t gm = m0 + tid, gn = n0 + tid;
+    bool ok = true, mma_pending = false, any = false;
+    uint32_t pm = 0;
+    for (int64_t k0 = k_begin; k0 < k_end; k0 += kGKs) {
+        stage_row(S.a, tid, A, gm * sAm, sAk, gm < M, k0, k_end);
+        stage_row(S.b, tid, B, gn * sBn, sBk, gn < N, k0, k_end);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after();
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        float cs[2] = {0.f, 0.f};
+            for (int k = 0; k < kGKs / 16; ++k)
+                tc::mma_bf16(tmem, tc::smem_desc(S.a + k * 2 * kGT * 8, kGT * 16, 128),
+                             tc::smem_desc(S.b + k * 2 * kGT * 8, kGT * 16, 128), id, (any || k > 0) ? 1u : 0u);
+            tc::mma_commit(&S.bar);
+        }
+        any = true;
+        mma_pending = true;
+        ok = __syncthreads_and(tc::mbar_wait(&S.bar, pm, kWaitLimit));
+        if (!ok) break;
+        pm ^= 1;
+        mma_pending = false;
+    }
+    if (ok && any) {
+        tc::tc_fence_after();
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int c = 0; c < kGT / 16; ++c) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), v);
+            if (gm >= M) continue;
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t gm = m0 + wm + mt * 16 + g + (q >= 2 ? 8 : 0);
-                const int64_t gn = n0 + wn + nt * 8 + 2 * t + (q & 1);
-                if (gm >= M || gn >= N) continue;
+            for (int j = 0; j < 16; ++j) {
+                const int64_t n = n0 + c * 16 + j;
+                if (n >= N) continue;
                 if (EPI == kEpiAtomic) {
-                    atomicAdd(C + gm * ldc + gn, acc[mt][nt][q]);
+                    atomicAdd(C + gm * ldc + n, v[j]);
                 } else {
-                    const bool on = __bfloat162float(mask[gm * ldc + gn]) > 0.f;
-                    const bf16 v = __float2bfloat16_rn(on ? acc[mt][nt][q] : 0.f);
-                    outb[gm * ldc + gn] = v;
-                    cs[q & 1] += __bfloat162float(v);
+                    const bool on = __bfloat162float(mask[gm * ldc + n]) > 0.f;
+                    outb[gm * ldc + n] = __float2bfloat16_rn(on ? v[j] : 0.f);
                 }
             }
         }
-        if (EPI == kEpiMaskBf16) {
-            // reduce over the 8 row-groups g of the warp, then one atomic per column
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                cs[0] += __shfl_xor_sync(kFull, cs[0], o);
-                cs[1] += __shfl_xor_sync(kFull, cs[1], o);
-            }
-            if (g == 0) {
-                const int64_t gn = n0 + wn + nt * 8 + 2 * t;
-                if (gn < N) atomicAdd(colsum + gn, cs[0]);
-                if (gn + 1 < N) atomicAdd(colsum + gn + 1, cs[1]);
-            }
-        }
+    } else if (!ok) {
+        if (tid == 0) atomicExch(err, 1u);
+        if (mma_pending) tc::mbar_wait(&S.bar, pm, kWaitLimit);
     }
+    if (EPI == kEpiMaskBf16 && !any && gm < M)  // empty K: the product is zero
+        for (int64_t n = n0; n < min(N, n0 + kGT); ++n) outb[gm * ldc + n] = __float2bfloat16_rn(0.f);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, kGT);
+}
+
+// out[j] += sum over rows of Z[r][j] (bf16 [R][128]); one warp per row, four
+// columns per lane.
+__global__ void k_colsum_bf16(const bf16 *Z, int64_t R, float *out)
+{
+    __shared__ float cs[kH];
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) cs[i] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += __bfloat162float(Z[r * kH + lane + 32 * q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) atomicAdd(&cs[lane + 32 * q], acc[q]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) atomicAdd(out + i, cs[i]);
 }
 
 // dy = (y - t)/R; loss += (y - t)^2 / (2R); dZ2 = dy (x) w3 * [H2 > 0] (bf16);
@@ -538,7 +673,9 @@ __global__ void k_gather_rows(const bf16 *X, const int32_t *rows_idx, int64_t R,
 // rare large batch cannot blow the weights up.
 constexpr float kClip = 1.0f;
 
-__global__ void k_mlp_sgd(float *p, float *v, float *gr, float lr, float mu, bf16 *W1t, bf16 *W2t, bf16 *W2b)
+// W1c / W2c are the tensor-core B operands in the K-block layout (row = out,
+// K = in); W2b = W2 row-major (B operand of dZ2 W2^T).
+__global__ void k_mlp_sgd(float *p, float *v, float *gr, float lr, float mu, bf16 *W1c, bf16 *W2c, bf16 *W2b)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNumParams; i += gridDim.x * blockDim.x) {
         if (lr != 0.f || mu != 0.f) {
@@ -549,12 +686,12 @@ __global__ void k_mlp_sgd(float *p, float *v, float *gr, float lr, float mu, bf1
         }
         gr[i] = 0.f;
         const float w = p[i];
-        if (i < kOffB1) {                         // W1[in][out] -> W1t[out][in]
+        if (i < kOffB1) {                         // W1[in][out]
             const int in = i / kH, out = i % kH;
-            W1t[out * kF + in] = __float2bfloat16_rn(w);
-        } else if (i >= kOffW2 && i < kOffB2) {   // W2[in][out] -> W2t[out][in] and W2b = W2
+            W1c[kblk(out, in, kH)] = __float2bfloat16_rn(w);
+        } else if (i >= kOffW2 && i < kOffB2) {   // W2[in][out]
             const int j = i - kOffW2, in = j / kH, out = j % kH;
-            W2t[out * kH + in] = __float2bfloat16_rn(w);
+            W2c[kblk(out, in, kH)] = __float2bfloat16_rn(w);
             W2b[j] = __float2bfloat16_rn(w);
         }
     }
@@ -583,9 +720,10 @@ static unsigned grid_cap(int64_t work, int threads)
 // ------------------------------------------------------------ the network object
 struct dbl_mlp {
     float *p = nullptr, *v = nullptr, *gr = nullptr;  // fp32 parameters, momentum, gradients
-    dbl::bf16 *W1t = nullptr, *W2t = nullptr, *W2b = nullptr;
+    dbl::bf16 *W1c = nullptr, *W2c = nullptr, *W2b = nullptr;
     dbl::bf16 *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr, *Xg = nullptr;
     float *y = nullptr;
+    uint32_t *d_err = nullptr;  // raised by a tensor-core kernel whose bounded wait ran out
     int64_t cap_rows = 0;
     std::string err;
 };
@@ -626,16 +764,92 @@ static dbl_status mlp_scratch(dbl_mlp *m, int64_t rows, cudaStream_t s)
     return DBL_OK;
 }
 
-static MlpDev mlp_dev(const dbl_mlp *m) { return MlpDev{m->W1t, m->W2t, m->p}; }
+static MlpDev mlp_dev(const dbl_mlp *m) { return MlpDev{m->W1c, m->W2c, m->p}; }
 
-static void launch_forward(dbl_mlp *m, const bf16 *X, const int32_t *idx, int64_t R, float *y, bf16 *H1, bf16 *H2,
-                           cudaStream_t s)
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
 {
-    int64_t warps = (R + 15) / 16;
-    int64_t blocks = (warps + 3) / 4;
-    int64_t cap = (int64_t)num_sms() * 8;
-    if (blocks > cap) blocks = cap;
-    k_mlp_forward<<<(unsigned)(blocks < 1 ? 1 : blocks), 128, 0, s>>>(mlp_dev(m), X, idx, R, y, H1, H2);
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// X [R][16] bf16 as a 3-D tensor (k % 8, row, k / 8) with byte strides
+// (32, 16): a box of (8, 128, 2) lands in shared memory as [2][128][8], the
+// K-block layout of a 128 x 16 operand tile.  Rows beyond R read as zero.
+static bool x_tensor_map(const bf16 *X, int64_t R, CUtensorMap *map)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {8, (cuuint64_t)R, 2};
+    const cuuint64_t strides[2] = {kF * sizeof(bf16), 8 * sizeof(bf16)};
+    const cuuint32_t box[3] = {8, kTileR, 2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)X, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool set_smem_attrs()
+{
+    static int done = 0;
+    if (!done) {
+        bool ok = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmemBytes) ==
+                      cudaSuccess &&
+                  cudaFuncSetAttribute(k_gemm<kEpiAtomic>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kGemmSmemBytes) == cudaSuccess &&
+                  cudaFuncSetAttribute(k_gemm<kEpiMaskBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kGemmSmemBytes) == cudaSuccess;
+        done = ok ? 1 : -1;
+    }
+    return done == 1;
+}
+
+// Contiguous rows whose base is 16-byte aligned go through the tensor copy;
+// gathered (rows_idx) or unaligned rows are staged by the threads.
+static dbl_status launch_forward(dbl_mlp *m, const bf16 *X, const int32_t *idx, int64_t R, float *y, bf16 *H1,
+                                 bf16 *H2, cudaStream_t s)
+{
+    if (!set_smem_attrs()) return mlp_fail(m, DBL_ERR_CUDA, "mlp: shared-memory attribute refused");
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    int use_tma = 0;
+    if (!idx && ((uintptr_t)X & 15u) == 0) {
+        if (!x_tensor_map(X, R, &map)) return mlp_fail(m, DBL_ERR_CUDA, "mlp: cuTensorMapEncodeTiled failed");
+        use_tma = 1;
+    }
+    const int64_t tiles = (R + kTileR - 1) / kTileR;
+    int64_t blocks = (int64_t)num_sms() * 2;
+    if (blocks > tiles) blocks = tiles;
+    k_mlp_forward<<<(unsigned)(blocks < 1 ? 1 : blocks), kTileR, kFwdSmemBytes, s>>>(map, use_tma, mlp_dev(m), X, idx,
+                                                                                     R, y, H1, H2, m->d_err);
+    return DBL_OK;
+}
+
+template <int EPI>
+static void launch_gemm(dbl_mlp *m, int64_t M, int64_t N, int64_t K, const bf16 *A, int64_t sAm, int64_t sAk,
+                        const bf16 *B, int64_t sBk, int64_t sBn, float *C, int64_t ldc, const bf16 *mask, bf16 *outb,
+                        int64_t kchunk, cudaStream_t s)
+{
+    const dim3 grid((unsigned)((N + kGT - 1) / kGT), (unsigned)((M + kGT - 1) / kGT),
+                    (unsigned)((K + kchunk - 1) / kchunk));
+    k_gemm<EPI><<<grid, kGT, kGemmSmemBytes, s>>>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc, mask, outb, kchunk,
+                                                   m->d_err);
 }
 
 // Gradients of the mean squared error / 2 over R rows into m->gr (zeroed by the previous SGD call).
@@ -644,25 +858,24 @@ static dbl_status mlp_backward(dbl_mlp *m, const bf16 *X, const float *tgt, cons
 {
     dbl_status st = mlp_scratch(m, R, s);
     if (st) return st;
-    launch_forward(m, X, idx, R, m->y, m->H1, m->H2, s);
+    if ((st = launch_forward(m, X, idx, R, m->y, m->H1, m->H2, s))) return st;
     if (loss) cudaMemsetAsync(loss, 0, sizeof(float), s);
     k_mlp_out_grad<<<grid_cap(R * 32, 256), 256, 0, s>>>(m->y, tgt, idx, R, m->H2, m->p, m->dZ2, m->gr, loss);
     const int64_t kchunk = 1024;
-    const unsigned zs = (unsigned)((R + kchunk - 1) / kchunk);
     // dW2 = H1^T dZ2: M = 128 (in), N = 128 (out), K = R
-    k_gemm<kEpiAtomic><<<dim3(2, 2, zs), 128, 0, s>>>(kH, kH, R, m->H1, 1, kH, m->dZ2, kH, 1, m->gr + kOffW2, kH,
-                                                      nullptr, nullptr, nullptr, kchunk);
+    launch_gemm<kEpiAtomic>(m, kH, kH, R, m->H1, 1, kH, m->dZ2, kH, 1, m->gr + kOffW2, kH, nullptr, nullptr, kchunk,
+                            s);
     // dZ1 = (dZ2 W2^T) * [H1 > 0]: M = R, N = 128 (in), K = 128 (out); B(k=out, n=in) = W2[in][out]
-    k_gemm<kEpiMaskBf16><<<dim3(2, (unsigned)((R + kGM - 1) / kGM), 1), 128, 0, s>>>(
-        R, kH, kH, m->dZ2, kH, 1, m->W2b, 1, kH, nullptr, kH, m->H1, m->dZ1, m->gr + kOffB1, kH);
+    launch_gemm<kEpiMaskBf16>(m, R, kH, kH, m->dZ2, kH, 1, m->W2b, 1, kH, nullptr, kH, m->H1, m->dZ1, kH, s);
+    // db1 = column sums of dZ1
+    k_colsum_bf16<<<grid_cap(R * 32, 256), 256, 0, s>>>(m->dZ1, R, m->gr + kOffB1);
     // dW1 = X^T dZ1: M = 16, N = 128, K = R
     const bf16 *Xr = X;
     if (idx) {
         k_gather_rows<<<grid_cap(R * kF, 256), 256, 0, s>>>(X, idx, R, m->Xg);
         Xr = m->Xg;
     }
-    k_gemm<kEpiAtomic><<<dim3(2, 1, zs), 128, 0, s>>>(kF, kH, R, Xr, 1, kF, m->dZ1, kH, 1, m->gr + kOffW1, kH,
-                                                      nullptr, nullptr, nullptr, kchunk);
+    launch_gemm<kEpiAtomic>(m, kF, kH, R, Xr, 1, kF, m->dZ1, kH, 1, m->gr + kOffW1, kH, nullptr, nullptr, kchunk, s);
     cudaError_t e = cudaGetLastError();
     return e ? mlp_fail(m, DBL_ERR_CUDA, std::string("mlp backward: ") + cudaGetErrorString(e)) : DBL_OK;
 }
@@ -719,8 +932,9 @@ dbl_status dbl_mlp_create(const float *params_host, dbl_mlp **out, void *stream)
     if ((st = mlp_alloc(m, (void **)&m->p, sizeof(float) * kNumParams, s)) ||
         (st = mlp_alloc(m, (void **)&m->v, sizeof(float) * kNumParams, s)) ||
         (st = mlp_alloc(m, (void **)&m->gr, sizeof(float) * kNumParams, s)) ||
-        (st = mlp_alloc(m, (void **)&m->W1t, sizeof(bf16) * kF * kH, s)) ||
-        (st = mlp_alloc(m, (void **)&m->W2t, sizeof(bf16) * kH * kH, s)) ||
+        (st = mlp_alloc(m, (void **)&m->W1c, sizeof(bf16) * kF * kH, s)) ||
+        (st = mlp_alloc(m, (void **)&m->W2c, sizeof(bf16) * kH * kH, s)) ||
+        (st = mlp_alloc(m, (void **)&m->d_err, 16, s)) ||
         (st = mlp_alloc(m, (void **)&m->W2b, sizeof(bf16) * kH * kH, s))) {
         dbl_mlp_destroy(m, stream);
         return st;
@@ -728,7 +942,8 @@ dbl_status dbl_mlp_create(const float *params_host, dbl_mlp **out, void *stream)
     cudaMemcpyAsync(m->p, params_host, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(m->v, 0, sizeof(float) * kNumParams, s);
     cudaMemsetAsync(m->gr, 0, sizeof(float) * kNumParams, s);
-    k_mlp_sgd<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->p, m->v, m->gr, 0.f, 0.f, m->W1t, m->W2t, m->W2b);
+    cudaMemsetAsync(m->d_err, 0, 16, s);
+    k_mlp_sgd<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->p, m->v, m->gr, 0.f, 0.f, m->W1c, m->W2c, m->W2b);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) {
         dbl_mlp_destroy(m, stream);
@@ -742,7 +957,7 @@ void dbl_mlp_destroy(dbl_mlp *m, void *stream)
 {
     if (!m) return;
     cudaStream_t s = (cudaStream_t)stream;
-    void *ps[] = {m->p, m->v, m->gr, m->W1t, m->W2t, m->W2b, m->H1, m->H2, m->dZ2, m->dZ1, m->Xg, m->y};
+    void *ps[] = {m->p, m->v, m->gr, m->W1c, m->W2c, m->W2b, m->H1, m->H2, m->dZ2, m->dZ1, m->Xg, m->y, m->d_err};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);
@@ -754,14 +969,18 @@ dbl_status dbl_mlp_params(dbl_mlp *m, float *params_host, void *stream)
     if (!m || !params_host) return DBL_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemcpyAsync(params_host, m->p, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s);
-    return cudaStreamSynchronize(s) ? DBL_ERR_CUDA : DBL_OK;
+    return dbl_mlp_sync(m, stream);
 }
 
 dbl_status dbl_mlp_forward(dbl_mlp *m, const uint16_t *X, const int32_t *rows_idx, int64_t rows, float *y, void *stream)
 {
     if (!m || !X || !y || rows < 0) return mlp_fail(m, DBL_ERR_INVALID, "mlp_forward: bad arguments");
+    if ((uintptr_t)X & 15u) return mlp_fail(m, DBL_ERR_INVALID, "mlp: X must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
-    if (rows) launch_forward(m, (const bf16 *)X, rows_idx, rows, y, nullptr, nullptr, s);
+    if (rows) {
+        dbl_status st = launch_forward(m, (const bf16 *)X, rows_idx, rows, y, nullptr, nullptr, s);
+        if (st) return st;
+    }
     cudaError_t e = cudaGetLastError();
     return e ? mlp_fail(m, DBL_ERR_CUDA, cudaGetErrorString(e)) : DBL_OK;
 }
@@ -770,6 +989,7 @@ dbl_status dbl_mlp_gradients(dbl_mlp *m, const uint16_t *X, const float *target,
                              float *grads, float *loss, void *stream)
 {
     if (!m || !X || !target || !grads || rows <= 0) return mlp_fail(m, DBL_ERR_INVALID, "mlp_gradients: bad arguments");
+    if ((uintptr_t)X & 15u) return mlp_fail(m, DBL_ERR_INVALID, "mlp: X must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     dbl_status st = mlp_backward(m, (const bf16 *)X, target, rows_idx, rows, loss, s);
     if (st) return st;
@@ -783,12 +1003,25 @@ dbl_status dbl_mlp_train_step(dbl_mlp *m, const uint16_t *X, const float *target
                               float lr, float momentum, float *loss, void *stream)
 {
     if (!m || !X || !target || rows <= 0) return mlp_fail(m, DBL_ERR_INVALID, "mlp_train_step: bad arguments");
+    if ((uintptr_t)X & 15u) return mlp_fail(m, DBL_ERR_INVALID, "mlp: X must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     dbl_status st = mlp_backward(m, (const bf16 *)X, target, rows_idx, rows, loss, s);
     if (st) return st;
-    k_mlp_sgd<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->p, m->v, m->gr, lr, momentum, m->W1t, m->W2t, m->W2b);
+    k_mlp_sgd<<<(kNumParams + 255) / 256, 256, 0, s>>>(m->p, m->v, m->gr, lr, momentum, m->W1c, m->W2c, m->W2b);
     cudaError_t e = cudaGetLastError();
     return e ? mlp_fail(m, DBL_ERR_CUDA, cudaGetErrorString(e)) : DBL_OK;
+}
+
+dbl_status dbl_mlp_sync(dbl_mlp *m, void *stream)
+{
+    if (!m) return DBL_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t flag = 0;
+    cudaMemcpyAsync(&flag, m->d_err, sizeof(flag), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return mlp_fail(m, DBL_ERR_CUDA, cudaGetErrorString(e));
+    if (flag) return mlp_fail(m, DBL_ERR_TIMEOUT, "mlp: a tensor-core wait ran out; outputs are invalid");
+    return DBL_OK;
 }
 
 const char *dbl_mlp_last_error(const dbl_mlp *m) { return m ? m->err.c_str() : ""; }
