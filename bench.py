@@ -45,7 +45,7 @@ UNIT = "ops/s (queries + inserted edges)"
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
 NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_152_413_000 + 21_857_792, "133eba2d8343"),
-                                             "propagate": (54_260_480 + 1_915_392, "c9371526e6e2")}
+                                             "propagate": (54_288_640 + 2_144_768, "5d5ed93f1061")}
 KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_insert.cu",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
 
@@ -386,6 +386,39 @@ def insertion_bytes(ix, w, I):
     return 8 * E + (E - loops) * (4 * 32 + 2 * 32 + 2 * 32) + applied * 2 * 32
 
 
+MLP_FLOPS_PER_ROW = 2 * (16 * 128 + 128 * 128 + 128)  # the scorer's three layers
+
+
+def scorer_roofline(ix, reps: int = 10):
+    """Tensor-core roofline of the scorer's fused forward (k_mlp_forward) over
+    every vertex's features, as at landmark selection: CUDA events around
+    `reps` back-to-back launches on the current stream."""
+    import torch
+
+    import paper_2101_09441_gb300 as dbl
+    peaks, src = measured_peaks()
+    feats = ix.features()
+    mlp = dbl.MLP(dbl.MLP.init_params(1))
+    y = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+    for _ in range(3):
+        mlp.forward(feats, out=y, sync=False)
+    mlp.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        mlp.forward(feats, out=y, sync=False)
+    e1.record()
+    mlp.sync()
+    ms = e0.elapsed_time(e1) / reps
+    mlp.close()
+    rows = int(feats.shape[0])
+    ach = rows * MLP_FLOPS_PER_ROW / (ms * 1e-3) / 1e12
+    return {"kernel": "k_mlp_forward (tcgen05, TMA)", "bound": "tensor", "achieved": ach,
+            "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "traffic": None,
+            "peak_source": f"bf16_tflops (burst) of {src}", "rows": rows, "flops_per_row": MLP_FLOPS_PER_ROW,
+            "ms_per_launch": ms}
+
+
 def build_roofline(form):
     """Achieved GB/s of the label build's propagation (CUDA events at build)."""
     peaks, src = measured_peaks()
@@ -474,6 +507,7 @@ def bench_gpu(args):
     _, lb, lr_ = plain_ix.selection()
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    roof_scorer = scorer_roofline(plain_ix)
     plain_ix.close()
     learned = run_form("learned", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
     learned_t = run_form("learned_timing", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
@@ -520,6 +554,7 @@ def bench_gpu(args):
             "roofline": roof,
             "roofline_label_test": roof_label,
             "roofline_build": build_roofline(learned_t),
+            "roofline_scorer": roof_scorer,
             "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
             "clocks": learned["clocks"],

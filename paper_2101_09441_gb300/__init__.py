@@ -560,13 +560,16 @@ class MLP:
         self._check(lib().dbl_mlp_params(self._h, out.ctypes.data, _stream_handle(self._stream)))
         return out
 
-    def forward(self, X, rows_idx=None, stream=None):
+    def forward(self, X, rows_idx=None, stream=None, out=None, sync=True):
+        """Scores of the rows (float32 [rows]); with sync=False the call only
+        queues the kernel (errors then surface at the next sync())."""
         import torch
         R = int(rows_idx.numel()) if rows_idx is not None else int(X.shape[0])
-        y = torch.empty(R, dtype=torch.float32, device=X.device)
+        y = out if out is not None else torch.empty(R, dtype=torch.float32, device=X.device)
         self._check(lib().dbl_mlp_forward(self._h, _ptr(X), _ptr(rows_idx), R, _ptr(y),
                                           _stream_handle(stream or self._stream)))
-        self.sync(stream)
+        if sync:
+            self.sync(stream)
         return y
 
     def gradients(self, X, target, rows_idx=None, stream=None):
