@@ -277,7 +277,12 @@ static void destroy_impl(dbl_index *ix, cudaStream_t s)
     ix->owned.clear();
     if (ix->h_pinned) cudaFreeHost(ix->h_pinned);
     if (ix->copy_stream) cudaStreamDestroy(ix->copy_stream);
+    if (ix->ins_copy_stream) cudaStreamDestroy(ix->ins_copy_stream);
     for (auto &e : ix->ev_stage_used)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : ix->ev_istage_used)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : ix->ev_istage_in)
         if (e) cudaEventDestroy(e);
     for (auto &r : ix->tranges) {
         cudaEventDestroy(r.a);
@@ -456,6 +461,13 @@ dbl_status dbl_query_ctx(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int
 
 const char *dbl_qctx_last_error(const dbl_qctx *c) { return c ? c->err.c_str() : ""; }
 
+static dbl_status ensure_copy_stream(dbl_index *ix, cudaStream_t *cs)
+{
+    if (*cs) return DBL_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking);
+    return e ? cuda_fail(ix, e, "copy stream") : DBL_OK;
+}
+
 static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
 {
     if (ix->stage_chunk >= chunk) return DBL_OK;
@@ -466,10 +478,7 @@ static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
         // u, v (int32) + ans, code (uint8) per pair
         if ((st = alloc_buf(ix, (void **)&ix->dstage[b], (size_t)chunk * 10 + 64, s))) return st;
     }
-    if (!ix->copy_stream) {
-        cudaError_t e = cudaStreamCreateWithFlags(&ix->copy_stream, cudaStreamNonBlocking);
-        if (e) return cuda_fail(ix, e, "copy stream");
-    }
+    if ((st = ensure_copy_stream(ix, &ix->copy_stream))) return st;
     for (auto &e : ix->ev_stage_used) {
         if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming)) return cuda_fail(ix, cudaGetLastError(), "stage events");
         // (re)allocated buffers: the first uploads wait for everything queued so far
@@ -538,18 +547,47 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
         return fail(ix, DBL_ERR_INVALID, "insert_host: bad batch");
     if (b == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st;
     if (b > ix->istage_cap) {
-        free_buf(ix, ix->istage, s);
-        ix->istage = nullptr;
+        // stream-ordered frees: after every insertion queued on s (each waited for its upload)
+        for (int k = 0; k < ix->istage_n; ++k) {
+            free_buf(ix, ix->istage[k], s);
+            ix->istage[k] = nullptr;
+        }
+        ix->istage_cap = 0;
+        ix->istage_n = 0;
         const int64_t cap = std::max<int64_t>(b, 1 << 16);
-        dbl_status st = alloc_buf(ix, &ix->istage, 8 * (size_t)cap, s);
-        if (st) return st;
+        const int nbuf = (int)std::min<int64_t>(dbl_index::kMaxIStage, std::max<int64_t>(2, (64ll << 20) / (8 * cap)));
+        for (int k = 0; k < nbuf; ++k) {
+            if ((st = alloc_buf(ix, &ix->istage[k], 8 * (size_t)cap, s))) return st;
+            ix->istage_n = k + 1;
+        }
+        if ((st = ensure_copy_stream(ix, &ix->ins_copy_stream))) return st;
+        for (int k = 0; k < nbuf; ++k) {
+            for (cudaEvent_t *e : {&ix->ev_istage_used[k], &ix->ev_istage_in[k]})
+                if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming))
+                    return cuda_fail(ix, cudaGetLastError(), "insertion stage events");
+            cudaEventRecord(ix->ev_istage_used[k], s);  // new buffers: first uploads follow what is queued
+        }
         ix->istage_cap = cap;
+        ix->istage_turn = 0;
     }
-    char *d = (char *)ix->istage;
-    cudaMemcpyAsync(d, src_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(d + 4 * ix->istage_cap, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, s);
-    dbl_status st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->istage_cap), b, s);
+    // The buffers in turn: a batch's upload (own copy stream) waits only until
+    // the insertion that last read its buffer is done, so uploads run ahead of
+    // the insertions (a step of up to istage_n batches uploads all of them
+    // before a query upload queued after it); the insertion waits for its own
+    // upload.
+    const int k = ix->istage_turn;
+    ix->istage_turn = (k + 1) % ix->istage_n;
+    char *d = (char *)ix->istage[k];
+    cudaStream_t cs = ix->ins_copy_stream;
+    cudaStreamWaitEvent(cs, ix->ev_istage_used[k], 0);
+    cudaMemcpyAsync(d, src_host, 4 * (size_t)b, cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(d + 4 * ix->istage_cap, dst_host, 4 * (size_t)b, cudaMemcpyHostToDevice, cs);
+    cudaEventRecord(ix->ev_istage_in[k], cs);
+    cudaStreamWaitEvent(s, ix->ev_istage_in[k], 0);
+    st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->istage_cap), b, s);
+    cudaEventRecord(ix->ev_istage_used[k], s);
     if (st) return st;
     return (ix->opt.flags & DBL_FLAG_ASYNC) ? DBL_OK : read_status(ix, s);
 }

@@ -263,9 +263,19 @@ struct dbl_index {
     void *dstage[2] = {nullptr, nullptr};  // query host form: double-buffered chunks
     int64_t stage_chunk = 0;
     cudaEvent_t ev_stage_used[2] = {nullptr, nullptr};  // recorded when a query chunk is done with its buffer
-    void *istage = nullptr;                // insertion host form: its own buffer, so query
-    int64_t istage_cap = 0;                //   uploads can overlap insertions
-    cudaStream_t copy_stream = nullptr;
+    // insertion host form: a ring of its own buffers (kMaxIStage at most, 64 MB
+    // together), so query uploads overlap insertions and later batches upload
+    // while earlier ones run
+    static constexpr int kMaxIStage = 16;
+    void *istage[kMaxIStage] = {};
+    int istage_n = 0;
+    int64_t istage_cap = 0;
+    int istage_turn = 0;
+    cudaEvent_t ev_istage_used[kMaxIStage] = {};  // recorded when an insertion is done with its buffer
+    cudaEvent_t ev_istage_in[kMaxIStage] = {};    // recorded when a buffer's upload is done
+    cudaStream_t copy_stream = nullptr;      // query uploads
+    cudaStream_t ins_copy_stream = nullptr;  // insertion uploads (a FIFO of their own: a query upload
+                                             //   does not queue behind uploads that wait for insertions)
 
     // DBL_FLAG_TIMING: event pairs per kernel class, harvested by dbl_timings
     struct TimedRange {
