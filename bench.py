@@ -294,6 +294,7 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     if build_t:
         res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
         res["build_algorithmic_bytes"] = build_bytes(ix, I, ix.info()["record_bytes"] // 2)
+        res["build_edges_relaxed"] = int(ix.stats()[10])
     if flags & dbl.FLAG_PERSISTENT and not args.no_autotune:
         # autotuned frontier schedule (sample: the step's insertions as one batch
         # and 1M queries; a few batches of the first hundred thousand edges do not
@@ -427,9 +428,11 @@ def build_roofline(form):
     if not ms or not alg:
         return None
     ach = alg / (ms * 1e-3) / 1e9
+    relaxed = form.get("build_edges_relaxed")
     return {"kernel": "propagate (label build)", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs of {src}",
-            "algorithmic_bytes": alg, "ms": ms}
+            "algorithmic_bytes": alg, "ms": ms, "edges_relaxed": relaxed,
+            "teps": relaxed / (ms * 1e-3) if relaxed else None}
 
 
 def roofline(form, ix, args, w, I, batches, persistent=True):
@@ -466,6 +469,10 @@ def roofline(form, ix, args, w, I, batches, persistent=True):
                 "ms_per_launch": kern[k]["ms_per_launch"]}
     out = obj(cand)
     out["dominant_kernel_by_time"] = dom
+    if cand == "propagate" and form.get("relaxed_per_step") is not None:
+        # repair traversal rate: edges relaxed per second of insertion-kernel time
+        out["edges_relaxed_per_launch"] = form["relaxed_per_step"] * args.steps / kern[cand]["launches"]
+        out["teps"] = form["relaxed_per_step"] * args.steps / (kern[cand]["ms_total"] * 1e-3)
     return out, (obj("query_label") if "achieved_gbs" in kern.get("query_label", {}) else None)
 
 

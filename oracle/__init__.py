@@ -67,6 +67,8 @@ def _load():
             lib.orc_destroy.restype = None
             lib.orc_degree_landmarks.argtypes = [P, P]
             lib.orc_zero_degree_leaves.argtypes = [P, P, P]
+            lib.orc_rank_landmarks.argtypes = [P, ctypes.c_int, P]
+            lib.orc_threshold_leaves.argtypes = [P, i64, P, P]
             lib.orc_leaf_hash.argtypes = [i32, i32]
             lib.orc_leaf_hash.restype = i32
             lib.orc_build.argtypes = [P, P, P, P, ctypes.c_int]
@@ -135,6 +137,24 @@ class OracleIndex:
         bucket = np.empty(self.n, dtype=np.int32)
         role = np.empty(self.n, dtype=np.uint8)
         _load().orc_zero_degree_leaves(self._h, _p(bucket), _p(role))
+        return bucket, role
+
+    # Section 6, "Label Node Selection" (Table 3 rankings, the M(u) <= r leaf rule)
+    RULES = {"M": 0, "A": 1, "B": 2, "C": 3}
+
+    def rank_landmarks(self, rule: str = "M") -> np.ndarray:
+        """Top-k by M = |Pre|*|Suc| or Table 3's A = max, B = min, C = sum; ties by id."""
+        out = np.empty(self.k, dtype=np.int32)
+        if _load().orc_rank_landmarks(self._h, self.RULES[rule], _p(out)):
+            raise ValueError(f"orc_rank_landmarks failed for rule {rule}")
+        return out
+
+    def threshold_leaves(self, r: int):
+        """Leaves with M(v) <= r (roles: Definition 2 when M(v) = 0, both otherwise)."""
+        bucket = np.empty(self.n, dtype=np.int32)
+        role = np.empty(self.n, dtype=np.uint8)
+        if _load().orc_threshold_leaves(self._h, int(r), _p(bucket), _p(role)):
+            raise ValueError("orc_threshold_leaves: r must be >= 0")
         return bucket, role
 
     # Algorithm 1

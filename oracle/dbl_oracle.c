@@ -9,10 +9,15 @@
  *
  * What it follows, step by step:
  *   - Landmark choice: rank by M(u) = |Pre(u)| * |Suc(u)|, keep the top k
- *     (Section 4.1, landmark heuristic); ties by smaller vertex id.
+ *     (Section 4.1, landmark heuristic); ties by smaller vertex id.  The other
+ *     rankings of Table 3 (Section 6, "Label Node Selection"): A = max(|Pre|,
+ *     |Suc|), B = min(|Pre|, |Suc|), C = |Pre| + |Suc|.
  *   - Leaves: zero in-degree vertices seed BL_in, zero out-degree vertices seed
  *     BL_out (Definition 2, "BL label"); bucket h(v) by Fibonacci hashing
- *     (Knuth, TAOCP vol. 3, 6.4), since the paper leaves h open.
+ *     (Knuth, TAOCP vol. 3, 6.4), since the paper leaves h open.  Section 6
+ *     ("Label Node Selection") widens the leaf set to every u with M(u) <= r;
+ *     a leaf with M(u) > 0 has both neighbour kinds and here seeds both BL_in
+ *     and BL_out (the paper does not say; Lemma 2 holds for any leaf sets).
  *   - Build: one queue BFS per landmark forward (DL_in) and backward (DL_out),
  *     and one multi-source BFS per leaf bucket (Algorithm 1 and the paragraph
  *     after it).  A landmark / leaf labels itself (as Figure 1 shows), and
@@ -173,14 +178,28 @@ static int cmp_rank(const void *pa, const void *pb)
     return (a > b) - (a < b);
 }
 
-int orc_degree_landmarks(const orc_index *h, int32_t *out)
+/* Ranking key of v: rule 0 = |Pre| * |Suc| (the paper's), 1 = A = max,
+ * 2 = B = min, 3 = C = sum of |Pre| and |Suc| (Table 3). */
+static int64_t rank_key(const orc_index *h, int32_t v, int rule)
+{
+    const int64_t p = h->pre[v].len, s = h->suc[v].len;
+    switch (rule) {
+    case 1: return p > s ? p : s;
+    case 2: return p < s ? p : s;
+    case 3: return p + s;
+    default: return p * s;
+    }
+}
+
+int orc_rank_landmarks(const orc_index *h, int rule, int32_t *out)
 {
     int32_t n = h->n;
+    if (rule < 0 || rule > 3) return 1;
     int64_t *M = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     if (!M || !ids) { free(M); free(ids); return 2; }
     for (int32_t v = 0; v < n; ++v) {
-        M[v] = (int64_t)h->pre[v].len * (int64_t)h->suc[v].len;
+        M[v] = rank_key(h, v, rule);
         ids[v] = v;
     }
     g_rank_M = M;
@@ -200,6 +219,26 @@ static int32_t leaf_hash(int32_t v, int32_t kp)
 }
 
 int32_t orc_leaf_hash(int32_t v, int32_t kp) { return leaf_hash(v, kp); }
+
+int orc_degree_landmarks(const orc_index *h, int32_t *out) { return orc_rank_landmarks(h, 0, out); }
+
+/* Leaves by threshold (Section 6, "Label Node Selection"): v is a leaf iff
+ * M(v) = |Pre(v)| * |Suc(v)| <= r.  With M(v) = 0 its roles are those of
+ * Definition 2 (zero in-degree seeds BL_in, zero out-degree seeds BL_out);
+ * a leaf with M(v) > 0 seeds both.  r = 0 is orc_zero_degree_leaves. */
+int orc_threshold_leaves(const orc_index *h, int64_t r, int32_t *bucket, uint8_t *role)
+{
+    if (r < 0) return 1;
+    for (int32_t v = 0; v < h->n; ++v) {
+        const int64_t M = (int64_t)h->pre[v].len * (int64_t)h->suc[v].len;
+        uint8_t ro = 0;
+        if (M == 0) ro = (uint8_t)((h->pre[v].len == 0 ? 1 : 0) | (h->suc[v].len == 0 ? 2 : 0));
+        else if (M <= r) ro = 3;
+        role[v] = ro;
+        bucket[v] = ro ? leaf_hash(v, h->kp) : -1;
+    }
+    return 0;
+}
 
 /* Leaves: zero in-degree -> role bit 0 (seeds BL_in), zero out-degree -> role
  * bit 1 (seeds BL_out) (Definition 2). */

@@ -254,3 +254,33 @@ def test_large_graph_incremental_equals_rebuild():
     assert bool((a1[1::2] == 1).all()), "a walk descendant was answered unreachable"
     inc.close()
     full.close()
+
+
+def test_large_graph_matches_oracle():
+    """n = 2^24, m = 2^28 (the learned and serving graph), k = k' = 64: every
+    label word after the 1M insertions (batches of 100k, persistent kernels)
+    against the oracle (Algorithm 1 build, then Algorithm 3 and its mirrors
+    edge by edge), and answers and deciding rules of the first 1M of the 10M
+    queries against Algorithm 2 on the oracle."""
+    dbl.build()
+    dbl_inputs.build()
+    oracle.build()
+    w = dbl_inputs.workload("large")
+    E = int(w["ins_src"].shape[0])
+    ix = dbl.DBLIndex(D(w["row_ptr"]), D(w["col"]), 64, 64, edge_capacity=E,
+                      flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC)
+    src, dst = D(w["ins_src"]), D(w["ins_dst"])
+    for a in range(0, E, 100_000):
+        ix.insert_edges(src[a:a + 100_000], dst[a:a + 100_000])
+    S = 1_000_000
+    ans, code = ix.query(D(w["q_u"][:S]), D(w["q_v"][:S]))
+    ix.sync()
+    got = labels_np(ix)
+    ans, code = ans.cpu().numpy(), code.cpu().numpy()
+    ix.close()
+    ref = oracle.OracleIndex(w["row_ptr"], w["col"], 64, 64).build(nthreads=THREADS)
+    ref.insert_edges(w["ins_src"], w["ins_dst"])
+    assert_same_labels(got, ref.labels(), "large graph, batches of 100k, persistent")
+    rans, rcode = ref.query(w["q_u"][:S], w["q_v"][:S], nthreads=THREADS)
+    bad = np.nonzero((ans != rans) | (code != rcode))[0]
+    assert bad.size == 0, f"large graph: {bad.size} of {S} queries differ, first {bad[:5]}"

@@ -241,6 +241,63 @@ def test_degree_landmark_rule():
     assert lm[0] == 1 and (lm[10:] == -1).all() and sorted(lm[:10]) == list(range(10))
 
 
+# Section 6, "Label Node Selection": Table 3's rankings and the M(u) <= r leaf rule,
+# worked by hand on edges 0->1, 0->2, 0->3, 1->2, 2->3, 4->2, 5->4:
+#   vertex (in, out):  0 (0,3)  1 (1,1)  2 (3,1)  3 (2,0)  4 (1,1)  5 (0,1)
+#   M = in*out:        0        1        3        0        1        0
+#   A = max:           3        1        3        2        1        1
+#   B = min:           0        1        1        0        1        0
+#   C = in+out:        3        2        4        2        2        1
+HAND_EDGES = ([0, 0, 0, 1, 2, 4, 5], [1, 2, 3, 2, 3, 2, 4])
+HAND_ORDER = {"M": [2, 1, 4, 0, 3, 5], "A": [0, 2, 3, 1, 4, 5], "B": [1, 2, 4, 0, 3, 5],
+              "C": [2, 0, 1, 3, 4, 5]}
+# roles: 1 = seeds BL_in (no in-edges), 2 = seeds BL_out (no out-edges), 3 = both (0 < M <= r)
+HAND_ROLES = {0: [1, 0, 0, 2, 0, 1], 1: [1, 3, 0, 2, 3, 1], 2: [1, 3, 0, 2, 3, 1], 3: [1, 3, 3, 2, 3, 1]}
+
+
+@pytest.mark.parametrize("rule", ["M", "A", "B", "C"])
+def test_table3_rankings_hand_example(rule):
+    o = OracleIndex(*H.csr_from_edges(6, *HAND_EDGES), 64, 64)
+    lm = o.rank_landmarks(rule)
+    assert lm[:6].tolist() == HAND_ORDER[rule] and (lm[6:] == -1).all()
+    if rule == "M":
+        assert np.array_equal(lm, o.degree_landmarks())
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_threshold_leaves_hand_example(r):
+    o = OracleIndex(*H.csr_from_edges(6, *HAND_EDGES), 64, 64)
+    bucket, role = o.threshold_leaves(r)
+    assert role.tolist() == HAND_ROLES[r]
+    assert ((bucket >= 0) == (role > 0)).all()
+    for v in np.nonzero(role)[0]:
+        assert bucket[v] == oracle.leaf_hash(int(v), 64)
+    if r == 0:
+        zb, zr = o.zero_degree_leaves()
+        assert np.array_equal(zb, bucket) and np.array_equal(zr, role)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[s[0] for s in SHAPES])
+@pytest.mark.parametrize("rule,r", [("A", 1), ("B", 4), ("C", 1000)])
+def test_selection_rules_match_closure(shape, rule, r):
+    """Labels and answers with Table 3 landmarks and M(u) <= r leaves equal the
+    closure-derived definitions (Lemma 1, Lemma 2 hold for any fixed sets)."""
+    name, n, s, d = shape
+    rp, col = H.csr_from_edges(n, s, d)
+    o = OracleIndex(rp, col, 64, 64)
+    lm = o.rank_landmarks(rule)
+    bucket, role = o.threshold_leaves(r)
+    o.build(lm, bucket, role)
+    R = H.closure(n, s, d)
+    exp = H.expected_labels(R, lm, bucket, role, 64, 64)
+    for e, g, nm in zip(exp, o.labels(), ["dl_in", "dl_out", "bl_in", "bl_out"]):
+        assert np.array_equal(e, g), nm
+    uu, vv = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ans, code = o.query(uu.ravel(), vv.ravel(), nthreads=4)
+    assert np.array_equal(ans.astype(bool), R.ravel())
+    _check_codes(R, exp, uu.ravel(), vv.ravel(), code)
+
+
 @pytest.mark.parametrize("kprime", [1, 2, 64, 128, 256, 100])
 def test_leaf_hash_fibonacci(kprime):
     phi = 0x9E3779B97F4A7C15
