@@ -723,6 +723,66 @@ def bench_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_sweep(args):
+    """Label widths, leaf threshold and landmark ranking (Section 6, Table 5,
+    Table 3 and "Label Node Selection"): the batched step (persistent kernels)
+    at k, k' in {64, 128, 256} with M-ranked landmarks and zero-degree leaves;
+    at k = k' = 64 with leaves M(u) <= r for r in {2, 16}, and with Table 3's
+    rankings A, B, C.  One JSON line with a row per
+    configuration: step time, throughput, per-kernel times (CUDA events), the
+    label test's achieved HBM fraction and which rule decided each query."""
+    import torch
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    dbl.build()
+    dbl_inputs.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = dbl_inputs.workload(args.workload)
+    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
+    I = Inputs(w, dev)
+    batches = step_batches(E, args.batch)
+    peaks, src = measured_peaks()
+    configs = ([(k, kp, 0, "M") for k in (64, 128, 256) for kp in (64, 128, 256)] +
+               [(64, 64, 2, "M"), (64, 64, 16, "M"), (64, 64, 0, "A"), (64, 64, 0, "B"), (64, 64, 0, "C")])
+    rows = []
+    for k, kp, r, rule in configs:
+        ix = dbl.DBLIndex(I.rp, I.col, k, kp, leaf_r=r, landmark_rule=rule, edge_capacity=max(E, 1 << 20),
+                          flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING)
+        ix.sync()
+        ix.snapshot(0)
+        step = make_step(ix, I, batches)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ix.timings()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        t = ix.timings()
+        rec = ix.info()["record_bytes"]
+        code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
+        lab_ms = t["query_label"][0] / max(1, t["query_label"][1])
+        leaves = int((ix.selection()[2] > 0).sum().item())
+        rows.append({"k": k, "kprime": kp, "leaf_r": r, "landmark_rule": rule, "record_bytes": rec, "leaves": leaves, "ms_per_step": ms,
+                     "ops_per_s": (E + Q) / (ms * 1e-3),
+                     "insert_ms_per_batch": t["propagate"][0] / max(1, t["propagate"][1]),
+                     "label_test_ms": lab_ms,
+                     "label_test_frac_of_hbm": Q * (8 + 2 * rec + 2) / (lab_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "search_ms": t["search_expand"][0] / max(1, t["search_expand"][1]),
+                     "decided_by": {n: int(code[i]) for i, n in enumerate(
+                         ["undecided", "self", "dl", "bl", "thm1", "thm2", "bfs_pos", "bfs_neg"])}})
+        ix.close()
+    print(json.dumps({"metric": "label width / leaf threshold sweep (batched step)", "unit": UNIT,
+                      "workload": args.workload, "steps": args.steps, "warmup": args.warmup,
+                      "peak_source": f"hbm_gbs of {src}", "sweep": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -746,12 +806,15 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
     ap.add_argument("--serve-workload", default="large", choices=["large", "social", "tiny"])
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.warmup < 3:
         args.warmup = 3
     if args.serve:
         bench_serve(args)
+    elif args.sweep:
+        bench_sweep(args)
     elif args.impl == "reference":
         bench_reference(args)
     else:

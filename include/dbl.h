@@ -122,7 +122,16 @@ typedef struct {
                               the first 2^x slots of its table (clamped to the
                               table); a lone 64-query group that overflows them
                               is rerun over the whole table; 0: 22 */
-    int32_t reserved[5];
+    int32_t landmark_rule; /* ranking of the landmarks chosen when dbl_build gets
+                              none (Section 6, Table 3): 0 = |Pre(u)| * |Suc(u)|
+                              (Section 4.1), 1 = max(|Pre|, |Suc|) (A),
+                              2 = min (B), 3 = |Pre| + |Suc| (C); ties by id */
+    int64_t leaf_r;        /* leaves chosen when dbl_build gets none: every u
+                              with M(u) = |Pre(u)| * |Suc(u)| <= leaf_r
+                              (Section 6); with M(u) = 0 the roles of
+                              Definition 2, otherwise both BL_in and BL_out;
+                              0: the zero-degree leaves of Definition 2 */
+    int32_t reserved[2];
 } dbl_options;
 
 /* Fill *opt with the defaults above. */
@@ -132,11 +141,14 @@ void dbl_default_options(dbl_options *opt);
  * Build the index for G (Algorithm 1 and the BL construction of Section 4.1).
  *   landmarks[k]   landmark of slot i, or -1 for an empty slot; NULL: the
  *                  top-k vertices by M(u) = |Pre(u)| * |Suc(u)| (Section 4.1,
- *                  landmark heuristic), ties by smaller id.
+ *                  landmark heuristic), or by the ranking landmark_rule of the
+ *                  options picks, ties by smaller id.
  *   k              multiple of 64, 64..256.
  *   leaf_buckets[n] bucket in [0, kprime) of a leaf, -1 for a non-leaf;
  *                  NULL: zero in-degree vertices seed BL_in and zero
- *                  out-degree vertices seed BL_out (Definition 2), bucket
+ *                  out-degree vertices seed BL_out (Definition 2; with
+ *                  options leaf_r > 0 also every u with 0 < M(u) <= leaf_r,
+ *                  seeding both), bucket
  *                  h(v) = floor(frac(v * 0x9E3779B97F4A7C15 / 2^64) * kprime)
  *                  (Fibonacci hashing; the paper leaves h open).
  *   leaf_roles[n]  bit0: seeds BL_in, bit1: seeds BL_out; required when

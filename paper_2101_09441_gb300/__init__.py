@@ -23,6 +23,10 @@ DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAP
 STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned"]
 CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
 FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2 = 1, 2, 4, 8
+# landmark rankings of dbl_options.landmark_rule: M = |Pre|*|Suc| (Section 4.1), and Table 3's
+# A = max, B = min, C = sum of the two degrees
+LANDMARK_RULES = {"M": 0, "A": 1, "B": 2, "C": 3}
+
 KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "insert_append", "insert_seed",
                 "build_prep", "other"]
 
@@ -56,7 +60,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p),
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
                 ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Graph(ctypes.Structure):
@@ -164,7 +168,8 @@ class DBLIndex:
 
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
-                 torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0):
+                 torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0,
+                 landmark_rule: str = "M", leaf_r: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -183,6 +188,8 @@ class DBLIndex:
         opt.team = int(team)
         opt.query_unroll = int(query_unroll)
         opt.search_first_log2 = int(search_first_log2)
+        opt.landmark_rule = LANDMARK_RULES[landmark_rule]
+        opt.leaf_r = int(leaf_r)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
 

@@ -314,6 +314,8 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         return fail(nullptr, DBL_ERR_INVALID, "options: alloc and free must be set together");
     if (opt && opt->team && opt->team != 1 && opt->team != 4 && opt->team != 8 && opt->team != 16 && opt->team != 32)
         return fail(nullptr, DBL_ERR_INVALID, "options: team must be 1, 4, 8, 16 or 32");
+    if (opt && (opt->landmark_rule < 0 || opt->landmark_rule > 3 || opt->leaf_r < 0))
+        return fail(nullptr, DBL_ERR_INVALID, "options: landmark_rule must be 0..3 and leaf_r >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     dbl_index *ix = new (std::nothrow) dbl_index();
     if (!ix) return fail(nullptr, DBL_ERR_OOM, "host allocation");

@@ -220,9 +220,12 @@ dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s)
 // The ranking key of a vertex: M(u) = |Suc(u)| * |Pre(u)| from the two CSRs,
 // or an explicit 64-bit key array (e.g. learned scores); larger ranks first,
 // ties by smaller id.
+// rule (without explicit keys): 0 = |Suc| * |Pre| (Section 4.1), and Table
+// 3's 1 = max, 2 = min, 3 = sum of the two degrees.
 struct KeySrc {
     const int32_t *op, *ip;
     const unsigned long long *keys;
+    int rule;
 };
 
 __device__ __forceinline__ unsigned long long key_of(const KeySrc &ks, int32_t v)
@@ -230,7 +233,12 @@ __device__ __forceinline__ unsigned long long key_of(const KeySrc &ks, int32_t v
     if (ks.keys) return ks.keys[v];
     unsigned long long o = (unsigned long long)(ks.op[v + 1] - ks.op[v]);
     unsigned long long i = (unsigned long long)(ks.ip[v + 1] - ks.ip[v]);
-    return o * i;
+    switch (ks.rule) {
+    case 1: return o > i ? o : i;
+    case 2: return o < i ? o : i;
+    case 3: return o + i;
+    default: return o * i;
+    }
 }
 
 struct SelState {
@@ -340,7 +348,7 @@ dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s)
 dbl_status select_top(dbl_index *ix, const int32_t *op, const int32_t *ip, const unsigned long long *keys, int32_t n,
                       int32_t k, int32_t *out, cudaStream_t s)
 {
-    const KeySrc ks{op, ip, keys};
+    const KeySrc ks{op, ip, keys, ix->opt.landmark_rule};
     cudaMemsetAsync(out, 0xff, sizeof(int32_t) * (size_t)k, s);  // -1
     const int64_t take = k < n ? k : n;
     if (take == 0) return DBL_OK;
@@ -391,13 +399,18 @@ __device__ __forceinline__ int32_t fib_bucket(int32_t v, int32_t kp)
     return (int32_t)__umul64hi(x, (unsigned long long)kp);
 }
 
-__global__ void k_leaves_degree(const int32_t *op, const int32_t *ip, int32_t n, int32_t kp, int32_t *bucket,
-                                uint8_t *role)
+// Leaves from the degrees: zero in-degree seeds BL_in, zero out-degree seeds
+// BL_out (Definition 2); with r > 0 also every v with 0 < M(v) <= r, seeding
+// both (Section 6, "Label Node Selection").
+__global__ void k_leaves_degree(const int32_t *op, const int32_t *ip, int32_t n, int32_t kp, long long r,
+                                int32_t *bucket, uint8_t *role)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        uint8_t r = (uint8_t)((ip[v + 1] == ip[v] ? 1 : 0) | (op[v + 1] == op[v] ? 2 : 0));
-        role[v] = r;
-        bucket[v] = r ? fib_bucket((int32_t)v, kp) : -1;
+        const long long din = ip[v + 1] - ip[v], dout = op[v + 1] - op[v];
+        uint8_t ro = (uint8_t)((din == 0 ? 1 : 0) | (dout == 0 ? 2 : 0));
+        if (!ro && din * dout <= r) ro = 3;
+        role[v] = ro;
+        bucket[v] = ro ? fib_bucket((int32_t)v, kp) : -1;
     }
 }
 
@@ -417,8 +430,8 @@ dbl_status select_leaves(dbl_index *ix, const int32_t *bucket, const uint8_t *ro
 {
     const unsigned grid = grid_for(ix->n);
     if (!bucket) {
-        k_leaves_degree<<<grid, kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, ix->n, ix->kp, ix->leaf_bucket,
-                                                ix->leaf_role);
+        k_leaves_degree<<<grid, kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, ix->n, ix->kp, (long long)ix->opt.leaf_r,
+                                                ix->leaf_bucket, ix->leaf_role);
         ++ix->launches;
         cudaError_t e = cudaGetLastError();
         return e ? cuda_fail(ix, e, "select_leaves") : DBL_OK;

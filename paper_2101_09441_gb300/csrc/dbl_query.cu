@@ -30,14 +30,22 @@ namespace dbl {
 __host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
 
 // ------------------------------------------------------------ label test
-// Each thread takes QPT queries (default 2) and issues all
-// of their record loads before using any, so that many DRAM sectors are in
-// flight per warp; answers and codes are written coalesced, the deciding
-// rules are counted per thread.  An undecided pair gets the answer byte
-// kAnsUndecided; the search compacts those from the answer array itself
-// (compact_undecided), so the label test writes nothing else (appending to an
-// undecided list here, one atomic per warp, took a third of the kernel's time;
-// one per block through a shared-memory stage still took a tenth).
+// A pair is handled by LPP = HS / 2 adjacent lanes: lane `sub` of the group
+// owns words 2*sub and 2*sub + 1 of each of the four half-records (DL_in |
+// BL_in and DL_out | BL_out of u and of v) and loads them with one 16-byte
+// load per half; the group's lanes together read each half as one contiguous
+// request, and every lane holds the same registers whatever the label width
+// (at 32-byte records the group is one lane).  Each lane evaluates Algorithm
+// 2's label tests on its words, the partial verdicts are OR-ed across the
+// group by shuffles, and lane 0 of the group writes the answer.  Each group
+// takes QPT pairs (default 2) and issues all of their record loads before
+// using any, so many DRAM sectors are in flight per warp; answers and codes
+// are written coalesced, the deciding rules are counted per thread.  An
+// undecided pair gets the answer byte kAnsUndecided; the search compacts those
+// from the answer array itself (compact_undecided), so the label test writes
+// nothing else (appending to an undecided list here, one atomic per warp,
+// took a third of the kernel's time; one per block through a shared-memory
+// stage still took a tenth).
 constexpr uint8_t kAnsUndecided = 2;
 
 template <int WD, int WB, int QPT>
@@ -47,70 +55,80 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
+    constexpr int LPP = HS / 2;
     const int lane = threadIdx.x & 31;
-    unsigned int counts[6] = {0, 0, 0, 0, 0, 0};  // per thread, by deciding rule (constant indices only)
-    const int64_t tile = (int64_t)blockDim.x * QPT;
+    const int sub = lane % LPP;
+    const int w0 = 2 * sub;  // first word of this lane in every half
+    unsigned int counts[6] = {0, 0, 0, 0, 0, 0};  // per group leader, by deciding rule (constant indices only)
+    const int64_t groups = blockDim.x / LPP;      // pair slots per block and j
+    const int64_t tile = groups * QPT;
     const int64_t stride = (int64_t)gridDim.x * tile;
-    for (int64_t base = (int64_t)blockIdx.x * tile; base < q; base += stride) {
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < q; base += stride) {  // block-uniform
         int32_t u[QPT], v[QPT];
         bool live[QPT];
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
-            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            const int64_t i = base + (int64_t)j * groups + threadIdx.x / LPP;
             live[j] = i < q;
             u[j] = live[j] ? __ldcs(qu + i) : 0;
             v[j] = live[j] ? __ldcs(qv + i) : 0;
         }
-        bool ok[QPT];
-        uint64_t fu[QPT][HS], bu[QPT][HS], fv[QPT][HS], bv[QPT][HS];
+        ulonglong2 fu[QPT], bu[QPT], fv[QPT], bv[QPT];
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
-            ok[j] = live[j] && (uint32_t)u[j] < (uint32_t)n && (uint32_t)v[j] < (uint32_t)n && u[j] != v[j];
-            const int32_t uu = ok[j] ? u[j] : 0, vv = ok[j] ? v[j] : 0;
-            load_half<HS>(rec + (size_t)uu * RW, fu[j]);
-            load_half<HS>(rec + (size_t)uu * RW + HS, bu[j]);
-            load_half<HS>(rec + (size_t)vv * RW, fv[j]);
-            load_half<HS>(rec + (size_t)vv * RW + HS, bv[j]);
+            const bool ok = live[j] && (uint32_t)u[j] < (uint32_t)n && (uint32_t)v[j] < (uint32_t)n && u[j] != v[j];
+            const int32_t uu = ok ? u[j] : 0, vv = ok ? v[j] : 0;
+            fu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + w0));
+            bu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + HS + w0));
+            fv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + w0));
+            bv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + HS + w0));
         }
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
-            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            // this lane's words: DL words are [0, WD), BL words [WD, WD + WB), the rest padding
+            uint64_t uv = 0, vu = 0, su = 0, sv = 0, blf = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int w = w0 + h;
+                const uint64_t a = h ? fu[j].y : fu[j].x, b = h ? bu[j].y : bu[j].x;
+                const uint64_t c = h ? fv[j].y : fv[j].x, d = h ? bv[j].y : bv[j].x;
+                if (w < WD) {
+                    uv |= b & c;  // DL_out(u) & DL_in(v)
+                    vu |= d & a;  // DL_out(v) & DL_in(u)
+                    su |= b & a;
+                    sv |= d & c;
+                } else if (w < WD + WB) {
+                    blf |= (a & ~c) | (d & ~b);  // BL_in(u) not in BL_in(v), BL_out(v) not in BL_out(u)
+                }
+            }
+            uint32_t fl = (uv ? 1u : 0u) | (blf ? 2u : 0u) | (vu ? 4u : 0u) | ((su | sv) ? 8u : 0u);
+#pragma unroll
+            for (int o = 1; o < LPP; o <<= 1) fl |= __shfl_xor_sync(kFull, fl, o);
+            const int64_t i = base + (int64_t)j * groups + threadIdx.x / LPP;
             uint8_t a = 0, c = DBL_CODE_UNDECIDED;
-            if (live[j]) {
+            if (live[j] && sub == 0) {
                 if ((uint32_t)u[j] >= (uint32_t)n || (uint32_t)v[j] >= (uint32_t)n) {
                     set_status(status, DBL_ERR_INVALID);
                 } else if (u[j] == v[j]) {
                     a = 1;
                     c = DBL_CODE_SELF;
+                } else if (fl & 1u) {
+                    a = 1;
+                    c = DBL_CODE_DL;
+                } else if (fl & 2u) {
+                    c = DBL_CODE_BL;
+                } else if (fl & 4u) {
+                    c = DBL_CODE_THM1;
+                } else if (fl & 8u) {
+                    c = DBL_CODE_THM2;
                 } else {
-                    uint64_t uv = 0, vu = 0, su = 0, sv = 0, blf = 0;
-#pragma unroll
-                    for (int w = 0; w < WD; ++w) {
-                        uv |= bu[j][w] & fv[j][w];
-                        vu |= bv[j][w] & fu[j][w];
-                        su |= bu[j][w] & fu[j][w];
-                        sv |= bv[j][w] & fv[j][w];
-                    }
-#pragma unroll
-                    for (int w = WD; w < WD + WB; ++w) blf |= (fu[j][w] & ~fv[j][w]) | (bv[j][w] & ~bu[j][w]);
-                    if (uv) {
-                        a = 1;
-                        c = DBL_CODE_DL;
-                    } else if (blf) {
-                        c = DBL_CODE_BL;
-                    } else if (vu) {
-                        c = DBL_CODE_THM1;
-                    } else if (su | sv) {
-                        c = DBL_CODE_THM2;
-                    } else {
-                        a = kAnsUndecided;
-                    }
+                    a = kAnsUndecided;
                 }
                 __stcs(ans + i, a);
                 if (code) __stcs(code + i, c);
             }
 #pragma unroll
-            for (int r = 1; r < 6; ++r) counts[r] += (live[j] && c == r) ? 1u : 0u;
+            for (int r = 1; r < 6; ++r) counts[r] += (live[j] && sub == 0 && c == r) ? 1u : 0u;
         }
     }
 #pragma unroll
@@ -900,11 +918,13 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     if (st) return st;
     uint32_t *cnt = c->d_counts;
     cudaMemsetAsync(cnt + kCntUnd, 0, sizeof(uint32_t), s);
-    // pairs per thread: option, else 2 (1 for 128-byte records); measured on
-    // 32-byte records, 2 beats 4 (more resident warps) and 1 (fewer loads in flight)
+    // pairs per lane group: option, else 2; measured on 32-byte records, 2
+    // beats 4 (more resident warps) and 1 (fewer loads in flight); a group of
+    // HS / 2 lanes keeps the same registers at every record width
     constexpr int HS = hs_of(WD + WB);
-    int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 8 ? 1 : 2);
-    int64_t blocks = (q + (int64_t)kBlock * qpt - 1) / ((int64_t)kBlock * qpt);
+    const int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : 2;
+    const int64_t pairs_per_block = (int64_t)(kBlock / (HS / 2)) * qpt;
+    int64_t blocks = (q + pairs_per_block - 1) / pairs_per_block;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
     qt_begin(ix, c, DBL_KERNEL_QUERY_LABEL, s);

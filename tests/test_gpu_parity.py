@@ -91,6 +91,31 @@ def test_tiny_selection_matches_oracle(tiny):
     assert np.array_equal(lb, rb) and np.array_equal(lr, rr)
 
 
+@pytest.mark.parametrize("rule,r", [("M", 2), ("A", 0), ("B", 8), ("C", 1000)])
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT])
+def test_selection_rules_match_oracle(tiny, rule, r, flags):
+    """Section 6 (Label Node Selection): Table 3's landmark rankings and the
+    M(u) <= r leaf rule chosen on the GPU equal the oracle's choice; labels
+    after the 10k insertions and every answer follow the oracle with them."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, landmark_rule=rule, leaf_r=r, flags=flags)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64)
+    lm, lb, lr = [t.cpu().numpy() for t in ix.selection()]
+    assert np.array_equal(lm, ref.rank_landmarks(rule))
+    rb, rr = ref.threshold_leaves(r)
+    assert np.array_equal(lb, rb) and np.array_equal(lr, rr)
+    if r > 0:
+        assert (rr == 3).any()                            # the threshold adds two-sided leaves
+    ref.build(lm, lb, lr)
+    assert_labels(ix, ref, f"build, rule {rule}, r {r}")
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    for b in range(0, s.shape[0], 2500):
+        ix.insert_edges(D(s[b:b + 2500]), D(d[b:b + 2500]))
+    ref.insert_edges(s, d)
+    ix.sync()
+    assert_labels(ix, ref, f"insertions, rule {rule}, r {r}")
+    assert_queries(ix, ref, tiny["q_u"], tiny["q_v"], f"queries, rule {rule}, r {r}")
+
+
 def test_tiny_full_pipeline(tiny):
     """Plain DBL, tiny: build, 10k insertions in batches of 1k (labels after
     every batch), then 100k mixed queries (answers and deciding rules)."""
