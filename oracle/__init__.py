@@ -68,6 +68,7 @@ def _load():
             lib.orc_degree_landmarks.argtypes = [P, P]
             lib.orc_zero_degree_leaves.argtypes = [P, P, P]
             lib.orc_rank_landmarks.argtypes = [P, ctypes.c_int, P]
+            lib.orc_add_vertices.argtypes = [P, i32]
             lib.orc_threshold_leaves.argtypes = [P, i64, P, P]
             lib.orc_leaf_hash.argtypes = [i32, i32]
             lib.orc_leaf_hash.restype = i32
@@ -173,6 +174,18 @@ class OracleIndex:
         if rc:
             raise ValueError(f"orc_build failed ({rc})")
         return self
+
+    # vertex insertion (Section 1): isolated vertices with empty labels
+    def add_vertices(self, count: int) -> int:
+        first = self.n
+        rc = _load().orc_add_vertices(self._h, int(count))
+        if rc:
+            raise ValueError(f"orc_add_vertices failed ({rc})")
+        self.n += int(count)
+        if getattr(self, "leaf_bucket", None) is not None:
+            self.leaf_bucket = np.concatenate([self.leaf_bucket, np.full(count, -1, np.int32)])
+            self.leaf_role = np.concatenate([self.leaf_role, np.zeros(count, np.uint8)])
+        return first
 
     # Algorithm 3 (+ mirrors), one edge at a time
     def insert_edges(self, src, dst):

@@ -28,6 +28,9 @@
  *     itself tested first (as the text and Figure 2 do); the DL_out mirror
  *     runs from u over Pre with DL_out(v) (Section 5); BL_in / BL_out the same
  *     way on their own words.
+ *   - Vertex insertion (Section 1: insert-only graphs gain edges and
+ *     vertices): new vertices are isolated, so their labels are empty; they
+ *     join neither the landmarks nor the leaves (both sets are fixed at build).
  *   - Query (Algorithm 2): u == v answers true (Des/Anc include the vertex,
  *     Table 1); then DL intersection -> true; BL containment fails -> false;
  *     Theorem 1 -> false; Theorem 2 -> false; else a BFS from u with a visited
@@ -562,11 +565,55 @@ void orc_csr(const orc_index *h, int64_t *row_ptr, int32_t *col)
     }
 }
 
+/* Vertex insertion: count isolated vertices n .. n + count - 1, with empty
+ * labels and no edges, not landmarks and not leaves.  Returns 0, 1 (count
+ * negative or the ids would not fit in int32) or 2 (out of memory; the index
+ * is then unusable). */
+int orc_add_vertices(orc_index *h, int32_t count)
+{
+    if (count < 0 || (int64_t)h->n + count >= ((int64_t)1 << 31)) return 1;
+    if (count == 0) return 0;
+    const size_t n0 = (size_t)h->n, n1 = n0 + (size_t)count;
+    adjlist *su = (adjlist *)realloc(h->suc, sizeof(adjlist) * n1);
+    if (!su) return 2;
+    h->suc = su;
+    adjlist *pr = (adjlist *)realloc(h->pre, sizeof(adjlist) * n1);
+    if (!pr) return 2;
+    h->pre = pr;
+    memset(h->suc + n0, 0, sizeof(adjlist) * (size_t)count);
+    memset(h->pre + n0, 0, sizeof(adjlist) * (size_t)count);
+    uint64_t **lab[4] = {&h->dl_in, &h->dl_out, &h->bl_in, &h->bl_out};
+    const int32_t words[4] = {h->wd, h->wd, h->wb, h->wb};
+    for (int i = 0; i < 4; ++i) {
+        uint64_t *t = (uint64_t *)realloc(*lab[i], 8 * n1 * (size_t)words[i]);
+        if (!t) return 2;
+        memset(t + n0 * (size_t)words[i], 0, 8 * (size_t)count * (size_t)words[i]);
+        *lab[i] = t;
+    }
+    int32_t *lb = (int32_t *)realloc(h->leaf_bucket, sizeof(int32_t) * n1);
+    if (!lb) return 2;
+    h->leaf_bucket = lb;
+    uint8_t *lr = (uint8_t *)realloc(h->leaf_role, n1);
+    if (!lr) return 2;
+    h->leaf_role = lr;
+    int32_t *q = (int32_t *)realloc(h->queue, sizeof(int32_t) * n1);
+    if (!q) return 2;
+    h->queue = q;
+    for (size_t v = n0; v < n1; ++v) {
+        h->leaf_bucket[v] = -1;
+        h->leaf_role[v] = 0;
+    }
+    h->n = (int32_t)n1;
+    return 0;
+}
+
 /* Save the labels and adjacency lengths; orc_rewind returns to them (so a
- * timed step can be repeated from the same state).  Returns 0 or 2. */
+ * timed step can be repeated from the same state); not across a vertex
+ * insertion.  Returns 0 or 2. */
 static uint64_t *g_mark_lab[4];
 static int32_t *g_mark_len[2];
 static const orc_index *g_mark_owner;
+static int32_t g_mark_n;
 
 int orc_mark(orc_index *h)
 {
@@ -586,12 +633,13 @@ int orc_mark(orc_index *h)
         for (int32_t v = 0; v < h->n; ++v) g_mark_len[d][v] = d ? h->pre[v].len : h->suc[v].len;
     }
     g_mark_owner = h;
+    g_mark_n = h->n;
     return 0;
 }
 
 int orc_rewind(orc_index *h)
 {
-    if (g_mark_owner != h) return 1;
+    if (g_mark_owner != h || g_mark_n != h->n) return 1;
     size_t nn = h->n > 0 ? (size_t)h->n : 1;
     size_t sz[4] = {nn * h->wd, nn * h->wd, nn * h->wb, nn * h->wb};
     uint64_t *dst[4] = {h->dl_in, h->dl_out, h->bl_in, h->bl_out};

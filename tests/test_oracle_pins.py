@@ -298,6 +298,56 @@ def test_selection_rules_match_closure(shape, rule, r):
     _check_codes(R, exp, uu.ravel(), vv.ravel(), code)
 
 
+# ------------------------------------------------------------ vertex insertion (Section 1)
+@pytest.mark.parametrize("seed", range(3))
+def test_vertex_insertion_matches_closure(seed):
+    """New vertices start isolated (empty labels, not landmarks, not leaves);
+    after edges touching them are inserted, every label and answer equals the
+    closure-derived definition on the final graph with the build's landmark
+    and leaf sets extended by non-leaves."""
+    rng = np.random.default_rng(40 + seed)
+    n0, add = 90, 30
+    s, d = H.random_graph(n0, 260, seed)
+    o = OracleIndex(*H.csr_from_edges(n0, s, d), 64, 64).build()
+    lm = o.landmarks.copy()
+    first = o.add_vertices(add)
+    assert first == n0 and o.n == n0 + add
+    lab = o.labels()
+    assert all((x[n0:] == 0).all() for x in lab)                # isolated: empty labels
+    ans, code = o.query(np.arange(n0, n0 + add), np.arange(n0, n0 + add))
+    assert ans.all() and (code == oracle.SELF).all()
+    ans, _ = o.query(np.full(n0, n0, np.int32), np.arange(n0))   # a new vertex reaches nothing else
+    assert not ans.any()
+    n = n0 + add
+    es = rng.integers(0, n, 400).astype(np.int32)
+    ed = rng.integers(0, n, 400).astype(np.int32)
+    o.insert_edges(es, ed)
+    fs, fd = np.concatenate([s, es]), np.concatenate([d, ed])
+    R = H.closure(n, fs, fd)
+    exp = H.expected_labels(R, lm, o.leaf_bucket, o.leaf_role, 64, 64)
+    for e, g, nm in zip(exp, o.labels(), ["dl_in", "dl_out", "bl_in", "bl_out"]):
+        assert np.array_equal(e, g), nm
+    assert (o.leaf_bucket[n0:] == -1).all() and (o.leaf_role[n0:] == 0).all()
+    uu, vv = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ans, code = o.query(uu.ravel(), vv.ravel(), nthreads=4)
+    assert np.array_equal(ans.astype(bool), R.ravel())
+    _check_codes(R, exp, uu.ravel(), vv.ravel(), code)
+
+
+def test_vertex_insertion_rejects_bad_counts_and_ids():
+    o = OracleIndex(*H.csr_from_edges(5, [0, 1], [1, 2]), 64, 64).build()
+    with pytest.raises(ValueError):
+        o.add_vertices(-1)
+    with pytest.raises(Exception):
+        o.insert_edges([0], [5])                                 # id 5 does not exist yet
+    o.add_vertices(1)
+    o.insert_edges([0], [5])
+    ans, code = o.query([1], [5])
+    assert not ans[0]
+    ans, code = o.query([0], [5])
+    assert ans[0]
+
+
 @pytest.mark.parametrize("kprime", [1, 2, 64, 128, 256, 100])
 def test_leaf_hash_fibonacci(kprime):
     phi = 0x9E3779B97F4A7C15
