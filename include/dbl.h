@@ -131,7 +131,10 @@ typedef struct {
                               (Section 6); with M(u) = 0 the roles of
                               Definition 2, otherwise both BL_in and BL_out;
                               0: the zero-degree leaves of Definition 2 */
-    int32_t reserved[2];
+    int64_t vertex_capacity; /* vertices the index can hold over its life
+                              (dbl_add_vertices); 0 or less than n: n; must
+                              be below 2^31 */
+    int32_t reserved[4];
 } dbl_options;
 
 /* Fill *opt with the defaults above. */
@@ -226,8 +229,23 @@ dbl_status dbl_labels(dbl_index *ix, uint64_t *dl_in, uint64_t *dl_out, uint64_t
 dbl_status dbl_selection(dbl_index *ix, int32_t *landmarks, int32_t *leaf_buckets,
                          uint8_t *leaf_roles, void *stream);
 
+/*
+ * Vertex insertion (Section 1: the graph grows by new edges and new
+ * vertices).  Appends `count` isolated vertices with ids n .. n + count - 1
+ * (*first, may be NULL, receives n): empty labels (they reach and are reached
+ * by nothing; they are neither landmarks nor leaves, since both sets are
+ * frozen at build) and no edges.  Later insertions and queries may name them.
+ * DBL_ERR_CAPACITY if n + count exceeds the vertex capacity, with the index
+ * unchanged.  The new rows are cleared on `stream`; the vertex count is host
+ * state, so a CUDA graph captured earlier keeps validating ids against the
+ * count it was captured with.  A restore returns to the snapshot's vertex
+ * count.
+ */
+dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *stream);
+
 /* Save / restore labels and inserted adjacency in snapshot slot 0..3
- * (device-to-device copies on `stream`).  dbl_restore clears a poisoned index. */
+ * (device-to-device copies on `stream`).  dbl_restore clears a poisoned index and
+ * returns to the snapshot's vertex count. */
 dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream);
 dbl_status dbl_restore(dbl_index *ix, int slot, void *stream);
 
@@ -263,8 +281,8 @@ dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *
 
 /* Facts about the index: [0] n, [1] k, [2] kprime, [3] inserted edges stored,
  * [4] edge capacity, [5] base edges m, [6] label record bytes per vertex,
- * [7] option flags, [8] kernels launched so far, [9] words per record half;
- * [10..15] zero. */
+ * [7] option flags, [8] kernels launched so far, [9] words per record half,
+ * [10] vertex capacity; [11..15] zero. */
 dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
 
 /*

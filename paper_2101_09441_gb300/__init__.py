@@ -31,7 +31,7 @@ KERNEL_NAMES = ["propagate", "query_label", "search_expand", "search_other", "in
                 "build_prep", "other"]
 
 EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", "dbl_query_host",
-           "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_snapshot", "dbl_restore", "dbl_sync",
+           "dbl_insert_edges_host", "dbl_labels", "dbl_selection", "dbl_add_vertices", "dbl_snapshot", "dbl_restore", "dbl_sync",
            "dbl_stats", "dbl_phase_trace", "dbl_timings", "dbl_info", "dbl_last_error", "dbl_destroy", "dbl_insert_edges_noalloc",
            "dbl_features", "dbl_coverage", "dbl_select_by_score", "dbl_mlp_create", "dbl_mlp_destroy",
            "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_sync", "dbl_mlp_last_error",
@@ -60,7 +60,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p),
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
                 ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
-                ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("reserved", ctypes.c_int32 * 2)]
+                ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("vertex_capacity", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Graph(ctypes.Structure):
@@ -97,6 +98,7 @@ def lib():
             L.dbl_insert_edges_noalloc.argtypes = [P, P, P, i64, P]
             L.dbl_labels.argtypes = [P, P, P, P, P, P]
             L.dbl_selection.argtypes = [P, P, P, P, P]
+            L.dbl_add_vertices.argtypes = [P, i64, P, P]
             L.dbl_snapshot.argtypes = [P, ctypes.c_int, P]
             L.dbl_restore.argtypes = [P, ctypes.c_int, P]
             L.dbl_sync.argtypes = [P, P]
@@ -169,7 +171,7 @@ class DBLIndex:
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
                  torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0,
-                 landmark_rule: str = "M", leaf_r: int = 0):
+                 landmark_rule: str = "M", leaf_r: int = 0, vertex_capacity: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -190,6 +192,7 @@ class DBLIndex:
         opt.search_first_log2 = int(search_first_log2)
         opt.landmark_rule = LANDMARK_RULES[landmark_rule]
         opt.leaf_r = int(leaf_r)
+        opt.vertex_capacity = int(vertex_capacity)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
 
@@ -319,6 +322,14 @@ class DBLIndex:
 
     def restore(self, slot: int = 0, stream=None):
         self._check(lib().dbl_restore(self._h, slot, self._s(stream)))
+        self.n = self.info()["n"]  # the snapshot's vertex count
+
+    def add_vertices(self, count: int, stream=None) -> int:
+        """dbl_add_vertices: `count` isolated vertices with empty labels; returns the first new id."""
+        first = ctypes.c_int32(0)
+        self._check(lib().dbl_add_vertices(self._h, int(count), ctypes.byref(first), self._s(stream)))
+        self.n = self.info()["n"]
+        return int(first.value)
 
     def sync(self, stream=None):
         self._check(lib().dbl_sync(self._h, self._s(stream)))
@@ -347,7 +358,7 @@ class DBLIndex:
         self._check(lib().dbl_info(self._h, out.ctypes.data))
         return dict(n=int(out[0]), k=int(out[1]), kprime=int(out[2]), edges_stored=int(out[3]),
                     edge_capacity=int(out[4]), m=int(out[5]), record_bytes=int(out[6]), flags=int(out[7]),
-                    launches=int(out[8]), half_words=int(out[9]))
+                    launches=int(out[8]), half_words=int(out[9]), vertex_capacity=int(out[10]))
 
     def autotune(self, src, dst, u, v, trials: int = 2, cache: str | None = None, stream=None) -> dict:
         """dbl_autotune on a sample insertion batch and query batch; keeps the

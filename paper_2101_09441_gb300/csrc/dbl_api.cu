@@ -214,7 +214,7 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
         c->und_cap = cap;
     }
     if (!c->table) {
-        int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n));
+        int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n_cap));
         if ((st = ctx_alloc(c, (void **)&c->table, sizeof(SearchSlot) * (size_t)slots, s))) return st;
         if ((st = ctx_alloc(c, (void **)&c->claimed, sizeof(int32_t) * (size_t)slots, s))) return st;
         if ((st = ctx_alloc(c, (void **)&c->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return st;
@@ -223,7 +223,7 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
         // key = empty (all ones) in every slot: set the key words with a strided memset
         cudaMemset2DAsync(c->table, sizeof(SearchSlot), 0xff, sizeof(unsigned long long), (size_t)slots, s);
         c->table_slots = slots;
-        int64_t tcap = (int64_t)ix->n + (ix->m + ix->edge_cap) / kChunk + 4096;
+        int64_t tcap = (int64_t)ix->n_cap + (ix->m + ix->edge_cap) / kChunk + 4096;
         if ((st = ctx_alloc(c, (void **)&c->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
         c->stask_cap = tcap;
         if ((st = ctx_alloc(c, &c->pstate, persist_state_bytes(), s))) return st;
@@ -316,6 +316,8 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         return fail(nullptr, DBL_ERR_INVALID, "options: team must be 1, 4, 8, 16 or 32");
     if (opt && (opt->landmark_rule < 0 || opt->landmark_rule > 3 || opt->leaf_r < 0))
         return fail(nullptr, DBL_ERR_INVALID, "options: landmark_rule must be 0..3 and leaf_r >= 0");
+    if (opt && opt->vertex_capacity >= (1ll << 31))
+        return fail(nullptr, DBL_ERR_INVALID, "options: vertex_capacity must be below 2^31");
     cudaStream_t s = (cudaStream_t)stream;
     dbl_index *ix = new (std::nothrow) dbl_index();
     if (!ix) return fail(nullptr, DBL_ERR_OOM, "host allocation");
@@ -330,6 +332,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32) != cudaSuccess) cudaGetLastError();
     }
     ix->n = g->n;
+    ix->n_cap = (int32_t)std::max<int64_t>(g->n, ix->opt.vertex_capacity);
     ix->m = g->m;
     ix->k = k;
     ix->kp = kprime;
@@ -343,7 +346,8 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     ix->pool_cap = 4 * ix->edge_cap + 64;
     if (ix->pool_cap >= (1ll << 31)) ix->pool_cap = (1ll << 31) - 1;
 
-    const size_t n = (size_t)ix->n, m = (size_t)ix->m;
+    // per-vertex arrays hold n_cap rows (vertex insertion); the base CSR holds the build's n
+    const size_t n = (size_t)ix->n_cap, m = (size_t)ix->m, nb = (size_t)ix->n;
     dbl_status st;
     auto A = [&](void **p, size_t bytes) { return alloc_buf(ix, p, bytes, s); };
     if (cudaMallocHost((void **)&ix->h_pinned, 64 * sizeof(uint32_t))) {
@@ -354,8 +358,8 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     std::memset(ix->h_pinned, 0, 64 * sizeof(uint32_t));
     ix->front_cap = 2 * ((int64_t)n + (int64_t)(m + ix->edge_cap) / kChunk + 64);
     ix->wpd = ((int64_t)n + 31) / 32 + 1;  // + 1: never zero words
-    if ((st = A((void **)&ix->out_ptr, 4 * (n + 1))) || (st = A((void **)&ix->out_col, 4 * m)) ||
-        (st = A((void **)&ix->in_ptr, 4 * (n + 1))) || (st = A((void **)&ix->in_col, 4 * m)) ||
+    if ((st = A((void **)&ix->out_ptr, 4 * (nb + 1))) || (st = A((void **)&ix->out_col, 4 * m)) ||
+        (st = A((void **)&ix->in_ptr, 4 * (nb + 1))) || (st = A((void **)&ix->in_col, 4 * m)) ||
         (st = A((void **)&ix->vm, sizeof(VMeta) * n)) ||
         (st = A((void **)&ix->pool_out, 4 * (size_t)ix->pool_cap)) ||
         (st = A((void **)&ix->pool_in, 4 * (size_t)ix->pool_cap)) || (st = A((void **)&ix->d_pool_top, 16)) ||
@@ -623,6 +627,28 @@ dbl_status dbl_selection(dbl_index *ix, int32_t *landmarks, int32_t *leaf_bucket
     return finish(ix, DBL_OK, s);
 }
 
+dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *stream)
+{
+    if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
+    if (ix->poisoned) return fail(ix, DBL_ERR_POISONED, "index poisoned; dbl_restore first");
+    if (count < 0) return fail(ix, DBL_ERR_INVALID, "add_vertices: negative count");
+    if ((int64_t)ix->n + count > (int64_t)ix->n_cap)
+        return fail(ix, DBL_ERR_CAPACITY, "add_vertices: vertex capacity " + std::to_string(ix->n_cap) + " exceeded");
+    if (first) *first = ix->n;
+    if (count == 0) return DBL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t v0 = (size_t)ix->n, c = (size_t)count;
+    // the rows may hold a vertex that a restore took away: clear them all
+    cudaMemsetAsync(ix->rec + v0 * ix->rw, 0, 8 * c * ix->rw, s);
+    cudaMemsetAsync(ix->vm + v0, 0, sizeof(VMeta) * c, s);
+    cudaMemsetAsync(ix->leaf_bucket + v0, 0xff, 4 * c, s);  // -1: not a leaf
+    cudaMemsetAsync(ix->leaf_role + v0, 0, c, s);
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "add_vertices");
+    ix->n += (int32_t)count;
+    return finish(ix, DBL_OK, s);
+}
+
 dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
 {
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
@@ -632,8 +658,9 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     Snapshot &sn = ix->snaps[slot];
     dbl_status st;
     const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
-    if (!sn.rec.p) {
-        if ((st = alloc_buf(ix, &sn.rec.p, rec_b, s)) || (st = alloc_buf(ix, &sn.vm.p, meta_b, s)) ||
+    if (!sn.rec.p) {  // sized for the vertex capacity: a later snapshot into the slot may hold more vertices
+        if ((st = alloc_buf(ix, &sn.rec.p, 8 * (size_t)ix->n_cap * ix->rw, s)) ||
+            (st = alloc_buf(ix, &sn.vm.p, sizeof(VMeta) * (size_t)ix->n_cap, s)) ||
             (st = alloc_buf(ix, &sn.top.p, 16, s)))
             return st;
     }
@@ -645,6 +672,7 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(ix, e, "snapshot");
     sn.edges_stored = ix->edges_stored;
+    sn.n = ix->n;
     sn.valid = true;
     return DBL_OK;
 }
@@ -655,7 +683,7 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     if (slot < 0 || slot >= 4 || !ix->snaps[slot].valid) return fail(ix, DBL_ERR_INVALID, "no snapshot in that slot");
     cudaStream_t s = (cudaStream_t)stream;
     Snapshot &sn = ix->snaps[slot];
-    const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
+    const size_t rec_b = 8 * (size_t)sn.n * ix->rw, meta_b = sizeof(VMeta) * (size_t)sn.n;
     cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->vm, sn.vm.p, meta_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->d_pool_top, sn.top.p, 16, cudaMemcpyDeviceToDevice, s);
@@ -665,6 +693,7 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     // aborted one (the index was poisoned) may have left bits behind
     cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
     ix->edges_stored = sn.edges_stored;
+    ix->n = sn.n;
     ix->poisoned = false;
     cudaError_t e = cudaGetLastError();
     if (e) return cuda_fail(ix, e, "restore");
@@ -754,6 +783,7 @@ dbl_status dbl_info(const dbl_index *ix, int64_t info[16])
     info[8] = (int64_t)ix->launches;
     info[9] = ix->hs;
     info[0] = ix->n;
+    info[10] = ix->n_cap;
     info[1] = ix->k;
     info[2] = ix->kp;
     info[3] = ix->edges_stored;

@@ -584,7 +584,7 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
         if (st) return fail(ix, st, "insert: vertex id out of range");
     }
     // 2. append
-    int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + n;
+    int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + ix->n_cap;  // [2][n_cap], zero between calls
     tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
     k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status);
     ++ix->launches;

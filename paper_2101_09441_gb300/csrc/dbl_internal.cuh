@@ -208,6 +208,7 @@ struct Buf {
 
 struct Snapshot {
     bool valid = false;
+    int32_t n = 0;      // vertex count at the snapshot (vertices added later go away on restore)
     Buf rec, vm;        // labels; per-vertex adjacency metadata
     Buf top;            // the two pool tops (device)
     int64_t edges_stored = 0;
@@ -217,7 +218,8 @@ struct Snapshot {
 
 struct dbl_index {
     int device = 0;
-    int32_t n = 0;
+    int32_t n = 0;      // vertices now (grows by dbl_add_vertices)
+    int32_t n_cap = 0;  // vertices every per-vertex array is sized for
     int64_t m = 0;
     int32_t k = 0, kp = 0, wd = 0, wb = 0, hs = 0, rw = 0;
     dbl_options opt{};
@@ -246,7 +248,7 @@ struct dbl_index {
     uint32_t *d_counts = nullptr;     // small device counters (see kCnt*)
 
     // insertion scratch
-    int32_t *ins_cnt = nullptr;       // [2][n] per-vertex batch counts
+    int32_t *ins_cnt = nullptr;       // [2][n_cap] per-vertex batch counts (zero between calls)
     int32_t *ins_pos = nullptr;       // [2][bcap] per-edge slot in its vertex batch
     int64_t ins_bcap = 0;
 

@@ -194,8 +194,8 @@ dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_s
     // per 2n vertices, lists, tasks) plus staging for max_batch pairs
     const int64_t W = 1 + ix->wd + 2 * ix->wb;
     int64_t table = 1;
-    while (table < std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n)) table <<= 1;
-    const int64_t per_slot = table * (32 + 12) + ((int64_t)ix->n + (ix->m + ix->edge_cap) / dbl::kChunk) * 24 +
+    while (table < std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n_cap)) table <<= 1;
+    const int64_t per_slot = table * (32 + 12) + ((int64_t)ix->n_cap + (ix->m + ix->edge_cap) / dbl::kChunk) * 24 +
                              o.max_batch * (int64_t)(4 + 8 * W + 9 + 1) + (64 << 20);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return dbl::fail(ix, DBL_ERR_CUDA, "server: cudaMemGetInfo");

@@ -116,6 +116,52 @@ def test_selection_rules_match_oracle(tiny, rule, r, flags):
     assert_queries(ix, ref, tiny["q_u"], tiny["q_v"], f"queries, rule {rule}, r {r}")
 
 
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
+def test_vertex_insertion_matches_oracle(tiny, flags):
+    """Vertex insertion (Section 1): isolated new vertices with empty labels,
+    then edges touching them; every label word and every answer against the
+    oracle doing the same; capacity errors leave the index unchanged; a
+    restore returns to the snapshot's vertices and re-added rows are clean."""
+    n0, add = int(tiny["n"]), 3000
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, vertex_capacity=n0 + add + 100, flags=flags)
+    assert ix.info()["vertex_capacity"] == n0 + add + 100
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    ix.sync()
+    ix.snapshot(0)
+    assert ix.add_vertices(add) == n0 and ix.n == n0 + add
+    ref.add_vertices(add)
+    assert_labels(ix, ref, "after adding vertices")
+    rng = np.random.default_rng(17)
+    n = n0 + add
+    new_src = rng.integers(n0, n, 4000).astype(np.int32)          # edges out of, into and between new vertices
+    new_dst = rng.integers(0, n, 4000).astype(np.int32)
+    into_src = rng.integers(0, n0, 4000).astype(np.int32)
+    into_dst = rng.integers(n0, n, 4000).astype(np.int32)
+    es = np.concatenate([tiny["ins_src"], new_src, into_src])
+    ed = np.concatenate([tiny["ins_dst"], new_dst, into_dst])
+    perm = rng.permutation(es.shape[0])
+    es, ed = es[perm], ed[perm]
+    for b in range(0, es.shape[0], 1500):
+        ix.insert_edges(D(es[b:b + 1500]), D(ed[b:b + 1500]))
+    ref.insert_edges(es, ed)
+    ix.sync()
+    assert_labels(ix, ref, "after insertions touching new vertices")
+    qu = np.concatenate([tiny["q_u"][:50_000], rng.integers(0, n, 50_000).astype(np.int32)])
+    qv = np.concatenate([tiny["q_v"][:50_000], rng.integers(n0, n, 25_000).astype(np.int32),
+                         rng.integers(0, n, 25_000).astype(np.int32)])
+    assert_queries(ix, ref, qu, qv, "queries with new vertices")
+    with pytest.raises(dbl.DblError):
+        ix.add_vertices(101)                                      # capacity n0 + add + 100
+    assert ix.n == n
+    ix.restore(0)
+    assert ix.n == n0
+    fresh = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
+    assert_labels(ix, fresh, "restored")
+    assert ix.add_vertices(5) == n0
+    assert all((t[n0:].cpu() == 0).all() for t in ix.labels())    # rows of the removed vertices are cleared
+    ix.close()
+
+
 def test_tiny_full_pipeline(tiny):
     """Plain DBL, tiny: build, 10k insertions in batches of 1k (labels after
     every batch), then 100k mixed queries (answers and deciding rules)."""
