@@ -383,7 +383,6 @@ __device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, in
 __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotList &cur, uint32_t *n_tasks)
 {
     const int64_t n = min((int64_t)ld_volatile_u32(cur.count), cur.cap);
-    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
