@@ -421,11 +421,12 @@ __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotL
 // task's mask, in Algorithm 2's order: y == v_j -> found; DL prune; BL prune;
 // otherwise y is visited for j, and bits new at y are pending for next level.
 // Tests of one edge x -> y against the live queries m of group g (Algorithm
-// 2's order), then the visit/pending update of (g, y).
+// 2's order) and the visit update of (g, y): returns the bits this thread
+// set first in y's visit word (it owns their expansion from y), and the slot.
 template <int WD, int WB>
-__device__ __forceinline__ void search_edge(const SearchArgs &a, int32_t y, uint32_t g, unsigned long long m,
-                                            uint32_t epoch, const SlotList &next, const IStage &cst,
-                                            const IStage &nst)
+__device__ __forceinline__ unsigned long long search_edge_visit(const SearchArgs &a, int32_t y, uint32_t g,
+                                                                unsigned long long m, const IStage &cst,
+                                                                int64_t &slot)
 {
     constexpr int HS = hs_of(WD + WB);
     constexpr int RW = 2 * HS;
@@ -456,40 +457,126 @@ __device__ __forceinline__ void search_edge(const SearchArgs &a, int32_t y, uint
         allowed |= bit;
     }
     if (hits) atomicOr(a.found + g, hits);
-    if (allowed) {
-        const int64_t s = slot_find_or_insert(a.c, ((unsigned long long)g << 32) | (uint32_t)y, cst);
-        if (s < 0) return;
-        const unsigned long long old = atomicOr(&a.c.table[s].visit, allowed);
-        const unsigned long long nb = allowed & ~old;
-        if (nb) mark_pending(a.c, s, nb, epoch, next, nst);
+    slot = -1;
+    if (!allowed) return 0;
+    slot = slot_find_or_insert(a.c, ((unsigned long long)g << 32) | (uint32_t)y, cst);
+    if (slot < 0) return 0;
+    const unsigned long long old = atomicOr(&a.c.table[slot].visit, allowed);
+    return allowed & ~old;
+}
+
+// search_edge_visit, with the new bits pending at (g, y) for the next level.
+template <int WD, int WB>
+__device__ __forceinline__ void search_edge(const SearchArgs &a, int32_t y, uint32_t g, unsigned long long m,
+                                            uint32_t epoch, const SlotList &next, const IStage &cst,
+                                            const IStage &nst)
+{
+    int64_t s;
+    const unsigned long long nb = search_edge_visit<WD, WB>(a, y, g, m, cst, s);
+    if (nb) mark_pending(a.c, s, nb, epoch, next, nst);
+}
+
+// Local continuation of the search (as in the label propagation): a state
+// (g, y) whose new bits this warp owns and whose vertex has at most kChunk
+// out-edges goes to the warp's list (shared memory) with y's adjacency range,
+// and the warp expands its list in further rounds of the same level (up to
+// kSLocalRounds), so chains of small vertices advance several hops per
+// level; what is left after the last round becomes pending at its slot for
+// the next level, as do states of larger vertices.  Each query bit of a
+// state is still expanded exactly once: by the thread whose OR set it first.
+struct SLocal {
+    int32_t slot, y;
+    uint32_t g;
+    int32_t b0, o0;
+    uint32_t deg;  // base degree | inserted degree << 16 (each at most kChunk)
+    unsigned long long mask;
+};
+constexpr int kSLocal = 16;
+constexpr int kSLocalRounds = 8;
+
+// Warp-collective: lane-held new bits nb at slot s for (g, y) -> the warp's
+// list or pending.
+__device__ __forceinline__ void search_continue(const SearchArgs &a, unsigned long long nb, int64_t s, int32_t y,
+                                                uint32_t g, uint32_t epoch, const SlotList &next, const IStage &nst,
+                                                SLocal *wl, int &wl_n)
+{
+    const int lane = threadIdx.x & 31;
+    AdjRange r{0, 0, 0, 0};
+    if (nb) r = adj_of(a.g, 0, y);
+    const int32_t d = r.bd + r.od;
+    const bool loc = nb && d > 0 && d <= kChunk;
+    const unsigned bl = __ballot_sync(kFull, loc);
+    const int rank = __popc(bl & ((1u << lane) - 1u));
+    const bool to_local = loc && wl_n + rank < kSLocal;
+    if (to_local)
+        wl[wl_n + rank] = SLocal{(int32_t)s, y, g, r.b0, r.o0, (uint32_t)r.bd | ((uint32_t)r.od << 16), nb};
+    wl_n = min(kSLocal, wl_n + __popc(bl));
+    if (nb && !to_local && d > 0) mark_pending(a.c, s, nb, epoch, next, nst);
+}
+
+// One flattened round: lane-held items (vertex x of group g, live bits m,
+// x's adjacency r, edge range [lo, lo + cnt)); the warp walks the
+// concatenation of the items' edges 32 at a time.
+template <int WD, int WB>
+__device__ __forceinline__ void search_round(const SearchArgs &a, uint32_t g, unsigned long long m, const AdjRange &r,
+                                             uint32_t lo, uint32_t cnt, uint32_t epoch, const SlotList &next,
+                                             const IStage &cst, const IStage &nst, SLocal *wl, int &wl_n,
+                                             unsigned long long &relaxed)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += x;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t e = base + lane;
+        const int owner = flat_owner(excl, e);
+        const AdjRange orr{__shfl_sync(kFull, r.b0, owner), __shfl_sync(kFull, r.bd, owner),
+                           __shfl_sync(kFull, r.o0, owner), 0};
+        const uint32_t opos = __shfl_sync(kFull, lo, owner) + (e - __shfl_sync(kFull, excl, owner));
+        const uint32_t og = __shfl_sync(kFull, g, owner);
+        const unsigned long long om = __shfl_sync(kFull, m, owner);
+        unsigned long long nb = 0;
+        int64_t sl = -1;
+        int32_t y = 0;
+        if (e < total) {
+            ++relaxed;
+            y = adj_at(a.g, 0, orr, (int32_t)opos);
+            nb = search_edge_visit<WD, WB>(a, y, og, om, cst, sl);
+        }
+        search_continue(a, nb, sl, y, og, epoch, next, nst, wl, wl_n);
     }
 }
 
 // Flattened search level (TEAM == 1): one task per lane per round, the warp
 // walks the concatenation of its tasks' edges 32 at a time (see
-// expand_level_flat).
+// expand_level_flat), then the warp's local rounds.
 template <int WD, int WB>
 __device__ __forceinline__ void search_expand_flat(const SearchArgs &a, uint32_t n_tasks_in, uint32_t epoch,
                                                    const SlotList &next, const IStage &cst, const IStage &nst)
 {
+    __shared__ SLocal s_sl[32 * kSLocal];
     const int lane = threadIdx.x & 31;
+    SLocal *wl = s_sl + (threadIdx.x >> 5) * kSLocal;
+    int wl_n = 0;  // warp-uniform
     const int64_t ntasks = min((int64_t)n_tasks_in, a.task_cap);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long relaxed = 0;
     for (int64_t r0 = 0; warp + nwarps * r0 < ntasks; r0 += 32) {  // warp-uniform
         const int64_t t = warp + nwarps * (r0 + lane);
-        int32_t b0 = 0, bd = 0, o0 = 0;
+        AdjRange r{0, 0, 0, 0};
         uint32_t lo = 0, cnt = 0, g = 0;
         unsigned long long m = 0;
         if (t < ntasks) {
             const SearchTask tk = a.tasks[t];
             m = tk.mask & ~__ldcg(a.found + tk.g);
             if (m) {
-                const AdjRange r = adj_of(a.g, 0, tk.x);
-                b0 = r.b0;
-                bd = r.bd;
-                o0 = r.o0;
+                r = adj_of(a.g, 0, tk.x);
                 g = tk.g;
                 const int32_t d = r.bd + r.od;
                 lo = tk.chunk * (uint32_t)kChunk;
@@ -497,27 +584,30 @@ __device__ __forceinline__ void search_expand_flat(const SearchArgs &a, uint32_t
                 cnt = hi > (int32_t)lo ? (uint32_t)(hi - (int32_t)lo) : 0u;
             }
         }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += x;
-        }
-        const uint32_t excl = incl - cnt;
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t e = base + lane;
-            const int owner = flat_owner(excl, e);
-            const AdjRange orr{__shfl_sync(kFull, b0, owner), __shfl_sync(kFull, bd, owner),
-                               __shfl_sync(kFull, o0, owner), 0};
-            const uint32_t opos = __shfl_sync(kFull, lo, owner) + (e - __shfl_sync(kFull, excl, owner));
-            const uint32_t og = __shfl_sync(kFull, g, owner);
-            const unsigned long long om = __shfl_sync(kFull, m, owner);
-            if (e < total) {
-                ++relaxed;
-                search_edge<WD, WB>(a, adj_at(a.g, 0, orr, (int32_t)opos), og, om, epoch, next, cst, nst);
+        search_round<WD, WB>(a, g, m, r, lo, cnt, epoch, next, cst, nst, wl, wl_n, relaxed);
+    }
+    for (int lr = 0; lr < kSLocalRounds && wl_n > 0; ++lr) {
+        __syncwarp();
+        const bool has = lane < wl_n;
+        const SLocal it = has ? wl[lane] : SLocal{0, 0, 0u, 0, 0, 0u, 0ull};
+        __syncwarp();
+        wl_n = 0;
+        unsigned long long m = 0;
+        AdjRange r{0, 0, 0, 0};
+        uint32_t cnt = 0;
+        if (has) {
+            m = it.mask & ~__ldcg(a.found + it.g);
+            if (m) {
+                r = AdjRange{it.b0, (int32_t)(it.deg & 0xffffu), it.o0, (int32_t)(it.deg >> 16)};
+                cnt = (uint32_t)(r.bd + r.od);
             }
         }
+        search_round<WD, WB>(a, it.g, m, r, 0u, cnt, epoch, next, cst, nst, wl, wl_n, relaxed);
+    }
+    __syncwarp();
+    if (lane < wl_n) {  // left for the next level
+        const SLocal it = wl[lane];
+        mark_pending(a.c, it.slot, it.mask, epoch, next, nst);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) relaxed += __shfl_xor_sync(kFull, relaxed, o);
