@@ -744,12 +744,14 @@ def bench_sweep(args):
     I = Inputs(w, dev)
     batches = step_batches(E, args.batch)
     peaks, src = measured_peaks()
-    configs = ([(k, kp, 0, "M") for k in (64, 128, 256) for kp in (64, 128, 256)] +
-               [(64, 64, 2, "M"), (64, 64, 16, "M"), (64, 64, 0, "A"), (64, 64, 0, "B"), (64, 64, 0, "C")])
+    configs = ([(k, kp, 0, "M", 0) for k in (64, 128, 256) for kp in (64, 128, 256)] +
+               [(64, 64, 2, "M", 0), (64, 64, 16, "M", 0), (64, 64, 0, "A", 0), (64, 64, 0, "B", 0),
+                (64, 64, 0, "C", 0)] +
+               [(128, 64, 0, "M", qpt) for qpt in (1, 4)] + [(256, 64, 0, "M", qpt) for qpt in (1, 4)])
     rows = []
-    for k, kp, r, rule in configs:
+    for k, kp, r, rule, qpt in configs:
         ix = dbl.DBLIndex(I.rp, I.col, k, kp, leaf_r=r, landmark_rule=rule, edge_capacity=max(E, 1 << 20),
-                          flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING)
+                          query_unroll=qpt, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING)
         ix.sync()
         ix.snapshot(0)
         step = make_step(ix, I, batches)
@@ -769,7 +771,8 @@ def bench_sweep(args):
         code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
         lab_ms = t["query_label"][0] / max(1, t["query_label"][1])
         leaves = int((ix.selection()[2] > 0).sum().item())
-        rows.append({"k": k, "kprime": kp, "leaf_r": r, "landmark_rule": rule, "record_bytes": rec, "leaves": leaves, "ms_per_step": ms,
+        rows.append({"k": k, "kprime": kp, "leaf_r": r, "landmark_rule": rule, "query_unroll": qpt or 2,
+                     "record_bytes": rec, "leaves": leaves, "ms_per_step": ms,
                      "ops_per_s": (E + Q) / (ms * 1e-3),
                      "insert_ms_per_batch": t["propagate"][0] / max(1, t["propagate"][1]),
                      "label_test_ms": lab_ms,

@@ -116,8 +116,8 @@ typedef struct {
     int32_t team;          /* lanes per expansion task (4, 8, 16, 32), or 1:
                               one task per lane with the warp walking its
                               tasks' edges 32 at a time; 0: 1 */
-    int32_t query_unroll;  /* query pairs per thread in the label test (1, 2, 4);
-                              0: 2, or 1 for 128-byte records */
+    int32_t query_unroll;  /* query pairs per lane group in the label test (1, 2,
+                              4); 0: 2 for 32-byte records, 4 for wider ones */
     int32_t search_first_log2; /* a search wave first hashes its states into
                               the first 2^x slots of its table (clamped to the
                               table); a lone 64-query group that overflows them
@@ -294,14 +294,18 @@ dbl_status dbl_info(const dbl_index *ix, int64_t info[16]);
  * options.  The index's labels and graph are restored afterwards.
  * report (may be NULL, else 16 doubles) receives [0..9] the fastest trial's ms per
  * candidate (level-by-level teams 1, 4, 8, 16, 32, then persistent teams
- * 1..32), [10] best team, [11] 1 if persistent, [12] best ms.  DBL_FLAG_ASYNC/TIMING are off during the trials
- * and restored after.  Synchronous.
+ * 1..32), [10] best team, [11] 1 if persistent, [12] best ms, [13..15] the
+ * fastest ms of the query batch alone under the chosen schedule with 1, 2
+ * and 4 label-test pairs per lane group (dbl_options.query_unroll; the
+ * fastest is kept).  DBL_FLAG_ASYNC/TIMING are off during the trials and
+ * restored after.  Synchronous.
  */
 dbl_status dbl_autotune(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, const int32_t *u,
                         const int32_t *v, int64_t q, uint8_t *ans, int32_t trials, double *report, void *stream);
-/* Apply a frontier schedule directly (e.g. one cached from dbl_autotune):
- * team width 1, 4, 8, 16 or 32; persistent != 0 sets DBL_FLAG_PERSISTENT. */
-dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent);
+/* Apply a schedule directly (e.g. one cached from dbl_autotune): team width
+ * 1, 4, 8, 16 or 32; persistent != 0 sets DBL_FLAG_PERSISTENT; query_unroll
+ * 1, 2 or 4 label-test pairs per lane group (0 keeps the current value). */
+dbl_status dbl_set_schedule(dbl_index *ix, int32_t team, int32_t persistent, int32_t query_unroll);
 
 /* ---------------------------------------------------------------------------
  * Concurrent query batches.  A query context holds the scratch of one query

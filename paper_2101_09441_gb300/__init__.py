@@ -112,7 +112,7 @@ def lib():
             L.dbl_destroy.restype = None
             f32 = ctypes.c_float
             L.dbl_autotune.argtypes = [P, P, P, i64, P, P, i64, P, i32, P, P]
-            L.dbl_set_schedule.argtypes = [P, i32, i32]
+            L.dbl_set_schedule.argtypes = [P, i32, i32, i32]
             L.dbl_qctx_create.argtypes = [P, P, P]
             L.dbl_qctx_destroy.argtypes = [P, P]
             L.dbl_qctx_destroy.restype = None
@@ -371,7 +371,7 @@ class DBLIndex:
             table = json.load(open(cache))
             if key in table:
                 r = table[key]
-                self._apply_schedule(int(r["team"]), bool(r["persistent"]))
+                self._apply_schedule(int(r["team"]), bool(r["persistent"]), int(r.get("query_unroll", 0)))
                 return dict(r, cached=True)
         src, dst = self._pair(src, dst)
         u, v = self._pair(u, v)
@@ -383,19 +383,23 @@ class DBLIndex:
         out = {"team": int(rep[10]), "persistent": bool(rep[11]), "best_ms": float(rep[12]),
                "level_ms": {t: float(rep[i]) for i, t in enumerate(teams)},
                "persistent_ms": {t: float(rep[5 + i]) for i, t in enumerate(teams)}}
+        if u.numel():
+            qms = {qpt: float(rep[13 + i]) for i, qpt in enumerate((1, 2, 4))}
+            out["query_unroll_ms"] = qms
+            out["query_unroll"] = min(qms, key=qms.get)
         if cache:
             table = json.load(open(cache)) if os.path.exists(cache) else {}
             table[key] = out
             json.dump(table, open(cache, "w"), indent=1)
         return out
 
-    def _apply_schedule(self, team: int, persistent: bool):
-        self._check(lib().dbl_set_schedule(self._h, int(team), int(persistent)))
+    def _apply_schedule(self, team: int, persistent: bool, query_unroll: int = 0):
+        self._check(lib().dbl_set_schedule(self._h, int(team), int(persistent), int(query_unroll)))
 
-    def set_schedule(self, team: int, persistent: bool):
-        """dbl_set_schedule: team width (1, 4, 8, 16, 32) and persistent or
-        level-by-level frontier loops."""
-        self._apply_schedule(team, persistent)
+    def set_schedule(self, team: int, persistent: bool, query_unroll: int = 0):
+        """dbl_set_schedule: team width (1, 4, 8, 16, 32), persistent or
+        level-by-level frontier loops, label-test pairs per lane group (1, 2, 4; 0 keeps)."""
+        self._apply_schedule(team, persistent, query_unroll)
 
     # ------------------------------------------------------------------ learned scorer
     def features(self, stream=None):

@@ -1007,11 +1007,13 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     if (st) return st;
     uint32_t *cnt = c->d_counts;
     cudaMemsetAsync(cnt + kCntUnd, 0, sizeof(uint32_t), s);
-    // pairs per lane group: option, else 2; measured on 32-byte records, 2
-    // beats 4 (more resident warps) and 1 (fewer loads in flight); a group of
-    // HS / 2 lanes keeps the same registers at every record width
+    // pairs per lane group: option, else 2 at 32-byte records (2 beats 4:
+    // more resident warps, and 1: fewer loads in flight) and 4 at wider ones
+    // (64-byte records: 4 -> 374 us, 2 -> 407 us, 1 -> 477 us per 10M pairs;
+    // 128-byte: 4 and 1 -> 523 us, 2 -> 559 us); a group of HS / 2 lanes
+    // keeps the same registers at every record width
     constexpr int HS = hs_of(WD + WB);
-    const int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : 2;
+    const int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 2 ? 2 : 4);
     const int64_t pairs_per_block = (int64_t)(kBlock / (HS / 2)) * qpt;
     int64_t blocks = (q + pairs_per_block - 1) / pairs_per_block;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;

@@ -456,10 +456,11 @@ def test_autotune_restores_index_and_keeps_parity(tiny, tmp_path):
     out = ix.autotune(D(s[:1000]), D(d[:1000]), D(tiny["q_u"][:20000]), D(tiny["q_v"][:20000]), trials=1, cache=cache)
     assert out["team"] in (1, 4, 8, 16, 32) and out["best_ms"] > 0
     assert len(out["level_ms"]) == 5 and len(out["persistent_ms"]) == 5
+    assert out["query_unroll"] in (1, 2, 4) and all(v > 0 for v in out["query_unroll_ms"].values())
     for a, b in zip(labels_np(ix), before):
         assert np.array_equal(a, b), "autotune changed the index"
     again = ix.autotune(D(s[:1000]), D(d[:1000]), D(tiny["q_u"][:100]), D(tiny["q_v"][:100]), cache=cache)
-    assert again.get("cached") and again["team"] == out["team"]
+    assert again.get("cached") and again["team"] == out["team"] and again["query_unroll"] == out["query_unroll"]
     ix.insert_edges(D(s), D(d))
     ref.insert_edges(s, d)
     ix.sync()
