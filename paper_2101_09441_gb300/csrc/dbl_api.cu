@@ -677,6 +677,18 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     return DBL_OK;
 }
 
+__global__ void k_restore_tail(int64_t *top, const int64_t *top_snap, uint32_t *status, uint32_t *counts,
+                               int ncounts, uint32_t *mark, int64_t mark_words)
+{
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0; i < mark_words; i += st) mark[i] = 0;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x < 2) top[threadIdx.x] = top_snap[threadIdx.x];
+        if (threadIdx.x == 0) *status = 0;
+        for (int i = threadIdx.x; i < ncounts; i += blockDim.x) counts[i] = 0;
+    }
+}
+
 dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
 {
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
@@ -686,12 +698,17 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     const size_t rec_b = 8 * (size_t)sn.n * ix->rw, meta_b = sizeof(VMeta) * (size_t)sn.n;
     cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(ix->vm, sn.vm.p, meta_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(ix->d_pool_top, sn.top.p, 16, cudaMemcpyDeviceToDevice, s);
-    cudaMemsetAsync(ix->d_status, 0, sizeof(uint32_t), s);
-    cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
-    // the frontier bitmaps are empty after every complete propagation; an
-    // aborted one (the index was poisoned) may have left bits behind
-    cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
+    // pool tops, status, counters and the frontier bitmaps in one launch (the
+    // bitmaps are empty after every complete propagation; an aborted one, on
+    // a poisoned index, may have left bits behind)
+    {
+        const int64_t words = 4 * ix->wpd;
+        int64_t blocks = (words + kBlock - 1) / kBlock;
+        if (blocks > (int64_t)num_sms() * 4) blocks = (int64_t)num_sms() * 4;
+        k_restore_tail<<<(unsigned)(blocks < 1 ? 1 : blocks), kBlock, 0, s>>>(
+            ix->d_pool_top, (const int64_t *)sn.top.p, ix->d_status, ix->d_counts, kCntWords, ix->mark, words);
+        ++ix->launches;
+    }
     ix->edges_stored = sn.edges_stored;
     ix->n = sn.n;
     ix->poisoned = false;

@@ -289,10 +289,12 @@ struct FwdSmem {
     bf16 h1[kTileR * kH];
     bf16 w2[kH * kH];
     float b1[kH], b2[kH], w3[kH];
+    float ypart[kTileR];  // second warpgroup's half of each row's output dot product
     uint64_t bar_w, bar_x[2], bar_mma;
     uint32_t tmem;
 };
 constexpr int kFwdSmemBytes = 112 * 1024;
+constexpr int kFwdThreads = 2 * kTileR;  // two warpgroups: each row's columns split in halves
 static_assert(sizeof(FwdSmem) + 1024 <= kFwdSmemBytes, "forward shared memory");
 static_assert(offsetof(FwdSmem, w2) + 7 * 4096 + 15 * 2048 + 256 <= kFwdSmemBytes, "descriptor reach");
 
@@ -302,11 +304,14 @@ static_assert(offsetof(FwdSmem, w2) + 7 * 4096 + 15 * 2048 + 256 <= kFwdSmemByte
 // [0, 128), the epilogue adds b1, applies ReLU and writes H1 as bf16 back to
 // shared memory, layer 2 is eight 128 x 128 x 16 MMAs into columns [128, 256),
 // and its epilogue adds b2, applies ReLU, rounds H2 to bf16 and takes the dot
-// product with w3.  Thread t owns row t of the tile (TMEM lane t).  The next
-// tile's X copy is in flight during the current tile.  Every wait is bounded:
+// product with w3.  Two warpgroups: warp w reads TMEM lanes 32 (w % 4) ..
+// 32 (w % 4) + 31 (its rows), warpgroup 0 columns 0-63 and warpgroup 1
+// columns 64-127 of each layer; the two halves of a row's dot product are
+// added through shared memory in a fixed order.  The next tile's X copy is in
+// flight during the current tile.  Every wait is bounded:
 // on a timeout the block raises *err, waits (bounded) for its copies and MMAs,
 // frees its TMEM and returns.
-__global__ void __launch_bounds__(kTileR, 1)
+__global__ void __launch_bounds__(kFwdThreads, 1)
     k_mlp_forward(const __grid_constant__ CUtensorMap xmap, int use_tma, MlpDev m, const bf16 *X,
                   const int32_t *rows_idx, int64_t R, float *y, bf16 *H1out, bf16 *H2out, uint32_t *err)
 {
@@ -331,7 +336,9 @@ __global__ void __launch_bounds__(kTileR, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = S.tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int row = (warp & 3) * 32 + (tid & 31);  // this thread's row of the tile (TMEM lane)
+    const int half = warp >> 2;                    // columns [64 half, 64 half + 64) of each layer
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const int64_t ntiles = (R + kTileR - 1) / kTileR;
     bool x_pending[2] = {false, false};  // a tensor copy into x[b] not yet waited for
     if (tid == 0) {
@@ -353,14 +360,14 @@ __global__ void __launch_bounds__(kTileR, 1)
     int it = 0;
     for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++it) {
         const int buf = it & 1;
-        const int64_t r = tile * kTileR + tid;
+        const int64_t r = tile * kTileR + row;
         if (use_tma) {
             ok = tc::mbar_wait(&S.bar_x[buf], px[buf], kWaitLimit);
             if (ok) {
                 px[buf] ^= 1;
                 x_pending[buf] = false;
             }
-        } else {
+        } else if (half == 0) {
             uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
             if (r < R) {
                 const int64_t src = rows_idx ? (int64_t)rows_idx[r] : r;
@@ -369,8 +376,8 @@ __global__ void __launch_bounds__(kTileR, 1)
                 hi = xp[1];
             }
             uint4 *xs = reinterpret_cast<uint4 *>(S.x[buf]);
-            xs[tid] = lo;           // K block 0
-            xs[kTileR + tid] = hi;  // K block 1
+            xs[row] = lo;           // K block 0
+            xs[kTileR + row] = hi;  // K block 1
             tc::fence_async_smem();
         }
         if (!__syncthreads_and(ok)) {
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kTileR, 1)
         tc::tc_fence_after();
         uint4 *h1 = reinterpret_cast<uint4 *>(S.h1);
 #pragma unroll 1
-        for (int c = 0; c < kH / 16; ++c) {
+        for (int c = half * 4; c < half * 4 + 4; ++c) {
             float v[16];
             tc::tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), v);
             uint32_t pk[8];
@@ -408,8 +415,8 @@ __global__ void __launch_bounds__(kTileR, 1)
                 pk[j] = pack_bf16(fmaxf(v[2 * j] + S.b1[col], 0.f), fmaxf(v[2 * j + 1] + S.b1[col + 1], 0.f));
             }
             const uint4 q0 = make_uint4(pk[0], pk[1], pk[2], pk[3]), q1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            h1[(2 * c) * kTileR + tid] = q0;
-            h1[(2 * c + 1) * kTileR + tid] = q1;
+            h1[(2 * c) * kTileR + row] = q0;
+            h1[(2 * c + 1) * kTileR + row] = q1;
             if (H1out && r < R) {
                 uint4 *g = reinterpret_cast<uint4 *>(H1out + r * kH + c * 16);
                 g[0] = q0;
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(kTileR, 1)
         tc::tc_fence_after();
         float acc = 0.f;
 #pragma unroll 1
-        for (int c = 0; c < kH / 16; ++c) {
+        for (int c = half * 4; c < half * 4 + 4; ++c) {
             float v[16];
             tc::tmem_ld16(tmem + lane_base + (uint32_t)(kH + c * 16), v);
             uint32_t pk[8];
@@ -454,9 +461,10 @@ __global__ void __launch_bounds__(kTileR, 1)
                 g[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
-        if (r < R) y[r] = acc + b3;
+        if (half) S.ypart[row] = acc;
         tc::tc_fence_before();
-        __syncthreads();  // TMEM and H1 are rewritten by the next tile
+        __syncthreads();  // TMEM and H1 are rewritten by the next tile; ypart is complete
+        if (!half && r < R) y[r] = (acc + S.ypart[row]) + b3;
     }
     if (!ok) {
         if (tid == 0) atomicExch(err, 1u);
@@ -836,7 +844,7 @@ static dbl_status launch_forward(dbl_mlp *m, const bf16 *X, const int32_t *idx, 
     const int64_t tiles = (R + kTileR - 1) / kTileR;
     int64_t blocks = (int64_t)num_sms() * 2;
     if (blocks > tiles) blocks = tiles;
-    k_mlp_forward<<<(unsigned)(blocks < 1 ? 1 : blocks), kTileR, kFwdSmemBytes, s>>>(map, use_tma, mlp_dev(m), X, idx,
+    k_mlp_forward<<<(unsigned)(blocks < 1 ? 1 : blocks), kFwdThreads, kFwdSmemBytes, s>>>(map, use_tma, mlp_dev(m), X, idx,
                                                                                      R, y, H1, H2, m->d_err);
     return DBL_OK;
 }

@@ -981,8 +981,9 @@ static dbl_status launch_search_persistent(dbl_index *ix, dbl_qctx *c, const int
     if (blocks_per_sm < 0)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_search_persistent<WD, WB, TEAM>, kPB, 0);
     if (blocks_per_sm < 1) return qfail(c, DBL_ERR_CUDA, "persistent search: kernel does not fit on an SM");
+    // every field is written by block 0 before any block reads it (after the
+    // first grid barrier), so the state needs no clearing here
     PersistState *ps = (PersistState *)c->pstate;
-    cudaMemsetAsync(ps, 0, sizeof(PersistState), s);
     SearchArgs a = search_args(ix, c, qu, qv, q, ans, code, &ps->n_claimed, &ps->overflow);
     const uint32_t *n_und = c->d_counts + kCntUnd;
     GridBarrier bar = grid_barrier_at(c->d_counts);
