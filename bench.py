@@ -771,7 +771,8 @@ def bench_sweep(args):
         code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
         lab_ms = t["query_label"][0] / max(1, t["query_label"][1])
         leaves = int((ix.selection()[2] > 0).sum().item())
-        rows.append({"k": k, "kprime": kp, "leaf_r": r, "landmark_rule": rule, "query_unroll": qpt or 2,
+        rows.append({"k": k, "kprime": kp, "leaf_r": r, "landmark_rule": rule,
+                     "query_unroll": qpt or (2 if rec == 32 else 4),  # the library's default when 0
                      "record_bytes": rec, "leaves": leaves, "ms_per_step": ms,
                      "ops_per_s": (E + Q) / (ms * 1e-3),
                      "insert_ms_per_batch": t["propagate"][0] / max(1, t["propagate"][1]),
