@@ -44,7 +44,7 @@ UNIT = "ops/s (queries + inserted edges)"
 
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_151_589_000 + 22_240_256, "5771a4876e1c"),
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_151_473_000 + 21_907_712, "6f473c38b2e8"),
                                              "propagate": (54_288_640 + 2_143_744, "37c9434330aa")}
 KERNEL_SOURCE = {"query_label": "dbl_query.cu", "propagate": "dbl_insert.cu",
                  "search_expand": "dbl_query.cu", "insert_seed": "dbl_insert.cu"}
