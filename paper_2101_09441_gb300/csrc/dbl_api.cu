@@ -677,10 +677,31 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     return DBL_OK;
 }
 
-__global__ void k_restore_tail(int64_t *top, const int64_t *top_snap, uint32_t *status, uint32_t *counts,
-                               int ncounts, uint32_t *mark, int64_t mark_words)
+// The whole restore in one launch: the labels and the adjacency metadata
+// (16-byte copies, four in flight per thread; both sizes are multiples of 16
+// bytes), the pool tops, and cleared status, counters and frontier bitmaps.
+__global__ void k_restore(uint4 *rec, const uint4 *rec_snap, int64_t rec_units, uint4 *vm, const uint4 *vm_snap,
+                          int64_t vm_units, int64_t *top, const int64_t *top_snap, uint32_t *status,
+                          uint32_t *counts, int ncounts, uint32_t *mark, int64_t mark_words)
 {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    const int64_t total = rec_units + vm_units;
+    for (int64_t i = i0; i < total; i += 4 * st) {
+        uint4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = i + k * st;
+            if (j < total) v[k] = j < rec_units ? __ldcs(rec_snap + j) : __ldcs(vm_snap + (j - rec_units));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = i + k * st;
+            if (j < total) {
+                if (j < rec_units) __stcs(rec + j, v[k]);
+                else __stcs(vm + (j - rec_units), v[k]);
+            }
+        }
+    }
     for (int64_t i = i0; i < mark_words; i += st) mark[i] = 0;
     if (blockIdx.x == 0) {
         if (threadIdx.x < 2) top[threadIdx.x] = top_snap[threadIdx.x];
@@ -696,19 +717,15 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     Snapshot &sn = ix->snaps[slot];
     const size_t rec_b = 8 * (size_t)sn.n * ix->rw, meta_b = sizeof(VMeta) * (size_t)sn.n;
-    cudaMemcpyAsync(ix->rec, sn.rec.p, rec_b, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(ix->vm, sn.vm.p, meta_b, cudaMemcpyDeviceToDevice, s);
-    // pool tops, status, counters and the frontier bitmaps in one launch (the
-    // bitmaps are empty after every complete propagation; an aborted one, on
-    // a poisoned index, may have left bits behind)
-    {
-        const int64_t words = 4 * ix->wpd;
-        int64_t blocks = (words + kBlock - 1) / kBlock;
-        if (blocks > (int64_t)num_sms() * 4) blocks = (int64_t)num_sms() * 4;
-        k_restore_tail<<<(unsigned)(blocks < 1 ? 1 : blocks), kBlock, 0, s>>>(
-            ix->d_pool_top, (const int64_t *)sn.top.p, ix->d_status, ix->d_counts, kCntWords, ix->mark, words);
-        ++ix->launches;
-    }
+    // one launch: labels, adjacency metadata, pool tops, and cleared status,
+    // counters and frontier bitmaps (the bitmaps are empty after every
+    // complete propagation; an aborted one, on a poisoned index, may have left
+    // bits behind)
+    k_restore<<<(unsigned)num_sms() * 8, kBlock, 0, s>>>(
+        (uint4 *)ix->rec, (const uint4 *)sn.rec.p, (int64_t)(rec_b / 16), (uint4 *)ix->vm, (const uint4 *)sn.vm.p,
+        (int64_t)(meta_b / 16), ix->d_pool_top, (const int64_t *)sn.top.p, ix->d_status, ix->d_counts, kCntWords,
+        ix->mark, 4 * ix->wpd);
+    ++ix->launches;
     ix->edges_stored = sn.edges_stored;
     ix->n = sn.n;
     ix->poisoned = false;
