@@ -492,7 +492,7 @@ struct SLocal {
     unsigned long long mask;
 };
 constexpr int kSLocal = 16;
-constexpr int kSLocalRounds = 8;
+constexpr int kSLocalRounds = 16;
 
 // Warp-collective: lane-held new bits nb at slot s for (g, y) -> the warp's
 // list or pending.
