@@ -125,6 +125,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, world: int, tdist, device="cpu") -> float:
+    """The largest value over the ranks (the slowest replica's time); every
+    rank gets it.  One process per GPU, replicas only: this reduction is the
+    only collective of a run."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, total_ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return world * units_per_rank / (total_ms * 1e-3)
+
+
 def step_batches(n_edges: int, batch: int):
     return [(b, min(b + batch, n_edges)) for b in range(0, n_edges, batch)]
 
@@ -345,11 +362,8 @@ def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
     total_ms, outs, clocks = time_steps(timed, args.steps, world, tdist, sampler,
                                         profile=args.profile and name == args.profile_form)
     ix.sync()
-    if world > 1:
-        t = torch.tensor([total_ms], device=I.qu.device)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    res.update(ms_per_step=total_ms / args.steps, value=world * args.steps * (E + Q) / (total_ms * 1e-3),
+    total_ms = max_over_ranks(total_ms, world, tdist, I.qu.device)
+    res.update(ms_per_step=total_ms / args.steps, value=whole_job_rate(args.steps * (E + Q), world, total_ms),
                gpu_launches=(launches_per_step * args.steps) if use_graph else ix.info()["launches"] - l0)
     if not use_graph:
         ins_ms = sum(ev[0].elapsed_time(ev[1]) for ev in outs)

@@ -1,0 +1,66 @@
+"""Host side of the multi-GPU path on CPU (gloo, world size 2).
+
+Several GPUs run independent replicas of the index (every rank holds the
+whole graph and labels and runs the whole step); the only collective is the
+timing reduction: the job's time is the slowest rank's, and the whole-job
+rate counts every rank's units.  The reference arm runs on rank 0 alone.
+"""
+import os
+import socket
+import subprocess
+import sys
+
+import torch.distributed as tdist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    local_ms = [3.0, 5.0][rank]
+    slowest = bench.max_over_ranks(local_ms, world, tdist)
+    rate = bench.whole_job_rate(1000.0, world, slowest)
+    tdist.barrier()
+    q.put((rank, slowest, rate))
+    tdist.destroy_process_group()
+
+
+def test_step_time_is_the_slowest_rank_and_rate_counts_every_rank():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, slowest, rate in got:
+        assert slowest == 5.0                       # every rank sees the slowest replica's time
+        assert abs(rate - 2 * 1000.0 / 5e-3) < 1e-6  # units of both ranks over that time
+
+
+def test_single_process_needs_no_collective():
+    import bench
+    assert bench.max_over_ranks(4.0, 1, None) == 4.0
+    assert bench.whole_job_rate(500.0, 1, 2.0) == 500.0 / 2e-3
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "1"],
+                       cwd=ROOT, env=env, capture_output=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == b""
