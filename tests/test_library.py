@@ -51,6 +51,27 @@ def test_default_options_and_errors_without_gpu(lib):
     assert lib.dbl_query(None, None, None, 0, None, None, None) == dbl.DBL_ERR_INVALID
 
 
+def test_option_checks_without_gpu(lib):
+    """Options are validated before any device work: Table 3 ranking rule,
+    leaf threshold, vertex capacity, team width; the newer entry points reject
+    a NULL handle."""
+    import ctypes
+    g = dbl._Graph(10, 0, 16, 0)  # row_ptr is never dereferenced before the checks below
+    h = ctypes.c_void_p()
+    for field, value in (("landmark_rule", 4), ("landmark_rule", -1), ("leaf_r", -1),
+                         ("vertex_capacity", 1 << 31), ("team", 3)):
+        opt = dbl._Options()
+        lib.dbl_default_options(ctypes.byref(opt))
+        setattr(opt, field, value)
+        st = lib.dbl_build(ctypes.byref(g), None, 64, None, None, 64, ctypes.byref(opt), None, ctypes.byref(h))
+        assert st == dbl.DBL_ERR_INVALID, (field, value, st)
+        assert not h.value
+    first = ctypes.c_int32(0)
+    assert lib.dbl_add_vertices(None, 1, ctypes.byref(first), None) == dbl.DBL_ERR_INVALID
+    assert lib.dbl_set_schedule(None, 1, 1, 0) == dbl.DBL_ERR_INVALID
+    assert lib.dbl_mlp_sync(None, None) == dbl.DBL_ERR_INVALID
+
+
 def test_kernels_compiled_for_sm103a():
     from paper_2101_09441_gb300 import native_build
     assert "arch=compute_103a,code=sm_103a" in native_build.ARCH
