@@ -8,7 +8,9 @@
  *               (Definition 1, Section 4.1);
  *   BL_in(x)  = hash buckets of zero in-degree leaves that reach x,
  *   BL_out(x) = hash buckets of zero out-degree leaves x reaches
- *               (Definition 2 and the hashing paragraph, Section 4.1).
+ *               (Definition 2 and the hashing paragraph, Section 4.1; with
+ *               dbl_options.leaf_r, also every vertex with M <= leaf_r,
+ *               Section 6).
  * Reachability is reflexive: Des(u) and Anc(u) contain u (Table 1).
  *
  * Conventions for every call:
@@ -16,11 +18,12 @@
  *     They are borrowed: the caller keeps them alive until the stream has
  *     passed the call.  Calls are ordered on `stream` (a cudaStream_t; NULL
  *     means the legacy default stream).
- *   - Vertex ids are int32 in [0, n).  Labels are uint64 words: landmark slot
+ *   - Vertex ids are int32 in [0, n), n growing by dbl_add_vertices.  Labels
+ *     are uint64 words: landmark slot
  *     i is word i/64 bit i%64, bucket b is word b/64 bit b%64.
  *   - An invalid argument is reported as DBL_ERR_INVALID before any state
- *     changes.  Running out of the index's edge capacity is DBL_ERR_CAPACITY,
- *     with the index unchanged.  A device loop that exceeds its iteration
+ *     changes.  Running out of the index's edge or vertex capacity is
+ *     DBL_ERR_CAPACITY, with the index unchanged.  A device loop that exceeds its iteration
  *     bound is DBL_ERR_TIMEOUT and leaves the index poisoned (every later
  *     call returns DBL_ERR_POISONED) until dbl_restore.
  *   - The index owns all of its device memory, obtained through
