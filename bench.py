@@ -125,6 +125,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+NOMINAL = {"GB/s": 7900.0, "TFLOP/s": 2250.0}  # GB300 HBM3e and dense bf16 tensor rate, for context
+
+
+def add_nominal(line: dict) -> dict:
+    """Each roofline object also against the nominal peak of its unit (the
+    fraction that counts is the one against the measured peak)."""
+    for key in ("roofline", "roofline_label_test", "roofline_build", "roofline_scorer"):
+        r = line.get(key)
+        if r and r.get("achieved") is not None and r.get("unit") in NOMINAL:
+            r["nominal_peak"] = NOMINAL[r["unit"]]
+            r["frac_of_nominal"] = r["achieved"] / NOMINAL[r["unit"]]
+    return line
+
+
 def max_over_ranks(x: float, world: int, tdist, device="cpu") -> float:
     """The largest value over the ranks (the slowest replica's time); every
     rank gets it.  One process per GPU, replicas only: this reduction is the
@@ -607,6 +621,7 @@ def bench_gpu(args):
         line["cpu_baseline"] = cpu_baseline(args, w)
     for f in list(forms.values()) + [learned, learned_t]:
         f["ix"].close()
+    add_nominal(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

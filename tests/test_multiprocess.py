@@ -64,3 +64,14 @@ def test_reference_arm_runs_on_rank_zero_only():
                        cwd=ROOT, env=env, capture_output=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == b""
+
+
+def test_rooflines_also_against_nominal_peaks():
+    import bench
+    line = {"roofline": {"achieved": 790.0, "unit": "GB/s", "frac": 0.1},
+            "roofline_scorer": {"achieved": 450.0, "unit": "TFLOP/s", "frac": 0.2},
+            "roofline_build": None}
+    bench.add_nominal(line)
+    assert abs(line["roofline"]["frac_of_nominal"] - 0.1) < 1e-12
+    assert abs(line["roofline_scorer"]["frac_of_nominal"] - 0.2) < 1e-12
+    assert line["roofline"]["frac"] == 0.1 and line["roofline_build"] is None
