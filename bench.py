@@ -228,10 +228,17 @@ def cpu_baseline(args, w):
     e_s = min(100_000, w["ins_src"].shape[0])
     q_s = min(1_000_000, w["q_u"].shape[0])
     t_ins, t_q = run_oracle_step(ref, w, step_batches(e_s, args.batch), q_s, cores)
+    # the paper's sequential DBL: the same insertions, a tenth of the queries on one thread
+    q_1 = max(1, q_s // 10)
+    t_ins1, t_q1 = run_oracle_step(ref, w, step_batches(e_s, args.batch), q_1, 1)
     return {"value": (e_s + q_s) / (t_ins + t_q), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {e_s} insertions (sequential, Algorithm 3) + first {q_s} queries "
                       f"(Algorithm 2, {cores} threads) of the step; same 1:10 mix",
-            "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q}
+            "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q,
+            "single_thread": {"value": (e_s + 10 * q_1) / (t_ins1 + 10 * t_q1), "unit": UNIT,
+                              "sample": f"first {e_s} insertions + first {q_1} queries on one thread, "
+                                        f"queries scaled to the 1:10 mix",
+                              "inserted_edges_per_s": e_s / t_ins1, "queries_per_s": q_1 / t_q1}}
 
 
 # ------------------------------------------------------------------ GPU arm

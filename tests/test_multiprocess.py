@@ -75,3 +75,20 @@ def test_rooflines_also_against_nominal_peaks():
     assert abs(line["roofline"]["frac_of_nominal"] - 0.1) < 1e-12
     assert abs(line["roofline_scorer"]["frac_of_nominal"] - 0.2) < 1e-12
     assert line["roofline"]["frac"] == 0.1 and line["roofline_build"] is None
+
+
+def test_cpu_baseline_reports_all_cores_and_one_thread():
+    """The oracle as it stands on a sample of the step: all host cores (the
+    paper's parallel DBL-P analogue) and one thread (its sequential DBL)."""
+    import argparse
+
+    import bench
+    import dbl_inputs
+    import oracle
+    oracle.build()
+    dbl_inputs.build()
+    w = dbl_inputs.workload("tiny")
+    r = bench.cpu_baseline(argparse.Namespace(k=64, kprime=64, batch=1000), w)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    one = r["single_thread"]
+    assert one["value"] > 0 and one["queries_per_s"] > 0 and one["inserted_edges_per_s"] > 0
