@@ -334,6 +334,35 @@ def test_vertex_insertion_matches_closure(seed):
     _check_codes(R, exp, uu.ravel(), vv.ravel(), code)
 
 
+@pytest.mark.parametrize("rule,r", [("A", 1), ("C", 3)])
+def test_vertex_insertion_with_selection_rules_equals_rebuild(rule, r):
+    """Table 3 landmarks, M(u) <= r leaves, then new vertices and edges touching
+    them: incremental labels equal a rebuild on the final graph with the same
+    landmark and leaf sets (new vertices are not leaves), and the closure."""
+    rng = np.random.default_rng(61)
+    n0, add = 150, 40
+    s, d = H.random_graph(n0, 420, 9)
+    o = OracleIndex(*H.csr_from_edges(n0, s, d), 64, 64)
+    lm = o.rank_landmarks(rule)
+    lb, lr = o.threshold_leaves(r)
+    o.build(lm, lb, lr)
+    o.add_vertices(add)
+    n = n0 + add
+    es = rng.integers(0, n, 500).astype(np.int32)
+    ed = rng.integers(0, n, 500).astype(np.int32)
+    for b in range(0, 500, 125):
+        o.insert_edges(es[b:b + 125], ed[b:b + 125])
+    fs, fd = np.concatenate([s, es]), np.concatenate([d, ed])
+    lb2 = np.concatenate([lb, np.full(add, -1, np.int32)])
+    lr2 = np.concatenate([lr, np.zeros(add, np.uint8)])
+    rebuilt = OracleIndex(*H.csr_from_edges(n, fs, fd), 64, 64).build(lm, lb2, lr2)
+    R = H.closure(n, fs, fd)
+    exp = H.expected_labels(R, lm, lb2, lr2, 64, 64)
+    for e, g, b2, nm in zip(exp, o.labels(), rebuilt.labels(), ["dl_in", "dl_out", "bl_in", "bl_out"]):
+        assert np.array_equal(e, g), nm
+        assert np.array_equal(g, b2), nm
+
+
 def test_vertex_insertion_rejects_bad_counts_and_ids():
     o = OracleIndex(*H.csr_from_edges(5, [0, 1], [1, 2]), 64, 64).build()
     with pytest.raises(ValueError):
