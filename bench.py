@@ -1,25 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the DBL reachability index on GB300.
 
-Workload "social" (the stand-in for LiveJournal's size in Table 2 of the
-paper): directed R-MAT (a,b,c,d = .57,.19,.19,.05), n = 4,847,571,
-m = 68,993,773, seed 2; k = 64 landmarks, k' = 64 leaf buckets.  One step =
-restore the built index, insert 1,000,000 new edges in batches of 100,000
-(label repair, Algorithm 3 and its mirrors) and answer 10,000,000 mixed
-queries (Algorithm 2: half uniform pairs, half (u, end of a random forward
-walk from u)).  Inputs are resident in HBM before the timed region; the
-labels (155 MB), pair arrays (80 MB) and adjacency (590 MB) exceed the 126 MB
-L2, so no flush is needed between steps.
+Default workload "large" (the learned-landmark configuration): directed R-MAT
+(a,b,c,d = .57,.19,.19,.05), n = 2^24, m = 2^28 (Graph500 edge factor 16),
+seed 3; k = 64 landmarks and k' = 64 leaf buckets, with the same comparison
+at k = 128.  One step = restore the built index, insert 1,000,000 new edges in
+batches of 100,000 (label repair, Algorithm 3 and its mirrors) and answer
+10,000,000 mixed queries (Algorithm 2: half uniform pairs, half (u, end of a
+random forward walk from u)).  Inputs are resident in HBM before the timed
+region; the labels (512 MB at k = 64), pair arrays (80 MB) and adjacency
+(2 GB) exceed the 126 MB L2, so no flush is needed between steps.
 
-Forms, all on the same graph and inputs:
+Forms, all on the same graph and inputs (none of them with per-kernel timing):
   plain    degree landmarks; frontier levels driven from the host (one launch
            and one read-back per level)
   batched  degree landmarks; persistent cooperative kernels, no host round trip
-  graph    batched, with the whole step captured once as a CUDA graph
-  learned  learned landmarks (scorer trained on sampled query outcomes),
+  graph    batched, each step part (restore, insertions, queries) replayed as
+           a captured CUDA graph
+  learned  top-k learned landmarks (scorer trained on sampled query outcomes),
            batched + graph: the headline `value`
+A separate pass of the learned form with per-kernel CUDA events gives the
+roofline figures.  Extra forms on the social workload (n = 4,847,571,
+m = 68,993,773): insertion batches of 1k, 10k and 100k edges, and the batched
+configuration (k = 128, log-uniform batch sizes).
 Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle on
-the same step instead.
+the same workload instead.
 """
 from __future__ import annotations
 
@@ -167,6 +172,24 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        outp = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in outp.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_oracle_step(ref, w, batches, nq, threads):
     ref.rewind()
     t0 = time.perf_counter()
@@ -178,15 +201,20 @@ def run_oracle_step(ref, w, batches, nq, threads):
     return t1 - t0, t2 - t1
 
 
-def workload_config(args, w, form="learned+batched (persistent kernels, CUDA graph)"):
-    return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "k": args.k, "kprime": args.kprime,
-            "insert_batch": args.batch, "inserted_edges_per_step": int(w["ins_src"].shape[0]),
+def workload_config(args, w, form="learned+batched (persistent kernels, CUDA graphs)"):
+    return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "seed": int(w["seed"]), "k": args.k,
+            "kprime": args.kprime, "k2": args.k2, "insert_batch": args.batch,
+            "inserted_edges_per_step": int(w["ins_src"].shape[0]),
             "queries_per_step": int(w["q_u"].shape[0]), "form": form,
             "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
 
 
 # ------------------------------------------------------------------ reference arm
 def bench_reference(args):
+    """The CPU oracle on the same workload: each step a bounded sample of the
+    GPU step (its first 100,000 insertions, applied one by one with
+    Algorithm 3, and its first 1,000,000 queries on every host core: the same
+    1:10 mix), so that the whole run ends within minutes."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -196,7 +224,8 @@ def bench_reference(args):
     cores = cpu_cores()
     ref = oracle.OracleIndex(w["row_ptr"], w["col"], args.k, args.kprime).build(nthreads=cores)
     ref.mark()
-    E, Q = w["ins_src"].shape[0], w["q_u"].shape[0]
+    E = min(args.ref_insertions, int(w["ins_src"].shape[0]))
+    Q = min(args.ref_queries, int(w["q_u"].shape[0]))
     batches = step_batches(E, args.batch)
     for _ in range(args.warmup):
         run_oracle_step(ref, w, batches, Q, cores)
@@ -207,14 +236,15 @@ def bench_reference(args):
         t_q += b
     total = t_ins + t_q
     value = args.steps * (E + Q) / total
+    sample = (f"per step: the first {E} insertions of the GPU step (sequential, Algorithm 3) + its first {Q} "
+              f"queries (Algorithm 2, {cores} threads)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(args, w, "CPU oracle (sequential insertion repair, threaded queries)"),
             "components": {"queries_per_s": args.steps * Q / t_q, "inserted_edges_per_s": args.steps * E / t_ins},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"full step: {E} sequential insertions (Algorithm 3) + {Q} queries "
-                                       f"(Algorithm 2, {cores} threads)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -223,18 +253,21 @@ def cpu_baseline(args, w):
     """The oracle, as it stands, on a bounded sample of the same step."""
     import oracle
     cores = cpu_cores()
+    t0 = time.perf_counter()
     ref = oracle.OracleIndex(w["row_ptr"], w["col"], args.k, args.kprime).build(nthreads=cores)
+    build_s = time.perf_counter() - t0
     ref.mark()
-    e_s = min(100_000, w["ins_src"].shape[0])
-    q_s = min(1_000_000, w["q_u"].shape[0])
+    e_s = min(args.ref_insertions, w["ins_src"].shape[0])
+    q_s = min(args.ref_queries, w["q_u"].shape[0])
     t_ins, t_q = run_oracle_step(ref, w, step_batches(e_s, args.batch), q_s, cores)
     # the paper's sequential DBL: the same insertions, a tenth of the queries on one thread
     q_1 = max(1, q_s // 10)
     t_ins1, t_q1 = run_oracle_step(ref, w, step_batches(e_s, args.batch), q_1, 1)
-    return {"value": (e_s + q_s) / (t_ins + t_q), "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": (e_s + q_s) / (t_ins + t_q), "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"first {e_s} insertions (sequential, Algorithm 3) + first {q_s} queries "
                       f"(Algorithm 2, {cores} threads) of the step; same 1:10 mix",
-            "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q,
+            "inserted_edges_per_s": e_s / t_ins, "queries_per_s": q_s / t_q, "oracle_build_s": build_s,
             "single_thread": {"value": (e_s + 10 * q_1) / (t_ins1 + 10 * t_q1), "unit": UNIT,
                               "sample": f"first {e_s} insertions + first {q_1} queries on one thread, "
                                         f"queries scaled to the 1:10 mix",
@@ -283,23 +316,69 @@ class Inputs:
         self.code = torch.empty(w["q_u"].shape[0], dtype=torch.uint8, device=dev)
 
 
-def make_step(ix, I, batches, events=False):
-    import torch
+class Step:
+    """One step of a form, in three parts: restore the built index, insert the
+    step's edges batch by batch, answer the step's queries batch by batch.
+    Eager (each part launched from the host) or replayed as three captured
+    CUDA graphs; CUDA events on the current stream between the parts give the
+    split of every step."""
 
-    def step():
-        ix.restore(0)
-        if events:
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            ev[0].record()
-        for a, b in batches:
-            ix.insert_edges(I.src[a:b], I.dst[a:b])
-        if events:
-            ev[1].record()
-        ix.query(I.qu, I.qv, out=(I.ans, I.code))
-        if events:
-            ev[2].record()
-            return ev
-    return step
+    def __init__(self, ix, I, batches, qbatches, use_graph: bool, queries: bool = True):
+        self.ix, self.I, self.batches, self.qbatches = ix, I, batches, qbatches
+        self.use_graph, self.queries = use_graph, queries
+        self.graphs = None
+        self.launches_per_step = None
+
+    def restore(self):
+        self.ix.restore(0)
+
+    def inserts(self):
+        I = self.I
+        for a, b in self.batches:
+            self.ix.insert_edges(I.src[a:b], I.dst[a:b])
+
+    def query(self):
+        if not self.queries:
+            return
+        I = self.I
+        for a, b in self.qbatches:
+            self.ix.query(I.qu[a:b], I.qv[a:b], out=(I.ans[a:b], I.code[a:b]))
+
+    def parts(self):
+        return (self.restore, self.inserts, self.query)
+
+    def capture(self):
+        """Capture the three parts (after warm-up) and count their launches."""
+        import torch
+        if not self.use_graph:
+            return
+        l0 = self.ix.info()["launches"]
+        self.graphs = []
+        for i, part in enumerate(self.parts()):
+            if i == 2 and not self.queries:
+                self.graphs.append(None)  # nothing to capture
+                continue
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                part()
+            self.graphs.append(g)
+        self.launches_per_step = self.ix.info()["launches"] - l0
+        for g in self.graphs:
+            if g is not None:
+                g.replay()
+        torch.cuda.synchronize()
+        self.ix.sync()
+
+    def __call__(self):
+        import torch
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        run = ([g.replay if g is not None else (lambda: None) for g in self.graphs] if self.graphs
+               else list(self.parts()))
+        for i, f in enumerate(run):
+            ev[i].record()
+            f()
+        ev[3].record()
+        return ev
 
 
 def time_steps(step, steps, world, tdist, sampler=None, profile=False):
@@ -325,87 +404,105 @@ def time_steps(step, steps, world, tdist, sampler=None, profile=False):
     return e0.elapsed_time(e1), outs, clocks
 
 
-def run_form(name, args, w, I, landmarks, leaves, batches, world, tdist, local):
-    """Build the form's index and time `steps` steps.  Returns a dict."""
+FORM_FLAGS = {  # library flags of each form (FLAG_TIMING only in the separate timing pass)
+    "plain": 0, "batched": "P|A", "graph": "P|A", "learned": "P|A", "learned_timing": "T|P|A",
+}
+
+
+def form_flags(name):
+    import paper_2101_09441_gb300 as dbl
+    spec = FORM_FLAGS[name]
+    f = 0
+    for c in (spec.split("|") if spec else []):
+        f |= {"P": dbl.FLAG_PERSISTENT, "A": dbl.FLAG_ASYNC, "T": dbl.FLAG_TIMING}[c]
+    return f
+
+
+def decided_by(code_t):
+    import torch
+    code = torch.bincount(code_t.long(), minlength=8).cpu().numpy()
+    return {n: int(code[i]) for i, n in enumerate(["undecided", "self", "dl", "bl", "thm1", "thm2", "bfs_pos",
+                                                   "bfs_neg"])}
+
+
+def run_form(name, args, w, I, k, kp, landmarks, leaves, batches, qbatches, world, tdist, local, steps,
+             queries=True, autotune=True, sample_clocks=False, keep=False):
+    """Build the form's index and time `steps` steps (restore, insertions,
+    queries).  Returns a dict (with the index under "ix" when keep)."""
     import torch
 
     import paper_2101_09441_gb300 as dbl
-    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
-    flags = {"plain": dbl.FLAG_TIMING, "batched": dbl.FLAG_TIMING | dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC,
-             "graph": dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC, "learned": dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC,
-             "learned_timing": dbl.FLAG_TIMING | dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC}[name]
+    E = int(batches[-1][1]) if batches else 0
+    Q = int(qbatches[-1][1]) if (queries and qbatches) else 0
+    flags = form_flags(name)
     kw = dict(flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
     if landmarks is not None:
         kw.update(landmarks=landmarks, leaf_buckets=leaves[0], leaf_roles=leaves[1])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = dbl.DBLIndex(I.rp, I.col, args.k, args.kprime, **kw)
+    ix = dbl.DBLIndex(I.rp, I.col, k, kp, **kw)
     ix.sync()
     build_s = time.perf_counter() - t0
     build_t = ix.timings() if flags & dbl.FLAG_TIMING else {}
     ix.snapshot(0)
-    res = {"build_s": build_s}
+    res = {"k": k, "kprime": kp, "landmarks": "learned" if landmarks is not None else "degree",
+           "flags": FORM_FLAGS[name] or "0", "build_s": build_s}
     if build_t:
-        res["build_kernel_ms"] = {k: v[0] for k, v in build_t.items() if v[1]}
+        res["build_kernel_ms"] = {kk: v[0] for kk, v in build_t.items() if v[1]}
         res["build_algorithmic_bytes"] = build_bytes(ix, I, ix.info()["record_bytes"] // 2)
         res["build_edges_relaxed"] = int(ix.stats()[10])
-    if flags & dbl.FLAG_PERSISTENT and not args.no_autotune:
+    if flags & dbl.FLAG_PERSISTENT and autotune and not args.no_autotune and E:
         # autotuned frontier schedule (sample: the step's insertions as one batch
-        # and 1M queries; a few batches of the first hundred thousand edges do not
-        # separate the candidates); the persistent forms keep the fastest
+        # and up to 1M queries); the persistent forms keep the fastest
         # persistent candidate
-        nq = min(1_000_000, Q)
-        tune = ix.autotune(I.src, I.dst, I.qu[:nq], I.qv[:nq], trials=4)
+        nq = min(1_000_000, int(I.qu.numel()))
+        tune = ix.autotune(I.src[:E], I.dst[:E], I.qu[:nq], I.qv[:nq], trials=3)
         team = min(tune["persistent_ms"], key=tune["persistent_ms"].get)
         ix.set_schedule(team, persistent=True)
         res["autotune"] = {"team": team, "persistent_ms": tune["persistent_ms"], "level_ms": tune["level_ms"]}
     use_graph = name in ("graph", "learned")
-    step = make_step(ix, I, batches, events=not use_graph)
+    step = Step(ix, I, batches, qbatches, use_graph, queries)
     for _ in range(args.warmup):
-        step()
+        for f in step.parts():
+            f()
     torch.cuda.synchronize()
     ix.sync()
-    if use_graph:
-        g = torch.cuda.CUDAGraph()
-        l0 = ix.info()["launches"]
-        with torch.cuda.graph(g):
-            step()
-        launches_per_step = ix.info()["launches"] - l0
-        g.replay()
-        torch.cuda.synchronize()
-        ix.sync()
-        timed = g.replay
-    else:
-        timed = step
+    step.capture()
+    if not use_graph:
         ix.timings()
-        l0 = ix.info()["launches"]
-    sampler = ClockSampler(local) if name == "learned" else None
-    total_ms, outs, clocks = time_steps(timed, args.steps, world, tdist, sampler,
-                                        profile=args.profile and name == args.profile_form)
+    l0 = ix.info()["launches"]
+    sampler = ClockSampler(local) if sample_clocks else None
+    total_ms, evs, clocks = time_steps(step, steps, world, tdist, sampler,
+                                       profile=args.profile and name == args.profile_form)
     ix.sync()
     total_ms = max_over_ranks(total_ms, world, tdist, I.qu.device)
-    res.update(ms_per_step=total_ms / args.steps, value=whole_job_rate(args.steps * (E + Q), world, total_ms),
-               gpu_launches=(launches_per_step * args.steps) if use_graph else ix.info()["launches"] - l0)
-    if not use_graph:
-        ins_ms = sum(ev[0].elapsed_time(ev[1]) for ev in outs)
-        q_ms = sum(ev[1].elapsed_time(ev[2]) for ev in outs)
-        res["queries_per_s"] = world * args.steps * Q / (q_ms * 1e-3)
-        res["inserted_edges_per_s"] = world * args.steps * E / (ins_ms * 1e-3)
-        res["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in ix.timings().items() if v[1]}
+    split = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in evs) / steps for i in range(3)]
+    split = [max_over_ranks(x, world, tdist, I.qu.device) for x in split]
+    ms = total_ms / steps
+    res.update(ms_per_step=ms, value=whole_job_rate(steps * (E + Q), world, total_ms),
+               restore_ms=split[0], insert_ms=split[1], query_ms=split[2],
+               value_excl_restore=whole_job_rate(steps * (E + Q), world, steps * (ms - split[0])),
+               inserted_edges_per_s=world * E / (split[1] * 1e-3) if E else None,
+               queries_per_s=world * Q / (split[2] * 1e-3) if Q else None,
+               gpu_launches=(step.launches_per_step * steps) if use_graph else ix.info()["launches"] - l0)
+    if flags & dbl.FLAG_TIMING:
+        res["kernels"] = {kk: {"ms_total": v[0], "launches": v[1]} for kk, v in ix.timings().items() if v[1]}
     # label-repair work of one step (edges relaxed), for the learned-vs-degree judge
     r0 = int(ix.stats()[10])
     ix.restore(0)
-    for a_, b_ in batches:
-        ix.insert_edges(I.src[a_:b_], I.dst[a_:b_])
+    step.inserts()
     ix.sync()
     res["relaxed_per_step"] = int(ix.stats()[10]) - r0
-    ix.query(I.qu, I.qv, out=(I.ans, I.code))
-    ix.sync()
-    code = torch.bincount(I.code.long(), minlength=8).cpu().numpy()
-    res["decided_by"] = {n: int(code[i]) for i, n in enumerate(
-        ["undecided", "self", "dl", "bl", "thm1", "thm2", "bfs_pos", "bfs_neg"])}
+    if queries:
+        step.query()
+        ix.sync()
+        res["decided_by"] = decided_by(I.code[:Q])
+        res["searched"] = res["decided_by"]["bfs_pos"] + res["decided_by"]["bfs_neg"]
     res["clocks"] = clocks
-    res["ix"] = ix
+    if keep:
+        res["ix"] = ix
+    else:
+        ix.close()
     return res
 
 
@@ -486,45 +583,152 @@ def build_roofline(form):
             "teps": relaxed / (ms * 1e-3) if relaxed else None}
 
 
-def roofline(form, ix, args, w, I, batches, persistent=True):
+def roofline(form, ix, steps, w, I, batches, persistent=True):
     """Achieved GB/s of the form's dominant kernel class (library CUDA events
     over the timed region) against the measured HBM copy peak.  In the
     persistent forms the `propagate` class is the insertion kernel (append,
-    seeds and repair in one launch per batch)."""
+    seeds and repair in one launch per batch); its fraction is given both
+    with the append/seed bytes counted and with the repair bytes alone."""
     import torch
     peaks, src = measured_peaks()
     Q = int(w["q_u"].shape[0])
     info = ix.info()
     rec = info["record_bytes"]
-    alg = {"query_label": args.steps * Q * (8 + 2 * rec + 2)}
+    alg = {"query_label": steps * Q * (8 + 2 * rec + 2)}
     kern = form["kernels"]
+    repair_only = None
     if "propagate" in kern:
         prop = changed_bytes(ix, w, batches, torch.diff(I.rp).long(), torch.bincount(I.col.long(), minlength=w["n"]),
                              rec // 2, I.src, I.dst)
-        alg["propagate"] = args.steps * (prop + (insertion_bytes(ix, w, I) if persistent else 0))
-    for k, v in kern.items():
+        alg["propagate"] = steps * (prop + (insertion_bytes(ix, w, I) if persistent else 0))
+        repair_only = steps * prop
+    for kk, v in kern.items():
         v["ms_per_launch"] = v["ms_total"] / v["launches"]
-        if k in alg and v["ms_total"] > 0:
-            v["algorithmic_bytes_per_launch"] = alg[k] / v["launches"]
-            v["achieved_gbs"] = alg[k] / (v["ms_total"] * 1e-3) / 1e9
+        if kk in alg and v["ms_total"] > 0:
+            v["algorithmic_bytes_per_launch"] = alg[kk] / v["launches"]
+            v["achieved_gbs"] = alg[kk] / (v["ms_total"] * 1e-3) / 1e9
             v["frac_of_hbm"] = v["achieved_gbs"] / peaks["hbm_gbs"]
-    dom = max(kern, key=lambda k: kern[k]["ms_total"])
-    cand = dom if "achieved_gbs" in kern[dom] else max((k for k in kern if "achieved_gbs" in kern[k]),
-                                                       key=lambda k: kern[k]["ms_total"])
-    def obj(k):
-        ach = kern[k]["achieved_gbs"]
-        traffic = NCU_TRAFFIC[k][0] if k in NCU_TRAFFIC and NCU_TRAFFIC[k][1] == source_sha(k) else None
-        return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+    dom = max(kern, key=lambda kk: kern[kk]["ms_total"])
+    cand = dom if "achieved_gbs" in kern[dom] else max((kk for kk in kern if "achieved_gbs" in kern[kk]),
+                                                       key=lambda kk: kern[kk]["ms_total"])
+
+    def obj(kk):
+        ach = kern[kk]["achieved_gbs"]
+        traffic = NCU_TRAFFIC[kk][0] if kk in NCU_TRAFFIC and NCU_TRAFFIC[kk][1] == source_sha(kk) else None
+        return {"kernel": kk, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
-                "algorithmic_bytes_per_launch": kern[k]["algorithmic_bytes_per_launch"],
-                "ms_per_launch": kern[k]["ms_per_launch"]}
+                "algorithmic_bytes_per_launch": kern[kk]["algorithmic_bytes_per_launch"],
+                "ms_per_launch": kern[kk]["ms_per_launch"]}
     out = obj(cand)
     out["dominant_kernel_by_time"] = dom
-    if cand == "propagate" and form.get("relaxed_per_step") is not None:
-        # repair traversal rate: edges relaxed per second of insertion-kernel time
-        out["edges_relaxed_per_launch"] = form["relaxed_per_step"] * args.steps / kern[cand]["launches"]
-        out["teps"] = form["relaxed_per_step"] * args.steps / (kern[cand]["ms_total"] * 1e-3)
+    if cand == "propagate":
+        if repair_only is not None:
+            ach_r = repair_only / (kern[cand]["ms_total"] * 1e-3) / 1e9
+            out["repair_bytes_only"] = {"algorithmic_bytes_per_launch": repair_only / kern[cand]["launches"],
+                                        "achieved": ach_r, "frac": ach_r / peaks["hbm_gbs"]}
+        if form.get("relaxed_per_step") is not None:
+            # repair traversal rate: edges relaxed per second of insertion-kernel time
+            out["edges_relaxed_per_launch"] = form["relaxed_per_step"] * steps / kern[cand]["launches"]
+            out["teps"] = form["relaxed_per_step"] * steps / (kern[cand]["ms_total"] * 1e-3)
     return out, (obj("query_label") if "achieved_gbs" in kern.get("query_label", {}) else None)
+
+
+def public(f):
+    return {kk: v for kk, v in f.items() if kk not in ("ix", "clocks")}
+
+
+def train_learned(args, w, I, k, kp, batches, dev):
+    """Train the scorer on the outcomes of a separate sample of queries on the
+    plain index (degree landmarks) after the step's insertions; returns the
+    learned landmark slots, the plain index's leaves, and the training facts."""
+    import torch
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    from paper_2101_09441_gb300 import learned as L
+    E = int(batches[-1][1])
+    t0 = time.perf_counter()
+    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], args.train_queries, w["seed"] + 300, False,
+                                w["ins_src"], w["ins_dst"])
+    tu, tv = torch.from_numpy(tu).to(dev), torch.from_numpy(tv).to(dev)
+    plain_ix = dbl.DBLIndex(I.rp, I.col, k, kp, edge_capacity=max(E, 1 << 20))
+    for a, b in batches:
+        plain_ix.insert_edges(I.src[a:b], I.dst[a:b])
+    base_slots = max(1, k // 8)
+    scores, tinfo = L.train_scorer(plain_ix, tu, tv, base_slots, steps=args.train_steps)
+    lm = L.select_landmarks(plain_ix, scores, k, base_slots)
+    _, lb, lr_ = plain_ix.selection()
+    torch.cuda.synchronize()
+    info = {"train_s": time.perf_counter() - t0, "base_slots": base_slots,
+            **{kk: v for kk, v in tinfo.items() if kk != "losses"}, "final_loss": tinfo["losses"][-1]}
+    return lm, (lb, lr_), info, plain_ix
+
+
+def learned_judge(learned, ref):
+    """Keep the learned landmarks only if they send no more pairs to the
+    search than the degree rule and keep the insertions' repair cheap."""
+    from paper_2101_09441_gb300 import learned as L
+    return not (learned["searched"] <= ref["searched"] and L.repair_ok(ref["relaxed_per_step"],
+                                                                        learned["relaxed_per_step"]))
+
+
+def gain(deg, lrn):
+    """What the learned landmarks change against the degree rule, same k."""
+    keys = ("ms_per_step", "value", "queries_per_s", "inserted_edges_per_s", "relaxed_per_step", "searched")
+    out = {"degree": {kk: deg.get(kk) for kk in keys}, "learned": {kk: lrn.get(kk) for kk in keys}}
+    out["degree"]["decided_by_dl"] = deg["decided_by"]["dl"]
+    out["learned"]["decided_by_dl"] = lrn["decided_by"]["dl"]
+    out["dl_decided_delta"] = lrn["decided_by"]["dl"] - deg["decided_by"]["dl"]
+    out["searched_delta"] = lrn["searched"] - deg["searched"]
+    out["value_ratio"] = lrn["value"] / deg["value"]
+    return out
+
+
+def restore_batches(sizes):
+    out, a = [], 0
+    for s in sizes:
+        out.append((a, a + int(s)))
+        a += int(s)
+    return out
+
+
+def bench_extras(args, world, tdist, local, dev):
+    """Extra timed forms on the social workload (stand-in for LiveJournal's
+    size): insertion throughput at batch sizes 1k, 10k and 100k (persistent +
+    CUDA graph, and plain), and the batched configuration (k = 128,
+    log-uniform insertion batches of 1..200k edges and query batches of
+    1k..4M pairs) in the graph form against the plain form."""
+    import dbl_inputs
+    w = dbl_inputs.workload("social")
+    I = Inputs(w, dev)
+    E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
+    steps = args.extra_steps
+    out = {"workload": "social", "n": int(w["n"]), "m": int(w["m"]), "steps": steps,
+           "inserted_edges_per_step": E, "queries_per_step": Q}
+    bs = {}
+    for b in (1000, 10_000, 100_000):
+        batches = step_batches(E, b)
+        row = {}
+        for name in ("graph", "plain"):
+            r = run_form(name, args, w, I, 64, 64, None, None, batches, None, world, tdist, local, steps,
+                         queries=False, autotune=False)
+            row[name] = {kk: r[kk] for kk in ("insert_ms", "restore_ms", "inserted_edges_per_s", "gpu_launches",
+                                              "relaxed_per_step")}
+            row[name]["us_per_batch"] = 1e3 * r["insert_ms"] / len(batches)
+        row["graph_vs_plain"] = row["graph"]["inserted_edges_per_s"] / row["plain"]["inserted_edges_per_s"]
+        bs[str(b)] = row
+    out["insert_batch_sizes"] = bs
+    ins_sizes = dbl_inputs.loguniform_batches(E, 1, 200_000, 11)
+    q_sizes = dbl_inputs.loguniform_batches(Q, 1000, 4_000_000, 12)
+    ib, qb = restore_batches(ins_sizes), restore_batches(q_sizes)
+    cfg = {"k": 128, "kprime": 64, "insert_batches": len(ib), "query_batches": len(qb),
+           "insert_sizes": "floor(exp(U[0, ln 200001)))", "query_sizes": "floor(exp(U[ln 1000, ln 4000001)))"}
+    for name in ("graph", "plain"):
+        r = run_form(name, args, w, I, 128, 64, None, None, ib, qb, world, tdist, local, steps, autotune=False)
+        cfg[name] = public(r)
+    cfg["graph_vs_plain"] = cfg["graph"]["value"] / cfg["plain"]["value"]
+    out["batched_config"] = cfg
+    return out
 
 
 def bench_gpu(args):
@@ -533,7 +737,6 @@ def bench_gpu(args):
 
     import dbl_inputs
     import paper_2101_09441_gb300 as dbl
-    from paper_2101_09441_gb300 import learned as L
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -544,49 +747,48 @@ def bench_gpu(args):
     w = dbl_inputs.workload(args.workload)
     E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
     batches = step_batches(E, args.batch)
+    qbatches = [(0, Q)]
     I = Inputs(w, dev)
+    k, kp, k2 = args.k, args.kprime, args.k2
+    S = args.steps
+    common = (world, tdist, local)
     forms = {}
     for name in ("plain", "batched", "graph"):
         if name in args.forms:
-            forms[name] = run_form(name, args, w, I, None, None, batches, world, tdist, local)
+            forms[name] = run_form(name, args, w, I, k, kp, None, None, batches, qbatches, *common, S)
 
-    # ---- learned landmarks: trained on the outcomes of a separate sample of
-    # 1M queries on the index after the step's insertions
-    t0 = time.perf_counter()
-    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], args.train_queries, w["seed"] + 300, False,
-                                w["ins_src"], w["ins_dst"])
-    tu, tv = torch.from_numpy(tu).to(dev), torch.from_numpy(tv).to(dev)
-    plain_ix = dbl.DBLIndex(I.rp, I.col, args.k, args.kprime, edge_capacity=max(E, 1 << 20))
-    for a, b in batches:
-        plain_ix.insert_edges(I.src[a:b], I.dst[a:b])
-    base_slots = max(1, args.k // 8)
-    scores, tinfo = L.train_scorer(plain_ix, tu, tv, base_slots, steps=args.train_steps)
-    lm = L.select_landmarks(plain_ix, scores, args.k, base_slots)
-    _, lb, lr_ = plain_ix.selection()
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+    # ---- learned landmarks (top-k scored) against degree landmarks, same k
+    lm, leaves, linfo, plain_ix = train_learned(args, w, I, k, kp, batches, dev)
     roof_scorer = scorer_roofline(plain_ix)
     plain_ix.close()
-    learned = run_form("learned", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
-    learned_t = run_form("learned_timing", args, w, I, lm, (lb, lr_), batches, world, tdist, local)
-    # fallback: keep the degree rule if the learned set sends more pairs to the
-    # search or makes the insertions' repair much dearer (edges relaxed per step)
-    dec_l = learned["decided_by"]
+    learned = run_form("learned", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
+                       sample_clocks=True, keep=True)
+    learned_t = run_form("learned_timing", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
+                         keep=True)
     ref_form = forms.get("graph") or forms.get("batched") or forms.get("plain")
-    dec_p = ref_form["decided_by"] if ref_form else dec_l
-    rep_l = learned["relaxed_per_step"]
-    rep_p = ref_form["relaxed_per_step"] if ref_form else rep_l
-    fallback = (dec_l["bfs_pos"] + dec_l["bfs_neg"] > dec_p["bfs_pos"] + dec_p["bfs_neg"]
-                or not L.repair_ok(rep_p, rep_l))
+    fallback = learned_judge(learned, ref_form) if ref_form else False
     head = forms["graph"] if (fallback and "graph" in forms) else learned
-    roof, roof_label = roofline(learned_t, learned_t["ix"], args, w, I, batches)
+    roof, roof_label = roofline(learned_t, learned_t["ix"], S, w, I, batches)
+    learned_t["ix"].close()
+
+    # ---- the same comparison at k2 landmarks (two words per direction at 128)
+    k2_forms = {}
+    if k2:
+        for name in ("plain", "graph"):
+            k2_forms[name] = run_form(name, args, w, I, k2, kp, None, None, batches, qbatches, *common, S)
+        lm2, leaves2, linfo2, pix2 = train_learned(args, w, I, k2, kp, batches, dev)
+        pix2.close()
+        k2_forms["learned"] = run_form("learned", args, w, I, k2, kp, lm2, leaves2, batches, qbatches, *common, S)
+        k2_forms["learned"]["training"] = linfo2
+        k2_forms["fallback_to_degree_rule"] = learned_judge(k2_forms["learned"], k2_forms["graph"])
+        k2_forms["learned_vs_plain"] = k2_forms["learned"]["value"] / k2_forms["plain"]["value"]
 
     # ---- end to end through the host-buffer C-ABI calls, headline index
     ix = learned["ix"]
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
     h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
-    e2e_steps = 0 if args.no_e2e else args.steps
+    e2e_steps = 0 if args.no_e2e else S
 
     def e2e_step():
         ix.restore(0)
@@ -598,36 +800,44 @@ def bench_gpu(args):
         for _ in range(args.warmup):  # the host forms' staging buffers are allocated here
             e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, tdist, dev)
+    ix.close()
 
-    def public(f):
-        return {k: v for k, v in f.items() if k not in ("ix", "clocks")}
+    extras = None if args.no_extras else bench_extras(args, *common, dev)
 
-    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    gain_k = gain(ref_form, learned) if ref_form else None
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": S,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": workload_config(args, w),
-            "forms": {**{k: public(v) for k, v in forms.items()}, "learned": public(learned),
+            "forms": {**{kk: public(v) for kk, v in forms.items()}, "learned": public(learned),
                       "learned_timing_pass": public(learned_t)},
             "learned_vs_plain": head["value"] / forms["plain"]["value"] if "plain" in forms else None,
-            "learned": {"fallback_to_degree_rule": bool(fallback), "train_s": train_s, "base_slots": base_slots,
-                        **{k: v for k, v in tinfo.items() if k != "losses"}, "final_loss": tinfo["losses"][-1]},
+            "learned": {"fallback_to_degree_rule": bool(fallback), **linfo},
+            "learned_gain": {f"k{k}": gain_k,
+                             **({f"k{k2}": gain(k2_forms["graph"], k2_forms["learned"])} if k2 else {})},
+            f"forms_k{k2}": {kk: (public(v) if isinstance(v, dict) else v) for kk, v in k2_forms.items()} if k2 else None,
+            "restore": {"ms": head["restore_ms"], "share_of_step": head["restore_ms"] / head["ms_per_step"],
+                        "value_excl_restore": head["value_excl_restore"],
+                        "note": "dbl_restore returns the index to its built state at the start of every step "
+                                "(labels and adjacency metadata copied back); it is not part of the method"},
             "roofline": roof,
             "roofline_label_test": roof_label,
             "roofline_build": build_roofline(learned_t),
             "roofline_scorer": roof_scorer,
             "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
+            "extras": extras,
             "clocks": learned["clocks"],
             "gpu_launches": head["gpu_launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
-    for f in list(forms.values()) + [learned, learned_t]:
-        f["ix"].close()
     add_nominal(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -806,7 +1016,7 @@ def bench_sweep(args):
                           query_unroll=qpt, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING)
         ix.sync()
         ix.snapshot(0)
-        step = make_step(ix, I, batches)
+        step = Step(ix, I, batches, [(0, Q)], use_graph=False)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -845,9 +1055,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dbl", "reference"], default="dbl")
-    ap.add_argument("--workload", default="social", choices=["social", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "social", "tiny"])
     ap.add_argument("--batch", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--k2", type=int, default=128, help="second landmark count compared (0: none)")
     ap.add_argument("--kprime", type=int, default=64)
     ap.add_argument("--team", type=int, default=0, help="frontier team width; 0: library default (1)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the persistent forms")
@@ -855,7 +1066,11 @@ def main():
     ap.add_argument("--train-queries", type=int, default=1_000_000)
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-insertions", type=int, default=100_000, help="oracle sample: insertions per step")
+    ap.add_argument("--ref-queries", type=int, default=1_000_000, help="oracle sample: queries per step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra forms on the social workload")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each extra form")
     ap.add_argument("--profile", action="store_true",
                     help="bracket one form's timed region with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     ap.add_argument("--profile-form", default="learned_timing")

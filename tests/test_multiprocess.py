@@ -88,7 +88,8 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     oracle.build()
     dbl_inputs.build()
     w = dbl_inputs.workload("tiny")
-    r = bench.cpu_baseline(argparse.Namespace(k=64, kprime=64, batch=1000), w)
-    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0
+    r = bench.cpu_baseline(argparse.Namespace(k=64, kprime=64, batch=1000, ref_insertions=10_000,
+                                              ref_queries=100_000), w)
+    assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0 and r["cpu_model"]
     one = r["single_thread"]
     assert one["value"] > 0 and one["queries_per_s"] > 0 and one["inserted_edges_per_s"] > 0
