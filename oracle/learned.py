@@ -12,7 +12,11 @@ which pairs the DL test decides changes (Lemma 1 holds for any landmark set).
                  u_j reaching c and c reaching v_j -- exactly the pairs that
                  DL_out(u_j) and DL_in(v_j) would share if c were a landmark
                  (Lemma 1 with L = {c}).
-* ``mlp_*``      16-128-128-1 ReLU network, squared loss, plain definitions.
+* ``mlp_*``      16-128-128-1 ReLU network, squared loss, plain definitions;
+                 optionally with the stored activations rounded to bf16, the
+                 network's storage type.
+* ``sgd_momentum`` the training step: momentum SGD on element-wise clipped
+                 gradients.
 """
 from __future__ import annotations
 
@@ -101,13 +105,33 @@ def coverage(row_ptr, col, u, v) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ the network
-def mlp_forward(X, P):
+def _identity(a):
+    return a
+
+
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the
+    8-bit-significand storage type of the network's operands.  Written from
+    the format's definition: keep the top 16 bits of the float32 pattern,
+    rounding on the 16 bits dropped."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.where(np.isfinite(f), out, f.astype(np.float64)).reshape(np.shape(a))
+
+
+def mlp_forward(X, P, q=_identity):
     """X [R,16]; P = dict(W1 [16,128], b1, W2 [128,128], b2, w3 [128], b3).
-    Returns y [R] and the cache for mlp_backward."""
+    Returns y [R] and the cache for mlp_backward.  `q` rounds the stored
+    activations H1, H2 (identity: the plain definition; bf16_round: the
+    network evaluated with bf16 activations, as its tensor-core kernels store
+    them)."""
     Z1 = X @ P["W1"] + P["b1"]
-    H1 = np.maximum(Z1, 0.0)
+    H1 = q(np.maximum(Z1, 0.0))
     Z2 = H1 @ P["W2"] + P["b2"]
-    H2 = np.maximum(Z2, 0.0)
+    H2 = q(np.maximum(Z2, 0.0))
     y = H2 @ P["w3"] + P["b3"]
     return y, (X, Z1, H1, Z2, H2)
 
@@ -117,23 +141,35 @@ def mlp_loss(y, t):
     return 0.5 * np.mean((y - t) ** 2)
 
 
-def mlp_backward(P, cache, y, t):
-    """Gradients of mlp_loss with respect to every parameter (chain rule)."""
+def mlp_backward(P, cache, y, t, q=_identity):
+    """Gradients of mlp_loss with respect to every parameter (chain rule).
+    `q` rounds the stored backward activations dZ2, dZ1 (as in mlp_forward)."""
     X, Z1, H1, Z2, H2 = cache
     R = X.shape[0]
     dy = (y - t) / R
     g = {"w3": H2.T @ dy, "b3": dy.sum()}
-    dZ2 = np.outer(dy, P["w3"]) * (Z2 > 0)
+    dZ2 = q(np.outer(dy, P["w3"]) * (H2 > 0))
     g["W2"] = H1.T @ dZ2
     g["b2"] = dZ2.sum(axis=0)
-    dZ1 = (dZ2 @ P["W2"].T) * (Z1 > 0)
+    dZ1 = q((dZ2 @ P["W2"].T) * (H1 > 0))
     g["W1"] = X.T @ dZ1
     g["b1"] = dZ1.sum(axis=0)
     return g
 
 
-def sgd_momentum(P, g, V, lr, mu):
-    """v <- mu*v + g; p <- p - lr*v, for every parameter."""
+CLIP = 1.0  # element-wise gradient clip of the scorer's training step
+
+
+def clip_grad(g, c=CLIP):
+    """Each gradient element limited to [-c, c]; a non-finite element is 0."""
+    g = np.asarray(g, dtype=np.float64)
+    return np.where(np.isfinite(g), np.clip(g, -c, c), 0.0)
+
+
+def sgd_momentum(P, g, V, lr, mu, clip=CLIP):
+    """v <- mu*v + clip(g); p <- p - lr*v, for every parameter (clip=None:
+    no clipping)."""
     for k in P:
-        V[k] = mu * V[k] + g[k]
+        gk = g[k] if clip is None else clip_grad(g[k], clip)
+        V[k] = mu * V[k] + gk
         P[k] = P[k] - lr * V[k]

@@ -183,3 +183,123 @@ def random_leaves(n: int, kprime: int, frac: float, seed: int):
     role = (rng.random(n) < frac).astype(np.uint8) | ((rng.random(n) < frac).astype(np.uint8) << 1)
     bucket = np.where(role > 0, rng.integers(0, kprime, n), -1).astype(np.int32)
     return bucket, role.astype(np.uint8)
+
+
+# ---------------------------------------------------------------- scorer error bound
+# The scorer's network computes with bf16 operands (features, weights, stored
+# activations) and fp32 accumulation.  The oracle evaluates the same
+# definition in fp64 with the same bf16 roundings (oracle.learned, q =
+# bf16_round).  Two such evaluations differ only by (a) accumulation order and
+# fp32 rounding in every sum of K terms, at most GAMMA_UNIT * K times the sum
+# of the absolute terms; (b) a bf16 rounding whose input differs: rounding
+# (and ReLU) are monotone, so if the input is known within e of v, the
+# rounded value lies in [q(v - e), q(v + e)], and it equals q(v) unless a
+# rounding boundary falls inside; (c) a ReLU mask that may differ where the
+# pre-activation is within its own error of zero.  mlp_error_bound carries
+# these as absolute error radii through the forward and backward pass (first
+# order, every term by its absolute value), so every element of the result
+# bounds |GPU - oracle| for that element.
+FP32_U = 2.0 ** -23      # two fp32 units of roundoff
+GAMMA_UNIT = 2.0 ** -22  # per accumulated term (4x fp32's worst case)
+
+
+def _gamma(K):
+    return GAMMA_UNIT * K
+
+
+def _q():
+    from oracle import learned as Lr
+    return Lr.bf16_round
+
+
+def _rounded_radius(v, e, relu=False):
+    """Radius around q(v) (q(relu(v)) with relu) of the rounded value of any
+    input within e of v."""
+    q = _q()
+    f = (lambda x: q(np.maximum(x, 0.0))) if relu else q
+    c = f(v)
+    return np.maximum(np.abs(f(v + e) - c), np.abs(f(v - e) - c))
+
+
+def _masked_radius(D, eD, m, amb):
+    """Radius of q(D' * m') around q(D * m), for D' within eD of D and a mask
+    m' equal to m except where amb (there it may be 0 or 1)."""
+    q = _q()
+    c = q(D * m)
+    hi = np.maximum(np.abs(q(D + eD)), np.abs(q(D - eD)))
+    sure = np.where(m, _rounded_radius(D, eD), 0.0)
+    return np.where(amb, hi + np.abs(c), sure)
+
+
+def mlp_error_bound(P, X, t, eP=None):
+    """Element-wise bounds on |g_gpu - g_oracle| for the gradients of the
+    network with parameters P (W1, W2 already bf16), features X (bf16), targets
+    t; eP: error radii of the parameters themselves (default zero).  Returns
+    (bounds dict per parameter, bound on y, bound on the loss)."""
+    q = _q()
+    eP = eP or {}
+    e = {k: np.asarray(eP.get(k, 0.0)) * np.ones_like(np.asarray(P[k], dtype=np.float64)) for k in P}
+    A = {k: np.abs(np.asarray(P[k], dtype=np.float64)) for k in P}
+    R = X.shape[0]
+    aX = np.abs(X)
+    Z1 = X @ P["W1"] + P["b1"]
+    eZ1 = aX @ e["W1"] + e["b1"] + _gamma(17) * (aX @ A["W1"] + A["b1"])
+    H1 = q(np.maximum(Z1, 0.0))
+    eH1 = _rounded_radius(Z1, eZ1, relu=True)
+    amb1 = (q(np.maximum(Z1 - eZ1, 0.0)) > 0) != (q(np.maximum(Z1 + eZ1, 0.0)) > 0)
+    aH1 = np.abs(H1)
+    Z2 = H1 @ P["W2"] + P["b2"]
+    eZ2 = eH1 @ A["W2"] + (aH1 + eH1) @ e["W2"] + e["b2"] + _gamma(129) * (aH1 @ A["W2"] + A["b2"])
+    H2 = q(np.maximum(Z2, 0.0))
+    eH2 = _rounded_radius(Z2, eZ2, relu=True)
+    amb2 = (q(np.maximum(Z2 - eZ2, 0.0)) > 0) != (q(np.maximum(Z2 + eZ2, 0.0)) > 0)
+    aH2 = np.abs(H2)
+    y = H2 @ P["w3"] + P["b3"]
+    ey = eH2 @ A["w3"] + (aH2 + eH2) @ e["w3"] + e["b3"] + _gamma(129) * (aH2 @ A["w3"] + A["b3"])
+    dy = (y - t) / R
+    edy = ey / R + FP32_U * np.abs(dy)
+    ady = np.abs(dy)
+    out = {"w3": eH2.T @ ady + (aH2 + eH2).T @ edy + _gamma(R) * (aH2.T @ ady),
+           "b3": edy.sum() + _gamma(R) * ady.sum()}
+    D2 = np.outer(dy, P["w3"])
+    eD2 = np.outer(edy, A["w3"]) + np.outer(ady + edy, e["w3"]) + FP32_U * np.abs(D2)
+    m2 = H2 > 0
+    dZ2 = q(D2 * m2)
+    edZ2 = _masked_radius(D2, eD2, m2, amb2)
+    adZ2 = np.abs(dZ2)
+    out["b2"] = edZ2.sum(axis=0) + _gamma(R) * adZ2.sum(axis=0)
+    out["W2"] = eH1.T @ adZ2 + (aH1 + eH1).T @ edZ2 + _gamma(R) * (aH1.T @ adZ2)
+    D1 = dZ2 @ P["W2"].T
+    eD1 = edZ2 @ A["W2"].T + (adZ2 + edZ2) @ e["W2"].T + _gamma(128) * (adZ2 @ A["W2"].T)
+    m1 = H1 > 0
+    dZ1 = q(D1 * m1)
+    edZ1 = _masked_radius(D1, eD1, m1, amb1)
+    adZ1 = np.abs(dZ1)
+    out["b1"] = edZ1.sum(axis=0) + _gamma(R) * adZ1.sum(axis=0)
+    out["W1"] = aX.T @ edZ1 + _gamma(R) * (aX.T @ adZ1)
+    r = y - t
+    eloss = (np.abs(r) * ey).sum() / R + _gamma(R) * (r * r).sum() / (2 * R)
+    return out, ey, eloss
+
+
+def bf16_weight_radius(p, e):
+    """Radius of bf16(p') for any p' within e of p, around bf16(p): a weight
+    whose fp32 value is only known within e may round to a neighbouring bf16
+    value."""
+    from oracle import learned as Lr
+    b = Lr.bf16_round(p)
+    return np.maximum(np.abs(Lr.bf16_round(p + e) - b), np.abs(Lr.bf16_round(p - e) - b))
+
+
+MLP_BLOCKS = (("W1", 0, 2048, (16, 128)), ("b1", 2048, 2176, (128,)), ("W2", 2176, 18560, (128, 128)),
+              ("b2", 18560, 18688, (128,)), ("w3", 18688, 18816, (128,)), ("b3", 18816, 18817, ()))
+
+
+def mlp_unflat(p):
+    """Flat parameter vector (the library's order) -> dict of float64 arrays."""
+    q = np.asarray(p, dtype=np.float64)
+    return {name: q[a:b].reshape(shape) for name, a, b, shape in MLP_BLOCKS}
+
+
+def mlp_flat(d):
+    return np.concatenate([np.asarray(d[name], dtype=np.float64).ravel() for name, _, _, _ in MLP_BLOCKS])
