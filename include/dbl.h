@@ -54,7 +54,8 @@ typedef enum {
     DBL_ERR_TIMEOUT = 4,  /* a device loop exceeded its bound; index poisoned */
     DBL_ERR_CAPACITY = 5, /* inserted-edge capacity exhausted; nothing changed */
     DBL_ERR_BUSY = 6,     /* the serving engine refused admission */
-    DBL_ERR_POISONED = 7  /* an earlier timeout poisoned the index */
+    DBL_ERR_POISONED = 7, /* an earlier timeout poisoned the index */
+    DBL_ERR_CANCELLED = 8 /* the serving engine dropped the request before it ran */
 } dbl_status;
 
 /* Deciding rule of a query, in the order of Algorithm 2. */
@@ -137,7 +138,20 @@ typedef struct {
     int64_t vertex_capacity; /* vertices the index can hold over its life
                               (dbl_add_vertices); 0 or less than n: n; must
                               be below 2^31 */
-    int32_t reserved[4];
+    int32_t initial_slots; /* inserted-edge slots reserved per vertex and
+                              direction at build (rounded up to a power of two,
+                              at most 64): an insertion batch whose endpoints
+                              all still have room appends, seeds and enqueues
+                              in one grid-wide phase; 0: 4; negative: none
+                              (segments are made at the first insertion).
+                              Costs 8 bytes per slot and vertex; dropped when
+                              the pool would not fit 2^31 entries */
+    int32_t build_split;   /* label build: 1 propagates the two directions one
+                              after the other, each over an array of its own
+                              halves (fewer address-translation misses on large
+                              graphs); -1 both together over the records; 0:
+                              split when the records exceed 256 MB */
+    int32_t reserved[2];
 } dbl_options;
 
 /* Fill *opt with the defaults above. */
@@ -149,7 +163,8 @@ void dbl_default_options(dbl_options *opt);
  *                  top-k vertices by M(u) = |Pre(u)| * |Suc(u)| (Section 4.1,
  *                  landmark heuristic), or by the ranking landmark_rule of the
  *                  options picks, ties by smaller id.
- *   k              multiple of 64, 64..256.
+ *   k              16, 32, 64, 128 or 256 (the label sizes of Table 5;
+ *                  below 64 the low k bits of one 64-bit word).
  *   leaf_buckets[n] bucket in [0, kprime) of a leaf, -1 for a non-leaf;
  *                  NULL: zero in-degree vertices seed BL_in and zero
  *                  out-degree vertices seed BL_out (Definition 2; with
@@ -159,7 +174,7 @@ void dbl_default_options(dbl_options *opt);
  *                  (Fibonacci hashing; the paper leaves h open).
  *   leaf_roles[n]  bit0: seeds BL_in, bit1: seeds BL_out; required when
  *                  leaf_buckets is given, ignored otherwise.
- *   kprime         multiple of 64, 64..256.
+ *   kprime         16, 32, 64, 128 or 256, as k.
  * Landmarks and leaf roles are frozen at build; later insertions keep them.
  * The graph arrays are copied; *out receives the new index.
  */
@@ -201,7 +216,9 @@ dbl_status dbl_query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t 
  *   - the device holding the index must be the current device;
  *   - the first call on a device looks up the array's device address (a
  *     cudaGetSymbolAddress, which allocates nothing); make that first call
- *     before any stream capture;
+ *     before any stream capture.  The address is kept for the life of the
+ *     process and is valid only in the context that was current at that
+ *     first call: after a cudaDeviceReset, do not call this entry point;
  *   - all calls in the process share the one array: calls whose device work
  *     overlaps (on different streams, or on different indexes of the same
  *     device) race on it and must be ordered by the caller.  Each call writes
@@ -248,12 +265,36 @@ dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *
 
 /* Save / restore labels and inserted adjacency in snapshot slot 0..3
  * (device-to-device copies on `stream`).  dbl_restore clears a poisoned index and
- * returns to the snapshot's vertex count. */
+ * returns to the snapshot's vertex count.  A restore drops every snapshot
+ * taken after the restored one (insertions after the restore reuse the part
+ * of the edge pool those snapshots name); older snapshots stay valid.  A
+ * captured restore does not drop them when the graph is replayed: after a
+ * replay, restore only to the captured slot or to older ones. */
 dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream);
 dbl_status dbl_restore(dbl_index *ix, int slot, void *stream);
 
 /* Wait for `stream` and return the first error latched on the device. */
 dbl_status dbl_sync(dbl_index *ix, void *stream);
+
+/*
+ * Check of the bounded waits (diagnostic; the paper has no counterpart).  One
+ * cooperative launch of one block per SM on the index's grid-barrier words:
+ * every block but absent_block meets at one barrier, and a block whose wait
+ * polls more than spin_limit (1 .. 2^24) times gives up.  absent_block = -1:
+ * every block arrives and the call returns DBL_OK.  absent_block in
+ * [0, SMs): that block never arrives, the waits run out, and the call returns
+ * DBL_ERR_TIMEOUT with the index poisoned (as after any device loop that gave
+ * up) until dbl_restore; every block still ends, and the barrier words are
+ * reset for the next launch.  Synchronous; labels and graph are untouched.
+ */
+dbl_status dbl_barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent_block, void *stream);
+
+/* Restores and change tracking: dbl_restore copies back only the vertices
+ * whose record or adjacency changed since the last dbl_snapshot or
+ * dbl_restore when its slot is the one the index then equalled, and
+ * everything otherwise (also after a timeout); the device decides, so a
+ * captured restore stays correct when later snapshots change the slot the
+ * index equals. */
 
 /*
  * Counters since build (synchronises `stream`):
@@ -352,13 +393,22 @@ void dbl_server_default_options(dbl_server_options *o);
 dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_server **out);
 dbl_status dbl_server_submit(dbl_server *s, int32_t kind, const int32_t *a_host, const int32_t *b_host, int64_t n,
                              uint8_t *ans_host, uint64_t *ticket);
-/* Block until the request is done; returns its status and latency (s). */
+/* Block until the request is done; returns its status and latency (s);
+ * DBL_ERR_CANCELLED for a cancelled request. */
 dbl_status dbl_server_wait(dbl_server *s, uint64_t ticket, double *latency_s);
+/* Cancel a request that no slot has taken yet: it is dropped from the queue
+ * (its answers are not written; a cancelled insertion is never applied, so
+ * later requests do not observe it) and dbl_server_wait returns
+ * DBL_ERR_CANCELLED for it.  DBL_ERR_BUSY if it is already running or done,
+ * DBL_ERR_INVALID for an unknown ticket.  (Request cancellation is part of
+ * serving; the paper has no counterpart.) */
+dbl_status dbl_server_cancel(dbl_server *s, uint64_t ticket);
 dbl_status dbl_server_drain(dbl_server *s);
 /* [0] query p50 s, [1] query p99 s, [2] insertion p50 s, [3] insertion p99 s,
  * [4] pairs answered, [5] edges inserted, [6] query requests, [7] insertion
  * requests, [8] slots, [9] seconds since creation or reset, [10] device
- * query batches, [11] query requests in them, [12] insertion epochs. */
+ * query batches, [11] query requests in them, [12] insertion epochs,
+ * [13] requests cancelled. */
 dbl_status dbl_server_report(dbl_server *s, double out[16]);
 dbl_status dbl_server_reset_stats(dbl_server *s);
 void dbl_server_destroy(dbl_server *s);

@@ -19,8 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libdbl.so")
 
 DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAPACITY, DBL_ERR_BUSY, \
-    DBL_ERR_POISONED = range(8)
-STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned"]
+    DBL_ERR_POISONED, DBL_ERR_CANCELLED = range(9)
+STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned", "cancelled"]
 CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
 FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2 = 1, 2, 4, 8
 # landmark rankings of dbl_options.landmark_rule: M = |Pre|*|Suc| (Section 4.1), and Table 3's
@@ -37,7 +37,8 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_mlp_params", "dbl_mlp_forward", "dbl_mlp_gradients", "dbl_mlp_train_step", "dbl_mlp_sync", "dbl_mlp_last_error",
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
-           "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule"]
+           "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule", "dbl_barrier_probe",
+           "dbl_server_cancel"]
 MLP_PARAMS = 18817
 
 
@@ -49,7 +50,7 @@ class _ServerOptions(ctypes.Structure):
 class DblError(RuntimeError):
     def __init__(self, status: int, msg: str):
         self.status = status
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -61,7 +62,7 @@ class _Options(ctypes.Structure):
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
                 ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
                 ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("vertex_capacity", ctypes.c_int64),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("initial_slots", ctypes.c_int32), ("build_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Graph(ctypes.Structure):
@@ -124,6 +125,8 @@ def lib():
             L.dbl_server_create.argtypes = [P, P, P]
             L.dbl_server_submit.argtypes = [P, i32, P, P, i64, P, P]
             L.dbl_server_wait.argtypes = [P, ctypes.c_uint64, P]
+            L.dbl_server_cancel.argtypes = [P, ctypes.c_uint64]
+            L.dbl_barrier_probe.argtypes = [P, i64, i32, P]
             L.dbl_server_drain.argtypes = [P]
             L.dbl_server_report.argtypes = [P, P]
             L.dbl_server_reset_stats.argtypes = [P]
@@ -171,7 +174,8 @@ class DBLIndex:
     def __init__(self, row_ptr, col, k: int = 64, kprime: int = 64, landmarks=None, leaf_buckets=None,
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
                  torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0,
-                 landmark_rule: str = "M", leaf_r: int = 0, vertex_capacity: int = 0):
+                 landmark_rule: str = "M", leaf_r: int = 0, vertex_capacity: int = 0, initial_slots: int = 0,
+                 build_split: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -193,10 +197,20 @@ class DBLIndex:
         opt.landmark_rule = LANDMARK_RULES[landmark_rule]
         opt.leaf_r = int(leaf_r)
         opt.vertex_capacity = int(vertex_capacity)
+        opt.initial_slots = int(initial_slots)
+        opt.build_split = int(build_split)
+        self._refuse = [0, 0]  # allocations to let through, then to refuse (fail_allocations)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
+            refuse = self._refuse
 
             def _alloc(nbytes, strm, ctx):
+                if refuse[1] > 0:
+                    if refuse[0] > 0:
+                        refuse[0] -= 1
+                    else:
+                        refuse[1] -= 1
+                        return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream=int(strm or 0))
                 except Exception:
@@ -221,6 +235,19 @@ class DBLIndex:
         if st != DBL_OK:
             raise DblError(st, L.dbl_last_error(None).decode())
         self._h = h
+
+    def barrier_probe(self, spin_limit: int = 1 << 20, absent_block: int = -1, stream=None):
+        """dbl_barrier_probe: one cooperative launch on the index's grid barrier
+        in which `absent_block` (-1: none) never arrives and the other blocks
+        give up after `spin_limit` polls (then DBL_ERR_TIMEOUT, index poisoned)."""
+        self._check(lib().dbl_barrier_probe(self._h, int(spin_limit), int(absent_block), self._s(stream)))
+
+    def fail_allocations(self, count: int = 1, after: int = 0):
+        """Make the allocator callback return NULL for `count` device
+        allocations the library asks for, after letting the next `after`
+        through (host-side fault injection: the library must report
+        DBL_ERR_OOM and leave the index unchanged)."""
+        self._refuse[0], self._refuse[1] = int(after), int(count)
 
     # ------------------------------------------------------------------
     def _check(self, st):
@@ -304,7 +331,7 @@ class DBLIndex:
     def labels(self, stream=None):
         """(dl_in, dl_out, bl_in, bl_out) as int64 tensors [n, words] (uint64 bit patterns)."""
         import torch
-        wd, wb = self.k // 64, self.kprime // 64
+        wd, wb = (self.k + 63) // 64, (self.kprime + 63) // 64
         out = [torch.empty((self.n, w), dtype=torch.int64, device=self.device) for w in (wd, wd, wb, wb)]
         self._check(lib().dbl_labels(self._h, *[_ptr(t) for t in out], self._s(stream)))
         return tuple(out)
@@ -511,6 +538,16 @@ class Server:
             raise DblError(st, "server request failed")
         return ans, float(lat.value)
 
+    def cancel(self, ticket: int) -> bool:
+        """dbl_server_cancel: True if the request was dropped before any slot
+        took it (wait() then raises DBL_ERR_CANCELLED), False if too late."""
+        st = lib().dbl_server_cancel(self._h, ctypes.c_uint64(ticket))
+        if st == DBL_ERR_BUSY:
+            return False
+        if st != DBL_OK:
+            raise DblError(st, "server cancel")
+        return True
+
     def drain(self):
         lib().dbl_server_drain(self._h)
 
@@ -518,7 +555,7 @@ class Server:
         out = np.zeros(16, dtype=np.float64)
         lib().dbl_server_report(self._h, out.ctypes.data)
         keys = ["query_p50_s", "query_p99_s", "insert_p50_s", "insert_p99_s", "pairs", "edges", "query_requests",
-                "insert_requests", "slots", "elapsed_s", "device_batches", "batched_requests", "epochs"]
+                "insert_requests", "slots", "elapsed_s", "device_batches", "batched_requests", "epochs", "cancelled"]
         return {k: float(out[i]) for i, k in enumerate(keys)}
 
     def reset_stats(self):

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "dbl_internal.cuh"
+#include "dbl_persistent.cuh"
 
 namespace dbl {
 
@@ -206,6 +207,7 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
         c->und = nullptr;
         c->qtab = nullptr;
         c->found = nullptr;
+        c->und_cap = 0;  // a failed allocation below leaves nothing to reuse
         int64_t cap = std::max<int64_t>(q, 1 << 16);
         if ((st = ctx_alloc(c, (void **)&c->und, sizeof(int32_t) * (size_t)cap, s))) return st;
         if ((st = ctx_alloc(c, (void **)&c->qtab, sizeof(uint64_t) * (size_t)(cap + 64) * W, s))) return st;
@@ -215,18 +217,29 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
     }
     if (!c->table) {
         int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n_cap));
-        if ((st = ctx_alloc(c, (void **)&c->table, sizeof(SearchSlot) * (size_t)slots, s))) return st;
-        if ((st = ctx_alloc(c, (void **)&c->claimed, sizeof(int32_t) * (size_t)slots, s))) return st;
-        if ((st = ctx_alloc(c, (void **)&c->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return st;
-        if ((st = ctx_alloc(c, (void **)&c->slot_list[1], sizeof(int32_t) * (size_t)slots, s))) return st;
+        // all or nothing: a failure frees what was taken, so the next call starts over
+        auto undo = [&](dbl_status err) {
+            for (void **p : {(void **)&c->table, (void **)&c->claimed, (void **)&c->slot_list[0],
+                             (void **)&c->slot_list[1], (void **)&c->stask, &c->pstate}) {
+                ctx_free(c, *p, s);
+                *p = nullptr;
+            }
+            c->table_slots = 0;
+            c->stask_cap = 0;
+            return err;
+        };
+        if ((st = ctx_alloc(c, (void **)&c->table, sizeof(SearchSlot) * (size_t)slots, s))) return undo(st);
+        if ((st = ctx_alloc(c, (void **)&c->claimed, sizeof(int32_t) * (size_t)slots, s))) return undo(st);
+        if ((st = ctx_alloc(c, (void **)&c->slot_list[0], sizeof(int32_t) * (size_t)slots, s))) return undo(st);
+        if ((st = ctx_alloc(c, (void **)&c->slot_list[1], sizeof(int32_t) * (size_t)slots, s))) return undo(st);
         cudaMemsetAsync(c->table, 0, sizeof(SearchSlot) * (size_t)slots, s);
         // key = empty (all ones) in every slot: set the key words with a strided memset
         cudaMemset2DAsync(c->table, sizeof(SearchSlot), 0xff, sizeof(unsigned long long), (size_t)slots, s);
         c->table_slots = slots;
         int64_t tcap = (int64_t)ix->n_cap + (ix->m + ix->edge_cap) / kChunk + 4096;
-        if ((st = ctx_alloc(c, (void **)&c->stask, sizeof(SearchTask) * (size_t)tcap, s))) return st;
+        if ((st = ctx_alloc(c, (void **)&c->stask, sizeof(SearchTask) * (size_t)tcap, s))) return undo(st);
         c->stask_cap = tcap;
-        if ((st = ctx_alloc(c, &c->pstate, persist_state_bytes(), s))) return st;
+        if ((st = ctx_alloc(c, &c->pstate, persist_state_bytes(), s))) return undo(st);
     }
     return DBL_OK;
 }
@@ -253,7 +266,9 @@ using namespace dbl;
 
 static int hs_for(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
 
-static bool width_ok(int32_t bits) { return bits == 64 || bits == 128 || bits == 256; }
+// Label widths of Table 5 (16 .. 256 bits).  Widths below 64 use the low
+// bits of one 64-bit word; the rest of the word stays zero.
+static bool width_ok(int32_t bits) { return bits == 16 || bits == 32 || bits == 64 || bits == 128 || bits == 256; }
 
 extern "C" {
 
@@ -308,7 +323,8 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     *out = nullptr;
     if (!g || g->n < 0 || g->m < 0 || g->m >= (1ll << 31) || !g->row_ptr || (g->m > 0 && !g->col))
         return fail(nullptr, DBL_ERR_INVALID, "graph: need n >= 0, 0 <= m < 2^31 and device row_ptr/col");
-    if (!width_ok(k) || !width_ok(kprime)) return fail(nullptr, DBL_ERR_INVALID, "k and kprime must be 64, 128 or 256");
+    if (!width_ok(k) || !width_ok(kprime))
+        return fail(nullptr, DBL_ERR_INVALID, "k and kprime must be 16, 32, 64, 128 or 256");
     if (leaf_buckets && !leaf_roles) return fail(nullptr, DBL_ERR_INVALID, "leaf_roles required with leaf_buckets");
     if (opt && ((opt->alloc == nullptr) != (opt->free == nullptr)))
         return fail(nullptr, DBL_ERR_INVALID, "options: alloc and free must be set together");
@@ -336,15 +352,29 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     ix->m = g->m;
     ix->k = k;
     ix->kp = kprime;
-    ix->wd = k / 64;
-    ix->wb = kprime / 64;
+    ix->wd = (k + 63) / 64;
+    ix->wb = (kprime + 63) / 64;
     ix->hs = hs_for(ix->wd + ix->wb);
     ix->rw = 2 * ix->hs;
     ix->edge_cap = ix->opt.edge_capacity > 0 ? ix->opt.edge_capacity : std::max<int64_t>(1 << 20, g->m / 4);
     if (ix->edge_cap > (1ll << 29)) ix->edge_cap = 1ll << 29;  // per-vertex slots then fit in 30 bits
     if (ix->edge_cap + g->m >= (1ll << 31)) ix->edge_cap = (1ll << 31) - 1 - g->m;
-    ix->pool_cap = 4 * ix->edge_cap + 64;
-    if (ix->pool_cap >= (1ll << 31)) ix->pool_cap = (1ll << 31) - 1;
+    // slots reserved per vertex and direction: a power of two (the capacity is
+    // kept as its log2), at least 2, at most 64; none if they would take more
+    // than half of the pool's 2^31 addressable entries
+    {
+        int32_t want = ix->opt.initial_slots == 0 ? 4 : ix->opt.initial_slots;
+        int32_t s0 = 0;
+        if (want > 0) {
+            s0 = 2;
+            while (s0 < want && s0 < 64) s0 <<= 1;
+        }
+        if ((int64_t)s0 * std::max<int64_t>(g->n, ix->opt.vertex_capacity) > (1ll << 30)) s0 = 0;
+        ix->slots0 = s0;
+    }
+    const int64_t reserved_slots = (int64_t)ix->slots0 * std::max<int64_t>(g->n, ix->opt.vertex_capacity);
+    if (reserved_slots + 4 * ix->edge_cap + 64 >= (1ll << 31)) ix->edge_cap = ((1ll << 31) - 65 - reserved_slots) / 4;
+    ix->pool_cap = reserved_slots + 4 * ix->edge_cap + 64;
 
     // per-vertex arrays hold n_cap rows (vertex insertion); the base CSR holds the build's n
     const size_t n = (size_t)ix->n_cap, m = (size_t)ix->m, nb = (size_t)ix->n;
@@ -370,24 +400,32 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         (st = A((void **)&ix->front[1], sizeof(FTask) * (size_t)ix->front_cap)) || (st = A((void **)&ix->d_counts, 4 * kCntWords)) ||
         (st = A((void **)&ix->d_status, 16)) || (st = A((void **)&ix->d_stats, 8 * 16)) ||
         (st = A((void **)&ix->d_trace, 8 * 64)) ||
-        (st = A((void **)&ix->ins_cnt, 8 * n))) {
+        (st = A((void **)&ix->ins_cnt, 8 * n)) ||
+        (st = A((void **)&ix->dirty, 4 * (n / 32 + 1))) || (st = A((void **)&ix->d_restore_base, 16))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
         return fail(nullptr, st, msg);
     }
     cudaMemsetAsync(ix->vm, 0, sizeof(VMeta) * n, s);
-    cudaMemsetAsync(ix->d_pool_top, 0, 16, s);
+    {   // the pools start after the reserved slots of every vertex row
+        const int64_t top0[2] = {reserved_slots, reserved_slots};
+        cudaMemcpyAsync(ix->d_pool_top, top0, 16, cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);  // top0 lives on this stack frame
+    }
     cudaMemsetAsync(ix->mark, 0, 16 * (size_t)ix->wpd, s);
     cudaMemsetAsync(ix->d_counts, 0, 4 * kCntWords, s);
     cudaMemsetAsync(ix->d_status, 0, 16, s);
     cudaMemsetAsync(ix->d_stats, 0, 8 * 16, s);
     cudaMemsetAsync(ix->d_trace, 0, 8 * 64, s);
     cudaMemsetAsync(ix->ins_cnt, 0, 8 * n, s);
+    ix->dirty_words = (int64_t)(n / 32 + 1);
+    cudaMemsetAsync(ix->dirty, 0, 4 * (size_t)ix->dirty_words, s);
+    cudaMemsetAsync(ix->d_restore_base, 0xff, 16, s);  // no snapshot yet
 
     tbegin(ix, DBL_KERNEL_BUILD_PREP, s);
     if ((st = prep_graph(ix, g, s)) || (st = select_landmarks(ix, landmarks, s)) ||
         (st = select_leaves(ix, leaf_buckets, leaf_roles, s)) || (st = seed_labels(ix, s)) ||
-        (tend(ix, s), st = propagate(ix, s))) {
+        (tend(ix, s), st = build_propagate(ix, s))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
         return fail(nullptr, st, msg);
@@ -402,6 +440,7 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         destroy_impl(ix, s);
         return cuda_fail(nullptr, e, "build");
     }
+    ix->track_dirty = true;  // from here on every change is recorded for restores
     *out = ix;
     return DBL_OK;
 }
@@ -478,6 +517,7 @@ static dbl_status ensure_stage(dbl_index *ix, int64_t chunk, cudaStream_t s)
 {
     if (ix->stage_chunk >= chunk) return DBL_OK;
     dbl_status st;
+    ix->stage_chunk = 0;  // a failed allocation below leaves nothing to reuse
     for (int b = 0; b < 2; ++b) {
         free_buf(ix, ix->dstage[b], s);
         ix->dstage[b] = nullptr;
@@ -640,7 +680,7 @@ dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *
     const size_t v0 = (size_t)ix->n, c = (size_t)count;
     // the rows may hold a vertex that a restore took away: clear them all
     cudaMemsetAsync(ix->rec + v0 * ix->rw, 0, 8 * c * ix->rw, s);
-    cudaMemsetAsync(ix->vm + v0, 0, sizeof(VMeta) * c, s);
+    init_vmeta_rows(ix, (int32_t)v0, (int32_t)c, s);  // no edges; each row's reserved slots
     cudaMemsetAsync(ix->leaf_bucket + v0, 0xff, 4 * c, s);  // -1: not a leaf
     cudaMemsetAsync(ix->leaf_role + v0, 0, c, s);
     cudaError_t e = cudaGetLastError();
@@ -648,6 +688,9 @@ dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *
     ix->n += (int32_t)count;
     return finish(ix, DBL_OK, s);
 }
+
+// The snapshot slot the index equals from now on (see k_restore).
+__global__ void k_set_restore_base(uint32_t *base, uint32_t slot) { *base = slot; }
 
 dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
 {
@@ -658,33 +701,70 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     Snapshot &sn = ix->snaps[slot];
     dbl_status st;
     const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
-    if (!sn.rec.p) {  // sized for the vertex capacity: a later snapshot into the slot may hold more vertices
+    if (!sn.rec.p || !sn.vm.p || !sn.top.p) {  // sized for the vertex capacity: a later snapshot into the slot may hold more vertices
         if ((st = alloc_buf(ix, &sn.rec.p, 8 * (size_t)ix->n_cap * ix->rw, s)) ||
             (st = alloc_buf(ix, &sn.vm.p, sizeof(VMeta) * (size_t)ix->n_cap, s)) ||
-            (st = alloc_buf(ix, &sn.top.p, 16, s)))
+            (st = alloc_buf(ix, &sn.top.p, 16, s))) {
+            for (void **p : {&sn.rec.p, &sn.vm.p, &sn.top.p}) {  // all or nothing
+                free_buf(ix, *p, s);
+                *p = nullptr;
+            }
             return st;
+        }
     }
     cudaMemcpyAsync(sn.rec.p, ix->rec, rec_b, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(sn.vm.p, ix->vm, meta_b, cudaMemcpyDeviceToDevice, s);
     // pool tops stay on the device, so that a restore is all device-to-device
     // copies (and can be captured in a CUDA graph)
     cudaMemcpyAsync(sn.top.p, ix->d_pool_top, 16, cudaMemcpyDeviceToDevice, s);
+    // the index now equals this slot: track changes from here
+    cudaMemsetAsync(ix->dirty, 0, 4 * (size_t)ix->dirty_words, s);
+    k_set_restore_base<<<1, 1, 0, s>>>(ix->d_restore_base, (uint32_t)slot);
+    ++ix->launches;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return cuda_fail(ix, e, "snapshot");
     sn.edges_stored = ix->edges_stored;
     sn.n = ix->n;
+    sn.seq = ++ix->snap_seq;
     sn.valid = true;
     return DBL_OK;
 }
 
-// The whole restore in one launch: the labels and the adjacency metadata
-// (16-byte copies, four in flight per thread; both sizes are multiples of 16
-// bytes), the pool tops, and cleared status, counters and frontier bitmaps.
+// Restore, first kernel: the labels and the adjacency metadata.  If the index
+// last equalled this slot (device word *base, set by the snapshot or restore
+// that cleared the change bitmap) and no device error is latched, only the
+// vertices marked in the change bitmap are copied back (every record or
+// metadata write since then marked its vertex); otherwise everything is
+// copied (16-byte copies, four in flight per thread), and the frontier
+// bitmaps are cleared (they are empty after every complete propagation; an
+// aborted one may have left bits behind).  Every block reads *base and
+// *status before any block could change them: both are written only by the
+// second kernel.  The change bitmap is cleared either way.
 __global__ void k_restore(uint4 *rec, const uint4 *rec_snap, int64_t rec_units, uint4 *vm, const uint4 *vm_snap,
-                          int64_t vm_units, int64_t *top, const int64_t *top_snap, uint32_t *status,
-                          uint32_t *counts, int ncounts, uint32_t *mark, int64_t mark_words)
+                          int64_t vm_units, const uint32_t *base, uint32_t slot, const uint32_t *status, int force_full,
+                          uint32_t *dirty, int64_t dirty_words, int32_t n_snap, int rec_row_units, uint32_t *mark,
+                          int64_t mark_words)
 {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    const bool full = force_full || *(const volatile uint32_t *)base != slot || *(const volatile uint32_t *)status != 0;
+    if (!full) {
+        for (int64_t w = i0; w < dirty_words; w += st) {
+            uint32_t d = dirty[w];
+            if (!d) continue;
+            dirty[w] = 0;
+            while (d) {
+                const int b = __ffs(d) - 1;
+                d &= d - 1;
+                const int64_t x = w * 32 + b;
+                if (x >= n_snap) break;  // added after the snapshot: not restored (the vertex count goes back)
+                for (int u = 0; u < rec_row_units; ++u)
+                    rec[x * rec_row_units + u] = __ldcs(rec_snap + x * rec_row_units + u);
+                vm[2 * x] = __ldcs(vm_snap + 2 * x);
+                vm[2 * x + 1] = __ldcs(vm_snap + 2 * x + 1);
+            }
+        }
+        return;
+    }
     const int64_t total = rec_units + vm_units;
     for (int64_t i = i0; i < total; i += 4 * st) {
         uint4 v[4];
@@ -703,11 +783,20 @@ __global__ void k_restore(uint4 *rec, const uint4 *rec_snap, int64_t rec_units, 
         }
     }
     for (int64_t i = i0; i < mark_words; i += st) mark[i] = 0;
-    if (blockIdx.x == 0) {
-        if (threadIdx.x < 2) top[threadIdx.x] = top_snap[threadIdx.x];
-        if (threadIdx.x == 0) *status = 0;
-        for (int i = threadIdx.x; i < ncounts; i += blockDim.x) counts[i] = 0;
+    for (int64_t i = i0; i < dirty_words; i += st) dirty[i] = 0;
+}
+
+// Restore, second kernel: pool tops, cleared status and counters, and the
+// slot the index now equals.
+__global__ void k_restore_finish(int64_t *top, const int64_t *top_snap, uint32_t *status, uint32_t *counts,
+                                 int ncounts, uint32_t *base, uint32_t slot)
+{
+    if (threadIdx.x < 2) top[threadIdx.x] = top_snap[threadIdx.x];
+    if (threadIdx.x == 0) {
+        *status = 0;
+        *base = slot;
     }
+    for (int i = threadIdx.x; i < ncounts; i += blockDim.x) counts[i] = 0;
 }
 
 dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
@@ -716,22 +805,37 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     if (slot < 0 || slot >= 4 || !ix->snaps[slot].valid) return fail(ix, DBL_ERR_INVALID, "no snapshot in that slot");
     cudaStream_t s = (cudaStream_t)stream;
     Snapshot &sn = ix->snaps[slot];
+    // Snapshots taken after this one name inserted-edge segments in the part
+    // of the edge pool (and in the spare room of segments) that insertions
+    // after this restore reuse: they are dropped.  Older snapshots stay valid.
+    for (Snapshot &o : ix->snaps)
+        if (&o != &sn && o.valid && o.seq > sn.seq) o.valid = false;
     const size_t rec_b = 8 * (size_t)sn.n * ix->rw, meta_b = sizeof(VMeta) * (size_t)sn.n;
-    // one launch: labels, adjacency metadata, pool tops, and cleared status,
-    // counters and frontier bitmaps (the bitmaps are empty after every
-    // complete propagation; an aborted one, on a poisoned index, may have left
-    // bits behind)
+    // a poisoned index (an aborted update) is always copied back in full
     k_restore<<<(unsigned)num_sms() * 8, kBlock, 0, s>>>(
         (uint4 *)ix->rec, (const uint4 *)sn.rec.p, (int64_t)(rec_b / 16), (uint4 *)ix->vm, (const uint4 *)sn.vm.p,
-        (int64_t)(meta_b / 16), ix->d_pool_top, (const int64_t *)sn.top.p, ix->d_status, ix->d_counts, kCntWords,
-        ix->mark, 4 * ix->wpd);
-    ++ix->launches;
+        (int64_t)(meta_b / 16), ix->d_restore_base, (uint32_t)slot, ix->d_status, ix->poisoned ? 1 : 0, ix->dirty,
+        ix->dirty_words, sn.n, ix->rw / 2, ix->mark, 4 * ix->wpd);
+    k_restore_finish<<<1, 32, 0, s>>>(ix->d_pool_top, (const int64_t *)sn.top.p, ix->d_status, ix->d_counts,
+                                      kCntWords, ix->d_restore_base, (uint32_t)slot);
+    ix->launches += 2;
     ix->edges_stored = sn.edges_stored;
     ix->n = sn.n;
     ix->poisoned = false;
     cudaError_t e = cudaGetLastError();
     if (e) return cuda_fail(ix, e, "restore");
     return finish(ix, DBL_OK, s);
+}
+
+dbl_status dbl_barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent_block, void *stream)
+{
+    DBL_CHECK_IX(ix);
+    if (spin_limit < 1 || spin_limit > (int64_t)kSpinLimit || absent_block < -1 || absent_block >= num_sms())
+        return fail(ix, DBL_ERR_INVALID, "barrier_probe: spin_limit must be 1..2^24, absent_block -1..SMs-1");
+    cudaStream_t s = (cudaStream_t)stream;
+    dbl_status st = barrier_probe(ix, spin_limit, absent_block, s);
+    if (st) return st;
+    return read_status(ix, s);  // a wait that ran out: DBL_ERR_TIMEOUT, index poisoned
 }
 
 dbl_status dbl_sync(dbl_index *ix, void *stream)

@@ -34,7 +34,8 @@ __global__ void k_ins_validate(const int32_t *src, const int32_t *dst, int64_t b
 __device__ __forceinline__ bool status_set(const uint32_t *status) { return *(const volatile uint32_t *)status != 0; }
 
 __global__ void k_ins_count(const int32_t *src, const int32_t *dst, int64_t b, int32_t *cnt_out, int32_t *cnt_in,
-                            int32_t *pos_out, int32_t *pos_in, unsigned long long *stats, const uint32_t *status)
+                            int32_t *pos_out, int32_t *pos_in, unsigned long long *stats, const uint32_t *status,
+                            uint32_t *dirty)
 {
     if (status_set(status)) return;
     unsigned long long loops = 0;
@@ -48,6 +49,8 @@ __global__ void k_ins_count(const int32_t *src, const int32_t *dst, int64_t b, i
         }
         pos_out[i] = atomicAdd(cnt_out + u, 1);
         pos_in[i] = atomicAdd(cnt_in + v, 1);
+        mark_dirty(dirty, u);  // both endpoints' adjacency metadata change
+        mark_dirty(dirty, v);
     }
     if (loops) atomicAdd(stats + 13, loops);
 }
@@ -164,16 +167,22 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
 // see that bit, and a load that misses bits the OR brings means the word
 // grows.  Callers read the frontier only after a grid barrier or a launch.
 template <int HS, int WD>
-__device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, bool &want_f, bool &want_b)
+__device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, uint32_t *dirty, bool &want_f,
+                                         bool &want_b)
 {
     constexpr int RW = 2 * HS;
     uint64_t *fu = rec + (size_t)u * RW, *bu = fu + HS;
     uint64_t *fv = rec + (size_t)v * RW, *bv = fv + HS;
     uint64_t a[HS], c[HS], x[HS], y[HS];
-    load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
-    load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
-    load_half<HS>(fu, x);  // DL_in(u)  | BL_in(u)
-    load_half<HS>(bv, y);  // DL_out(v) | BL_out(v)
+    if constexpr (HS == 2) {  // 32-byte records: one load per record
+        load_rec32(fu, x[0], x[1], a[0], a[1]);
+        load_rec32(fv, c[0], c[1], y[0], y[1]);
+    } else {
+        load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
+        load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
+        load_half<HS>(fu, x);  // DL_in(u)  | BL_in(u)
+        load_half<HS>(bv, y);  // DL_out(v) | BL_out(v)
+    }
     uint64_t inter = 0;
 #pragma unroll
     for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
@@ -189,6 +198,8 @@ __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, bo
             want_b = true;
         }
     }
+    if (want_f) mark_dirty(dirty, v);
+    if (want_b) mark_dirty(dirty, u);
     return true;
 }
 
@@ -206,7 +217,7 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
             u = src[i];
             v = dst[i];
             if (u != v) {
-                if (seed_one<HS, WD>(u, v, rec, want_f, want_b)) ++applied;
+                if (seed_one<HS, WD>(u, v, rec, g.dirty, want_f, want_b)) ++applied;
                 else ++skipped;
             }
         }
@@ -255,8 +266,15 @@ struct InsArgs {
     int64_t wpd;
     unsigned long long *stats;
     uint32_t *status;
-    uint32_t *bad;  // this batch has an invalid id (zero before the launch)
+    uint32_t *bad;   // this batch has an invalid id (zero before the launch)
+    uint32_t *grow;  // some segment of this batch must grow (zero before the launch)
 };
+
+// Adjacency metadata of one direction from a VMeta sector loaded as four words.
+__device__ __forceinline__ VAdj vadj_of_words(uint64_t lo, uint64_t hi)
+{
+    return VAdj{(int32_t)(uint32_t)lo, (uint32_t)(lo >> 32), (int32_t)(uint32_t)hi, (int32_t)(uint32_t)(hi >> 32)};
+}
 
 template <int HS, int WD, int TEAM>
 __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, const Stage &st, int64_t max_levels)
@@ -272,9 +290,13 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
     // P1: validate and count: each edge takes its slots from the live segment
     // lengths (atomicAdd on len, so no commit pass is needed); an invalid id
     // raises the batch's own flag, and then every slot taken is given back
-    // after the barrier and nothing else changes
+    // after the barrier and nothing else changes.  The segments' capacities
+    // are read in the same round trip (no segment grows in this phase): a slot
+    // at or past its segment's capacity raises the batch's grow flag.
+    bool grow_any;
     {
         unsigned long long loops = 0;
+        bool grow = false;
         for (int64_t i = t0; i < a.b; i += nt) {
             const int32_t u = a.src[i], v = a.dst[i];
             if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
@@ -287,9 +309,16 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 ++loops;
                 continue;
             }
-            a.slot_out[i] = atomicAdd(&a.vm[u].d[0].len, 1);
-            a.slot_in[i] = atomicAdd(&a.vm[v].d[1].len, 1);
+            const int32_t so = atomicAdd(&a.vm[u].d[0].len, 1);
+            const int32_t si = atomicAdd(&a.vm[v].d[1].len, 1);
+            const uint32_t dcu = __ldcg(&a.vm[u].d[0].dc), dcv = __ldcg(&a.vm[v].d[1].dc);
+            a.slot_out[i] = so;
+            a.slot_in[i] = si;
+            grow |= so >= va_cap(dcu) || si >= va_cap(dcv);
+            mark_dirty(a.g.dirty, u);
+            mark_dirty(a.g.dirty, v);
         }
+        if (__any_sync(kFull, grow) && lane == 0) atomicOr(a.grow, 1u);
         if (leader) a.c3[0] = a.c3[1] = a.c3[2] = 0;
         if (!gs.sync(a.status)) return;
         if (ld_volatile_u32(a.bad)) {
@@ -298,15 +327,55 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 atomicSub(&a.vm[a.src[i]].d[0].len, 1);
                 atomicSub(&a.vm[a.dst[i]].d[1].len, 1);
             }
-            if (!gs.sync(a.status)) return;  // every block has read the flag
+            if (!gs.sync(a.status)) return;  // every block has read the flags
             if (leader) {
                 *(volatile uint32_t *)a.bad = 0;
+                *(volatile uint32_t *)a.grow = 0;
                 set_status(a.status, DBL_ERR_INVALID);
             }
             return;
         }
+        grow_any = ld_volatile_u32(a.grow) != 0;  // the same for every block
         warp_stat_add(a.stats, 13, loops);
     }
+    if (!grow_any) {
+        // P2 (no segment grows): seeds, the batch's ids into their slots, and
+        // the level-0 frontier, in one phase.  Lengths are final and no
+        // segment moves, so each endpoint's metadata sector (both directions,
+        // one load) gives both where its id goes and the task's edge range.
+        FrontierOut f{a.f0, a.c3, a.cap, a.mark, a.wpd, a.status};  // level-0 frontier: parity 0
+        unsigned long long skipped = 0, applied = 0;
+        for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x; wbase < a.b; wbase += nt) {  // block-uniform
+            const int64_t i = wbase + threadIdx.x;
+            bool want_f = false, want_b = false;
+            int32_t u = 0, v = 0;
+            VAdj eu{0, 0u, 0, 0}, ev{0, 0u, 0, 0};
+            if (i < a.b) {
+                const int32_t so = a.slot_out[i], si = a.slot_in[i];
+                u = a.src[i];
+                v = a.dst[i];
+                if (so >= 0) {
+                    uint64_t mu[4], mv[4];
+                    load_rec32(reinterpret_cast<const uint64_t *>(a.vm + u), mu[0], mu[1], mu[2], mu[3]);
+                    load_rec32(reinterpret_cast<const uint64_t *>(a.vm + v), mv[0], mv[1], mv[2], mv[3]);
+                    if (seed_one<HS, WD>(u, v, a.rec, a.g.dirty, want_f, want_b)) ++applied;
+                    else ++skipped;
+                    const VAdj au = vadj_of_words(mu[0], mu[1]), av = vadj_of_words(mv[2], mv[3]);
+                    eu = vadj_of_words(mu[2], mu[3]);  // u's in-edges: bwd(u) changed
+                    ev = vadj_of_words(mv[0], mv[1]);  // v's out-edges: fwd(v) changed
+                    a.pool_out[(int64_t)au.off + so] = v;
+                    a.pool_in[(int64_t)av.off + si] = u;
+                }
+            }
+            stage_enqueue_at(want_f, v, 0, AdjRange{ev.start, va_deg(ev.dc), ev.off, ev.len}, f, st);
+            stage_enqueue_at(want_b, u, 1, AdjRange{eu.start, va_deg(eu.dc), eu.off, eu.len}, f, st);
+        }
+        stage_flush(f, st);
+        warp_stat_add(a.stats, 12, skipped);
+        warp_stat_add(a.stats, 11, applied);
+        if (!gs.sync(a.status)) return;
+        if (leader) *(volatile uint32_t *)a.grow = 0;  // every block read it before this barrier
+    } else {
     // P2: seeds (Algorithm 3's skip test, then the endpoint ORs; whether
     // fwd(v) / bwd(u) gained bits is kept in bit 30 of the edge's slot words,
     // slots being < 2^29), and growth of the segments that overflowed: both
@@ -336,7 +405,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 }
                 if (sw[0] >= 0) {
                     bool want_f = false, want_b = false;
-                    if (seed_one<HS, WD>(x[0], x[1], a.rec, want_f, want_b)) ++applied;
+                    if (seed_one<HS, WD>(x[0], x[1], a.rec, a.g.dirty, want_f, want_b)) ++applied;
                     else ++skipped;
                     if (want_b) a.slot_out[i] = sw[0] | kWantBit;
                     if (want_f) a.slot_in[i] = sw[1] | kWantBit;
@@ -392,6 +461,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         warp_stat_add(a.stats, 11, applied);
     }
     if (!gs.sync(a.status)) return;
+    if (leader) *(volatile uint32_t *)a.grow = 0;  // every block read it before this barrier
     // P3: write the batch's ids into their slots, and enqueue the seeds'
     // changed endpoints (their tasks carry the final adjacency locations)
     {
@@ -424,6 +494,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         stage_flush(f, st);
     }
     if (!gs.sync(a.status)) return;
+    }  // P2 and P3 when a segment grows
     // P4: propagation levels
     const int64_t warp0 = t0 >> 5, nwarps = nt >> 5;
     int64_t L = 0;
@@ -438,7 +509,8 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         uint32_t *cur_mark = a.mark + (size_t)(L & 1) * 2 * (size_t)a.wpd;
         uint32_t *nxt_mark = a.mark + (size_t)((L + 1) & 1) * 2 * (size_t)a.wpd;
         FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, nxt_mark, a.wpd, a.status};
-        expand_level<HS, TEAM>(a.g, a.rec, (L & 1) ? a.f1 : a.f0, ntk, cur_mark, f, a.stats, warp0, nwarps, st);
+        expand_level<HS, TEAM>(a.g, RecView{a.rec, 2 * HS, HS}, (L & 1) ? a.f1 : a.f0, ntk, cur_mark, f, a.stats,
+                               warp0, nwarps, st);
         if (!gs.sync(a.status)) break;
     }
     if (leader) a.stats[8] += (unsigned long long)L;
@@ -510,6 +582,7 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     a.stats = ix->d_stats;
     a.status = ix->d_status;
     a.bad = ix->d_counts + kCntBad;
+    a.grow = ix->d_counts + kCntGrow;
     tbegin(ix, DBL_KERNEL_PROPAGATE, s);
     dbl_status st;
     switch (ix->hs * 16 + ix->wd) {
@@ -551,6 +624,7 @@ dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, i
     if (b > ix->ins_bcap) {
         if (ix->ins_pos) free_buf(ix, ix->ins_pos, s);
         ix->ins_pos = nullptr;
+        ix->ins_bcap = 0;  // a failed allocation below leaves nothing to reuse
         int64_t nb = b < (1 << 16) ? (1 << 16) : b;
         dbl_status st = alloc_buf(ix, (void **)&ix->ins_pos, sizeof(int32_t) * 2 * (size_t)nb, s);
         if (st) return st;
@@ -586,7 +660,8 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     // 2. append
     int32_t *cnt_out = ix->ins_cnt, *cnt_in = ix->ins_cnt + ix->n_cap;  // [2][n_cap], zero between calls
     tbegin(ix, DBL_KERNEL_INSERT_APPEND, s);
-    k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status);
+    k_ins_count<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->d_stats, ix->d_status,
+                                        dev_graph(ix).dirty);
     ++ix->launches;
     k_ins_grow<<<grid, kBlock, 0, s>>>(src, dst, b, cnt_out, cnt_in, pos_out, pos_in, ix->vm, ix->pool_out,
                                        ix->pool_in, ix->d_pool_top, ix->pool_cap, ix->d_status);

@@ -71,7 +71,15 @@ struct DevGraph {
     VMeta *vm;
     const int32_t *out_col, *in_col;
     const int32_t *pool_out, *pool_in;
+    uint32_t *dirty;  // vertices whose record or adjacency changed since the last snapshot / restore (NULL: untracked)
 };
+
+// Note that x's record or adjacency metadata changed (a bit per vertex; the
+// result is unused, so this is a fire-and-forget reduction).
+__device__ __forceinline__ void mark_dirty(uint32_t *dirty, int32_t x)
+{
+    if (dirty) atomicOr(dirty + (x >> 5), 1u << (x & 31));
+}
 
 __device__ __forceinline__ VAdj load_vadj(const VMeta *vm, int dir, int32_t x)
 {
@@ -108,10 +116,37 @@ __device__ __forceinline__ int32_t adj_at(const DevGraph &g, int dir, const AdjR
     return __ldcg((dir ? g.pool_in : g.pool_out) + r.o0 + (e - r.bd));
 }
 
+// Where the label halves live: half `dir` of vertex x starts at
+// rec + x * stride + dir * boff.  The index's records: stride 2*HS, boff HS
+// (forward half, then backward half).  A build pass over one direction alone
+// runs on an array of that direction's halves: stride HS, boff 0.
+struct RecView {
+    uint64_t *rec;
+    int64_t stride;
+    int64_t boff;
+};
+
+__device__ __forceinline__ uint64_t *rec_half(const RecView &r, int32_t x, int dir)
+{
+    return r.rec + (size_t)x * (size_t)r.stride + (dir ? (size_t)r.boff : 0);
+}
+
 // Latch the first error code in the device status word.
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code)
 {
     atomicCAS(status, 0u, code);
+}
+
+// A whole 32-byte record (both 16-byte halves at k + k' <= 128) in one
+// 256-bit load, cached in L2 only: one request for the record's one DRAM
+// sector instead of two 16-byte requests.  p must be 32-byte aligned.
+template <typename T>
+__device__ __forceinline__ void load_rec32(const uint64_t *p, T &w0, T &w1, T &w2, T &w3)
+{
+    static_assert(sizeof(T) == 8, "64-bit words");
+    asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+                 : "l"(p));
 }
 
 template <int HS>
@@ -208,6 +243,7 @@ struct Buf {
 
 struct Snapshot {
     bool valid = false;
+    uint64_t seq = 0;   // order of the snapshots (a restore drops the ones taken after it)
     int32_t n = 0;      // vertex count at the snapshot (vertices added later go away on restore)
     Buf rec, vm;        // labels; per-vertex adjacency metadata
     Buf top;            // the two pool tops (device)
@@ -231,6 +267,7 @@ struct dbl_index {
     dbl::VMeta *vm = nullptr;  // [n] adjacency metadata incl. the inserted-edge segments
     int32_t *pool_out = nullptr, *pool_in = nullptr;
     int64_t pool_cap = 0, edge_cap = 0;
+    int32_t slots0 = 0;           // inserted-edge slots reserved per vertex and direction at build
     int64_t edges_stored = 0;     // host mirror of inserted edges stored
     int64_t *d_pool_top = nullptr; // [2] device bump pointers (out, in)
     int64_t h_pool_top[2] = {0, 0};
@@ -254,6 +291,19 @@ struct dbl_index {
 
     // query scratch of calls without an explicit context (dbl_query)
     struct dbl_qctx *qc = nullptr;
+
+    // change tracking for restores: a bit per vertex whose record or adjacency
+    // metadata changed since the last snapshot or restore, and (device word)
+    // the snapshot slot the index then equalled (0xffffffff: none).  A restore
+    // to that slot copies back only the marked vertices.
+    uint32_t *dirty = nullptr;
+    int64_t dirty_words = 0;
+    uint32_t *d_restore_base = nullptr;
+    bool track_dirty = false;  // off during the build (nothing to restore to yet)
+
+    // the propagation's view of the labels when it is not the index's records
+    // (a build pass over one direction's halves); rec == nullptr: the records
+    dbl::RecView prop_view{nullptr, 0, 0};
 
     // status, counters
     uint32_t *d_status = nullptr;
@@ -291,6 +341,7 @@ struct dbl_index {
     std::atomic<uint64_t> h_stats[16] = {};  // host-side counters merged into dbl_stats
     std::atomic<uint64_t> launches{0};       // kernels launched by this index
     dbl::Snapshot snaps[4];
+    uint64_t snap_seq = 0;
     std::vector<dbl::Buf> owned;      // for teardown
     std::mutex alloc_mu;              // allocations may come from several query contexts
 };
@@ -331,6 +382,7 @@ enum {
     kCntClaimed = 6,    // claimed slots
     kCntOverflow = 7,   // search wave overflow flag
     kCntBad = 8,        // the persistent insertion's invalid-id flag (zero between launches)
+    kCntGrow = 9,       // the persistent insertion's some-segment-must-grow flag (zero between launches)
     kCntP0 = 10,        // (3 words) persistent propagation level counts
     kCntBarLeft = 13,   // grid barrier: blocks done with the launch
     kCntBarCount = 14,  // (2 words, 8-byte aligned) grid barrier: arrivals, uint64
@@ -361,6 +413,13 @@ inline uint32_t *mark_of(const dbl_index *ix, int parity)
     return ix->mark + (size_t)parity * 2 * (size_t)ix->wpd;
 }
 
+// The labels as the propagation sees them.
+inline RecView rec_view(const dbl_index *ix)
+{
+    if (ix->prop_view.rec) return ix->prop_view;
+    return RecView{ix->rec, (int64_t)ix->rw, (int64_t)ix->hs};
+}
+
 inline DevGraph dev_graph(const dbl_index *ix)
 {
     DevGraph g;
@@ -370,6 +429,7 @@ inline DevGraph dev_graph(const dbl_index *ix)
     g.in_col = ix->in_col;
     g.pool_out = ix->pool_out;
     g.pool_in = ix->pool_in;
+    g.dirty = ix->track_dirty ? ix->dirty : nullptr;
     return g;
 }
 
@@ -391,7 +451,9 @@ dbl_status select_landmarks(dbl_index *ix, const int32_t *user, cudaStream_t s);
 dbl_status select_top(dbl_index *ix, const int32_t *op, const int32_t *ip, const unsigned long long *keys, int32_t n,
                       int32_t k, int32_t *out, cudaStream_t s);
 dbl_status select_leaves(dbl_index *ix, const int32_t *bucket, const uint8_t *role, cudaStream_t s);
-dbl_status seed_labels(dbl_index *ix, cudaStream_t s);
+dbl_status seed_labels(dbl_index *ix, cudaStream_t s);                 // seeds only
+dbl_status build_propagate(dbl_index *ix, cudaStream_t s);             // seed frontier + fixpoint
+void init_vmeta_rows(dbl_index *ix, int32_t v0, int32_t c, cudaStream_t s);
 dbl_status exclusive_scan_i32(dbl_index *ix, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 
 // propagation (dbl_propagate.cu): run the fixpoint from frontier buffer 0
@@ -399,7 +461,8 @@ dbl_status exclusive_scan_i32(dbl_index *ix, const int32_t *in, int32_t *out, in
 dbl_status propagate(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s);
-void launch_seed_frontier(dbl_index *ix, cudaStream_t s);  // all vertices with a non-zero half
+dbl_status barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent, cudaStream_t s);
+void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)
 
 // insertion (dbl_insert.cu)
 dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);

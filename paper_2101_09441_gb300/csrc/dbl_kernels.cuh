@@ -64,12 +64,11 @@ __device__ __forceinline__ void enqueue_local(bool want, int32_t x, int dir, con
 // vertices' bits are cleared in clear_mark (fence after the clear when the
 // bitmap is the one being filled: local tasks).
 template <int HS>
-__device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, bool has, const FTask &tk,
+__device__ __forceinline__ void flat_round(const DevGraph &g, const RecView &rw, bool has, const FTask &tk,
                                            uint32_t *clear_mark, bool local, const FrontierOut &f, const Stage &st,
                                            FTask *wl, int &wl_n, unsigned long long &relaxed,
                                            unsigned long long &ntask)
 {
-    constexpr int RW = 2 * HS;
     const int lane = threadIdx.x & 31;
     int32_t col0 = 0, ncol = 0, pool0 = 0;
     uint32_t cnt = 0;
@@ -87,7 +86,7 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, boo
         ncol = task_ncol(tk);
         pool0 = tk.pool0;
         cnt = (uint32_t)task_edges(tk);
-        load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
+        load_half<HS>(rec_half(rw, tk.v, dir), rv);
         ++ntask;
     }
     uint32_t incl = cnt;
@@ -113,7 +112,7 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, boo
         if (e < total) {
             x = task_edge(g, odir, ocol0, oncol, opool0, oe);
             ++relaxed;
-            uint64_t *px = rec + (size_t)x * RW + (odir ? HS : 0);
+            uint64_t *px = rec_half(rw, x, odir);
             uint64_t rx[HS];
             load_half<HS>(px, rx);
 #pragma unroll
@@ -123,6 +122,7 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, boo
                     want |= (orv[i] & ~old) != 0;
                 }
             }
+            if (want) mark_dirty(g.dirty, x);
         }
         enqueue_local(want, x, odir, g, f, st, wl, wl_n);
     }
@@ -135,7 +135,7 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, uint64_t *rec, boo
 // A round costs ceil(edges of the warp's tasks / 32) iterations, whatever the
 // mix of task sizes.  Then the warp's local rounds (above).
 template <int HS>
-__device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *rec, const FTask *tasks,
+__device__ __forceinline__ void expand_level_flat(const DevGraph &g, const RecView &rw, const FTask *tasks,
                                                   uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                                   unsigned long long *stats, int64_t warp, int64_t nwarps,
                                                   const Stage &st)
@@ -150,7 +150,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
         const int64_t t = warp + nwarps * (r0 + lane);
         const bool has = t < (int64_t)ntasks;
         const FTask tk = has ? load_ftask(tasks, t) : FTask{0, 0u, 0, 0};
-        flat_round<HS>(g, rec, has, tk, cur_mark, false, f, st, wl, wl_n, relaxed, ntask);
+        flat_round<HS>(g, rw, has, tk, cur_mark, false, f, st, wl, wl_n, relaxed, ntask);
     }
     for (int lr = 0; lr < kLocalRounds && wl_n > 0; ++lr) {
         __syncwarp();
@@ -158,7 +158,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
         const FTask tk = has ? wl[lane] : FTask{0, 0u, 0, 0};
         __syncwarp();
         wl_n = 0;
-        flat_round<HS>(g, rec, has, tk, f.mark, true, f, st, wl, wl_n, relaxed, ntask);
+        flat_round<HS>(g, rw, has, tk, f.mark, true, f, st, wl, wl_n, relaxed, ntask);
     }
     __syncwarp();
     {
@@ -179,16 +179,15 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, uint64_t *r
 // New tasks go through the block's stage (stage_enqueue); the stage is flushed
 // at the end, so every thread of the block must call this.
 template <int HS, int TEAM>
-__device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, const FTask *tasks,
+__device__ __forceinline__ void expand_level(const DevGraph &g, const RecView &rw, const FTask *tasks,
                                              uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                              unsigned long long *stats, int64_t warp0, int64_t nwarps,
                                              const Stage &st)
 {
     if constexpr (TEAM == 1) {
-        expand_level_flat<HS>(g, rec, tasks, ntasks, cur_mark, f, stats, warp0, nwarps, st);
+        expand_level_flat<HS>(g, rw, tasks, ntasks, cur_mark, f, stats, warp0, nwarps, st);
     } else {
         constexpr int TPW = 32 / TEAM;
-        constexpr int RW = 2 * HS;
         const int lane = threadIdx.x & 31;
         const int team = lane / TEAM, tl = lane % TEAM;
         unsigned long long relaxed = 0, ntask = 0;
@@ -209,7 +208,7 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                 ncol = task_ncol(tk);
                 pool0 = tk.pool0;
                 cnt = task_edges(tk);
-                load_half<HS>(rec + (size_t)tk.v * RW + (dir ? HS : 0), rv);
+                load_half<HS>(rec_half(rw, tk.v, dir), rv);
                 if (tl == 0) ++ntask;
             }
             int iters = (cnt + TEAM - 1) / TEAM;
@@ -222,7 +221,7 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                 if (has && e < cnt) {
                     x = task_edge(g, dir, col0, ncol, pool0, e);
                     ++relaxed;
-                    uint64_t *px = rec + (size_t)x * RW + (dir ? HS : 0);
+                    uint64_t *px = rec_half(rw, x, dir);
                     uint64_t rx[HS];
                     load_half<HS>(px, rx);
                     bool changed = false;
@@ -234,6 +233,7 @@ __device__ __forceinline__ void expand_level(const DevGraph &g, uint64_t *rec, c
                         }
                     }
                     want = changed;
+                    if (changed) mark_dirty(g.dirty, x);
                 }
                 stage_enqueue(want, x, dir, g, f, st);
             }

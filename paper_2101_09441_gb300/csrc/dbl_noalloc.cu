@@ -24,6 +24,10 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[2 * kNoAllocMaxBatch]
 
 // Device address of the array, looked up once per device.  In host code the
 // array's name is only a host-side stand-in, so it is never passed to a kernel.
+// The address belongs to the device's primary context as it was at the first
+// call: a process that resets the device (cudaDeviceReset) and goes on
+// computing gets a new context, where the module may load elsewhere, so such
+// a process must not call this entry point after the reset.
 constexpr int kMaxDevices = 64;
 static std::mutex g_scratch_mu;
 static int32_t *g_scratch_addr[kMaxDevices];

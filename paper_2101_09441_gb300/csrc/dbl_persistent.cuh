@@ -7,7 +7,7 @@
 // last block to leave zeroes the counter and the leave count, so the next
 // launch, whatever its grid size, starts from zero.
 //
-// Every wait is bounded: a block that polls more than kSpinLimit times latches
+// Every wait is bounded: a block that polls more than spin_limit times latches
 // DBL_ERR_TIMEOUT in the status word and stops waiting; every loop of a
 // persistent kernel checks the status after each barrier and returns, so the
 // launch always ends and the host sees the timeout.
@@ -17,10 +17,13 @@
 
 namespace dbl {
 
+constexpr unsigned long long kSpinLimit = 1ull << 24;  // polls of ~0.3-1 us each: seconds, not forever
+
 struct GridBarrier {
     unsigned long long *count;          // arrivals in this launch
     unsigned int *left;                 // blocks that have finished this launch
     unsigned long long *trace = nullptr;  // optional phase trace: [0] marks, [1..63] %globaltimer
+    unsigned long long spin_limit = kSpinLimit;  // polls before a wait gives up
 };
 
 constexpr int kTraceWords = 64;
@@ -28,10 +31,9 @@ constexpr int kTraceWords = 64;
 // Barrier words inside a d_counts array (kCntBarLeft, kCntBarCount: 8-byte aligned).
 inline GridBarrier grid_barrier_at(uint32_t *counts)
 {
-    return GridBarrier{reinterpret_cast<unsigned long long *>(counts + kCntBarCount), counts + kCntBarLeft, nullptr};
+    return GridBarrier{reinterpret_cast<unsigned long long *>(counts + kCntBarCount), counts + kCntBarLeft, nullptr,
+                       kSpinLimit};
 }
-
-constexpr unsigned long long kSpinLimit = 1ull << 24;  // polls of ~0.3-1 us each: seconds, not forever
 
 // Threads per block of the persistent kernels: one block per SM.  Records of
 // 8 words per direction need more than 64 registers a thread, so those
@@ -94,7 +96,7 @@ struct GridSync {
             const unsigned long long target = (unsigned long long)gridDim.x * (passed + 1);
             unsigned long long spins = 0;
             while (ld_acquire_u64(b.count) < target) {
-                if (++spins > kSpinLimit) {
+                if (++spins > b.spin_limit) {
                     atomicCAS(status, 0u, (uint32_t)DBL_ERR_TIMEOUT);
                     ok = 0;
                     break;

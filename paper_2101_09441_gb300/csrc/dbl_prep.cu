@@ -157,16 +157,33 @@ __global__ void k_scatter_in(const int32_t *row_ptr, const int32_t *col, int32_t
     }
 }
 
-// Per-vertex adjacency metadata from the two CSRs (no inserted edges yet).
-__global__ void k_fill_vmeta(const int32_t *out_ptr, const int32_t *in_ptr, int32_t n, VMeta *vm, uint32_t *status)
+// Per-vertex adjacency metadata from the two CSRs (no inserted edges yet):
+// vertex x's inserted edges start in its slots0 reserved pool entries at
+// x * slots0 (both pools), empty.
+__global__ void k_fill_vmeta(const int32_t *out_ptr, const int32_t *in_ptr, int32_t n, int32_t slots0, VMeta *vm,
+                             uint32_t *status)
 {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t o0 = out_ptr[x], od = out_ptr[x + 1] - o0;
         const int32_t i0 = in_ptr[x], id = in_ptr[x + 1] - i0;
         if (od >= (1 << kDegBits) || id >= (1 << kDegBits)) set_status(status, DBL_ERR_INVALID);
+        const int32_t off = (int32_t)(x * slots0);
         VMeta v;
-        v.d[0] = VAdj{o0, va_dc(od, 0), 0, 0};
-        v.d[1] = VAdj{i0, va_dc(id, 0), 0, 0};
+        v.d[0] = VAdj{o0, va_dc(od, slots0), off, 0};
+        v.d[1] = VAdj{i0, va_dc(id, slots0), off, 0};
+        vm[x] = v;
+    }
+}
+
+// Rows [v0, v0 + c) of vertices added later: no edges, their reserved slots.
+__global__ void k_init_vmeta_rows(int32_t v0, int32_t c, int32_t slots0, VMeta *vm)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = v0 + i;
+        const int32_t off = (int32_t)(x * slots0);
+        VMeta v;
+        v.d[0] = VAdj{0, va_dc(0, slots0), off, 0};
+        v.d[1] = VAdj{0, va_dc(0, slots0), off, 0};
         vm[x] = v;
     }
 }
@@ -178,6 +195,12 @@ static unsigned grid_for(int64_t work, int per_block = kBlock)
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
+}
+
+void init_vmeta_rows(dbl_index *ix, int32_t v0, int32_t c, cudaStream_t s)
+{
+    k_init_vmeta_rows<<<grid_for(c), kBlock, 0, s>>>(v0, c, ix->slots0, ix->vm);
+    ++ix->launches;
 }
 
 dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s)
@@ -207,7 +230,7 @@ dbl_status prep_graph(dbl_index *ix, const dbl_graph *g, cudaStream_t s)
     cudaMemcpyAsync(cnt, ix->in_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s);
     if (m) { k_scatter_in<<<grid_for((int64_t)n * 32), kBlock, 0, s>>>(ix->out_ptr, ix->out_col, n, cnt, ix->in_col); ++ix->launches; }
     free_buf(ix, cnt, s);
-    k_fill_vmeta<<<grid_for(n), kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, n, ix->vm, ix->d_status);
+    k_fill_vmeta<<<grid_for(n), kBlock, 0, s>>>(ix->out_ptr, ix->in_ptr, n, ix->slots0, ix->vm, ix->d_status);
     ++ix->launches;
     e = cudaGetLastError();
     if (e) return cuda_fail(ix, e, "prep_graph");
@@ -470,7 +493,8 @@ __global__ void k_seed_leaves(const int32_t *bucket, const uint8_t *role, int32_
 }
 
 // every vertex with a non-zero half joins the frontier in that direction
-__global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, DevGraph g, FrontierOut f)
+// (directions in `dirs`: bit 0 forward, bit 1 backward)
+__global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, DevGraph g, FrontierOut f, int dirs)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += stride) {
@@ -484,23 +508,92 @@ __global__ void k_seed_frontier(const uint64_t *rec, int32_t rw, int32_t hs, Dev
                 a |= p[i];
                 b |= p[hs + i];
             }
-            fw = a != 0;
-            bw = b != 0;
+            fw = (dirs & 1) && a != 0;
+            bw = (dirs & 2) && b != 0;
         }
         warp_enqueue(fw, (int32_t)v, 0, g, f);
         warp_enqueue(bw, (int32_t)v, 1, g, f);
     }
 }
 
-void launch_seed_frontier(dbl_index *ix, cudaStream_t s)
+void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs)
 {
     FrontierOut f{ix->front[0], ix->d_counts + kCntFront0, ix->front_cap, mark_of(ix, 0), ix->wpd, ix->d_status};
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     int64_t blocks = ((int64_t)ix->n + kBlock - 1) / kBlock;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
-    k_seed_frontier<<<(unsigned)blocks, kBlock, 0, s>>>(ix->rec, ix->rw, ix->hs, dev_graph(ix), f);
+    k_seed_frontier<<<(unsigned)blocks, kBlock, 0, s>>>(ix->rec, ix->rw, ix->hs, dev_graph(ix), f, dirs);
     ++ix->launches;
+}
+
+// The build's propagation to the least fixpoint from the seeded records.
+// When the records are larger than the address-translation caches cover
+// (random 32-byte gathers drop from ~70 G/s over 256 MB to ~30 G/s over
+// 512 MB on GB300), the two directions are propagated one after the other,
+// each over an array of that direction's halves alone (half the bytes
+// touched at random), and interleaved back into the records at the end.
+// Both give the same least fixpoint: the directions never read each other.
+constexpr size_t kSplitBuildBytes = 256ull << 20;
+
+__global__ void k_split_halves(const uint64_t *rec, int64_t n, int hs, uint64_t *fw, uint64_t *bw)
+{
+    const int64_t words = n * hs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i / hs, w = i % hs;
+        fw[i] = rec[x * 2 * hs + w];
+        bw[i] = rec[x * 2 * hs + hs + w];
+    }
+}
+
+__global__ void k_join_halves(uint64_t *rec, int64_t n, int hs, const uint64_t *fw, const uint64_t *bw)
+{
+    const int64_t words = n * hs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i / hs, w = i % hs;
+        rec[x * 2 * hs + w] = fw[i];
+        rec[x * 2 * hs + hs + w] = bw[i];
+    }
+}
+
+dbl_status build_propagate(dbl_index *ix, cudaStream_t s)
+{
+    const size_t rec_bytes = sizeof(uint64_t) * (size_t)ix->n * ix->rw;
+    const bool split = ix->opt.build_split > 0 || (ix->opt.build_split == 0 && rec_bytes > kSplitBuildBytes);
+    if (!split) {
+        launch_seed_frontier(ix, s, 3);
+        return propagate(ix, s);
+    }
+    uint64_t *half[2] = {nullptr, nullptr};
+    dbl_status st;
+    for (int d = 0; d < 2; ++d)
+        if ((st = alloc_buf(ix, (void **)&half[d], rec_bytes / 2, s))) {
+            free_buf(ix, half[0], s);
+            return st;
+        }
+    const unsigned grid = grid_for((int64_t)ix->n * ix->hs);
+    tbegin(ix, DBL_KERNEL_PROPAGATE, s);  // the copies count as the build's propagation
+    k_split_halves<<<grid, kBlock, 0, s>>>(ix->rec, ix->n, ix->hs, half[0], half[1]);
+    ++ix->launches;
+    tend(ix, s);
+    st = DBL_OK;
+    for (int d = 0; d < 2 && !st; ++d) {
+        launch_seed_frontier(ix, s, 1 << d);
+        ix->prop_view = RecView{half[d], (int64_t)ix->hs, 0};
+        st = propagate(ix, s);
+        ix->prop_view = RecView{nullptr, 0, 0};
+    }
+    if (!st) {
+        tbegin(ix, DBL_KERNEL_PROPAGATE, s);
+        k_join_halves<<<grid, kBlock, 0, s>>>(ix->rec, ix->n, ix->hs, half[0], half[1]);
+        ++ix->launches;
+        tend(ix, s);
+    }
+    free_buf(ix, half[0], s);
+    free_buf(ix, half[1], s);
+    cudaError_t e = cudaGetLastError();
+    if (!st && e) st = cuda_fail(ix, e, "build propagation");
+    return st;
 }
 
 dbl_status seed_labels(dbl_index *ix, cudaStream_t s)
@@ -511,7 +604,6 @@ dbl_status seed_labels(dbl_index *ix, cudaStream_t s)
     k_seed_leaves<<<grid_for(ix->n), kBlock, 0, s>>>(ix->leaf_bucket, ix->leaf_role, ix->n, ix->rec, ix->rw, ix->hs,
                                                       ix->wd);
     ++ix->launches;
-    launch_seed_frontier(ix, s);
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(ix, e, "seed_labels") : DBL_OK;
 }

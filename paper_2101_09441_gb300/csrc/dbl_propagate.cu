@@ -20,12 +20,12 @@
 namespace dbl {
 
 template <int HS, int TEAM>
-__global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, uint64_t *rec, const FTask *tasks,
+__global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, RecView rw, const FTask *tasks,
                                                    const uint32_t *ntasks_p, uint32_t *cur_mark, FrontierOut f,
                                                    unsigned long long *stats)
 {
     DBL_BLOCK_STAGE(st);
-    expand_level<HS, TEAM>(g, rec, tasks, *ntasks_p, cur_mark, f, stats,
+    expand_level<HS, TEAM>(g, rw, tasks, *ntasks_p, cur_mark, f, stats,
                            ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                            ((int64_t)gridDim.x * blockDim.x) >> 5, st);
 }
@@ -41,7 +41,7 @@ static void launch_expand(dbl_index *ix, int cur, uint32_t ntasks, const Frontie
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_expand<HS, TEAM><<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), ix->rec, ix->front[cur],
+    k_expand<HS, TEAM><<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), rec_view(ix), ix->front[cur],
                                                            ix->d_counts + kCntFront0 + cur, mark_of(ix, cur), f,
                                                            ix->d_stats);
     ++ix->launches;
@@ -141,7 +141,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
 // runaway into DBL_ERR_TIMEOUT instead of a hang.
 template <int HS, int TEAM>
 __global__ void __launch_bounds__(pblock_of(HS), 1)
-    k_propagate_persistent(DevGraph g, uint64_t *rec, FTask *f0, FTask *f1, uint32_t *c3, int64_t cap,
+    k_propagate_persistent(DevGraph g, RecView rw, FTask *f0, FTask *f1, uint32_t *c3, int64_t cap,
                            uint32_t *mark, int64_t wpd, uint32_t *status, unsigned long long *stats,
                            GridBarrier bar, int64_t max_levels)
 {
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(pblock_of(HS), 1)
         uint32_t *cur_mark = mark + (size_t)(L & 1) * 2 * (size_t)wpd;
         uint32_t *nxt_mark = mark + (size_t)((L + 1) & 1) * 2 * (size_t)wpd;
         FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, nxt_mark, wpd, status};
-        expand_level<HS, TEAM>(g, rec, (L & 1) ? f1 : f0, nt, cur_mark, f, stats, warp0, nwarps, st);
+        expand_level<HS, TEAM>(g, rw, (L & 1) ? f1 : f0, nt, cur_mark, f, stats, warp0, nwarps, st);
         if (!gs.sync(status)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -189,7 +189,8 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
     GridBarrier bar = grid_barrier_at(ix->d_counts);
     if (ix->opt.flags & DBL_FLAG_TIMING) bar.trace = ix->d_trace;
     int64_t max_levels = (int64_t)ix->n + 2;
-    void *args[] = {&g, &ix->rec, &f0, &f1, &c3, &cap, &mark, &wpd, &status, &stats, &bar, &max_levels};
+    RecView rw = rec_view(ix);
+    void *args[] = {&g, &rw, &f0, &f1, &c3, &cap, &mark, &wpd, &status, &stats, &bar, &max_levels};
     dim3 grid((unsigned)num_sms()), block(pblock_of(HS));
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_propagate_persistent<HS, TEAM>, grid, block, args, 0, s);
     ++ix->launches;
@@ -230,6 +231,33 @@ dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s)
     if (e) return cuda_fail(ix, e, "persistent propagate");
     code = ix->h_pinned[8];
     return code ? propagate_error(ix, code, s) : DBL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Check of the bounded grid barrier (dbl_barrier_probe): every block but
+// `absent` meets at one barrier of the index's barrier words, whose wait
+// gives up after bar.spin_limit polls; the absent block only leaves.  With
+// absent < 0 every block arrives and the launch ends without error; otherwise
+// the waits run out, DBL_ERR_TIMEOUT is latched, and every block still leaves
+// (the last one resets the barrier words for the next launch).
+__global__ void k_barrier_probe(GridBarrier bar, uint32_t *status, int absent)
+{
+    GridSync gs(bar);
+    if ((int)blockIdx.x != absent) gs.sync(status);
+    gs.leave();
+}
+
+dbl_status barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent, cudaStream_t s)
+{
+    GridBarrier bar = grid_barrier_at(ix->d_counts);
+    bar.spin_limit = (unsigned long long)spin_limit;
+    uint32_t *status = ix->d_status;
+    int ab = absent;
+    void *args[] = {&bar, &status, &ab};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3((unsigned)num_sms()), dim3(32),
+                                                args, 0, s);
+    ++ix->launches;
+    return e ? cuda_fail(ix, e, "barrier probe launch") : DBL_OK;
 }
 
 }  // namespace dbl

@@ -78,10 +78,16 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
         for (int j = 0; j < QPT; ++j) {
             const bool ok = live[j] && (uint32_t)u[j] < (uint32_t)n && (uint32_t)v[j] < (uint32_t)n && u[j] != v[j];
             const int32_t uu = ok ? u[j] : 0, vv = ok ? v[j] : 0;
-            fu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + w0));
-            bu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + HS + w0));
-            fv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + w0));
-            bv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + HS + w0));
+            if constexpr (HS == 2) {
+                // a 32-byte record is one sector: one load for both halves
+                load_rec32(rec + (size_t)uu * RW, fu[j].x, fu[j].y, bu[j].x, bu[j].y);
+                load_rec32(rec + (size_t)vv * RW, fv[j].x, fv[j].y, bv[j].x, bv[j].y);
+            } else {
+                fu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + w0));
+                bu[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)uu * RW + HS + w0));
+                fv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + w0));
+                bv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + (size_t)vv * RW + HS + w0));
+            }
         }
 #pragma unroll
         for (int j = 0; j < QPT; ++j) {
@@ -433,8 +439,12 @@ __device__ __forceinline__ unsigned long long search_edge_visit(const SearchArgs
     constexpr int W = QT<WD, WB>::W;
     const uint64_t *qg = a.qtab + (size_t)g * 64 * W;
     uint64_t fy[HS], by[HS];
-    load_half<HS>(a.rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
-    load_half<HS>(a.rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
+    if constexpr (HS == 2) {  // 32-byte records: one load for both halves
+        load_rec32(a.rec + (size_t)y * RW, fy[0], fy[1], by[0], by[1]);
+    } else {
+        load_half<HS>(a.rec + (size_t)y * RW, fy);       // DL_in(y) | BL_in(y)
+        load_half<HS>(a.rec + (size_t)y * RW + HS, by);  // DL_out(y) | BL_out(y)
+    }
     unsigned long long hits = 0, allowed = 0, rest = m;
     while (rest) {
         const int b = __ffsll((long long)rest) - 1;

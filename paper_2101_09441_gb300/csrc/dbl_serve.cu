@@ -61,7 +61,7 @@ struct dbl_server {
     bool stop = false;
     uint64_t epoch = 0;
     std::vector<double> lat_q, lat_i;
-    uint64_t queries_done = 0, edges_done = 0, batches = 0, batched_requests = 0;
+    uint64_t queries_done = 0, edges_done = 0, batches = 0, batched_requests = 0, cancelled = 0;
     Clock::time_point t0;
     bool started = false;
     std::string err;
@@ -276,6 +276,28 @@ dbl_status dbl_server_wait(dbl_server *S, uint64_t ticket, double *latency_s)
     return st;
 }
 
+dbl_status dbl_server_cancel(dbl_server *S, uint64_t ticket)
+{
+    if (!S) return DBL_ERR_INVALID;
+    Request *r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->all.find(ticket);
+        if (it == S->all.end()) return DBL_ERR_INVALID;
+        r = it->second;
+        auto q = std::find(S->pending.begin(), S->pending.end(), r);
+        if (r->done || q == S->pending.end()) return DBL_ERR_BUSY;  // a slot has it, or it is over
+        S->pending.erase(q);
+        r->status = DBL_ERR_CANCELLED;
+        r->t_done = Clock::now();
+        r->done = true;
+        ++S->cancelled;
+    }
+    S->cv_work.notify_all();  // the request may have been holding up the queue head
+    S->cv_done.notify_all();
+    return DBL_OK;
+}
+
 dbl_status dbl_server_drain(dbl_server *S)
 {
     if (!S) return DBL_ERR_INVALID;
@@ -303,6 +325,7 @@ dbl_status dbl_server_report(dbl_server *S, double out[16])
     out[10] = (double)S->batches;
     out[11] = (double)S->batched_requests;
     out[12] = (double)S->epoch;
+    out[13] = (double)S->cancelled;
     return DBL_OK;
 }
 
@@ -312,7 +335,7 @@ dbl_status dbl_server_reset_stats(dbl_server *S)
     std::lock_guard<std::mutex> lk(S->mu);
     S->lat_q.clear();
     S->lat_i.clear();
-    S->queries_done = S->edges_done = S->batches = S->batched_requests = 0;
+    S->queries_done = S->edges_done = S->batches = S->batched_requests = S->cancelled = 0;
     S->t0 = Clock::now();
     return DBL_OK;
 }

@@ -182,7 +182,8 @@ def test_tiny_full_pipeline(tiny):
 
 # ---------------------------------------------------------------- label widths
 @pytest.mark.parametrize("k,kprime", [(64, 64), (128, 64), (64, 128), (128, 128), (256, 64), (64, 256),
-                                      (256, 256), (128, 256), (256, 128)])
+                                      (256, 256), (128, 256), (256, 128), (16, 16), (32, 32), (16, 32),
+                                      (32, 16), (16, 64), (64, 16), (32, 256), (256, 32)])
 def test_widths_random_selection(k, kprime):
     rp, col = dbl_inputs.rmat_csr(3000, 12_000, 31 + k + kprime)
     n = 3000
@@ -338,6 +339,138 @@ def test_snapshot_restore(tiny):
     ref.insert_edges(s[:4000], d[:4000])
     assert_labels(ix, ref, "after restore + insert")
     assert_queries(ix, ref, tiny["q_u"][:30000], tiny["q_v"][:30000], "after restore")
+
+
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
+def test_restore_of_changed_vertices_only(tiny, flags):
+    """A restore to the snapshot the index last equalled copies back only the
+    vertices whose record or adjacency changed since; a restore to another
+    slot copies everything.  The choice is made on the device, so a captured
+    restore stays right when later snapshots change which slot the index last
+    equalled.  A restore drops the snapshots taken after it.  Every case ends
+    in the oracle's labels and answers."""
+    rp, col = tiny["row_ptr"], tiny["col"]
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    A, B = (s[:5000], d[:5000]), (s[5000:], d[5000:])
+    qu, qv = tiny["q_u"][:20000], tiny["q_v"][:20000]
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64, flags=flags, edge_capacity=1 << 16, vertex_capacity=len(rp) + 63)
+    refA = oracle.OracleIndex(rp, col, 64, 64).build()
+    refA.insert_edges(*A)
+    refAB = oracle.OracleIndex(rp, col, 64, 64).build()
+    refAB.insert_edges(s, d)
+    ix.sync()
+    L0 = labels_np(ix)
+    ix.snapshot(0)
+
+    def same(want, what):
+        ix.sync()
+        for a, b in zip(labels_np(ix), want):
+            assert np.array_equal(a, b), what
+
+    ix.insert_edges(D(A[0]), D(A[1]))
+    ix.restore(0)                              # changed vertices only
+    same(L0, "restore of the changes")
+    ix.insert_edges(D(A[0]), D(A[1]))
+    ix.sync()
+    assert_labels(ix, refA, "A after restore")
+    ix.snapshot(1)                             # the index now equals slot 1
+    ix.insert_edges(D(B[0]), D(B[1]))
+    ix.restore(1)                              # changed vertices only
+    ix.sync()
+    assert_labels(ix, refA, "restore to slot 1")
+    assert_queries(ix, refA, qu, qv, "after restore to slot 1")
+    ix.restore(0)                              # another slot: everything; slot 1 is dropped
+    same(L0, "full restore")
+    with pytest.raises(dbl.DblError) as e:
+        ix.restore(1)
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    ix.insert_edges(D(s), D(d))
+    ix.sync()
+    assert_labels(ix, refAB, "A+B after full restore")
+    assert_queries(ix, refAB, qu, qv, "A+B after full restore")
+    ix.restore(0)
+    ix.restore(0)                              # nothing changed in between
+    same(L0, "restore with nothing changed")
+    # vertices added after the snapshot go away; their rows return cleared
+    first = ix.add_vertices(3)
+    ix.insert_edges(D(np.array([first, first + 1], np.int32)), D(np.array([int(s[0]), first + 2], np.int32)))
+    ix.restore(0)
+    ix.sync()
+    assert ix.n == first
+    same(L0, "restore after vertex insertion")
+    ix.insert_edges(D(A[0]), D(A[1]))
+    ix.sync()
+    assert_labels(ix, refA, "A after the vertex round trip")
+    assert_queries(ix, refA, qu, qv, "A after the vertex round trip")
+    if flags & dbl.FLAG_ASYNC:
+        # a captured restore + insertion, replayed after a snapshot to another slot
+        ix.restore(0)
+        ix.sync()
+        g = torch.cuda.CUDAGraph()
+        dA0, dA1 = D(A[0]), D(A[1])
+        with torch.cuda.graph(g):
+            ix.restore(0)
+            ix.insert_edges(dA0, dA1)
+        for _ in range(2):
+            g.replay()
+            torch.cuda.synchronize()
+            assert_labels(ix, refA, "captured restore + insert")
+        ix.snapshot(2)                         # the index now equals slot 2
+        g.replay()                             # the captured restore(0) must copy everything
+        torch.cuda.synchronize()
+        assert_labels(ix, refA, "captured restore after another snapshot")
+        assert_queries(ix, refA, qu, qv, "captured restore after another snapshot")
+    ix.close()
+
+
+@pytest.mark.parametrize("slots", [-1, 2, 4, 64])
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
+def test_reserved_slots_and_segment_growth(tiny, slots, flags):
+    """Inserted-edge slots reserved per vertex at build (dbl_options
+    initial_slots): batches whose endpoints all have room take the
+    one-phase append of the persistent insertion, a batch in which a hub
+    gains 300 out-edges and 300 in-edges grows segments; with no reserved
+    slots every first insertion grows one.  Labels and answers equal the
+    oracle's after every batch."""
+    rp, col = tiny["row_ptr"], tiny["col"]
+    n = len(rp) - 1
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    hub = int(np.argmax(np.diff(rp)))
+    have = set(col[rp[hub]:rp[hub + 1]].tolist())
+    outs = np.array([t for t in range(n) if t != hub and t not in have][:300], np.int32)
+    ins_from = np.array([t for t in range(n - 1, -1, -1) if t != hub and hub not in
+                         set(col[rp[t]:rp[t + 1]].tolist())][:300], np.int32)
+    batches = [(s[:2000], d[:2000]),
+               (np.concatenate([np.full(300, hub, np.int32), ins_from, s[2000:3000]]),
+                np.concatenate([outs, np.full(300, hub, np.int32), d[2000:3000]])),
+               (s[3000:], d[3000:])]
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64, flags=flags, initial_slots=slots, edge_capacity=1 << 16)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    for k, (bs, bd) in enumerate(batches):
+        ix.insert_edges(D(bs), D(bd))
+        ref.insert_edges(bs, bd)
+        ix.sync()
+        assert_labels(ix, ref, f"slots={slots}, batch {k}")
+    assert_queries(ix, ref, tiny["q_u"][:20000], tiny["q_v"][:20000], f"slots={slots}")
+    ix.close()
+
+
+@pytest.mark.parametrize("k,kp", [(64, 64), (128, 64), (256, 256)])
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT])
+def test_split_build_equals_joint_build(tiny, k, kp, flags):
+    """The label build over each direction's halves in turn (dbl_options
+    build_split = 1) gives the same least fixpoint as the joint build, and
+    both equal the oracle's labels (Algorithm 1)."""
+    rp, col = tiny["row_ptr"], tiny["col"]
+    a = dbl.DBLIndex(D(rp), D(col), k, kp, flags=flags, build_split=1)
+    b = dbl.DBLIndex(D(rp), D(col), k, kp, flags=flags, build_split=-1)
+    ref = oracle.OracleIndex(rp, col, k, kp).build()
+    assert_labels(a, ref, f"split build k={k} k'={kp}")
+    assert_labels(b, ref, f"joint build k={k} k'={kp}")
+    a.insert_edges(D(tiny["ins_src"]), D(tiny["ins_dst"]))
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    a.sync()
+    assert_labels(a, ref, "split build, after insertions")
 
 
 def test_batch_size_invariance(tiny):

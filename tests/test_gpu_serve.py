@@ -125,3 +125,40 @@ def test_server_backpressure_and_report(tiny):
     assert rep["pairs"] == 4000 * len(tickets)
     with pytest.raises(dbl.DblError):
         dbl.Server(ix, slots=2, max_batch=1 << 12).submit(0, np.zeros(5000, np.int32), np.zeros(5000, np.int32))
+
+
+def test_server_cancel_drops_queued_requests(tiny):
+    """Requests cancelled before a slot takes them are dropped: their waits
+    report DBL_ERR_CANCELLED, a cancelled insertion is never applied, and
+    every other result equals a serial replay of the requests that were not
+    cancelled."""
+    reqs = _request_stream(tiny, 300, 13)
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    srv = dbl.Server(ix, slots=2, max_batch=1 << 12)
+    tickets = [srv.submit(k, a, b) for k, a, b in reqs]
+    cancelled = {i for i in range(len(reqs) - 1, 0, -3) if srv.cancel(tickets[i])}
+    got = {}
+    for i, t in enumerate(tickets):
+        if i in cancelled:
+            with pytest.raises(dbl.DblError) as e:
+                srv.wait(t)
+            assert e.value.status == dbl.DBL_ERR_CANCELLED
+        else:
+            got[i] = srv.wait(t)[0]
+    with pytest.raises(dbl.DblError) as e:
+        srv.cancel(tickets[0])                 # waited for already: an unknown ticket
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    rep = srv.report()
+    srv.close()
+    assert cancelled and rep["cancelled"] == len(cancelled)
+    assert any(reqs[i][0] == 1 for i in cancelled) or len(cancelled) > 5
+    alone = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    for i, (k, a, b) in enumerate(reqs):
+        if i in cancelled:
+            continue
+        if k == 1:
+            alone.insert_edges(D(a), D(b))
+        else:
+            assert np.array_equal(got[i], alone.query(D(a), D(b))[0].cpu().numpy())
+    for x, y in zip(ix.labels(), alone.labels()):
+        assert torch.equal(x, y)

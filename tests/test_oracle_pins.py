@@ -130,7 +130,8 @@ def _selections(n, k, kprime, o, mode, seed):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=[s[0] for s in SHAPES])
 @pytest.mark.parametrize("k,kprime,mode", [(64, 64, "degree"), (128, 64, "random"),
-                                           (64, 128, "random"), (3, 5, "random")])
+                                           (64, 128, "random"), (3, 5, "random"), (16, 16, "degree"),
+                                           (32, 16, "random"), (16, 32, "random"), (32, 32, "degree")])
 def test_labels_and_answers_match_closure(shape, k, kprime, mode):
     name, n, s, d = shape
     rp, col = H.csr_from_edges(n, s, d)

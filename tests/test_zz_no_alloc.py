@@ -29,12 +29,15 @@ def _labels(ix):
     return [t.cpu().numpy().view(np.uint64) for t in ix.labels()]
 
 
-def test_noalloc_insert_matches_allocating_insert():
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT, dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC])
+def test_noalloc_insert_matches_allocating_insert(flags):
+    """Level-by-level kernels, and the persistent insertion kernel (which keeps
+    its per-edge slot words in the same scratch), synchronous and not."""
     dbl.build()
     w = dbl_inputs.workload("tiny", with_queries=False)
     rp, col = _dev(w["row_ptr"]), _dev(w["col"])
-    a = dbl.DBLIndex(rp, col, 64, 64)   # allocating entry point
-    b = dbl.DBLIndex(rp, col, 64, 64)   # allocation-free entry point
+    a = dbl.DBLIndex(rp, col, 64, 64, flags=flags)   # allocating entry point
+    b = dbl.DBLIndex(rp, col, 64, 64, flags=flags)   # allocation-free entry point
     L = dbl.lib()
     s = torch.cuda.current_stream().cuda_stream
     src, dst = _dev(w["ins_src"]), _dev(w["ins_dst"])
@@ -43,6 +46,8 @@ def test_noalloc_insert_matches_allocating_insert():
         st = L.dbl_insert_edges_noalloc(ctypes.c_void_p(b._h.value), ctypes.c_void_p(src[lo:hi].data_ptr()),
                                         ctypes.c_void_p(dst[lo:hi].data_ptr()), hi - lo, ctypes.c_void_p(s))
         assert st == dbl.DBL_OK, L.dbl_last_error(b._h).decode()
+        a.sync()
+        b.sync()
         torch.cuda.synchronize()
         for x, y in zip(_labels(a), _labels(b)):
             assert np.array_equal(x, y)
@@ -51,6 +56,8 @@ def test_noalloc_insert_matches_allocating_insert():
     qv = _dev(np.arange(1, 16381, 3, dtype=np.int32))
     ra, ca = a.query(qu, qv)
     rb, cb = b.query(qu, qv)
+    a.sync()
+    b.sync()
     assert torch.equal(ra, rb) and torch.equal(ca, cb)
 
 
