@@ -161,6 +161,30 @@ def whole_job_rate(units_per_rank: float, world: int, total_ms: float) -> float:
     return world * units_per_rank / (total_ms * 1e-3)
 
 
+def shard_range(q: int, rank: int, world: int) -> tuple[int, int]:
+    """Rank `rank`'s contiguous slice of q queries: the slices of all ranks
+    cover [0, q) once, in rank order, sizes differing by at most one."""
+    base, extra = divmod(q, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def gather_answers(local, q: int, world: int, tdist):
+    """Every rank's answers (uint8 tensor of its shard_range slice) back in
+    input order on every rank: one all_gather of equal-length padded pieces
+    (the only collective, and only after the timed region)."""
+    import torch
+    if world <= 1:
+        return local
+    width = q // world + 1
+    buf = torch.zeros(width, dtype=torch.uint8, device=local.device)
+    buf[:local.numel()] = local
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    tdist.all_gather(parts, buf)
+    out = [parts[r][:shard_range(q, r, world)[1] - shard_range(q, r, world)[0]] for r in range(world)]
+    return torch.cat(out)
+
+
 def step_batches(n_edges: int, batch: int):
     return [(b, min(b + batch, n_edges)) for b in range(0, n_edges, batch)]
 
@@ -201,12 +225,14 @@ def run_oracle_step(ref, w, batches, nq, threads):
     return t1 - t0, t2 - t1
 
 
-def workload_config(args, w, form="learned+batched (persistent kernels, CUDA graphs)"):
+def workload_config(args, w, form="learned+batched (persistent kernels, CUDA graphs)", world=1):
     return {"workload": args.workload, "n": int(w["n"]), "m": int(w["m"]), "seed": int(w["seed"]), "k": args.k,
             "kprime": args.kprime, "k2": args.k2, "insert_batch": args.batch,
             "inserted_edges_per_step": int(w["ins_src"].shape[0]),
             "queries_per_step": int(w["q_u"].shape[0]), "form": form,
-            "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas"}
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": "replicas" if world <= 1 else
+            f"{world} replicas: every rank applies every insertion, rank r answers its 1/{world} slice of the queries"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -433,7 +459,7 @@ def run_form(name, args, w, I, k, kp, landmarks, leaves, batches, qbatches, worl
 
     import paper_2101_09441_gb300 as dbl
     E = int(batches[-1][1]) if batches else 0
-    Q = int(qbatches[-1][1]) if (queries and qbatches) else 0
+    Q = sum(int(b) - int(a) for a, b in qbatches) if (queries and qbatches) else 0  # this rank's queries
     flags = form_flags(name)
     kw = dict(flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
     if landmarks is not None:
@@ -496,7 +522,7 @@ def run_form(name, args, w, I, k, kp, landmarks, leaves, batches, qbatches, worl
     if queries:
         step.query()
         ix.sync()
-        res["decided_by"] = decided_by(I.code[:Q])
+        res["decided_by"] = decided_by(I.code[qbatches[0][0]:qbatches[-1][1]])
         res["searched"] = res["decided_by"]["bfs_pos"] + res["decided_by"]["bfs_neg"]
     res["clocks"] = clocks
     if keep:
@@ -747,7 +773,10 @@ def bench_gpu(args):
     w = dbl_inputs.workload(args.workload)
     E, Q = int(w["ins_src"].shape[0]), int(w["q_u"].shape[0])
     batches = step_batches(E, args.batch)
-    qbatches = [(0, Q)]
+    # replicas: every rank applies every insertion batch; the query batch is
+    # sharded, rank r answering its slice (no collective on the data path)
+    q_lo, q_hi = shard_range(Q, rank, world)
+    qbatches = [(q_lo, q_hi)]
     I = Inputs(w, dev)
     k, kp, k2 = args.k, args.kprime, args.k2
     S = args.steps
@@ -778,6 +807,9 @@ def bench_gpu(args):
             k2_forms[name] = run_form(name, args, w, I, k2, kp, None, None, batches, qbatches, *common, S)
         lm2, leaves2, linfo2, pix2 = train_learned(args, w, I, k2, kp, batches, dev)
         pix2.close()
+        if not args.no_serve:
+            # serving on the learned k2 index (the serving configuration of the workload)
+            k2_forms["serving"] = serving_pass(w, I, k2, kp, lm2, leaves2, args.serve_requests)
         k2_forms["learned"] = run_form("learned", args, w, I, k2, kp, lm2, leaves2, batches, qbatches, *common, S)
         k2_forms["learned"]["training"] = linfo2
         k2_forms["fallback_to_degree_rule"] = learned_judge(k2_forms["learned"], k2_forms["graph"])
@@ -785,9 +817,10 @@ def bench_gpu(args):
 
     # ---- end to end through the host-buffer C-ABI calls, headline index
     ix = learned["ix"]
-    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-    h_src, h_dst, h_qu, h_qv = pin(w["ins_src"]), pin(w["ins_dst"]), pin(w["q_u"]), pin(w["q_v"])
-    h_ans = torch.empty(Q, dtype=torch.uint8).pin_memory().numpy()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_src, h_dst = pin(w["ins_src"]), pin(w["ins_dst"])
+    h_qu, h_qv = pin(w["q_u"][q_lo:q_hi]), pin(w["q_v"][q_lo:q_hi])
+    h_ans = torch.empty(q_hi - q_lo, dtype=torch.uint8).pin_memory().numpy()
     e2e_steps = 0 if args.no_e2e else S
 
     def e2e_step():
@@ -815,14 +848,15 @@ def bench_gpu(args):
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": S,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(args, w),
+            "config": workload_config(args, w, world=world),
             "forms": {**{kk: public(v) for kk, v in forms.items()}, "learned": public(learned),
                       "learned_timing_pass": public(learned_t)},
             "learned_vs_plain": head["value"] / forms["plain"]["value"] if "plain" in forms else None,
             "learned": {"fallback_to_degree_rule": bool(fallback), **linfo},
             "learned_gain": {f"k{k}": gain_k,
                              **({f"k{k2}": gain(k2_forms["graph"], k2_forms["learned"])} if k2 else {})},
-            f"forms_k{k2}": {kk: (public(v) if isinstance(v, dict) else v) for kk, v in k2_forms.items()} if k2 else None,
+            f"forms_k{k2}": {kk: (public(v) if isinstance(v, dict) else v) for kk, v in k2_forms.items()
+                             if kk != "serving"} if k2 else None,
             "restore": {"ms": head["restore_ms"], "share_of_step": head["restore_ms"] / head["ms_per_step"],
                         "value_excl_restore": head["value_excl_restore"],
                         "note": "dbl_restore returns the index to its built state at the start of every step "
@@ -831,8 +865,9 @@ def bench_gpu(args):
             "roofline_label_test": roof_label,
             "roofline_build": build_roofline(learned_t),
             "roofline_scorer": roof_scorer,
-            "e2e": {"value": world * e2e_steps * (E + Q) / e2e_s if e2e_steps else None, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (E + Q), "d2h_bytes_per_step": Q},
+            "e2e": {"value": world * e2e_steps * (E + q_hi - q_lo) / e2e_s if e2e_steps else None, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (E + q_hi - q_lo), "d2h_bytes_per_step": q_hi - q_lo},
+            "serving": k2_forms.get("serving"),
             "extras": extras,
             "clocks": learned["clocks"],
             "gpu_launches": head["gpu_launches"]}
@@ -925,6 +960,41 @@ def run_serving(srv, reqs, rate=None, seed=0):
     return rep
 
 
+def serving_pass(w, I, k, kp, lm, leaves, n_req, slots=4):
+    """Serving on a resident index with the given landmarks: a closed-loop run
+    gives the peak request rate, then Poisson streams at 50% and 90% of it
+    report p50/p99 latency per request kind and sustained pairs/s and
+    edges/s.  Every run starts from the built index."""
+    import paper_2101_09441_gb300 as dbl
+    E = int(w["ins_src"].shape[0])
+    ix = dbl.DBLIndex(I.rp, I.col, k, kp, landmarks=lm, leaf_buckets=leaves[0], leaf_roles=leaves[1],
+                      edge_capacity=max(2 * E, 1 << 20), flags=dbl.FLAG_PERSISTENT)
+    ix.sync()
+    ix.snapshot(0)
+
+    def run(reqs, rate, seed):
+        ix.restore(0)
+        ix.sync()
+        srv = dbl.Server(ix, slots=slots)
+        try:
+            return run_serving(srv, reqs, rate, seed)
+        finally:
+            srv.close()
+
+    warm, _, _ = serve_requests(w, max(1, n_req // 4), 99)
+    run(warm, None, 0)
+    reqs, _, _ = serve_requests(w, n_req, 100)
+    peak = run(reqs, None, 0)
+    loads = {}
+    for i, frac in enumerate((0.5, 0.9)):
+        reqs, _, _ = serve_requests(w, n_req, 200 + i, q_off=(i + 1) * 3_000_000)
+        loads[str(frac)] = run(reqs, frac * peak["requests_per_s"], 300 + i)
+    ix.close()
+    return {"k": k, "kprime": kp, "slots": slots, "requests_per_run": n_req,
+            "mix": "90% query / 10% insertion requests, sizes floor(exp(U[0, ln 65537)))",
+            "closed_loop_peak": peak, "poisson": loads}
+
+
 def bench_serve(args):
     """Serving measurement: the learned index (k = 128, k' = 64) resident on
     the device behind dbl_server; a closed-loop run gives the peak request
@@ -934,7 +1004,6 @@ def bench_serve(args):
 
     import dbl_inputs
     import paper_2101_09441_gb300 as dbl
-    from paper_2101_09441_gb300 import learned as L
     dbl.build()
     w = dbl_inputs.workload(args.serve_workload)
     dev = torch.device("cuda", 0)
@@ -942,46 +1011,13 @@ def bench_serve(args):
     E = int(w["ins_src"].shape[0])
     k, kp = 128, 64
     t0 = time.perf_counter()
-    plain = dbl.DBLIndex(I.rp, I.col, k, kp, edge_capacity=max(E, 1 << 20))
-    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], args.train_queries, w["seed"] + 300, False,
-                                w["ins_src"], w["ins_dst"])
-    base_slots = k // 8
-    scores, tinfo = L.train_scorer(plain, torch.from_numpy(tu).to(dev), torch.from_numpy(tv).to(dev), base_slots,
-                                   steps=args.train_steps)
-    lm = L.select_landmarks(plain, scores, k, base_slots)
-    _, lb, lr_ = plain.selection()
+    lm, leaves, tinfo, plain = train_learned(args, w, I, k, kp, step_batches(E, args.batch), dev)
     plain.close()
-    ix = dbl.DBLIndex(I.rp, I.col, k, kp, landmarks=lm, leaf_buckets=lb, leaf_roles=lr_,
-                      edge_capacity=max(2 * E, 1 << 20), flags=dbl.FLAG_PERSISTENT)
-    ix.sync()
-    ix.snapshot(0)
     setup_s = time.perf_counter() - t0
-    n_req = args.serve_requests
-
-    def run(reqs, rate, seed):
-        # every run starts from the built index, so each one inserts new edges only
-        ix.restore(0)
-        ix.sync()
-        srv = dbl.Server(ix, slots=4)
-        try:
-            return run_serving(srv, reqs, rate, seed)
-        finally:
-            srv.close()
-
-    warm, _, _ = serve_requests(w, n_req // 4, 99)
-    run(warm, None, 0)
-    reqs, _, _ = serve_requests(w, n_req, 100)
-    peak = run(reqs, None, 0)
-    loads = {}
-    for i, frac in enumerate((0.5, 0.9)):
-        reqs, _, _ = serve_requests(w, n_req, 200 + i, q_off=(i + 1) * 3_000_000)
-        loads[str(frac)] = run(reqs, frac * peak["requests_per_s"], 300 + i)
-    ix.close()
+    rep = serving_pass(w, I, k, kp, lm, leaves, args.serve_requests)
     line = {"metric": "serving: p50/p99 latency and sustained throughput under Poisson load", "impl": "dbl",
-            "workload": args.serve_workload, "n": int(w["n"]), "m": int(w["m"]), "k": k, "kprime": kp,
-            "landmarks": "learned", "mix": "90% query / 10% insertion requests, sizes floor(exp(U[0, ln 65537)))",
-            "requests_per_run": n_req, "setup_s": setup_s, "closed_loop_peak": peak, "poisson": loads,
-            "learned": {kk: v for kk, v in tinfo.items() if kk != "losses"}}
+            "workload": args.serve_workload, "n": int(w["n"]), "m": int(w["m"]), "landmarks": "learned",
+            "setup_s": setup_s, **rep, "learned": tinfo}
     print(json.dumps(line), flush=True)
 
 
@@ -1077,6 +1113,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving measurement instead of the step benchmark")
     ap.add_argument("--serve-workload", default="large", choices=["large", "social", "tiny"])
     ap.add_argument("--serve-requests", type=int, default=1500)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving pass of the step benchmark")
     ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]

@@ -93,3 +93,46 @@ def test_cpu_baseline_reports_all_cores_and_one_thread():
     assert r["kind"] == "oracle" and r["cores"] >= 1 and r["value"] > 0 and r["cpu_model"]
     one = r["single_thread"]
     assert one["value"] > 0 and one["queries_per_s"] > 0 and one["inserted_edges_per_s"] > 0
+
+
+def test_query_shards_cover_the_batch_once_in_order():
+    import bench
+    for world in range(1, 8):
+        for q in (0, 1, 5, 7, 1003, 10_000_000):
+            parts = [bench.shard_range(q, r, world) for r in range(world)]
+            assert parts[0][0] == 0 and parts[-1][1] == q
+            for (a, b), (c, d) in zip(parts, parts[1:]):
+                assert b == c and a <= b
+            sizes = [b - a for a, b in parts]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _shard_worker(rank, world, port, q):
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    Q = 1003
+    lo, hi = bench.shard_range(Q, rank, world)
+    local = (torch.arange(lo, hi) * 7 % 251).to(torch.uint8)   # this rank's "answers"
+    got = bench.gather_answers(local, Q, world, tdist)
+    want = (torch.arange(Q) * 7 % 251).to(torch.uint8)
+    q.put((rank, bool(torch.equal(got, want)), hi - lo))
+    tdist.destroy_process_group()
+
+
+def test_sharded_answers_gather_back_in_input_order():
+    """Two gloo ranks answer their slices of a query batch; the gathered
+    answers come back complete and in input order on every rank."""
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    assert all(ok for _, ok, _ in got)
+    assert sum(n for _, _, n in got) == 1003
