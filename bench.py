@@ -435,10 +435,13 @@ FORM_FLAGS = {  # library flags of each form (FLAG_TIMING only in the separate t
 }
 
 
-def form_flags(name):
+def form_flags(name, fine_l2=False):
+    """The form's library flags; fine_l2 adds DBL_FLAG_FINE_L2 (a process-wide
+    setting: the first index built with it sets it for every later kernel, so
+    it is given to every form or to none)."""
     import paper_2101_09441_gb300 as dbl
     spec = FORM_FLAGS[name]
-    f = 0
+    f = dbl.FLAG_FINE_L2 if fine_l2 else 0
     for c in (spec.split("|") if spec else []):
         f |= {"P": dbl.FLAG_PERSISTENT, "A": dbl.FLAG_ASYNC, "T": dbl.FLAG_TIMING}[c]
     return f
@@ -460,7 +463,7 @@ def run_form(name, args, w, I, k, kp, landmarks, leaves, batches, qbatches, worl
     import paper_2101_09441_gb300 as dbl
     E = int(batches[-1][1]) if batches else 0
     Q = sum(int(b) - int(a) for a, b in qbatches) if (queries and qbatches) else 0  # this rank's queries
-    flags = form_flags(name)
+    flags = form_flags(name, args.fine_l2)
     kw = dict(flags=flags, team=args.team, edge_capacity=max(E, 1 << 20))
     if landmarks is not None:
         kw.update(landmarks=landmarks, leaf_buckets=leaves[0], leaf_roles=leaves[1])
@@ -1085,6 +1088,46 @@ def bench_sweep(args):
                       "peak_source": f"hbm_gbs of {src}", "sweep": rows}), flush=True)
 
 
+def bench_kernel_case(args):
+    """A small, single-index run of one kernel for an ncu capture: `label`
+    builds the index (k, k'), applies the workload's insertions and answers
+    its query batch `args.steps` times; `insert` applies the insertions in
+    batches of `args.batch` (persistent kernels, asynchronous calls).  Prints
+    per-kernel CUDA-event times (one JSON line)."""
+    import torch
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    dbl.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = dbl_inputs.workload(args.workload, with_queries=args.kernel_case == "label")
+    I = Inputs(w, dev) if args.kernel_case == "label" else None
+    rp = torch.from_numpy(w["row_ptr"]).to(dev)
+    col = torch.from_numpy(w["col"]).to(dev)
+    src, dst = torch.from_numpy(w["ins_src"]).to(dev), torch.from_numpy(w["ins_dst"]).to(dev)
+    E = int(src.numel())
+    flags = dbl.FLAG_PERSISTENT | dbl.FLAG_TIMING | (dbl.FLAG_FINE_L2 if args.fine_l2 else 0)
+    if args.kernel_case == "insert":
+        flags |= dbl.FLAG_ASYNC
+    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, edge_capacity=max(E, 1 << 20), flags=flags)
+    ix.sync()
+    ix.timings()
+    for a, b in step_batches(E, args.batch):
+        ix.insert_edges(src[a:b], dst[a:b])
+    ix.sync()
+    if args.kernel_case == "label":
+        for _ in range(args.steps):
+            ix.query(I.qu, I.qv, out=(I.ans, I.code))
+        ix.sync()
+    t = ix.timings()
+    print(json.dumps({"kernel_case": args.kernel_case, "workload": args.workload, "k": args.k,
+                      "kprime": args.kprime, "fine_l2": bool(args.fine_l2),
+                      "ms_per_launch": {kk: v[0] / max(1, v[1]) for kk, v in t.items() if v[1]},
+                      "launches": {kk: v[1] for kk, v in t.items() if v[1]}}), flush=True)
+    ix.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1115,11 +1158,17 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving pass of the step benchmark")
     ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
+    ap.add_argument("--kernel-case", choices=["label", "insert"], default=None,
+                    help="a small single-index run of one kernel (for an ncu capture) instead of the step")
+    ap.add_argument("--fine-l2", action="store_true",
+                    help="DBL_FLAG_FINE_L2 in every form: 32-byte L2 fetch granularity for the whole process")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.warmup < 3:
         args.warmup = 3
-    if args.serve:
+    if args.kernel_case:
+        bench_kernel_case(args)
+    elif args.serve:
         bench_serve(args)
     elif args.sweep:
         bench_sweep(args)
