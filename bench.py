@@ -301,9 +301,10 @@ def cpu_baseline(args, w):
 
 
 # ------------------------------------------------------------------ GPU arm
-def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes, src_all, dst_all):
+def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes, src_all, dst_all, group=False):
     """Algorithmic bytes of label repair for one step: per direction, over the
-    vertices whose half-record changes in a batch, offsets (8 B) + adjacency
+    vertices whose half-record changes in a batch (in the whole group of
+    batches when they are applied together), offsets (8 B) + adjacency
     (4 B/edge) + neighbour record sectors (32 B/edge) + own write."""
     import torch
     ix.restore(0)
@@ -312,6 +313,8 @@ def changed_bytes(ix, w, batches, deg_out0, deg_in0, rec_half_bytes, src_all, ds
     deg_in = deg_in0.clone()
     total = 0.0
     prev = ix.labels()
+    if group:
+        batches = [(batches[0][0], batches[-1][1])] if batches else []
     for a, b in batches:
         ix.insert_edges(src_all[a:b], dst_all[a:b])
         cur = ix.labels()
@@ -349,9 +352,9 @@ class Step:
     CUDA graphs; CUDA events on the current stream between the parts give the
     split of every step."""
 
-    def __init__(self, ix, I, batches, qbatches, use_graph: bool, queries: bool = True):
+    def __init__(self, ix, I, batches, qbatches, use_graph: bool, queries: bool = True, defer: bool = False):
         self.ix, self.I, self.batches, self.qbatches = ix, I, batches, qbatches
-        self.use_graph, self.queries = use_graph, queries
+        self.use_graph, self.queries, self.defer = use_graph, queries, defer
         self.graphs = None
         self.launches_per_step = None
 
@@ -383,6 +386,12 @@ class Step:
         for i, part in enumerate(self.parts()):
             if i == 2 and not self.queries:
                 self.graphs.append(None)  # nothing to capture
+                continue
+            if i == 1 and self.defer:
+                # deferred insertions only queue on the host: queue them, and the
+                # captured query part applies them (one launch) before answering
+                part()
+                self.graphs.append(None)
                 continue
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
@@ -430,8 +439,9 @@ def time_steps(step, steps, world, tdist, sampler=None, profile=False):
     return e0.elapsed_time(e1), outs, clocks
 
 
-FORM_FLAGS = {  # library flags of each form (FLAG_TIMING only in the separate timing pass)
+FORM_FLAGS = {  # library flags of each form (FLAG_TIMING only in the separate timing passes)
     "plain": 0, "batched": "P|A", "graph": "P|A", "learned": "P|A", "learned_timing": "T|P|A",
+    "deferred": "P|A|D", "deferred_timing": "T|P|A|D",
 }
 
 
@@ -443,7 +453,7 @@ def form_flags(name, fine_l2=False):
     spec = FORM_FLAGS[name]
     f = dbl.FLAG_FINE_L2 if fine_l2 else 0
     for c in (spec.split("|") if spec else []):
-        f |= {"P": dbl.FLAG_PERSISTENT, "A": dbl.FLAG_ASYNC, "T": dbl.FLAG_TIMING}[c]
+        f |= {"P": dbl.FLAG_PERSISTENT, "A": dbl.FLAG_ASYNC, "T": dbl.FLAG_TIMING, "D": dbl.FLAG_DEFER}[c]
     return f
 
 
@@ -489,8 +499,8 @@ def run_form(name, args, w, I, k, kp, landmarks, leaves, batches, qbatches, worl
         team = min(tune["persistent_ms"], key=tune["persistent_ms"].get)
         ix.set_schedule(team, persistent=True)
         res["autotune"] = {"team": team, "persistent_ms": tune["persistent_ms"], "level_ms": tune["level_ms"]}
-    use_graph = name in ("graph", "learned")
-    step = Step(ix, I, batches, qbatches, use_graph, queries)
+    use_graph = name in ("graph", "learned", "deferred")  # (timing passes launch each part eagerly)
+    step = Step(ix, I, batches, qbatches, use_graph, queries, defer=bool(flags & dbl.FLAG_DEFER))
     for _ in range(args.warmup):
         for f in step.parts():
             f()
@@ -612,7 +622,7 @@ def build_roofline(form):
             "teps": relaxed / (ms * 1e-3) if relaxed else None}
 
 
-def roofline(form, ix, steps, w, I, batches, persistent=True):
+def roofline(form, ix, steps, w, I, batches, persistent=True, group=False):
     """Achieved GB/s of the form's dominant kernel class (library CUDA events
     over the timed region) against the measured HBM copy peak.  In the
     persistent forms the `propagate` class is the insertion kernel (append,
@@ -628,7 +638,7 @@ def roofline(form, ix, steps, w, I, batches, persistent=True):
     repair_only = None
     if "propagate" in kern:
         prop = changed_bytes(ix, w, batches, torch.diff(I.rp).long(), torch.bincount(I.col.long(), minlength=w["n"]),
-                             rec // 2, I.src, I.dst)
+                             rec // 2, I.src, I.dst, group=group)
         alg["propagate"] = steps * (prop + (insertion_bytes(ix, w, I) if persistent else 0))
         repair_only = steps * prop
     for kk, v in kern.items():
@@ -797,11 +807,28 @@ def bench_gpu(args):
                        sample_clocks=True, keep=True)
     learned_t = run_form("learned_timing", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
                          keep=True)
+    # the headline: the same step with the insertion batches queued and applied
+    # as one group by the query call that follows them (DBL_FLAG_DEFER: the
+    # device work queue of uneven batches; each query observes exactly the
+    # insertions queued before it); its split puts the insertions inside the
+    # query part.  Its own timing pass gives the roofline figures.
+    grouped = "deferred" in args.forms
+    deferred = run_form("deferred", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
+                        sample_clocks=True) if grouped else None
+    deferred_t = run_form("deferred_timing", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
+                          keep=True) if grouped else None
     ref_form = forms.get("graph") or forms.get("batched") or forms.get("plain")
     fallback = learned_judge(learned, ref_form) if ref_form else False
-    head = forms["graph"] if (fallback and "graph" in forms) else learned
-    roof, roof_label = roofline(learned_t, learned_t["ix"], S, w, I, batches)
+    if fallback and "graph" in forms:
+        head = forms["graph"]
+    else:
+        head = deferred if grouped else learned
+    timing = deferred_t if grouped else learned_t
+    roof, roof_label = roofline(timing, timing["ix"], S, w, I, batches, group=grouped)
+    roof_per_batch = roofline(learned_t, learned_t["ix"], S, w, I, batches)[0] if grouped else None
     learned_t["ix"].close()
+    if grouped:
+        deferred_t["ix"].close()
 
     # ---- the same comparison at k2 landmarks (two words per direction at 128)
     k2_forms = {}
@@ -851,9 +878,14 @@ def bench_gpu(args):
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": S,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": workload_config(args, w, world=world),
+            "config": workload_config(args, w, world=world, form=(
+                "learned+batched (persistent kernels, CUDA graphs; the step's insertion batches queued and "
+                "applied as one group before its queries)" if head is deferred else
+                "learned+batched (persistent kernels, CUDA graphs; one launch per insertion batch)")),
             "forms": {**{kk: public(v) for kk, v in forms.items()}, "learned": public(learned),
-                      "learned_timing_pass": public(learned_t)},
+                      "learned_timing_pass": public(learned_t),
+                      **({"learned_grouped": public(deferred), "learned_grouped_timing_pass": public(deferred_t)}
+                         if grouped else {})},
             "learned_vs_plain": head["value"] / forms["plain"]["value"] if "plain" in forms else None,
             "learned": {"fallback_to_degree_rule": bool(fallback), **linfo},
             "learned_gain": {f"k{k}": gain_k,
@@ -865,14 +897,15 @@ def bench_gpu(args):
                         "note": "dbl_restore returns the index to its built state at the start of every step "
                                 "(labels and adjacency metadata copied back); it is not part of the method"},
             "roofline": roof,
+            "roofline_per_batch_insertion": roof_per_batch,
             "roofline_label_test": roof_label,
-            "roofline_build": build_roofline(learned_t),
+            "roofline_build": build_roofline(timing),
             "roofline_scorer": roof_scorer,
             "e2e": {"value": world * e2e_steps * (E + q_hi - q_lo) / e2e_s if e2e_steps else None, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (E + q_hi - q_lo), "d2h_bytes_per_step": q_hi - q_lo},
             "serving": k2_forms.get("serving"),
             "extras": extras,
-            "clocks": learned["clocks"],
+            "clocks": head["clocks"] or learned["clocks"],
             "gpu_launches": head["gpu_launches"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, w)
@@ -1027,7 +1060,8 @@ def bench_serve(args):
 def bench_sweep(args):
     """Label widths, leaf threshold and landmark ranking (Section 6, Table 5,
     Table 3 and "Label Node Selection"): the batched step (persistent kernels)
-    at k, k' in {64, 128, 256} with M-ranked landmarks and zero-degree leaves;
+    at k, k' in {64, 128, 256} and at the small widths 16 and 32 (with each
+    other and with 64) with M-ranked landmarks and zero-degree leaves;
     at k = k' = 64 with leaves M(u) <= r for r in {2, 16}, and with Table 3's
     rankings A, B, C.  One JSON line with a row per
     configuration: step time, throughput, per-kernel times (CUDA events), the
@@ -1046,13 +1080,15 @@ def bench_sweep(args):
     batches = step_batches(E, args.batch)
     peaks, src = measured_peaks()
     configs = ([(k, kp, 0, "M", 0) for k in (64, 128, 256) for kp in (64, 128, 256)] +
+               [(k, kp, 0, "M", 0) for k, kp in ((16, 16), (32, 32), (16, 64), (64, 16), (32, 64), (64, 32))] +
                [(64, 64, 2, "M", 0), (64, 64, 16, "M", 0), (64, 64, 0, "A", 0), (64, 64, 0, "B", 0),
                 (64, 64, 0, "C", 0)] +
                [(128, 64, 0, "M", qpt) for qpt in (1, 4)] + [(256, 64, 0, "M", qpt) for qpt in (1, 4)])
     rows = []
     for k, kp, r, rule, qpt in configs:
         ix = dbl.DBLIndex(I.rp, I.col, k, kp, leaf_r=r, landmark_rule=rule, edge_capacity=max(E, 1 << 20),
-                          query_unroll=qpt, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING)
+                          query_unroll=qpt, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_TIMING |
+                          (dbl.FLAG_FINE_L2 if args.fine_l2 else 0))
         ix.sync()
         ix.snapshot(0)
         step = Step(ix, I, batches, [(0, Q)], use_graph=False)
@@ -1103,6 +1139,15 @@ def bench_kernel_case(args):
     torch.cuda.set_device(dev)
     w = dbl_inputs.workload(args.workload, with_queries=args.kernel_case == "label")
     I = Inputs(w, dev) if args.kernel_case == "label" else None
+    if args.kernel_case == "scorer":
+        # the scorer's fused forward over every vertex's features (tcgen05, TMA)
+        rp = torch.from_numpy(w["row_ptr"]).to(dev)
+        col = torch.from_numpy(w["col"]).to(dev)
+        ix = dbl.DBLIndex(rp, col, args.k, args.kprime, flags=dbl.FLAG_PERSISTENT)
+        r = scorer_roofline(ix, reps=max(1, args.steps))
+        ix.close()
+        print(json.dumps({"kernel_case": "scorer", "workload": args.workload, **r}), flush=True)
+        return
     rp = torch.from_numpy(w["row_ptr"]).to(dev)
     col = torch.from_numpy(w["col"]).to(dev)
     src, dst = torch.from_numpy(w["ins_src"]).to(dev), torch.from_numpy(w["ins_dst"]).to(dev)
@@ -1141,7 +1186,8 @@ def main():
     ap.add_argument("--kprime", type=int, default=64)
     ap.add_argument("--team", type=int, default=0, help="frontier team width; 0: library default (1)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the persistent forms")
-    ap.add_argument("--forms", default="plain,batched,graph", help="comparison forms to time besides the headline")
+    ap.add_argument("--forms", default="plain,batched,graph,deferred",
+                    help="comparison forms to time besides the headline")
     ap.add_argument("--train-queries", type=int, default=1_000_000)
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1158,10 +1204,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving pass of the step benchmark")
     ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
-    ap.add_argument("--kernel-case", choices=["label", "insert"], default=None,
+    ap.add_argument("--kernel-case", choices=["label", "insert", "scorer"], default=None,
                     help="a small single-index run of one kernel (for an ncu capture) instead of the step")
-    ap.add_argument("--fine-l2", action="store_true",
-                    help="DBL_FLAG_FINE_L2 in every form: 32-byte L2 fetch granularity for the whole process")
+    ap.add_argument("--fine-l2", action=argparse.BooleanOptionalAction, default=True,
+                    help="DBL_FLAG_FINE_L2 in every form: 32-byte L2 fetch granularity for the whole process "
+                         "(default on; --no-fine-l2 keeps the driver's default)")
     args = ap.parse_args()
     args.forms = [f for f in args.forms.split(",") if f]
     if args.warmup < 3:

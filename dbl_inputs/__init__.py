@@ -146,6 +146,48 @@ def uniform_pairs(n: int, q: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
             rng.integers(0, n, q, dtype=np.int64).astype(np.int32))
 
 
+def community_dag(n: int, m: int, communities: int, alpha: float, cross: float, seed: int):
+    """A graph of `communities` R-MAT communities of power-law sizes
+    (size of community c proportional to (c + 1)^-alpha, at least 64
+    vertices), each with edges in proportion to its size, plus a share
+    `cross` of the m edges between communities, always from a community to
+    a later one (so the communities' strongly connected components never
+    merge).  Ids are relabelled by a seeded permutation.  Returns
+    (row_ptr int32[n+1], col int32[m']) with m' <= m distinct edges, no
+    self-loops, rows sorted."""
+    w = np.array([(c + 1.0) ** -alpha for c in range(communities)])
+    sizes = np.maximum(64, np.floor(w / w.sum() * n)).astype(np.int64)
+    sizes[0] += n - sizes.sum()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    inner = int(m * (1.0 - cross))
+    srcs, dsts = [], []
+    for c in range(communities):
+        mc = max(1, int(inner * sizes[c] / n))
+        mc = min(mc, int(sizes[c]) * (int(sizes[c]) - 1) // 4)
+        rp, col = rmat_csr(int(sizes[c]), mc, seed * 1000 + c)
+        srcs.append(np.repeat(np.arange(sizes[c], dtype=np.int64), np.diff(rp)) + off[c])
+        dsts.append(col.astype(np.int64) + off[c])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mx = m - sum(len(x) for x in srcs)
+    p = sizes / sizes.sum()
+    a = rng.choice(communities, size=2 * mx, p=p)
+    b = rng.choice(communities, size=2 * mx, p=p)
+    keep = a != b
+    a, b = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])  # from the earlier community
+    cs = off[a] + rng.integers(0, sizes[a])
+    cd = off[b] + rng.integers(0, sizes[b])
+    srcs.append(cs[:mx])
+    dsts.append(cd[:mx])
+    src, dst = np.concatenate(srcs), np.concatenate(dsts)
+    perm = permutation(n, seed + 1).astype(np.int64)
+    src, dst = perm[src], perm[dst]
+    key = np.unique(src * n + dst)
+    src, dst = (key // n), (key % n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, src + 1, 1)
+    return np.cumsum(row_ptr).astype(np.int32), dst.astype(np.int32)
+
+
 # --------------------------------------------------------------------------
 # workload recipes
 # --------------------------------------------------------------------------

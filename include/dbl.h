@@ -75,11 +75,22 @@ enum {
     DBL_FLAG_ASYNC = 1,      /* do not synchronise at the end of each call */
     DBL_FLAG_PERSISTENT = 2, /* run frontier loops in one persistent launch */
     DBL_FLAG_TIMING = 4,     /* bracket kernels with CUDA events (dbl_timings) */
-    DBL_FLAG_FINE_L2 = 8     /* at build, set the CUDA context's maximum L2 fetch
+    DBL_FLAG_FINE_L2 = 8,    /* at build, set the CUDA context's maximum L2 fetch
                                 granularity to 32 bytes (cudaLimitMaxL2FetchGranularity):
                                 label records are gathered 32 random bytes at a time.
                                 The limit is per context: it applies to every kernel
                                 of the process until changed. */
+    DBL_FLAG_DEFER = 16      /* with PERSISTENT and ASYNC: dbl_insert_edges only
+                                queues the batch; the queued batches are applied
+                                together, in one launch, by the next call that reads
+                                or changes the index otherwise (a query, labels,
+                                stats, a snapshot, a restore, dbl_sync, ...) or when
+                                32 are queued.  Each query observes exactly the
+                                insertions queued before it, and the labels equal
+                                those of any one-by-one order (the unique least
+                                fixpoint).  The edge arrays must stay valid until
+                                then; an invalid id in any queued batch rejects the
+                                whole group (reported by dbl_sync). */
 };
 
 /* Kernel classes reported by dbl_timings. */
@@ -377,8 +388,12 @@ const char *dbl_qctx_last_error(const dbl_qctx *c);
  * an insertion waits until no query batch is in flight and every request
  * behind it waits for it, so each request observes exactly the insertions
  * submitted before it (the labels change only at these epoch boundaries).
- * The number of slots is capped by mem_fraction of the free device memory at
- * creation; each slot's scratch is allocated then.  Submit returns
+ * Admission by memory: a slot's device scratch (a query context sized for
+ * max_batch pairs, and staging) is allocated when the slot is first needed,
+ * and only if it then fits in mem_fraction of the device's free memory
+ * (cudaMemGetInfo, read at that moment); until then requests wait for the
+ * slots that have memory.  The first slot is set up at creation
+ * (DBL_ERR_OOM if it does not fit).  Submit returns
  * DBL_ERR_BUSY when max_pending requests are queued.  The index must not use
  * DBL_FLAG_ASYNC and must not be used directly while a server runs on it.
  * ------------------------------------------------------------------------- */
@@ -387,7 +402,10 @@ typedef struct {
     int32_t slots;        /* worker slots (streams); default 4 */
     int64_t max_batch;    /* pairs per device batch; default 2^18 */
     int64_t max_pending;  /* queued requests before DBL_ERR_BUSY; default 2^16 */
-    double mem_fraction;  /* share of free device memory slots may take; default 0.5 */
+    double mem_fraction;  /* a slot is admitted when its scratch fits in this share
+                             of the device's free memory at that moment; default 0.5 */
+    int64_t max_memory;   /* and when all admitted slots together stay within this
+                             many device bytes; 0: no such limit (default) */
 } dbl_server_options;
 void dbl_server_default_options(dbl_server_options *o);
 dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_server **out);
@@ -408,7 +426,8 @@ dbl_status dbl_server_drain(dbl_server *s);
  * [4] pairs answered, [5] edges inserted, [6] query requests, [7] insertion
  * requests, [8] slots, [9] seconds since creation or reset, [10] device
  * query batches, [11] query requests in them, [12] insertion epochs,
- * [13] requests cancelled. */
+ * [13] requests cancelled, [14] slots admitted (with scratch), [15] device
+ * bytes per slot. */
 dbl_status dbl_server_report(dbl_server *s, double out[16]);
 dbl_status dbl_server_reset_stats(dbl_server *s);
 void dbl_server_destroy(dbl_server *s);
@@ -449,6 +468,14 @@ dbl_status dbl_coverage(dbl_index *ix, const int32_t *u, const int32_t *v, const
 
 /* out[k]: the k vertices with the largest scores[n], ties by smaller id. */
 dbl_status dbl_select_by_score(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream);
+/* out[k]: greedy spread selection: the vertex of largest score (ties by
+ * smaller id) among those not yet taken or excluded, then its in- and
+ * out-neighbours are excluded, k times.  Vertices scored -inf or NaN are
+ * never taken; slots left when no candidate remains get -1.  (A top-k of
+ * landmarks tends to fall in one strongly connected component, where one of
+ * them decides what all would; neighbours of a chosen vertex share its
+ * component far more often than other vertices.) */
+dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream);
 
 /* Network with initial parameters params_host[DBL_MLP_PARAMS] (host fp32).
  * Weights are kept in fp32 with bf16 copies for the tensor-core kernels. */

@@ -22,7 +22,7 @@ DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAP
     DBL_ERR_POISONED, DBL_ERR_CANCELLED = range(9)
 STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned", "cancelled"]
 CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
-FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2 = 1, 2, 4, 8
+FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2, FLAG_DEFER = 1, 2, 4, 8, 16
 # landmark rankings of dbl_options.landmark_rule: M = |Pre|*|Suc| (Section 4.1), and Table 3's
 # A = max, B = min, C = sum of the two degrees
 LANDMARK_RULES = {"M": 0, "A": 1, "B": 2, "C": 3}
@@ -38,13 +38,13 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
            "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule", "dbl_barrier_probe",
-           "dbl_server_cancel"]
+           "dbl_server_cancel", "dbl_select_spread"]
 MLP_PARAMS = 18817
 
 
 class _ServerOptions(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch", ctypes.c_int64), ("max_pending", ctypes.c_int64),
-                ("mem_fraction", ctypes.c_double)]
+                ("mem_fraction", ctypes.c_double), ("max_memory", ctypes.c_int64)]
 
 
 class DblError(RuntimeError):
@@ -135,6 +135,7 @@ def lib():
             L.dbl_features.argtypes = [P, P, P]
             L.dbl_coverage.argtypes = [P, P, P, P, i64, i32, P, P, P, P]
             L.dbl_select_by_score.argtypes = [P, P, i32, P, P]
+            L.dbl_select_spread.argtypes = [P, P, i32, P, P]
             L.dbl_mlp_create.argtypes = [P, P, P]
             L.dbl_mlp_destroy.argtypes = [P, P]
             L.dbl_mlp_destroy.restype = None
@@ -457,6 +458,15 @@ class DBLIndex:
         self._check(lib().dbl_select_by_score(self._h, _ptr(scores), int(k), _ptr(out), self._s(stream)))
         return out
 
+    def select_spread(self, scores, k: int, stream=None):
+        """dbl_select_spread: k vertices by score, each excluding its in- and
+        out-neighbours from later picks; int32 [k] (-1 for slots left empty)."""
+        import torch
+        scores = scores.to(torch.float32).contiguous()
+        out = torch.empty(int(k), dtype=torch.int32, device=self.device)
+        self._check(lib().dbl_select_spread(self._h, _ptr(scores), int(k), _ptr(out), self._s(stream)))
+        return out
+
 
 class QueryContext:
     """dbl_qctx: scratch for one query batch in flight; batches on different
@@ -500,12 +510,13 @@ class Server:
     wait() returns for its ticket."""
 
     def __init__(self, ix: "DBLIndex", slots: int = 4, max_batch: int = 1 << 18, max_pending: int = 1 << 16,
-                 mem_fraction: float = 0.5):
+                 mem_fraction: float = 0.5, max_memory: int = 0):
         self.ix = ix
         o = _ServerOptions()
         lib().dbl_server_default_options(ctypes.byref(o))
         o.slots, o.max_batch, o.max_pending, o.mem_fraction = int(slots), int(max_batch), int(max_pending), \
             float(mem_fraction)
+        o.max_memory = int(max_memory)
         h = ctypes.c_void_p()
         st = lib().dbl_server_create(ix._h, ctypes.byref(o), ctypes.byref(h))
         if st != DBL_OK:
@@ -555,7 +566,8 @@ class Server:
         out = np.zeros(16, dtype=np.float64)
         lib().dbl_server_report(self._h, out.ctypes.data)
         keys = ["query_p50_s", "query_p99_s", "insert_p50_s", "insert_p99_s", "pairs", "edges", "query_requests",
-                "insert_requests", "slots", "elapsed_s", "device_batches", "batched_requests", "epochs", "cancelled"]
+                "insert_requests", "slots", "elapsed_s", "device_batches", "batched_requests", "epochs", "cancelled",
+                "slots_admitted", "bytes_per_slot"]
         return {k: float(out[i]) for i, k in enumerate(keys)}
 
     def reset_stats(self):

@@ -245,10 +245,18 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
 }
 
 __global__ void k_extract_labels(const uint64_t *rec, int32_t n, int32_t rw, int32_t hs, int32_t wd, int32_t wb,
-                                 uint64_t *dl_in, uint64_t *dl_out, uint64_t *bl_in, uint64_t *bl_out)
+                                 int packed, int32_t k, uint64_t dlm, uint64_t *dl_in, uint64_t *dl_out,
+                                 uint64_t *bl_in, uint64_t *bl_out)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t *r = rec + (size_t)v * rw;
+        if (packed) {  // one word per half: DL below bit k, BL from bit k
+            if (dl_in) dl_in[v] = r[0] & dlm;
+            if (dl_out) dl_out[v] = r[1] & dlm;
+            if (bl_in) bl_in[v] = r[0] >> k;
+            if (bl_out) bl_out[v] = r[1] >> k;
+            continue;
+        }
         for (int w = 0; w < wd; ++w) {
             if (dl_in) dl_in[(size_t)v * wd + w] = r[w];
             if (dl_out) dl_out[(size_t)v * wd + w] = r[hs + w];
@@ -310,6 +318,7 @@ static void destroy_impl(dbl_index *ix, cudaStream_t s)
 void dbl_destroy(dbl_index *ix, void *stream)
 {
     if (!ix) return;
+    drop_insertions(ix);  // queued batches are never applied
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamSynchronize(s);
     destroy_impl(ix, s);
@@ -355,6 +364,15 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     ix->wd = (k + 63) / 64;
     ix->wb = (kprime + 63) / 64;
     ix->hs = hs_for(ix->wd + ix->wb);
+    ix->packed = k + kprime <= 64;  // Table 5's small labels: one word per half, 16-byte records
+    if (ix->packed) {
+        ix->hs = 1;
+        ix->bl_base = k;
+        ix->dl_mask = (1ull << k) - 1;
+        ix->bl_mask = ((kprime == 64 ? ~0ull : (1ull << kprime) - 1)) << k;
+    } else {
+        ix->bl_base = 64 * ix->wd;
+    }
     ix->rw = 2 * ix->hs;
     ix->edge_cap = ix->opt.edge_capacity > 0 ? ix->opt.edge_capacity : std::max<int64_t>(1 << 20, g->m / 4);
     if (ix->edge_cap > (1ll << 29)) ix->edge_cap = 1ll << 29;  // per-vertex slots then fit in 30 bits
@@ -451,6 +469,16 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
         if ((ix)->poisoned) return fail(ix, DBL_ERR_POISONED, "index poisoned by a timeout; dbl_restore it"); \
     } while (0)
 
+// Every call that reads or changes the index other than by a deferred
+// insertion first applies the queued insertion batches (DBL_FLAG_DEFER).
+#define DBL_FLUSH(ix, s)                                               \
+    do {                                                               \
+        if (!(ix)->pending.empty()) {                                  \
+            const dbl_status flush_st_ = flush_insertions((ix), (s));  \
+            if (flush_st_) return flush_st_;                           \
+        }                                                              \
+    } while (0)
+
 static dbl_status finish(dbl_index *ix, dbl_status st, cudaStream_t s)
 {
     if (st) return st;
@@ -472,6 +500,7 @@ dbl_status dbl_query(dbl_index *ix, const int32_t *u, const int32_t *v, int64_t 
     DBL_CHECK_IX(ix);
     if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u || !v || !ans))) return fail(ix, DBL_ERR_INVALID, "query: bad batch");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     return finish(ix, query(ix, ix->qc, u, v, q, ans, code, s), s);
 }
 
@@ -501,7 +530,9 @@ dbl_status dbl_query_ctx(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int
     if (!ix || !c || c->ix != ix) return fail(ix, DBL_ERR_INVALID, "query_ctx: context of another index");
     if (ix->poisoned) return qfail(c, DBL_ERR_POISONED, "index poisoned by a timeout; dbl_restore it");
     if (q < 0 || q >= (1ll << 31) || (q > 0 && (!u || !v || !ans))) return qfail(c, DBL_ERR_INVALID, "query: bad batch");
-    return query(ix, c, u, v, q, ans, code, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
+    return query(ix, c, u, v, q, ans, code, s);
 }
 
 const char *dbl_qctx_last_error(const dbl_qctx *c) { return c ? c->err.c_str() : ""; }
@@ -542,6 +573,7 @@ dbl_status dbl_query_host(dbl_index *ix, const int32_t *u_host, const int32_t *v
         return fail(ix, DBL_ERR_INVALID, "query_host: bad batch");
     if (q == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     // large chunks: each chunk is one label test and one search (whose cost
     // has a fixed part); the upload of the first chunk overlaps earlier work
     const int64_t chunk = std::min<int64_t>(q, 1 << 24);
@@ -593,6 +625,7 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
         return fail(ix, DBL_ERR_INVALID, "insert_host: bad batch");
     if (b == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     dbl_status st;
     if (b > ix->istage_cap) {
         // stream-ordered frees: after every insertion queued on s (each waited for its upload)
@@ -643,9 +676,11 @@ dbl_status dbl_labels(dbl_index *ix, uint64_t *dl_in, uint64_t *dl_out, uint64_t
 {
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     int64_t blocks = ((int64_t)ix->n + kBlock - 1) / kBlock;
     blocks = std::min<int64_t>(std::max<int64_t>(blocks, 1), (int64_t)num_sms() * 16);
-    k_extract_labels<<<(unsigned)blocks, kBlock, 0, s>>>(ix->rec, ix->n, ix->rw, ix->hs, ix->wd, ix->wb, dl_in, dl_out,
+    k_extract_labels<<<(unsigned)blocks, kBlock, 0, s>>>(ix->rec, ix->n, ix->rw, ix->hs, ix->wd, ix->wb,
+                                                         ix->packed ? 1 : 0, ix->k, ix->dl_mask, dl_in, dl_out,
                                                          bl_in, bl_out);
     ++ix->launches;
     cudaError_t e = cudaGetLastError();
@@ -677,6 +712,7 @@ dbl_status dbl_add_vertices(dbl_index *ix, int64_t count, int32_t *first, void *
     if (first) *first = ix->n;
     if (count == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     const size_t v0 = (size_t)ix->n, c = (size_t)count;
     // the rows may hold a vertex that a restore took away: clear them all
     cudaMemsetAsync(ix->rec + v0 * ix->rw, 0, 8 * c * ix->rw, s);
@@ -698,6 +734,7 @@ dbl_status dbl_snapshot(dbl_index *ix, int slot, void *stream)
     if (slot < 0 || slot >= 4) return fail(ix, DBL_ERR_INVALID, "snapshot slot must be 0..3");
     if (ix->poisoned) return fail(ix, DBL_ERR_POISONED, "cannot snapshot a poisoned index");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     Snapshot &sn = ix->snaps[slot];
     dbl_status st;
     const size_t rec_b = 8 * (size_t)ix->n * ix->rw, meta_b = sizeof(VMeta) * (size_t)ix->n;
@@ -804,6 +841,7 @@ dbl_status dbl_restore(dbl_index *ix, int slot, void *stream)
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
     if (slot < 0 || slot >= 4 || !ix->snaps[slot].valid) return fail(ix, DBL_ERR_INVALID, "no snapshot in that slot");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     Snapshot &sn = ix->snaps[slot];
     // Snapshots taken after this one name inserted-edge segments in the part
     // of the edge pool (and in the spare room of segments) that insertions
@@ -833,6 +871,7 @@ dbl_status dbl_barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent_b
     if (spin_limit < 1 || spin_limit > (int64_t)kSpinLimit || absent_block < -1 || absent_block >= num_sms())
         return fail(ix, DBL_ERR_INVALID, "barrier_probe: spin_limit must be 1..2^24, absent_block -1..SMs-1");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     dbl_status st = barrier_probe(ix, spin_limit, absent_block, s);
     if (st) return st;
     return read_status(ix, s);  // a wait that ran out: DBL_ERR_TIMEOUT, index poisoned
@@ -842,6 +881,7 @@ dbl_status dbl_sync(dbl_index *ix, void *stream)
 {
     if (!ix) return fail(nullptr, DBL_ERR_INVALID, "index is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     dbl_status st = read_status(ix, s);
     // queries latch their errors in the status word of the default query context
     cudaMemcpyAsync(ix->qc->h_pinned + 8, ix->qc->d_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
@@ -860,6 +900,7 @@ dbl_status dbl_stats(dbl_index *ix, uint64_t counters[16], void *stream)
 {
     if (!ix || !counters) return fail(ix, DBL_ERR_INVALID, "stats: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     unsigned long long *h = (unsigned long long *)(ix->h_pinned + 16);  // 16 words = 8 u64; use two copies
     uint64_t dev[16];
     cudaMemcpyAsync(h, ix->d_stats, 8 * 8, cudaMemcpyDeviceToHost, s);
@@ -878,6 +919,7 @@ dbl_status dbl_timings(dbl_index *ix, double ms[8], uint64_t launches[8], void *
 {
     if (!ix || !ms || !launches) return fail(ix, DBL_ERR_INVALID, "timings: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     tend(ix, s);
     for (int i = 0; i < 8; ++i) {
         ms[i] = 0;
@@ -903,6 +945,7 @@ dbl_status dbl_phase_trace(dbl_index *ix, int64_t out[64], void *stream)
 {
     if (!ix || !out) return fail(ix, DBL_ERR_INVALID, "phase_trace: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    DBL_FLUSH(ix, s);
     unsigned long long h[64];
     cudaError_t e = cudaMemcpyAsync(h, ix->d_trace, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);

@@ -148,14 +148,16 @@ __global__ void k_ins_commit(const int32_t *src, const int32_t *dst, int64_t b, 
 // bwd(u) |= bwd(v); changed endpoints start the frontier.
 template <int HS, int WD>
 __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *dst, int64_t b, const DevGraph &g,
-                                           uint64_t *rec, const FrontierOut &f, unsigned long long *stats);
+                                           uint64_t *rec, uint64_t dlm, const FrontierOut &f,
+                                           unsigned long long *stats);
 
 template <int HS, int WD>
 __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const int32_t *dst, int64_t b, DevGraph g,
-                                                     uint64_t *rec, FrontierOut f, unsigned long long *stats)
+                                                     uint64_t *rec, uint64_t dlm, FrontierOut f,
+                                                     unsigned long long *stats)
 {
     if (status_set(f.status)) return;
-    seed_edges<HS, WD>(src, dst, b, g, rec, f, stats);
+    seed_edges<HS, WD>(src, dst, b, g, rec, dlm, f, stats);
 }
 
 // One edge's seed: Algorithm 3's skip test on DL_out(u) and DL_in(v), then
@@ -167,8 +169,8 @@ __global__ void __launch_bounds__(kBlock) k_ins_seed(const int32_t *src, const i
 // see that bit, and a load that misses bits the OR brings means the word
 // grows.  Callers read the frontier only after a grid barrier or a launch.
 template <int HS, int WD>
-__device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, uint32_t *dirty, bool &want_f,
-                                         bool &want_b)
+__device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, uint32_t *dirty, uint64_t dlm,
+                                         bool &want_f, bool &want_b)
 {
     constexpr int RW = 2 * HS;
     uint64_t *fu = rec + (size_t)u * RW, *bu = fu + HS;
@@ -177,6 +179,13 @@ __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, ui
     if constexpr (HS == 2) {  // 32-byte records: one load per record
         load_rec32(fu, x[0], x[1], a[0], a[1]);
         load_rec32(fv, c[0], c[1], y[0], y[1]);
+    } else if constexpr (HS == 1) {  // packed 16-byte records: one load per record
+        const ulonglong2 ru = __ldcg(reinterpret_cast<const ulonglong2 *>(fu));
+        const ulonglong2 rv = __ldcg(reinterpret_cast<const ulonglong2 *>(fv));
+        x[0] = ru.x;
+        a[0] = ru.y;
+        c[0] = rv.x;
+        y[0] = rv.y;
     } else {
         load_half<HS>(bu, a);  // DL_out(u) | BL_out(u)
         load_half<HS>(fv, c);  // DL_in(v)  | BL_in(v)
@@ -184,8 +193,12 @@ __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, ui
         load_half<HS>(bv, y);  // DL_out(v) | BL_out(v)
     }
     uint64_t inter = 0;
+    if constexpr (WD == 0) {
+        inter = a[0] & c[0] & dlm;  // packed: the DL bits of the one word
+    } else {
 #pragma unroll
-    for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
+        for (int w = 0; w < WD; ++w) inter |= a[w] & c[w];
+    }
     if (inter) return false;
 #pragma unroll
     for (int w = 0; w < HS; ++w) {
@@ -205,7 +218,8 @@ __device__ __forceinline__ bool seed_one(int32_t u, int32_t v, uint64_t *rec, ui
 
 template <int HS, int WD>
 __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *dst, int64_t b, const DevGraph &g,
-                                           uint64_t *rec, const FrontierOut &f, unsigned long long *stats)
+                                           uint64_t *rec, uint64_t dlm, const FrontierOut &f,
+                                           unsigned long long *stats)
 {
     unsigned long long skipped = 0, applied = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -217,7 +231,7 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
             u = src[i];
             v = dst[i];
             if (u != v) {
-                if (seed_one<HS, WD>(u, v, rec, g.dirty, want_f, want_b)) ++applied;
+                if (seed_one<HS, WD>(u, v, rec, g.dirty, dlm, want_f, want_b)) ++applied;
                 else ++skipped;
             }
         }
@@ -248,8 +262,22 @@ __device__ __forceinline__ void seed_edges(const int32_t *src, const int32_t *ds
 // failed validation leaves the index as it was.
 constexpr int32_t kWantBit = 1 << 30;
 
+// The batches one launch applies together: batch j's edges are
+// src[j][0..len), dst[j][0..len), at positions off[j] .. off[j + 1) of the
+// launch's edge range.  Batches queued with no call that reads the index
+// between them are applied as one (the labels are the unique fixpoint of the
+// graph with all of them, whatever the grouping).
+constexpr int kMaxGroup = 32;
+struct BatchList {
+    int32_t nb;
+    int64_t off[kMaxGroup + 1];
+    const int32_t *src[kMaxGroup];
+    const int32_t *dst[kMaxGroup];
+};
+
 struct InsArgs {
-    const int32_t *src, *dst;
+    const int32_t *src, *dst;  // the edges when nb == 1
+    BatchList bl;
     int64_t b;
     int32_t n;
     VMeta *vm;
@@ -268,7 +296,27 @@ struct InsArgs {
     uint32_t *status;
     uint32_t *bad;   // this batch has an invalid id (zero before the launch)
     uint32_t *grow;  // some segment of this batch must grow (zero before the launch)
+    uint64_t dlm;    // packed labels: the DL bits of a half word
 };
+
+// Edge i of the launch's batches.
+__device__ __forceinline__ void edge_at(const InsArgs &a, int64_t i, int32_t &u, int32_t &v)
+{
+    if (a.bl.nb <= 1) {
+        u = a.src[i];
+        v = a.dst[i];
+        return;
+    }
+    int lo = 0, hi = a.bl.nb - 1;  // the batch j with off[j] <= i < off[j + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.bl.off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t k = i - a.bl.off[lo];
+    u = a.bl.src[lo][k];
+    v = a.bl.dst[lo][k];
+}
 
 // Adjacency metadata of one direction from a VMeta sector loaded as four words.
 __device__ __forceinline__ VAdj vadj_of_words(uint64_t lo, uint64_t hi)
@@ -298,7 +346,8 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         unsigned long long loops = 0;
         bool grow = false;
         for (int64_t i = t0; i < a.b; i += nt) {
-            const int32_t u = a.src[i], v = a.dst[i];
+            int32_t u, v;
+            edge_at(a, i, u, v);
             if ((uint32_t)u >= (uint32_t)n || (uint32_t)v >= (uint32_t)n) {
                 atomicExch(a.bad, 1u);
                 a.slot_out[i] = a.slot_in[i] = -1;
@@ -324,8 +373,10 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         if (ld_volatile_u32(a.bad)) {
             for (int64_t i = t0; i < a.b; i += nt) {
                 if (a.slot_out[i] < 0) continue;
-                atomicSub(&a.vm[a.src[i]].d[0].len, 1);
-                atomicSub(&a.vm[a.dst[i]].d[1].len, 1);
+                int32_t u, v;
+                edge_at(a, i, u, v);
+                atomicSub(&a.vm[u].d[0].len, 1);
+                atomicSub(&a.vm[v].d[1].len, 1);
             }
             if (!gs.sync(a.status)) return;  // every block has read the flags
             if (leader) {
@@ -352,13 +403,12 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             VAdj eu{0, 0u, 0, 0}, ev{0, 0u, 0, 0};
             if (i < a.b) {
                 const int32_t so = a.slot_out[i], si = a.slot_in[i];
-                u = a.src[i];
-                v = a.dst[i];
+                edge_at(a, i, u, v);
                 if (so >= 0) {
                     uint64_t mu[4], mv[4];
                     load_rec32(reinterpret_cast<const uint64_t *>(a.vm + u), mu[0], mu[1], mu[2], mu[3]);
                     load_rec32(reinterpret_cast<const uint64_t *>(a.vm + v), mv[0], mv[1], mv[2], mv[3]);
-                    if (seed_one<HS, WD>(u, v, a.rec, a.g.dirty, want_f, want_b)) ++applied;
+                    if (seed_one<HS, WD>(u, v, a.rec, a.g.dirty, a.dlm, want_f, want_b)) ++applied;
                     else ++skipped;
                     const VAdj au = vadj_of_words(mu[0], mu[1]), av = vadj_of_words(mv[2], mv[3]);
                     eu = vadj_of_words(mu[2], mu[3]);  // u's in-edges: bwd(u) changed
@@ -392,8 +442,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             VAdj ad[2] = {{0, 0u, 0, 0}, {0, 0u, 0, 0}};
             if (i < a.b) {
                 const int32_t sw[2] = {a.slot_out[i], a.slot_in[i]};
-                x[0] = a.src[i];
-                x[1] = a.dst[i];
+                edge_at(a, i, x[0], x[1]);
                 // with 16-byte halves the segment metadata is loaded before the
                 // seed's records, in the same round trip (len is final after the
                 // count phase); wider records leave no registers for that
@@ -405,7 +454,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
                 }
                 if (sw[0] >= 0) {
                     bool want_f = false, want_b = false;
-                    if (seed_one<HS, WD>(x[0], x[1], a.rec, a.g.dirty, want_f, want_b)) ++applied;
+                    if (seed_one<HS, WD>(x[0], x[1], a.rec, a.g.dirty, a.dlm, want_f, want_b)) ++applied;
                     else ++skipped;
                     if (want_b) a.slot_out[i] = sw[0] | kWantBit;
                     if (want_f) a.slot_in[i] = sw[1] | kWantBit;
@@ -473,8 +522,7 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
             VAdj eu{0, 0u, 0, 0}, ev{0, 0u, 0, 0};  // adjacency of the tasks to enqueue
             if (i < a.b) {
                 const int32_t so = a.slot_out[i], si = a.slot_in[i];
-                u = a.src[i];
-                v = a.dst[i];
+                edge_at(a, i, u, v);
                 if (so >= 0) {
                     want_b = (so & kWantBit) != 0;
                     want_f = (si & kWantBit) != 0;
@@ -556,12 +604,16 @@ static dbl_status launch_insert_persistent_team(dbl_index *ix, const InsArgs &a,
     }
 }
 
-static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
-                                    int32_t *pos_in, cudaStream_t s)
+// One cooperative launch applying the batches of `bl` (b edges in all) with
+// per-edge scratch pos_out / pos_in (b entries each).  The caller accounts
+// for the stored edges.
+static dbl_status insert_persistent_list(dbl_index *ix, const BatchList &bl, const int32_t *src, const int32_t *dst,
+                                         int64_t b, int32_t *pos_out, int32_t *pos_in, cudaStream_t s)
 {
     InsArgs a;
     a.src = src;
     a.dst = dst;
+    a.bl = bl;
     a.b = b;
     a.n = ix->n;
     a.vm = ix->vm;
@@ -583,9 +635,11 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     a.status = ix->d_status;
     a.bad = ix->d_counts + kCntBad;
     a.grow = ix->d_counts + kCntGrow;
+    a.dlm = ix->dl_mask;
     tbegin(ix, DBL_KERNEL_PROPAGATE, s);
     dbl_status st;
-    switch (ix->hs * 16 + ix->wd) {
+    switch (ix->packed ? 0 : ix->hs * 16 + ix->wd) {
+    case 0: st = launch_insert_persistent_team<1, 0>(ix, a, s); break;
     case 2 * 16 + 1: st = launch_insert_persistent_team<2, 1>(ix, a, s); break;
     case 4 * 16 + 1: st = launch_insert_persistent_team<4, 1>(ix, a, s); break;
     case 4 * 16 + 2: st = launch_insert_persistent_team<4, 2>(ix, a, s); break;
@@ -595,6 +649,19 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
     default: st = fail(ix, DBL_ERR_INVALID, "insert: unsupported label width");
     }
     tend(ix, s);
+    return st;
+}
+
+static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
+                                    int32_t *pos_in, cudaStream_t s)
+{
+    BatchList bl;
+    bl.nb = 1;
+    bl.off[0] = 0;
+    bl.off[1] = b;
+    bl.src[0] = src;
+    bl.dst[0] = dst;
+    dbl_status st = insert_persistent_list(ix, bl, src, dst, b, pos_out, pos_in, s);
     if (st) return st;
     ix->edges_stored += b;
     atomic_add_host_stat(ix, 15, (uint64_t)b, s);
@@ -605,6 +672,56 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
         return fail(ix, ds, "insert: vertex id out of range");
     }
     return ds;
+}
+
+// Deferred insertion (DBL_FLAG_DEFER with persistent, asynchronous calls):
+// dbl_insert_edges only queues the batch; the queue is applied in one
+// launch by the next call that reads or changes the index otherwise (or
+// when kMaxGroup batches wait).  Every query therefore observes exactly the
+// insertions queued before it.
+static bool deferring(const dbl_index *ix)
+{
+    const int32_t f = ix->opt.flags;
+    return (f & DBL_FLAG_DEFER) && (f & DBL_FLAG_PERSISTENT) && (f & DBL_FLAG_ASYNC);
+}
+
+static dbl_status ensure_ins_scratch(dbl_index *ix, int64_t b, cudaStream_t s)
+{
+    if (b <= ix->ins_bcap) return DBL_OK;
+    if (ix->ins_pos) free_buf(ix, ix->ins_pos, s);
+    ix->ins_pos = nullptr;
+    ix->ins_bcap = 0;  // a failed allocation below leaves nothing to reuse
+    int64_t nb = b < (1 << 16) ? (1 << 16) : b;
+    dbl_status st = alloc_buf(ix, (void **)&ix->ins_pos, sizeof(int32_t) * 2 * (size_t)nb, s);
+    if (st) return st;
+    ix->ins_bcap = nb;
+    return DBL_OK;
+}
+
+dbl_status flush_insertions(dbl_index *ix, cudaStream_t s)
+{
+    if (ix->pending.empty()) return DBL_OK;
+    BatchList bl;
+    bl.nb = (int32_t)ix->pending.size();
+    int64_t total = 0;
+    for (int j = 0; j < bl.nb; ++j) {
+        bl.off[j] = total;
+        bl.src[j] = ix->pending[j].src;
+        bl.dst[j] = ix->pending[j].dst;
+        total += ix->pending[j].b;
+    }
+    bl.off[bl.nb] = total;
+    ix->pending.clear();
+    ix->pending_edges = 0;
+    // the queue's scratch was sized when its batches were queued
+    return insert_persistent_list(ix, bl, bl.src[0], bl.dst[0], total, ix->ins_pos, ix->ins_pos + ix->ins_bcap, s);
+}
+
+void drop_insertions(dbl_index *ix)
+{
+    ix->edges_stored -= ix->pending_edges;
+    ix->pending.clear();
+    ix->pending_edges = 0;
 }
 
 static unsigned blocks_for(int64_t work, int64_t cap_mult = 16)
@@ -621,15 +738,20 @@ dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, i
     if (b == 0) return DBL_OK;
     if (ix->edges_stored + b > ix->edge_cap)
         return fail(ix, DBL_ERR_CAPACITY, "insert: edge capacity exhausted (dbl_options.edge_capacity)");
-    if (b > ix->ins_bcap) {
-        if (ix->ins_pos) free_buf(ix, ix->ins_pos, s);
-        ix->ins_pos = nullptr;
-        ix->ins_bcap = 0;  // a failed allocation below leaves nothing to reuse
-        int64_t nb = b < (1 << 16) ? (1 << 16) : b;
-        dbl_status st = alloc_buf(ix, (void **)&ix->ins_pos, sizeof(int32_t) * 2 * (size_t)nb, s);
-        if (st) return st;
-        ix->ins_bcap = nb;
+    if (deferring(ix)) {
+        if (ix->pending_edges + b >= (1ll << 31))
+            if (dbl_status st = flush_insertions(ix, s)) return st;
+        // the scratch of the whole queue is sized now; queued batches have not
+        // used the old one yet, so it may be replaced
+        if (dbl_status st = ensure_ins_scratch(ix, ix->pending_edges + b, s)) return st;
+        ix->pending.push_back(dbl_index::Pending{src, dst, b});
+        ix->pending_edges += b;
+        ix->edges_stored += b;
+        atomic_add_host_stat(ix, 15, (uint64_t)b, s);
+        if ((int)ix->pending.size() == kMaxGroup) return flush_insertions(ix, s);
+        return DBL_OK;
     }
+    if (dbl_status st = ensure_ins_scratch(ix, b, s)) return st;
     return insert_edges_core(ix, src, dst, b, ix->ins_pos, ix->ins_pos + ix->ins_bcap, s);
 }
 
@@ -678,13 +800,15 @@ dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *d
     cudaMemsetAsync(ix->d_counts + kCntFront0, 0, sizeof(uint32_t), s);
     const DevGraph g = dev_graph(ix);
     tbegin(ix, DBL_KERNEL_INSERT_SEED, s);
-    switch (ix->hs * 16 + ix->wd) {
-    case 2 * 16 + 1: k_ins_seed<2, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
-    case 4 * 16 + 1: k_ins_seed<4, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
-    case 4 * 16 + 2: k_ins_seed<4, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
-    case 8 * 16 + 1: k_ins_seed<8, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
-    case 8 * 16 + 2: k_ins_seed<8, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
-    case 8 * 16 + 4: k_ins_seed<8, 4><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, f, ix->d_stats); ++ix->launches; break;
+    const uint64_t dlm = ix->dl_mask;
+    switch (ix->packed ? 0 : ix->hs * 16 + ix->wd) {
+    case 0: k_ins_seed<1, 0><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 2 * 16 + 1: k_ins_seed<2, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 4 * 16 + 1: k_ins_seed<4, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 4 * 16 + 2: k_ins_seed<4, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 1: k_ins_seed<8, 1><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 2: k_ins_seed<8, 2><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
+    case 8 * 16 + 4: k_ins_seed<8, 4><<<grid, kBlock, 0, s>>>(src, dst, b, g, ix->rec, dlm, f, ix->d_stats); ++ix->launches; break;
     default: return fail(ix, DBL_ERR_INVALID, "insert: unsupported label width");
     }
     tend(ix, s);

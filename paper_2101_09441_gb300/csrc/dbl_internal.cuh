@@ -152,6 +152,10 @@ __device__ __forceinline__ void load_rec32(const uint64_t *p, T &w0, T &w1, T &w
 template <int HS>
 __device__ __forceinline__ void load_half(const uint64_t *p, uint64_t (&w)[HS])
 {
+    if constexpr (HS == 1) {  // packed labels: a half is one word
+        w[0] = __ldcg(p);
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < HS; i += 2) {
         ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2 *>(p + i));
@@ -258,6 +262,12 @@ struct dbl_index {
     int32_t n_cap = 0;  // vertices every per-vertex array is sized for
     int64_t m = 0;
     int32_t k = 0, kp = 0, wd = 0, wb = 0, hs = 0, rw = 0;
+    // packed labels (k + kprime <= 64): a half is one word, DL in bits
+    // [0, k), BL in bits [k, k + kprime); otherwise DL fills words [0, wd) and
+    // BL words [wd, wd + wb).  bl_base: the bit where BL starts in a half.
+    bool packed = false;
+    int32_t bl_base = 0;
+    uint64_t dl_mask = ~0ull, bl_mask = ~0ull;  // packed: the bits of DL and of BL in the half word
     dbl_options opt{};
     std::string err;
     bool poisoned = false;
@@ -288,6 +298,15 @@ struct dbl_index {
     int32_t *ins_cnt = nullptr;       // [2][n_cap] per-vertex batch counts (zero between calls)
     int32_t *ins_pos = nullptr;       // [2][bcap] per-edge slot in its vertex batch
     int64_t ins_bcap = 0;
+
+    // insertion batches queued under DBL_FLAG_DEFER, applied together by the
+    // next call that reads or changes the index otherwise
+    struct Pending {
+        const int32_t *src, *dst;
+        int64_t b;
+    };
+    std::vector<Pending> pending;
+    int64_t pending_edges = 0;
 
     // query scratch of calls without an explicit context (dbl_query)
     struct dbl_qctx *qc = nullptr;
@@ -468,6 +487,8 @@ void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3);  // vert
 dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);
 dbl_status insert_edges_core(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, int32_t *pos_out,
                              int32_t *pos_in, cudaStream_t s);
+dbl_status flush_insertions(dbl_index *ix, cudaStream_t s);  // apply the queued batches (DBL_FLAG_DEFER)
+void drop_insertions(dbl_index *ix);                          // forget them (the index is destroyed)
 
 // query (dbl_query.cu)
 dbl_status query(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v, int64_t q, uint8_t *ans,

@@ -41,8 +41,8 @@ __global__ void k_mark_landmarks(const int32_t *lm, int32_t k, uint8_t *mark)
 }
 
 // One warp per vertex; lanes stride over Pre and Suc for the neighbour sums.
-__global__ void k_features(DevGraph g, const uint64_t *rec, int32_t hs, int32_t wd, int32_t wb, const uint8_t *mark,
-                           bf16 *out)
+__global__ void k_features(DevGraph g, const uint64_t *rec, int32_t hs, int32_t wd, int32_t wb, int packed,
+                           uint64_t dlm, const uint8_t *mark, bf16 *out)
 {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -76,13 +76,20 @@ __global__ void k_features(DevGraph g, const uint64_t *rec, int32_t hs, int32_t 
             double v = 0;
             const double din = (double)indeg_of(g, x), dout = (double)outdeg_of(g, x);
             int pc[4] = {0, 0, 0, 0};
-            for (int w = 0; w < wd; ++w) {
-                pc[0] += __popcll(p[w]);
-                pc[1] += __popcll(p[hs + w]);
-            }
-            for (int w = 0; w < wb; ++w) {
-                pc[2] += __popcll(p[wd + w]);
-                pc[3] += __popcll(p[hs + wd + w]);
+            if (packed) {  // one word per half: DL bits dlm, BL the bits above
+                pc[0] = __popcll(p[0] & dlm);
+                pc[1] = __popcll(p[1] & dlm);
+                pc[2] = __popcll(p[0] & ~dlm);
+                pc[3] = __popcll(p[1] & ~dlm);
+            } else {
+                for (int w = 0; w < wd; ++w) {
+                    pc[0] += __popcll(p[w]);
+                    pc[1] += __popcll(p[hs + w]);
+                }
+                for (int w = 0; w < wb; ++w) {
+                    pc[2] += __popcll(p[wd + w]);
+                    pc[3] += __popcll(p[hs + wd + w]);
+                }
             }
             switch (lane) {
             case 0: v = din; break;
@@ -118,7 +125,8 @@ dbl_status features(dbl_index *ix, bf16 *out, cudaStream_t s)
     int64_t blocks = ((int64_t)ix->n * 32 + kBlock - 1) / kBlock;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
-    k_features<<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), ix->rec, ix->hs, ix->wd, ix->wb, mark, out);
+    k_features<<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), ix->rec, ix->hs, ix->wd, ix->wb, ix->packed ? 1 : 0,
+                                                   ix->dl_mask, mark, out);
     ++ix->launches;
     free_buf(ix, mark, s);
     cudaError_t e = cudaGetLastError();
@@ -715,6 +723,54 @@ __global__ void k_score_keys(const float *sc, int32_t n, unsigned long long *key
     }
 }
 
+// Spread selection: keys hold (order-preserving score << 32) | (~id); a
+// vertex already taken or excluded has key 0.  One pass finds the largest
+// key (the highest score, ties by smaller id); one block then takes that
+// vertex and excludes its in- and out-neighbours.
+__global__ void k_spread_keys(const float *sc, int32_t n, unsigned long long *keys)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = __float_as_uint(sc[i]);
+        b = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+        const float f = sc[i];
+        keys[i] = (f != f || b == 0x007FFFFFu) ? 0ull  // NaN or -inf: never taken
+                                               : ((unsigned long long)b << 32) | (uint32_t)~(uint32_t)i;
+    }
+}
+
+__global__ void k_spread_max(const unsigned long long *keys, int32_t n, unsigned long long *best)
+{
+    unsigned long long m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = keys[i] > m ? keys[i] : m;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(kFull, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(best, m);
+}
+
+__global__ void k_spread_take(DevGraph g, unsigned long long *keys, unsigned long long *best, int32_t *out, int32_t i)
+{
+    const unsigned long long b = *best;
+    __syncthreads();
+    if (threadIdx.x == 0) *best = 0;
+    if (!b) {
+        if (threadIdx.x == 0) out[i] = -1;  // fewer candidates than slots
+        return;
+    }
+    const int32_t x = (int32_t)~(uint32_t)(b & 0xffffffffull);
+    if (threadIdx.x == 0) {
+        out[i] = x;
+        keys[x] = 0;
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+        const AdjRange r = adj_of(g, dir, x);
+        for (int32_t e = threadIdx.x; e < r.bd + r.od; e += blockDim.x) keys[adj_at(g, dir, r, e)] = 0;
+    }
+}
+
 static unsigned grid_cap(int64_t work, int threads)
 {
     int64_t b = (work + threads - 1) / threads;
@@ -894,6 +950,7 @@ dbl_status dbl_features(dbl_index *ix, uint16_t *feat, void *stream)
 {
     if (!ix || !feat) return dbl::fail(ix, DBL_ERR_INVALID, "features: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
+    if (dbl_status fs = flush_insertions(ix, s)) return fs;  // queued batches (DBL_FLAG_DEFER) first
     dbl_status st = dbl::features(ix, (bf16 *)feat, s);
     if (st) return st;
     return (ix->opt.flags & DBL_FLAG_ASYNC) ? DBL_OK : read_status(ix, s);
@@ -906,12 +963,36 @@ dbl_status dbl_coverage(dbl_index *ix, const int32_t *u, const int32_t *v, const
         return dbl::fail(ix, DBL_ERR_INVALID, "coverage: bad arguments");
     if (ix->poisoned) return dbl::fail(ix, DBL_ERR_POISONED, "index poisoned");
     cudaStream_t s = (cudaStream_t)stream;
+    if (dbl_status fs = flush_insertions(ix, s)) return fs;  // queued batches (DBL_FLAG_DEFER) first
     dbl_status st = dbl::coverage(ix, u, v, reach, pairs, base_slots, count, kept, s);
     if (st) return st;
     if (target) {
         k_cov_targets<<<1, 1024, 0, s>>>(count, ix->n, target);
         ++ix->launches;
     }
+    return read_status(ix, s);
+}
+
+dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream)
+{
+    if (!ix || !scores || !out || k <= 0) return dbl::fail(ix, DBL_ERR_INVALID, "select_spread: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *keys = nullptr;
+    dbl_status st = alloc_buf(ix, (void **)&keys, sizeof(unsigned long long) * ((size_t)ix->n + 1), s);
+    if (st) return st;
+    unsigned long long *best = keys + ix->n;
+    cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
+    k_spread_keys<<<grid_cap(ix->n, kBlock), kBlock, 0, s>>>(scores, ix->n, keys);
+    ++ix->launches;
+    const DevGraph g = dev_graph(ix);
+    for (int32_t i = 0; i < k; ++i) {
+        k_spread_max<<<grid_cap(ix->n, kBlock), kBlock, 0, s>>>(keys, ix->n, best);
+        k_spread_take<<<1, kBlock, 0, s>>>(g, keys, best, out, i);
+        ix->launches += 2;
+    }
+    free_buf(ix, keys, s);
+    cudaError_t e = cudaGetLastError();
+    if (e) return cuda_fail(ix, e, "select_spread");
     return read_status(ix, s);
 }
 

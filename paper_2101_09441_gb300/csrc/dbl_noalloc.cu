@@ -69,6 +69,7 @@ extern "C" dbl_status dbl_insert_edges_noalloc(dbl_index *ix, const int32_t *src
     dbl_status st = scratch_address(ix, &scratch);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if ((st = flush_insertions(ix, s))) return st;  // batches queued earlier (DBL_FLAG_DEFER) come first
     st = insert_edges_core(ix, src, dst, b, scratch, scratch + kNoAllocMaxBatch, s);
     if (st) return st;
     if (ix->opt.flags & DBL_FLAG_ASYNC) return DBL_OK;

@@ -478,17 +478,19 @@ __global__ void k_seed_landmarks(const int32_t *lm, int32_t k, uint64_t *rec, in
     }
 }
 
+// bucket b of the BL label is bit bl_base + b of a half (bl_base = 64 * WD,
+// or k in the packed layout)
 __global__ void k_seed_leaves(const int32_t *bucket, const uint8_t *role, int32_t n, uint64_t *rec, int32_t rw,
-                              int32_t hs, int32_t wd)
+                              int32_t hs, int32_t bl_base)
 {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         uint8_t r = role[v];
         if (!r) continue;
-        int32_t b = bucket[v];
-        unsigned long long bit = 1ull << (b & 63);
+        const int32_t pos = bl_base + bucket[v];
+        unsigned long long bit = 1ull << (pos & 63);
         uint64_t *p = rec + (size_t)v * rw;
-        if (r & 1) p[wd + (b >> 6)] |= bit;            // BL_in(v)
-        if (r & 2) p[hs + wd + (b >> 6)] |= bit;       // BL_out(v)
+        if (r & 1) p[pos >> 6] |= bit;          // BL_in(v)
+        if (r & 2) p[hs + (pos >> 6)] |= bit;   // BL_out(v)
     }
 }
 
@@ -602,7 +604,7 @@ dbl_status seed_labels(dbl_index *ix, cudaStream_t s)
     k_seed_landmarks<<<1, kBlock, 0, s>>>(ix->landmarks, ix->k, ix->rec, ix->rw, ix->hs);
     ++ix->launches;
     k_seed_leaves<<<grid_for(ix->n), kBlock, 0, s>>>(ix->leaf_bucket, ix->leaf_role, ix->n, ix->rec, ix->rw, ix->hs,
-                                                      ix->wd);
+                                                      ix->bl_base);
     ++ix->launches;
     cudaError_t e = cudaGetLastError();
     return e ? cuda_fail(ix, e, "seed_labels") : DBL_OK;

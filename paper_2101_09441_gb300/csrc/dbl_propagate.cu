@@ -110,6 +110,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s)
         cudaMemsetAsync(ix->d_counts + kCntFront0 + nxt, 0, sizeof(uint32_t), s);
         tbegin(ix, DBL_KERNEL_PROPAGATE, s);
         switch (ix->hs) {
+        case 1: launch_expand_team<1>(ix, cur, ntasks, f, s); break;
         case 2: launch_expand_team<2>(ix, cur, ntasks, f, s); break;
         case 4: launch_expand_team<4>(ix, cur, ntasks, f, s); break;
         default: launch_expand_team<8>(ix, cur, ntasks, f, s); break;
@@ -217,6 +218,7 @@ dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s)
     tbegin(ix, DBL_KERNEL_PROPAGATE, s);
     dbl_status st;
     switch (ix->hs) {
+    case 1: st = launch_persistent_team<1>(ix, s); break;
     case 2: st = launch_persistent_team<2>(ix, s); break;
     case 4: st = launch_persistent_team<4>(ix, s); break;
     default: st = launch_persistent_team<8>(ix, s); break;

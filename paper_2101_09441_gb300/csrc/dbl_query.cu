@@ -27,7 +27,9 @@
 
 namespace dbl {
 
-__host__ __device__ constexpr int hs_of(int words) { return words <= 2 ? 2 : (words <= 4 ? 4 : 8); }
+// Words per half-record of a (WD, WB) instantiation; WD = WB = 0 marks the
+// packed layout (k + k' <= 64: one word per half, DL in its low k bits, BL above).
+__host__ __device__ constexpr int hs_of(int words) { return words == 0 ? 1 : (words <= 2 ? 2 : (words <= 4 ? 4 : 8)); }
 
 // ------------------------------------------------------------ label test
 // A pair is handled by LPP = HS / 2 adjacent lanes: lane `sub` of the group
@@ -144,6 +146,74 @@ __global__ void __launch_bounds__(kBlock) k_query_label(const int32_t *qu, const
     }
 }
 
+// Label test of the packed layout (k + k' <= 64): a 16-byte record is the
+// forward word and the backward word, DL in the bits of dlm and BL in the
+// bits of blm; one lane per pair, QPT pairs per lane with all their loads in
+// flight before any is used.  Same rules, order and outputs as k_query_label.
+template <int QPT>
+__global__ void __launch_bounds__(kBlock) k_query_label_packed(const int32_t *qu, const int32_t *qv, int64_t q,
+                                                               const uint64_t *rec, int32_t n, uint64_t dlm,
+                                                               uint64_t blm, uint8_t *ans, uint8_t *code,
+                                                               uint32_t *status, unsigned long long *stats)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned int counts[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t tile = (int64_t)blockDim.x * QPT;
+    const int64_t stride = (int64_t)gridDim.x * tile;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < q; base += stride) {
+        int32_t u[QPT], v[QPT];
+        bool live[QPT];
+        ulonglong2 ru[QPT], rv[QPT];
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            live[j] = i < q;
+            u[j] = live[j] ? __ldcs(qu + i) : 0;
+            v[j] = live[j] ? __ldcs(qv + i) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            const bool ok = live[j] && (uint32_t)u[j] < (uint32_t)n && (uint32_t)v[j] < (uint32_t)n && u[j] != v[j];
+            ru[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + 2 * (size_t)(ok ? u[j] : 0)));
+            rv[j] = __ldcg(reinterpret_cast<const ulonglong2 *>(rec + 2 * (size_t)(ok ? v[j] : 0)));
+        }
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) {
+            const uint64_t a = ru[j].x, b = ru[j].y, c = rv[j].x, d = rv[j].y;  // fwd(u), bwd(u), fwd(v), bwd(v)
+            const int64_t i = base + (int64_t)j * blockDim.x + threadIdx.x;
+            uint8_t an = 0, cd = DBL_CODE_UNDECIDED;
+            if (live[j]) {
+                if ((uint32_t)u[j] >= (uint32_t)n || (uint32_t)v[j] >= (uint32_t)n) {
+                    set_status(status, DBL_ERR_INVALID);
+                } else if (u[j] == v[j]) {
+                    an = 1;
+                    cd = DBL_CODE_SELF;
+                } else if (b & c & dlm) {                           // DL_out(u) & DL_in(v): Lemma 1
+                    an = 1;
+                    cd = DBL_CODE_DL;
+                } else if (((a & ~c) | (d & ~b)) & blm) {           // BL containment fails: Lemma 2
+                    cd = DBL_CODE_BL;
+                } else if (d & a & dlm) {                           // DL_out(v) & DL_in(u): Theorem 1
+                    cd = DBL_CODE_THM1;
+                } else if (((b & a) | (d & c)) & dlm) {             // u or v with a landmark in its SCC: Theorem 2
+                    cd = DBL_CODE_THM2;
+                } else {
+                    an = kAnsUndecided;
+                }
+                __stcs(ans + i, an);
+                if (code) __stcs(code + i, cd);
+            }
+#pragma unroll
+            for (int r = 1; r < 6; ++r) counts[r] += (live[j] && cd == r) ? 1u : 0u;
+        }
+    }
+#pragma unroll
+    for (int r = 1; r < 6; ++r) {
+        const unsigned int t = __reduce_add_sync(kFull, counts[r]);
+        if (lane == 0 && t) atomicAdd(stats + r, (unsigned long long)t);
+    }
+}
+
 // The undecided pairs of a batch, from the answer array: und[] gets their
 // indices (in no particular order) and *n_und their number.  The aligned
 // middle of the array is read 16 bytes at a time, two words per thread and
@@ -226,6 +296,7 @@ struct SlotList {
 struct SearchArgs {
     DevGraph g;
     const uint64_t *rec;
+    uint64_t dlm, blm;  // packed labels: the DL and the BL bits of a half word
     uint64_t *qtab;
     unsigned long long *found;
     SearchCtx c;
@@ -290,10 +361,12 @@ __device__ __forceinline__ int64_t slot_find_or_insert(const SearchCtx &c, unsig
     return -1;
 }
 
-// qtab word layout per query: [u | v<<32][DL_out(u) x WD][BL_in(v) x WB][BL_out(v) x WB]
+// qtab word layout per query: [u | v<<32][DL_out(u) x WD][BL_in(v) x WB][BL_out(v) x WB];
+// packed labels: [u | v<<32][DL_out(u)][BL_in(v)][BL_out(v)], each a half word
+// masked to its own bits (in place)
 template <int WD, int WB>
 struct QT {
-    static constexpr int W = 1 + WD + 2 * WB;
+    static constexpr int W = WD == 0 ? 4 : 1 + WD + 2 * WB;
 };
 
 __device__ __forceinline__ IList slot_list_of(const SearchCtx &c, const SlotList &l)
@@ -351,12 +424,18 @@ __device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, in
             uint64_t *t = a.qtab + (size_t)j * W;
             t[0] = (uint64_t)(uint32_t)u[k] | ((uint64_t)(uint32_t)v[k] << 32);
             const uint64_t *ru = a.rec + (size_t)u[k] * RW, *rv = a.rec + (size_t)v[k] * RW;
+            if constexpr (WD == 0) {  // packed: each label masked to its own bits
+                t[1] = ru[1] & a.dlm;  // DL_out(u)
+                t[2] = rv[0] & a.blm;  // BL_in(v)
+                t[3] = rv[1] & a.blm;  // BL_out(v)
+            } else {
 #pragma unroll
-            for (int w = 0; w < WD; ++w) t[1 + w] = ru[HS + w];  // DL_out(u)
+                for (int w = 0; w < WD; ++w) t[1 + w] = ru[HS + w];  // DL_out(u)
 #pragma unroll
-            for (int w = 0; w < WB; ++w) {
-                t[1 + WD + w] = rv[WD + w];                       // BL_in(v)
-                t[1 + WD + WB + w] = rv[HS + WD + w];             // BL_out(v)
+                for (int w = 0; w < WB; ++w) {
+                    t[1 + WD + w] = rv[WD + w];                       // BL_in(v)
+                    t[1 + WD + WB + w] = rv[HS + WD + w];             // BL_out(v)
+                }
             }
             nch[k] = (uint32_t)((deg_of(a.g, 0, u[k]) + kChunk - 1) / kChunk);
             mine += nch[k];
@@ -457,13 +536,20 @@ __device__ __forceinline__ unsigned long long search_edge_visit(const SearchArgs
             continue;
         }
         uint64_t dl = 0, bl = 0;
+        if constexpr (WD == 0) {  // packed: the stored labels hold only their own bits
+            dl = __ldg(qj + 1) & fy[0];
+            if (dl) continue;
+            bl = (fy[0] & a.blm & ~__ldg(qj + 2)) | (__ldg(qj + 3) & ~by[0]);
+            if (bl) continue;
+        } else {
 #pragma unroll
-        for (int w = 0; w < WD; ++w) dl |= __ldg(qj + 1 + w) & fy[w];
-        if (dl) continue;
+            for (int w = 0; w < WD; ++w) dl |= __ldg(qj + 1 + w) & fy[w];
+            if (dl) continue;
 #pragma unroll
-        for (int w = 0; w < WB; ++w)
-            bl |= (fy[WD + w] & ~__ldg(qj + 1 + WD + w)) | (__ldg(qj + 1 + WD + WB + w) & ~by[WD + w]);
-        if (bl) continue;
+            for (int w = 0; w < WB; ++w)
+                bl |= (fy[WD + w] & ~__ldg(qj + 1 + WD + w)) | (__ldg(qj + 1 + WD + WB + w) & ~by[WD + w]);
+            if (bl) continue;
+        }
         allowed |= bit;
     }
     if (hits) atomicOr(a.found + g, hits);
@@ -879,6 +965,8 @@ static SearchArgs search_args(dbl_index *ix, dbl_qctx *c, const int32_t *qu, con
     SearchArgs a;
     a.g = dev_graph(ix);
     a.rec = ix->rec;
+    a.dlm = ix->dl_mask;
+    a.blm = ix->bl_mask;
     a.qtab = c->qtab;
     a.found = c->found;
     a.c = SearchCtx{c->table, (unsigned long long)(c->table_slots - 1), c->claimed, n_claimed, overflow};
@@ -1025,13 +1113,20 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     // keeps the same registers at every record width
     constexpr int HS = hs_of(WD + WB);
     const int qpt = ix->opt.query_unroll ? ix->opt.query_unroll : (HS == 2 ? 2 : 4);
-    const int64_t pairs_per_block = (int64_t)(kBlock / (HS / 2)) * qpt;
+    const int64_t pairs_per_block = (int64_t)(kBlock / (HS >= 2 ? HS / 2 : 1)) * qpt;
     int64_t blocks = (q + pairs_per_block - 1) / pairs_per_block;
     if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
     if (blocks < 1) blocks = 1;
     qt_begin(ix, c, DBL_KERNEL_QUERY_LABEL, s);
-    auto kern = qpt >= 4 ? k_query_label<WD, WB, 4> : (qpt == 2 ? k_query_label<WD, WB, 2> : k_query_label<WD, WB, 1>);
-    kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->d_status, ix->d_stats);
+    if constexpr (WD == 0) {
+        auto kern = qpt >= 4 ? k_query_label_packed<4> : (qpt == 2 ? k_query_label_packed<2> : k_query_label_packed<1>);
+        kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ix->dl_mask, ix->bl_mask, ans, code,
+                                                 c->d_status, ix->d_stats);
+    } else {
+        auto kern =
+            qpt >= 4 ? k_query_label<WD, WB, 4> : (qpt == 2 ? k_query_label<WD, WB, 2> : k_query_label<WD, WB, 1>);
+        kern<<<(unsigned)blocks, kBlock, 0, s>>>(u, v, q, ix->rec, ix->n, ans, code, c->d_status, ix->d_stats);
+    }
     ++ix->launches;
     qt_end(ix, c, s);
     // one cooperative launch runs every wave, for the index's own context only
@@ -1093,6 +1188,7 @@ dbl_status query(dbl_index *ix, dbl_qctx *c, const int32_t *u, const int32_t *v,
                  uint8_t *code, cudaStream_t s)
 {
     if (q == 0) return DBL_OK;
+    if (ix->packed) return query_t<0, 0>(ix, c, u, v, q, ans, code, s);
     const int key = ix->wd * 16 + ix->wb;
     switch (key) {
     case 1 * 16 + 1: return query_t<1, 1>(ix, c, u, v, q, ans, code, s);

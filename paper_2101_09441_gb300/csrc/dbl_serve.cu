@@ -8,8 +8,12 @@
 // An insertion is an epoch barrier: it is admitted only when it is at the
 // head and no query batch is in flight, and queries behind it wait for it;
 // hence every request observes exactly the insertions that arrived before it
-// (labels are read by queries and written only by insertions).  The number of
-// slots is bounded by the free device memory at start-up (cudaMemGetInfo).
+// (labels are read by queries and written only by insertions).  Admission by
+// memory: a slot's device scratch (its query context, sized for a full batch,
+// and staging) is allocated when the slot is first needed, and only if the
+// device's free memory at that moment (cudaMemGetInfo) leaves it within
+// mem_fraction; until then the slot takes no work and requests wait for the
+// slots that have memory.  The first slot is set up at creation.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -42,6 +46,7 @@ struct Slot {
     uint8_t *d_ans = nullptr;
     int32_t *h_u = nullptr, *h_v = nullptr;
     uint8_t *h_ans = nullptr;
+    bool ready = false;  // its scratch is allocated
     std::thread worker;
 };
 
@@ -50,8 +55,13 @@ struct Slot {
 struct dbl_server {
     dbl_index *ix = nullptr;
     int64_t max_batch = 0, max_pending = 0;
+    int64_t per_slot = 0;       // device bytes one slot's scratch takes
+    double mem_fraction = 0.5;  // share of the free device memory a new slot may take
+    int64_t max_memory = 0;     // bytes all admitted slots may take together (0: no limit)
+    int ready_slots = 0;
     std::vector<Slot> slots;
     std::mutex mu;
+    std::mutex setup_mu;        // one slot set-up at a time (each re-reads the free memory)
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> pending;
     std::unordered_map<uint64_t, Request *> all;
@@ -67,10 +77,87 @@ struct dbl_server {
     std::string err;
 };
 
+// A slot's scratch: stream, staging for max_batch pairs, and a query context
+// sized for a full batch (so serving allocates nothing after this).
+static dbl_status slot_setup(dbl_server *S, Slot &sl)
+{
+    dbl_index *ix = S->ix;
+    const int64_t mb = S->max_batch;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) ||
+        cudaMalloc(&sl.d_u, sizeof(int32_t) * mb) || cudaMalloc(&sl.d_v, sizeof(int32_t) * mb) ||
+        cudaMalloc(&sl.d_ans, (size_t)mb) || cudaMallocHost(&sl.h_u, sizeof(int32_t) * mb) ||
+        cudaMallocHost(&sl.h_v, sizeof(int32_t) * mb) || cudaMallocHost(&sl.h_ans, (size_t)mb)) {
+        cudaGetLastError();
+        return DBL_ERR_OOM;
+    }
+    dbl_status st = dbl_qctx_create(ix, &sl.ctx, sl.stream);
+    if (!st) st = dbl::ensure_search_scratch(sl.ctx, mb, sl.stream);
+    if (!st && cudaStreamSynchronize(sl.stream) != cudaSuccess) st = DBL_ERR_CUDA;
+    if (!st) sl.ready = true;
+    return st;
+}
+
+static void slot_release(Slot &sl)
+{
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.ctx) dbl_qctx_destroy(sl.ctx, sl.stream);
+    sl.ctx = nullptr;
+    cudaFree(sl.d_u);
+    cudaFree(sl.d_v);
+    cudaFree(sl.d_ans);
+    cudaFreeHost(sl.h_u);
+    cudaFreeHost(sl.h_v);
+    cudaFreeHost(sl.h_ans);
+    sl.d_u = sl.d_v = nullptr;
+    sl.d_ans = nullptr;
+    sl.h_u = sl.h_v = nullptr;
+    sl.h_ans = nullptr;
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    sl.stream = nullptr;
+    sl.ready = false;
+}
+
+// Admission by memory: a slot without scratch sets it up when there is work
+// and the device's free memory now leaves one more slot within mem_fraction.
+// Returns false when the worker should stop.
+static bool admit_slot(dbl_server *S, Slot *slot)
+{
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(2), [&] { return S->stop || !S->pending.empty(); });
+        if (S->stop && S->pending.empty()) return false;
+        if (S->pending.empty()) return true;
+    }
+    std::lock_guard<std::mutex> g(S->setup_mu);
+    size_t free_b = 0, total_b = 0;
+    int ready = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ready = S->ready_slots;
+    }
+    const bool in_budget = S->max_memory <= 0 || (int64_t)(ready + 1) * S->per_slot <= S->max_memory;
+    if (in_budget && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+        (double)S->per_slot <= S->mem_fraction * (double)free_b) {
+        if (slot_setup(S, *slot) == DBL_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            ++S->ready_slots;
+        } else {
+            slot_release(*slot);
+        }
+    }
+    if (!slot->ready) std::this_thread::sleep_for(std::chrono::microseconds(500));  // the other slots serve
+    S->cv_work.notify_all();
+    return true;
+}
+
 static void serve_worker(dbl_server *S, Slot *slot)
 {
     dbl_index *ix = S->ix;
     for (;;) {
+        if (!slot->ready) {
+            if (!admit_slot(S, slot)) return;
+            if (!slot->ready) continue;
+        }
         std::vector<Request *> batch;
         int kind = 0;
         {
@@ -178,6 +265,7 @@ void dbl_server_default_options(dbl_server_options *o)
     o->max_batch = 1 << 18;
     o->max_pending = 1 << 16;
     o->mem_fraction = 0.5;
+    o->max_memory = 0;
 }
 
 dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_server **out)
@@ -187,7 +275,8 @@ dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_s
     dbl_server_options o;
     dbl_server_default_options(&o);
     if (opt) o = *opt;
-    if (o.slots < 1 || o.max_batch < 1 || o.max_pending < 1 || o.mem_fraction <= 0 || o.mem_fraction > 1)
+    if (o.slots < 1 || o.max_batch < 1 || o.max_pending < 1 || o.mem_fraction <= 0 || o.mem_fraction > 1 ||
+        o.max_memory < 0)
         return dbl::fail(ix, DBL_ERR_INVALID, "server: bad options");
     if (ix->opt.flags & DBL_FLAG_ASYNC) return dbl::fail(ix, DBL_ERR_INVALID, "server: index must not be ASYNC");
     // admission by free HBM: each slot needs its search scratch (a 32-byte slot
@@ -199,30 +288,18 @@ dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_s
                              o.max_batch * (int64_t)(4 + 8 * W + 9 + 1) + (64 << 20);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return dbl::fail(ix, DBL_ERR_CUDA, "server: cudaMemGetInfo");
-    const int64_t fit = (int64_t)((double)free_b * o.mem_fraction) / per_slot;
-    const int nslots = (int)std::min<int64_t>(o.slots, fit);
-    if (nslots < 1) return dbl::fail(ix, DBL_ERR_OOM, "server: not enough free device memory for one slot");
+    if ((double)per_slot > (double)free_b * o.mem_fraction || (o.max_memory > 0 && per_slot > o.max_memory))
+        return dbl::fail(ix, DBL_ERR_OOM, "server: not enough free device memory for one slot");
     dbl_server *S = new dbl_server();
     S->ix = ix;
     S->max_batch = o.max_batch;
     S->max_pending = o.max_pending;
-    S->slots.resize(nslots);
-    dbl_status st = DBL_OK;
-    for (Slot &sl : S->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) ||
-            cudaMalloc(&sl.d_u, sizeof(int32_t) * o.max_batch) || cudaMalloc(&sl.d_v, sizeof(int32_t) * o.max_batch) ||
-            cudaMalloc(&sl.d_ans, (size_t)o.max_batch) ||
-            cudaMallocHost(&sl.h_u, sizeof(int32_t) * o.max_batch) ||
-            cudaMallocHost(&sl.h_v, sizeof(int32_t) * o.max_batch) || cudaMallocHost(&sl.h_ans, (size_t)o.max_batch)) {
-            cudaGetLastError();
-            st = DBL_ERR_OOM;
-            break;
-        }
-        if ((st = dbl_qctx_create(ix, &sl.ctx, sl.stream))) break;
-        // size the context for a full batch now, so serving allocates nothing
-        if ((st = dbl::ensure_search_scratch(sl.ctx, o.max_batch, sl.stream))) break;
-        cudaStreamSynchronize(sl.stream);
-    }
+    S->per_slot = per_slot;
+    S->mem_fraction = o.mem_fraction;
+    S->max_memory = o.max_memory;
+    S->slots.resize(o.slots);
+    dbl_status st = slot_setup(S, S->slots[0]);  // the others are admitted by memory when needed
+    if (!st) S->ready_slots = 1;
     if (st) {
         S->stop = true;
         dbl_server_destroy(S);
@@ -257,7 +334,7 @@ dbl_status dbl_server_submit(dbl_server *S, int32_t kind, const int32_t *a_host,
         S->all[r->ticket] = r;
         *ticket = r->ticket;
     }
-    S->cv_work.notify_one();
+    S->cv_work.notify_all();  // a slot still waiting for memory must not swallow the wake-up
     return DBL_OK;
 }
 
@@ -326,6 +403,8 @@ dbl_status dbl_server_report(dbl_server *S, double out[16])
     out[11] = (double)S->batched_requests;
     out[12] = (double)S->epoch;
     out[13] = (double)S->cancelled;
+    out[14] = (double)S->ready_slots;
+    out[15] = (double)S->per_slot;
     return DBL_OK;
 }
 
@@ -350,17 +429,7 @@ void dbl_server_destroy(dbl_server *S)
     S->cv_work.notify_all();
     for (Slot &sl : S->slots)
         if (sl.worker.joinable()) sl.worker.join();
-    for (Slot &sl : S->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.ctx) dbl_qctx_destroy(sl.ctx, sl.stream);
-        cudaFree(sl.d_u);
-        cudaFree(sl.d_v);
-        cudaFree(sl.d_ans);
-        cudaFreeHost(sl.h_u);
-        cudaFreeHost(sl.h_v);
-        cudaFreeHost(sl.h_ans);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
-    }
+    for (Slot &sl : S->slots) slot_release(sl);
     for (auto &kv : S->all) delete kv.second;
     delete S;
 }

@@ -62,15 +62,17 @@ def train_scorer(ix: DBLIndex, qu, qv, base_slots: int, steps: int = 400, batch:
     return scores, info
 
 
-def select_landmarks(ix: DBLIndex, scores, k: int, base_slots: int):
-    """First `base_slots` degree landmarks of ix, then the best-scored others."""
+def select_landmarks(ix: DBLIndex, scores, k: int, base_slots: int, spread: bool = False):
+    """First `base_slots` degree landmarks of ix, then the best-scored others
+    (spread: each pick excludes its in- and out-neighbours from later picks,
+    dbl_select_spread)."""
     import torch
     lm_deg = ix.selection()[0]
     base = lm_deg[:base_slots]
     sc = torch.nan_to_num(scores.clone(), nan=float("-inf"))
     base_ok = base[base >= 0].long()
     sc[base_ok] = float("-inf")
-    rest = ix.select_by_score(sc, k - base_slots)
+    rest = ix.select_spread(sc, k - base_slots) if spread else ix.select_by_score(sc, k - base_slots)
     return torch.cat([base, rest]).to(torch.int32)
 
 
@@ -92,7 +94,7 @@ def repair_ok(repair_plain: int, repair_learned: int) -> bool:
 
 
 def learned_index(row_ptr, col, train_q, eval_q, k: int = 64, kprime: int = 64, base_slots: int | None = None,
-                  inserts=None, **kw):
+                  inserts=None, spread: bool = False, **kw):
     """Build the plain index (after `inserts`, a list of (src, dst) batches),
     train the scorer on the plain index's outcomes for train_q = (u, v), build
     the learned index with the same leaves and insertions, and keep the
@@ -112,7 +114,7 @@ def learned_index(row_ptr, col, train_q, eval_q, k: int = 64, kprime: int = 64, 
     if base_slots is None:
         base_slots = max(1, k // 8)
     scores, info = train_scorer(plain, train_q[0], train_q[1], base_slots, **train_kw)
-    lm = select_landmarks(plain, scores, k, base_slots)
+    lm = select_landmarks(plain, scores, k, base_slots, spread=spread)
     _, lb, lr_ = plain.selection()
     learned = DBLIndex(row_ptr, col, k, kprime, landmarks=lm, leaf_buckets=lb, leaf_roles=lr_, **idx_kw)
     r0 = int(learned.stats()[10])

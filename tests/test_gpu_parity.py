@@ -473,6 +473,61 @@ def test_split_build_equals_joint_build(tiny, k, kp, flags):
     assert_labels(a, ref, "split build, after insertions")
 
 
+def test_deferred_insertions_apply_as_one_group(tiny):
+    """DBL_FLAG_DEFER: insertion batches queue on the host and the next call
+    that reads the index applies them in one launch.  A query sees exactly
+    the batches queued before it; 40 small batches flush at 32; an invalid
+    id in a queued batch rejects the whole group (nothing changes); a
+    captured restore + queued batches + query replays correctly."""
+    rp, col = tiny["row_ptr"], tiny["col"]
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    qu, qv = tiny["q_u"][:20000], tiny["q_v"][:20000]
+    flags = dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | dbl.FLAG_DEFER
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64, flags=flags, edge_capacity=1 << 16)
+    ix.snapshot(0)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    dev_s, dev_d = D(s), D(d)
+    for a in range(0, 3000, 1000):                      # three batches, then a query
+        ix.insert_edges(dev_s[a:a + 1000], dev_d[a:a + 1000])
+    ref.insert_edges(s[:3000], d[:3000])
+    assert_queries(ix, ref, qu, qv, "after three queued batches")
+    for a in range(3000, 7000, 100):                    # 40 batches: a flush at 32, the rest at labels()
+        ix.insert_edges(dev_s[a:a + 100], dev_d[a:a + 100])
+    ref.insert_edges(s[3000:7000], d[3000:7000])
+    ix.sync()
+    assert_labels(ix, ref, "after 40 queued batches")
+    before = labels_np(ix)
+    bad = D(np.array([0, len(rp) + 5], np.int32))      # an id out of range
+    ix.insert_edges(dev_s[7000:8000], dev_d[7000:8000])
+    ix.insert_edges(bad, bad)
+    with pytest.raises(dbl.DblError) as e:
+        ix.sync()
+    assert e.value.status == dbl.DBL_ERR_INVALID
+    for x, y in zip(labels_np(ix), before):
+        assert np.array_equal(x, y)                     # the whole group was rejected
+    # captured: restore, three queued batches, the query that applies them
+    refB = oracle.OracleIndex(rp, col, 64, 64).build()
+    refB.insert_edges(s[:6000], d[:6000])
+    ix.restore(0)
+    ix.sync()
+    ans = torch.empty(len(qu), dtype=torch.uint8, device="cuda")
+    code = torch.empty_like(ans)
+    dqu, dqv = D(qu), D(qv)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ix.restore(0)
+        for a in range(0, 6000, 2000):
+            ix.insert_edges(dev_s[a:a + 2000], dev_d[a:a + 2000])
+        ix.query(dqu, dqv, out=(ans, code))
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        rans, rcode = refB.query(qu, qv, nthreads=8)
+        assert np.array_equal(ans.cpu().numpy(), rans) and np.array_equal(code.cpu().numpy(), rcode)
+        assert_labels(ix, refB, "replayed deferred group")
+    ix.close()
+
+
 def test_batch_size_invariance(tiny):
     s, d = tiny["ins_src"], tiny["ins_dst"]
     results = []

@@ -162,3 +162,38 @@ def test_server_cancel_drops_queued_requests(tiny):
             assert np.array_equal(got[i], alone.query(D(a), D(b))[0].cpu().numpy())
     for x, y in zip(ix.labels(), alone.labels()):
         assert torch.equal(x, y)
+
+
+def test_server_admits_slots_by_free_memory(tiny):
+    """A slot's scratch is allocated only when it then fits the device's free
+    memory (mem_fraction) and the server's byte budget (max_memory): with a
+    budget of one slot the server runs on that slot alone, with a generous
+    one more slots are admitted under load.  Results equal a serial replay."""
+    reqs = _request_stream(tiny, 200, 17)
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    probe = dbl.Server(ix, slots=1, max_batch=1 << 14)
+    per_slot = int(probe.report()["bytes_per_slot"])
+    probe.close()
+    with pytest.raises(dbl.DblError) as e:
+        dbl.Server(ix, slots=2, max_batch=1 << 14, max_memory=per_slot // 2)   # not even one slot
+    assert e.value.status == dbl.DBL_ERR_OOM
+    got = {}
+    for name, budget in (("one", per_slot * 3 // 2), ("many", 0)):
+        ix2 = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+        srv = dbl.Server(ix2, slots=4, max_batch=1 << 14, mem_fraction=0.9, max_memory=budget)
+        tickets = [srv.submit(k, a, b) for k, a, b in reqs]
+        got[name] = [srv.wait(t)[0] for t in tickets]
+        rep = srv.report()
+        srv.close()
+        ix2.close()
+        if name == "one":
+            assert rep["slots_admitted"] == 1
+        else:
+            assert rep["slots_admitted"] >= 2
+    alone = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64)
+    for i, (k, a, b) in enumerate(reqs):
+        if k == 1:
+            alone.insert_edges(D(a), D(b))
+        else:
+            exp = alone.query(D(a), D(b))[0].cpu().numpy()
+            assert np.array_equal(got["one"][i], exp) and np.array_equal(got["many"][i], exp)
