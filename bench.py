@@ -616,10 +616,15 @@ def build_roofline(form):
         return None
     ach = alg / (ms * 1e-3) / 1e9
     relaxed = form.get("build_edges_relaxed")
+    prep = form.get("build_kernel_ms", {}).get("build_prep")
     return {"kernel": "propagate (label build)", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs of {src}",
             "algorithmic_bytes": alg, "ms": ms, "edges_relaxed": relaxed,
-            "teps": relaxed / (ms * 1e-3) if relaxed else None}
+            "teps": relaxed / (ms * 1e-3) if relaxed else None,
+            "prep_ms": prep, "build_ms": ms + prep if prep else None,
+            "note": "ms: the propagation (seeds, frontier levels, record copies); prep_ms: the graph preparation "
+                    "before it (CSR-in transpose, landmark and leaf selection, seeds, and on graphs whose records "
+                    "exceed 256 MB the degree-grouped renumbering the propagation runs on)"}
 
 
 def roofline(form, ix, steps, w, I, batches, persistent=True, group=False):
@@ -1000,7 +1005,8 @@ def serving_pass(w, I, k, kp, lm, leaves, n_req, slots=4):
     """Serving on a resident index with the given landmarks: a closed-loop run
     gives the peak request rate, then Poisson streams at 50% and 90% of it
     report p50/p99 latency per request kind and sustained pairs/s and
-    edges/s.  Every run starts from the built index."""
+    edges/s.  Every run starts from the built index; one server serves all
+    runs (a warm-up run first admits its slots)."""
     import paper_2101_09441_gb300 as dbl
     E = int(w["ins_src"].shape[0])
     ix = dbl.DBLIndex(I.rp, I.col, k, kp, landmarks=lm, leaf_buckets=leaves[0], leaf_roles=leaves[1],
@@ -1008,24 +1014,28 @@ def serving_pass(w, I, k, kp, lm, leaves, n_req, slots=4):
     ix.sync()
     ix.snapshot(0)
 
+    srv = dbl.Server(ix, slots=slots)
+
     def run(reqs, rate, seed):
+        srv.drain()  # nothing in flight: the index goes back to its built state
         ix.restore(0)
         ix.sync()
-        srv = dbl.Server(ix, slots=slots)
-        try:
-            return run_serving(srv, reqs, rate, seed)
-        finally:
-            srv.close()
+        return run_serving(srv, reqs, rate, seed)
 
-    warm, _, _ = serve_requests(w, max(1, n_req // 4), 99)
-    run(warm, None, 0)
-    reqs, _, _ = serve_requests(w, n_req, 100)
-    peak = run(reqs, None, 0)
-    loads = {}
-    for i, frac in enumerate((0.5, 0.9)):
-        reqs, _, _ = serve_requests(w, n_req, 200 + i, q_off=(i + 1) * 3_000_000)
-        loads[str(frac)] = run(reqs, frac * peak["requests_per_s"], 300 + i)
-    ix.close()
+    try:
+        # the warm-up run admits the slots (each set up once, when the free
+        # memory allows and requests wait); the measured runs reuse them
+        warm, _, _ = serve_requests(w, max(1, n_req // 2), 99)
+        run(warm, None, 0)
+        reqs, _, _ = serve_requests(w, n_req, 100)
+        peak = run(reqs, None, 0)
+        loads = {}
+        for i, frac in enumerate((0.5, 0.9)):
+            reqs, _, _ = serve_requests(w, n_req, 200 + i, q_off=(i + 1) * 3_000_000)
+            loads[str(frac)] = run(reqs, frac * peak["requests_per_s"], 300 + i)
+    finally:
+        srv.close()
+        ix.close()
     return {"k": k, "kprime": kp, "slots": slots, "requests_per_run": n_req,
             "mix": "90% query / 10% insertion requests, sizes floor(exp(U[0, ln 65537)))",
             "closed_loop_peak": peak, "poisson": loads}
@@ -1128,7 +1138,8 @@ def bench_kernel_case(args):
     """A small, single-index run of one kernel for an ncu capture: `label`
     builds the index (k, k'), applies the workload's insertions and answers
     its query batch `args.steps` times; `insert` applies the insertions in
-    batches of `args.batch` (persistent kernels, asynchronous calls).  Prints
+    batches of `args.batch` (persistent kernels, asynchronous calls; with
+    `args.defer` queued and applied as one group).  Prints
     per-kernel CUDA-event times (one JSON line)."""
     import torch
 
@@ -1154,7 +1165,7 @@ def bench_kernel_case(args):
     E = int(src.numel())
     flags = dbl.FLAG_PERSISTENT | dbl.FLAG_TIMING | (dbl.FLAG_FINE_L2 if args.fine_l2 else 0)
     if args.kernel_case == "insert":
-        flags |= dbl.FLAG_ASYNC
+        flags |= dbl.FLAG_ASYNC | (dbl.FLAG_DEFER if args.defer else 0)
     ix = dbl.DBLIndex(rp, col, args.k, args.kprime, edge_capacity=max(E, 1 << 20), flags=flags)
     ix.sync()
     ix.timings()
@@ -1167,7 +1178,7 @@ def bench_kernel_case(args):
         ix.sync()
     t = ix.timings()
     print(json.dumps({"kernel_case": args.kernel_case, "workload": args.workload, "k": args.k,
-                      "kprime": args.kprime, "fine_l2": bool(args.fine_l2),
+                      "kprime": args.kprime, "fine_l2": bool(args.fine_l2), "defer": bool(args.defer),
                       "ms_per_launch": {kk: v[0] / max(1, v[1]) for kk, v in t.items() if v[1]},
                       "launches": {kk: v[1] for kk, v in t.items() if v[1]}}), flush=True)
     ix.close()
@@ -1206,6 +1217,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
     ap.add_argument("--kernel-case", choices=["label", "insert", "scorer"], default=None,
                     help="a small single-index run of one kernel (for an ncu capture) instead of the step")
+    ap.add_argument("--defer", action="store_true",
+                    help="kernel case insert: queue the batches and apply them as one group (DBL_FLAG_DEFER)")
     ap.add_argument("--fine-l2", action=argparse.BooleanOptionalAction, default=True,
                     help="DBL_FLAG_FINE_L2 in every form: 32-byte L2 fetch granularity for the whole process "
                          "(default on; --no-fine-l2 keeps the driver's default)")

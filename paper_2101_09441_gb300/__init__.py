@@ -62,7 +62,8 @@ class _Options(ctypes.Structure):
                 ("edge_capacity", ctypes.c_int64), ("flags", ctypes.c_int32), ("bfs_words", ctypes.c_int32),
                 ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
                 ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("vertex_capacity", ctypes.c_int64),
-                ("initial_slots", ctypes.c_int32), ("build_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("initial_slots", ctypes.c_int32), ("build_split", ctypes.c_int32), ("build_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Graph(ctypes.Structure):
@@ -176,7 +177,7 @@ class DBLIndex:
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
                  torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0,
                  landmark_rule: str = "M", leaf_r: int = 0, vertex_capacity: int = 0, initial_slots: int = 0,
-                 build_split: int = 0):
+                 build_split: int = 0, build_order: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -200,6 +201,7 @@ class DBLIndex:
         opt.vertex_capacity = int(vertex_capacity)
         opt.initial_slots = int(initial_slots)
         opt.build_split = int(build_split)
+        opt.build_order = int(build_order)
         self._refuse = [0, 0]  # allocations to let through, then to refuse (fail_allocations)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()

@@ -323,6 +323,9 @@ struct dbl_index {
     // the propagation's view of the labels when it is not the index's records
     // (a build pass over one direction's halves); rec == nullptr: the records
     dbl::RecView prop_view{nullptr, 0, 0};
+    // the graph the propagation runs over when it is not the index's own (the
+    // build's degree-ordered copy); vm == nullptr: the index's graph
+    dbl::DevGraph prop_graph{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
     // status, counters
     uint32_t *d_status = nullptr;
@@ -452,6 +455,8 @@ inline DevGraph dev_graph(const dbl_index *ix)
     return g;
 }
 
+inline DevGraph prop_graph(const dbl_index *ix) { return ix->prop_graph.vm ? ix->prop_graph : dev_graph(ix); }
+
 inline int num_sms()
 {
     static int v = 0;
@@ -481,7 +486,7 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s);
 dbl_status barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent, cudaStream_t s);
-void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)
+void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3, const int32_t *renum = nullptr);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)
 
 // insertion (dbl_insert.cu)
 dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);

@@ -40,17 +40,26 @@ __device__ __forceinline__ int flat_owner(uint32_t excl, uint32_t e)
 constexpr int kLocal = 32;
 constexpr int kLocalRounds = 8;
 
-__device__ __forceinline__ void enqueue_local(bool want, int32_t x, int dir, const DevGraph &g, const FrontierOut &f,
-                                              const Stage &st, FTask *wl, int &wl_n)
+// A changed neighbour x joins the next level (or the warp's local list) in
+// two halves, so that the memory operations of several edges (x's adjacency
+// metadata, its bit in the next level's bitmap) can be in flight together
+// before the warp-collective half runs: local_mark returns the number of x's
+// chunks when this call marked x (0 otherwise) ...
+__device__ __forceinline__ uint32_t local_mark(bool want, int32_t x, int dir, const DevGraph &g,
+                                               const FrontierOut &f, AdjRange &r)
+{
+    r = AdjRange{0, 0, 0, 0};
+    if (!want) return 0;
+    r = adj_of(g, dir, x);
+    const int32_t d = r.bd + r.od;
+    return mark_new(f, dir, x, d) ? (uint32_t)((d + kChunk - 1) / kChunk) : 0u;
+}
+
+// ... and local_put places the marked vertices (warp-collective).
+__device__ __forceinline__ void local_put(uint32_t nchunks, int32_t x, int dir, const AdjRange &r,
+                                          const FrontierOut &f, const Stage &st, FTask *wl, int &wl_n)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t nchunks = 0;
-    AdjRange r{0, 0, 0, 0};
-    if (want) {
-        r = adj_of(g, dir, x);
-        const int32_t d = r.bd + r.od;
-        if (mark_new(f, dir, x, d)) nchunks = (uint32_t)((d + kChunk - 1) / kChunk);
-    }
     const bool loc = nchunks == 1;
     const unsigned bl = __ballot_sync(kFull, loc);
     const int rank = __popc(bl & ((1u << lane) - 1u));
@@ -62,8 +71,11 @@ __device__ __forceinline__ void enqueue_local(bool want, int32_t x, int dir, con
 
 // One round of the flattened level: lane-held tasks (has, tk); their
 // vertices' bits are cleared in clear_mark (fence after the clear when the
-// bitmap is the one being filled: local tasks).
-template <int HS>
+// bitmap is the one being filled: local tasks).  The warp takes U x 32 edges
+// per step, and the column loads, then the neighbours' half-records, then
+// the ORs, then the marks of a step are issued together (U edges of each lane
+// in flight at each stage).
+template <int HS, int U>
 __device__ __forceinline__ void flat_round(const DevGraph &g, const RecView &rw, bool has, const FTask &tk,
                                            uint32_t *clear_mark, bool local, const FrontierOut &f, const Stage &st,
                                            FTask *wl, int &wl_n, unsigned long long &relaxed,
@@ -97,34 +109,52 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, const RecView &rw,
     }
     const uint32_t excl = incl - cnt;
     const uint32_t total = __shfl_sync(kFull, incl, 31);
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t e = base + lane;
-        const int owner = flat_owner(excl, e);
-        const int odir = __shfl_sync(kFull, dir, owner);
-        const int32_t ocol0 = __shfl_sync(kFull, col0, owner), oncol = __shfl_sync(kFull, ncol, owner);
-        const int32_t opool0 = __shfl_sync(kFull, pool0, owner);
-        const int32_t oe = (int32_t)(e - __shfl_sync(kFull, excl, owner));
-        uint64_t orv[HS];
+    for (uint32_t base = 0; base < total; base += 32u * U) {
+        int odir[U];
+        int32_t x[U];
+        bool ok[U], want[U];
+        uint64_t orv[U][HS], rx[U][HS];
 #pragma unroll
-        for (int i = 0; i < HS; ++i) orv[i] = __shfl_sync(kFull, rv[i], owner);
-        bool want = false;
-        int32_t x = 0;
-        if (e < total) {
-            x = task_edge(g, odir, ocol0, oncol, opool0, oe);
-            ++relaxed;
-            uint64_t *px = rec_half(rw, x, odir);
-            uint64_t rx[HS];
-            load_half<HS>(px, rx);
+        for (int k = 0; k < U; ++k) {
+            const uint32_t e = base + 32u * k + lane;
+            const int owner = flat_owner(excl, e);
+            odir[k] = __shfl_sync(kFull, dir, owner);
+            const int32_t ocol0 = __shfl_sync(kFull, col0, owner), oncol = __shfl_sync(kFull, ncol, owner);
+            const int32_t opool0 = __shfl_sync(kFull, pool0, owner);
+            const int32_t oe = (int32_t)(e - __shfl_sync(kFull, excl, owner));
+#pragma unroll
+            for (int i = 0; i < HS; ++i) orv[k][i] = __shfl_sync(kFull, rv[i], owner);
+            ok[k] = e < total;
+            x[k] = ok[k] ? task_edge(g, odir[k], ocol0, oncol, opool0, oe) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            if (ok[k]) load_half<HS>(rec_half(rw, x[k], odir[k]), rx[k]);
+            else {
+#pragma unroll
+                for (int i = 0; i < HS; ++i) rx[k][i] = ~0ull;  // nothing to add
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            want[k] = false;
+            relaxed += ok[k] ? 1 : 0;
+            uint64_t *px = rec_half(rw, x[k], odir[k]);
 #pragma unroll
             for (int i = 0; i < HS; ++i) {
-                if (orv[i] & ~rx[i]) {
-                    const unsigned long long old = atomicOr((unsigned long long *)(px + i), orv[i]);
-                    want |= (orv[i] & ~old) != 0;
+                if (orv[k][i] & ~rx[k][i]) {
+                    const unsigned long long old = atomicOr((unsigned long long *)(px + i), orv[k][i]);
+                    want[k] |= (orv[k][i] & ~old) != 0;
                 }
             }
-            if (want) mark_dirty(g.dirty, x);
+            if (want[k]) mark_dirty(g.dirty, x[k]);
         }
-        enqueue_local(want, x, odir, g, f, st, wl, wl_n);
+        uint32_t nch[U];
+        AdjRange r[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) nch[k] = local_mark(want[k], x[k], odir[k], g, f, r[k]);
+#pragma unroll
+        for (int k = 0; k < U; ++k) local_put(nch[k], x[k], odir[k], r[k], f, st, wl, wl_n);
     }
 }
 
@@ -134,7 +164,7 @@ __device__ __forceinline__ void flat_round(const DevGraph &g, const RecView &rw,
 // 32 at a time; each edge's task data come from the owner lane by shuffles.
 // A round costs ceil(edges of the warp's tasks / 32) iterations, whatever the
 // mix of task sizes.  Then the warp's local rounds (above).
-template <int HS>
+template <int HS, int U>
 __device__ __forceinline__ void expand_level_flat(const DevGraph &g, const RecView &rw, const FTask *tasks,
                                                   uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                                   unsigned long long *stats, int64_t warp, int64_t nwarps,
@@ -150,7 +180,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, const RecVi
         const int64_t t = warp + nwarps * (r0 + lane);
         const bool has = t < (int64_t)ntasks;
         const FTask tk = has ? load_ftask(tasks, t) : FTask{0, 0u, 0, 0};
-        flat_round<HS>(g, rw, has, tk, cur_mark, false, f, st, wl, wl_n, relaxed, ntask);
+        flat_round<HS, U>(g, rw, has, tk, cur_mark, false, f, st, wl, wl_n, relaxed, ntask);
     }
     for (int lr = 0; lr < kLocalRounds && wl_n > 0; ++lr) {
         __syncwarp();
@@ -158,7 +188,7 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, const RecVi
         const FTask tk = has ? wl[lane] : FTask{0, 0u, 0, 0};
         __syncwarp();
         wl_n = 0;
-        flat_round<HS>(g, rw, has, tk, f.mark, true, f, st, wl, wl_n, relaxed, ntask);
+        flat_round<HS, U>(g, rw, has, tk, f.mark, true, f, st, wl, wl_n, relaxed, ntask);
     }
     __syncwarp();
     {
@@ -178,14 +208,14 @@ __device__ __forceinline__ void expand_level_flat(const DevGraph &g, const RecVi
 //
 // New tasks go through the block's stage (stage_enqueue); the stage is flushed
 // at the end, so every thread of the block must call this.
-template <int HS, int TEAM>
+template <int HS, int TEAM, int U = 1>
 __device__ __forceinline__ void expand_level(const DevGraph &g, const RecView &rw, const FTask *tasks,
                                              uint32_t ntasks, uint32_t *cur_mark, const FrontierOut &f,
                                              unsigned long long *stats, int64_t warp0, int64_t nwarps,
                                              const Stage &st)
 {
     if constexpr (TEAM == 1) {
-        expand_level_flat<HS>(g, rw, tasks, ntasks, cur_mark, f, stats, warp0, nwarps, st);
+        expand_level_flat<HS, U>(g, rw, tasks, ntasks, cur_mark, f, stats, warp0, nwarps, st);
     } else {
         constexpr int TPW = 32 / TEAM;
         const int lane = threadIdx.x & 31;

@@ -19,13 +19,16 @@
 
 namespace dbl {
 
+// edges per lane in flight at each stage of a flattened level (team width 1)
+constexpr int kPropUnroll = 2;
+
 template <int HS, int TEAM>
 __global__ void __launch_bounds__(kBlock) k_expand(DevGraph g, RecView rw, const FTask *tasks,
                                                    const uint32_t *ntasks_p, uint32_t *cur_mark, FrontierOut f,
                                                    unsigned long long *stats)
 {
     DBL_BLOCK_STAGE(st);
-    expand_level<HS, TEAM>(g, rw, tasks, *ntasks_p, cur_mark, f, stats,
+    expand_level<HS, TEAM, kPropUnroll>(g, rw, tasks, *ntasks_p, cur_mark, f, stats,
                            ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                            ((int64_t)gridDim.x * blockDim.x) >> 5, st);
 }
@@ -41,7 +44,7 @@ static void launch_expand(dbl_index *ix, int cur, uint32_t ntasks, const Frontie
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_expand<HS, TEAM><<<(unsigned)blocks, kBlock, 0, s>>>(dev_graph(ix), rec_view(ix), ix->front[cur],
+    k_expand<HS, TEAM><<<(unsigned)blocks, kBlock, 0, s>>>(prop_graph(ix), rec_view(ix), ix->front[cur],
                                                            ix->d_counts + kCntFront0 + cur, mark_of(ix, cur), f,
                                                            ix->d_stats);
     ++ix->launches;
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(pblock_of(HS), 1)
         uint32_t *cur_mark = mark + (size_t)(L & 1) * 2 * (size_t)wpd;
         uint32_t *nxt_mark = mark + (size_t)((L + 1) & 1) * 2 * (size_t)wpd;
         FrontierOut f{(L & 1) ? f0 : f1, c3 + (L + 1) % 3, cap, nxt_mark, wpd, status};
-        expand_level<HS, TEAM>(g, rw, (L & 1) ? f1 : f0, nt, cur_mark, f, stats, warp0, nwarps, st);
+        expand_level<HS, TEAM, kPropUnroll>(g, rw, (L & 1) ? f1 : f0, nt, cur_mark, f, stats, warp0, nwarps, st);
         if (!gs.sync(status)) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -179,7 +182,7 @@ static dbl_status launch_persistent(dbl_index *ix, cudaStream_t s)
     if (blocks_per_sm < 0)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_propagate_persistent<HS, TEAM>, pblock_of(HS), 0);
     if (blocks_per_sm < 1) return fail(ix, DBL_ERR_CUDA, "persistent propagate: kernel does not fit on an SM");
-    DevGraph g = dev_graph(ix);
+    DevGraph g = prop_graph(ix);
     FTask *f0 = ix->front[0], *f1 = ix->front[1];
     uint32_t *c3 = ix->d_counts + kCntP0;
     int64_t cap = ix->front_cap;

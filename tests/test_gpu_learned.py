@@ -80,6 +80,51 @@ def test_select_by_score_ties_by_id(tiny):
     assert np.array_equal(got, exp)
 
 
+def _spread_reference(rp, col, sc, k):
+    """The greedy spread selection written out: k times, the untaken,
+    unexcluded vertex of largest score (smaller id on ties; -inf and NaN never),
+    then its in- and out-neighbours are excluded."""
+    n = rp.shape[0] - 1
+    ok = np.isfinite(sc) | (sc == np.inf)
+    order = np.lexsort((np.arange(n), -np.where(ok, sc, 0)))
+    order = order[ok[order]]
+    ins = [[] for _ in range(n)]
+    for u in range(n):
+        for x in col[rp[u]:rp[u + 1]]:
+            ins[x].append(u)
+    gone = np.zeros(n, bool)
+    out, pos = [], 0
+    while len(out) < k:
+        while pos < len(order) and gone[order[pos]]:
+            pos += 1
+        if pos == len(order):
+            out.append(-1)
+            continue
+        x = int(order[pos])
+        out.append(x)
+        gone[x] = True
+        gone[col[rp[x]:rp[x + 1]]] = True
+        gone[ins[x]] = True
+    return np.array(out, dtype=np.int32)
+
+
+def test_select_spread_matches_greedy(tiny):
+    rp, col = tiny["row_ptr"], tiny["col"]
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64)
+    rng = np.random.default_rng(6)
+    sc = rng.integers(-40, 40, ix.n).astype(np.float32) / 4   # ties
+    sc[rng.integers(0, ix.n, 500)] = -np.inf
+    sc[rng.integers(0, ix.n, 50)] = np.nan
+    got = ix.select_spread(D(sc), 60).cpu().numpy()
+    assert np.array_equal(got, _spread_reference(rp, col, sc, 60))
+    # fewer candidates than slots: the rest are -1
+    sc2 = np.full(ix.n, -np.inf, np.float32)
+    sc2[[5, 77, 1000]] = [1.0, 3.0, 2.0]
+    got2 = ix.select_spread(D(sc2), 6).cpu().numpy()
+    assert np.array_equal(got2, _spread_reference(rp, col, sc2, 6))
+    assert (got2[3:] == -1).all()
+
+
 def _quantised_params(seed):
     p = dbl.MLP.init_params(seed)
     p[2048:2176] = np.random.default_rng(seed).normal(0, 0.05, 128)     # non-zero biases

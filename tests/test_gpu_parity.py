@@ -473,6 +473,68 @@ def test_split_build_equals_joint_build(tiny, k, kp, flags):
     assert_labels(a, ref, "split build, after insertions")
 
 
+def _with_hubs(rp, col, n_hubs=3, seed=9):
+    """The graph plus n_hubs vertices joined to thousands of others in both
+    directions (rows above the ordering's block-per-row threshold of 1024)."""
+    n = rp.shape[0] - 1
+    rng = np.random.default_rng(seed)
+    src = np.repeat(np.arange(n), np.diff(rp)).astype(np.int64)
+    dst = col.astype(np.int64)
+    extra_s, extra_d = [src], [dst]
+    for h in rng.choice(n, n_hubs, replace=False):
+        outs = rng.choice(n, 3000, replace=False)
+        ins = rng.choice(n, 2000, replace=False)
+        extra_s += [np.full(3000, h), ins]
+        extra_d += [outs, np.full(2000, h)]
+    s_all, d_all = np.concatenate(extra_s), np.concatenate(extra_d)
+    keep = s_all != d_all
+    key = np.unique(s_all[keep] * n + d_all[keep])
+    s_all, d_all = key // n, key % n
+    rp2 = np.zeros(n + 1, np.int64)
+    np.add.at(rp2, s_all + 1, 1)
+    return np.cumsum(rp2).astype(np.int32), d_all.astype(np.int32)
+
+
+@pytest.mark.parametrize("k,kp", [(16, 16), (64, 64), (128, 64)])
+@pytest.mark.parametrize("split", [1, -1])
+@pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT])
+def test_degree_ordered_build_equals_oracle(tiny, k, kp, split, flags):
+    """The build over the degree-grouped renumbering of the graph
+    (dbl_options build_order = 1) stores the same least fixpoint (Algorithm 1)
+    as the oracle, with hub rows above and below the block-per-row threshold;
+    insertions and queries afterwards run on the index's own numbering."""
+    rp, col = _with_hubs(tiny["row_ptr"], tiny["col"])
+    ix = dbl.DBLIndex(D(rp), D(col), k, kp, flags=flags, build_split=split, build_order=1,
+                      vertex_capacity=rp.shape[0] + 100)
+    ref = oracle.OracleIndex(rp, col, k, kp).build()
+    assert_labels(ix, ref, f"ordered build k={k} k'={kp} split={split}")
+    ix.insert_edges(D(tiny["ins_src"]), D(tiny["ins_dst"]))
+    ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
+    ix.sync()
+    assert_labels(ix, ref, "ordered build, after insertions")
+    assert_queries(ix, ref, tiny["q_u"][:20000], tiny["q_v"][:20000], "ordered build, queries")
+
+
+@pytest.mark.parametrize("n,m", [(1, 0), (5, 0), (1500, 0), (3000, 9000)])
+def test_degree_ordered_build_small_and_edgeless(n, m):
+    """Degenerate graphs under the ordered build: one vertex, no edges, one
+    ordering tile with a ragged tail."""
+    rng = np.random.default_rng(n + m)
+    if m:
+        s = rng.integers(0, n, m)
+        d = rng.integers(0, n, m)
+        key = np.unique(s[s != d] * n + d[s != d])
+        s, d = key // n, key % n
+    else:
+        s = d = np.zeros(0, np.int64)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, s + 1, 1)
+    rp, col = np.cumsum(rp).astype(np.int32), d.astype(np.int32)
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64, build_order=1, build_split=1)
+    ref = oracle.OracleIndex(rp, col, 64, 64).build()
+    assert_labels(ix, ref, f"ordered build n={n} m={m}")
+
+
 def test_deferred_insertions_apply_as_one_group(tiny):
     """DBL_FLAG_DEFER: insertion batches queue on the host and the next call
     that reads the index applies them in one launch.  A query sees exactly
