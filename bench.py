@@ -699,11 +699,16 @@ def train_learned(args, w, I, k, kp, batches, dev):
     for a, b in batches:
         plain_ix.insert_edges(I.src[a:b], I.dst[a:b])
     base_slots = max(1, k // 8)
-    scores, tinfo = L.train_scorer(plain_ix, tu, tv, base_slots, steps=args.train_steps)
-    lm = L.select_landmarks(plain_ix, scores, k, base_slots)
+    if args.learn_rounds > 1:
+        lm, tinfo = L.select_in_rounds(plain_ix, I.rp, I.col, (tu, tv), k, kp, base_slots, args.learn_rounds,
+                                       idx_kw={"edge_capacity": max(E, 1 << 20)},
+                                       inserts=[(I.src[a:b], I.dst[a:b]) for a, b in batches], steps=args.train_steps)
+    else:
+        scores, tinfo = L.train_scorer(plain_ix, tu, tv, base_slots, steps=args.train_steps)
+        lm = L.select_landmarks(plain_ix, scores, k, base_slots)
     _, lb, lr_ = plain_ix.selection()
     torch.cuda.synchronize()
-    info = {"train_s": time.perf_counter() - t0, "base_slots": base_slots,
+    info = {"train_s": time.perf_counter() - t0, "base_slots": base_slots, "rounds": args.learn_rounds,
             **{kk: v for kk, v in tinfo.items() if kk != "losses"}, "final_loss": tinfo["losses"][-1]}
     return lm, (lb, lr_), info, plain_ix
 
@@ -772,6 +777,67 @@ def bench_extras(args, world, tdist, local, dev):
         cfg[name] = public(r)
     cfg["graph_vs_plain"] = cfg["graph"]["value"] / cfg["plain"]["value"]
     out["batched_config"] = cfg
+    return out
+
+
+def learned_gain_community(args, dev, reps=10):
+    """What the learned landmarks gain on a graph with several strongly
+    connected parts of real size (R-MAT gives none: section 8 of the notes):
+    128 R-MAT communities of power-law sizes (community c holds a share
+    proportional to 1/(c+1)) joined by 2% of the edges, always from an earlier
+    to a later community (dbl_inputs.community_dag), n = 500,000, m = 5M.
+    Degree landmarks against the learned selection in 7 rounds (k = k' = 64),
+    trained on the outcomes of 100k sampled queries and judged on 100k
+    others; then 1M further queries (label test + search, persistent kernels)
+    are timed with each landmark set (CUDA events, mean of `reps`)."""
+    import torch
+
+    import dbl_inputs
+    import paper_2101_09441_gb300 as dbl
+    from paper_2101_09441_gb300 import learned as L
+    t0 = time.perf_counter()
+    n, m, comm = 500_000, 5_000_000, 128
+    rp, col = dbl_inputs.community_dag(n, m, comm, 1.0, 0.02, 21)
+    qu, qv = dbl_inputs.queries(rp, col, 1_200_000, 22, False)
+
+    def dev_t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    tq = (dev_t(qu[:100_000]), dev_t(qv[:100_000]))
+    ev = (dev_t(qu[100_000:200_000]), dev_t(qv[100_000:200_000]))
+    tu, tv = dev_t(qu[200_000:]), dev_t(qv[200_000:])
+    flags = dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | (dbl.FLAG_FINE_L2 if args.fine_l2 else 0)
+    plain, chosen, learned, info = L.learned_index(dev_t(rp), dev_t(col), tq, ev, k=64, kprime=64, rounds=7,
+                                                   steps=args.train_steps, flags=flags)
+    out = {"graph": "community_dag", "n": n, "m": int(col.shape[0]), "communities": comm, "alpha": 1.0,
+           "cross": 0.02, "k": 64, "kprime": 64, "rounds": 7, "timed_queries": int(tu.numel()),
+           "setup_s": time.perf_counter() - t0, "judge_keeps_learned": not info["fallback"],
+           "judge_pairs": {"degree": info["eval_plain"], "learned": info["eval_learned"]}}
+    ans = torch.empty(tu.numel(), dtype=torch.uint8, device=dev)
+    code = torch.empty_like(ans)
+    ref = None
+    for name, ix in (("degree", plain), ("learned", learned)):
+        for _ in range(3):
+            ix.query(tu, tv, out=(ans, code))
+        ix.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ix.query(tu, tv, out=(ans, code))
+        e1.record()
+        ix.sync()
+        ms = e0.elapsed_time(e1) / reps
+        c = code.long()
+        out[name] = {"ms_per_batch": ms, "queries_per_s": tu.numel() / (ms * 1e-3),
+                     "decided_by_dl": int((c == dbl.CODE_DL).sum()),
+                     "searched": int(((c == dbl.CODE_BFS_POS) | (c == dbl.CODE_BFS_NEG)).sum())}
+        if ref is None:
+            ref = ans.clone()
+        else:
+            out["same_answers"] = bool(torch.equal(ref, ans))
+    out["queries_per_s_ratio"] = out["learned"]["queries_per_s"] / out["degree"]["queries_per_s"]
+    plain.close()
+    learned.close()
     return out
 
 
@@ -878,6 +944,7 @@ def bench_gpu(args):
     ix.close()
 
     extras = None if args.no_extras else bench_extras(args, *common, dev)
+    gain_comm = None if args.no_extras or rank != 0 else learned_gain_community(args, dev)
 
     gain_k = gain(ref_form, learned) if ref_form else None
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": S,
@@ -895,6 +962,7 @@ def bench_gpu(args):
             "learned": {"fallback_to_degree_rule": bool(fallback), **linfo},
             "learned_gain": {f"k{k}": gain_k,
                              **({f"k{k2}": gain(k2_forms["graph"], k2_forms["learned"])} if k2 else {})},
+            "learned_gain_community": gain_comm,
             f"forms_k{k2}": {kk: (public(v) if isinstance(v, dict) else v) for kk, v in k2_forms.items()
                              if kk != "serving"} if k2 else None,
             "restore": {"ms": head["restore_ms"], "share_of_step": head["restore_ms"] / head["ms_per_step"],
@@ -1201,6 +1269,8 @@ def main():
                     help="comparison forms to time besides the headline")
     ap.add_argument("--train-queries", type=int, default=1_000_000)
     ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--learn-rounds", type=int, default=1,
+                    help="learned selection in rounds (the index rebuilt with the picks so far before each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-insertions", type=int, default=100_000, help="oracle sample: insertions per step")
     ap.add_argument("--ref-queries", type=int, default=1_000_000, help="oracle sample: queries per step")

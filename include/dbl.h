@@ -135,8 +135,9 @@ typedef struct {
                               4); 0: 2 for 32-byte records, 4 for wider ones */
     int32_t search_first_log2; /* a search wave first hashes its states into
                               the first 2^x slots of its table (clamped to the
-                              table); a lone 64-query group that overflows them
-                              is rerun over the whole table; 0: 22 */
+                              table); a wave that overflows them is rerun over
+                              the whole table, and one that overflows the whole
+                              table is rerun in halves; 0: 22 */
     int32_t landmark_rule; /* ranking of the landmarks chosen when dbl_build gets
                               none (Section 6, Table 3): 0 = |Pre(u)| * |Suc(u)|
                               (Section 4.1), 1 = max(|Pre|, |Suc|) (A),
@@ -170,7 +171,11 @@ typedef struct {
                               records exceed 256 MB.  Same labels either way.
                               Costs a copy of the graph (8 B per edge, 40 B per
                               vertex) during the build */
-    int32_t reserved;
+    int32_t search_table_log2; /* 32-byte search states per query context:
+                              2^x (a lone 64-query group whose search needs
+                              more fails with DBL_ERR_CAPACITY); 0: the larger of
+                              2n and min(64n, 2^24), rounded up to a power of
+                              two (n: the vertex capacity) */
 } dbl_options;
 
 /* Fill *opt with the defaults above. */
@@ -484,6 +489,16 @@ dbl_status dbl_select_by_score(dbl_index *ix, const float *scores, int32_t k, in
  * them decides what all would; neighbours of a chosen vertex share its
  * component far more often than other vertices.) */
 dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream);
+/* out[k]: the greedy selection of dbl_select_spread (spread != 0) or by score
+ * alone (spread == 0; ties by smaller id, -1 for slots left empty), taking
+ * no vertex of the strongly connected component of one of the index's first
+ * covered_slots landmarks, i.e. no vertex whose DL_in and DL_out share one of
+ * those landmarks' bits (Section 4.1's DL labels): every pair such a vertex
+ * connects, that landmark connects too (u -> x -> landmark -> x -> v), so as a
+ * landmark it would decide nothing more.  Applies insertion batches queued
+ * under DBL_FLAG_DEFER first.  Synchronous. */
+dbl_status dbl_select_uncovered(dbl_index *ix, const float *scores, int32_t k, int32_t covered_slots, int32_t spread,
+                                int32_t *out, void *stream);
 
 /* Network with initial parameters params_host[DBL_MLP_PARAMS] (host fp32).
  * Weights are kept in fp32 with bf16 copies for the tensor-core kernels. */

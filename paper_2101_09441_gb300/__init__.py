@@ -38,7 +38,7 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
            "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule", "dbl_barrier_probe",
-           "dbl_server_cancel", "dbl_select_spread"]
+           "dbl_server_cancel", "dbl_select_spread", "dbl_select_uncovered"]
 MLP_PARAMS = 18817
 
 
@@ -63,7 +63,7 @@ class _Options(ctypes.Structure):
                 ("team", ctypes.c_int32), ("query_unroll", ctypes.c_int32), ("search_first_log2", ctypes.c_int32),
                 ("landmark_rule", ctypes.c_int32), ("leaf_r", ctypes.c_int64), ("vertex_capacity", ctypes.c_int64),
                 ("initial_slots", ctypes.c_int32), ("build_split", ctypes.c_int32), ("build_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("search_table_log2", ctypes.c_int32)]
 
 
 class _Graph(ctypes.Structure):
@@ -137,6 +137,7 @@ def lib():
             L.dbl_coverage.argtypes = [P, P, P, P, i64, i32, P, P, P, P]
             L.dbl_select_by_score.argtypes = [P, P, i32, P, P]
             L.dbl_select_spread.argtypes = [P, P, i32, P, P]
+            L.dbl_select_uncovered.argtypes = [P, P, i32, i32, i32, P, P]
             L.dbl_mlp_create.argtypes = [P, P, P]
             L.dbl_mlp_destroy.argtypes = [P, P]
             L.dbl_mlp_destroy.restype = None
@@ -177,7 +178,7 @@ class DBLIndex:
                  leaf_roles=None, edge_capacity: int = 0, flags: int = 0, team: int = 0, stream=None,
                  torch_allocator: bool = True, query_unroll: int = 0, search_first_log2: int = 0,
                  landmark_rule: str = "M", leaf_r: int = 0, vertex_capacity: int = 0, initial_slots: int = 0,
-                 build_split: int = 0, build_order: int = 0):
+                 build_split: int = 0, build_order: int = 0, search_table_log2: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DBLIndex needs a CUDA device")
@@ -202,6 +203,7 @@ class DBLIndex:
         opt.initial_slots = int(initial_slots)
         opt.build_split = int(build_split)
         opt.build_order = int(build_order)
+        opt.search_table_log2 = int(search_table_log2)
         self._refuse = [0, 0]  # allocations to let through, then to refuse (fail_allocations)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
@@ -458,6 +460,18 @@ class DBLIndex:
         scores = scores.to(torch.float32).contiguous()
         out = torch.empty(int(k), dtype=torch.int32, device=self.device)
         self._check(lib().dbl_select_by_score(self._h, _ptr(scores), int(k), _ptr(out), self._s(stream)))
+        return out
+
+    def select_uncovered(self, scores, k: int, covered_slots: int, spread: bool = False, stream=None):
+        """dbl_select_uncovered: k vertices by score (spread: excluding the
+        neighbours of earlier picks), none in the strongly connected component
+        of one of the first covered_slots landmarks; int32 [k] (-1 for slots
+        left empty)."""
+        import torch
+        scores = scores.to(torch.float32).contiguous()
+        out = torch.empty(int(k), dtype=torch.int32, device=self.device)
+        self._check(lib().dbl_select_uncovered(self._h, _ptr(scores), int(k), int(covered_slots), int(bool(spread)),
+                                               _ptr(out), self._s(stream)))
         return out
 
     def select_spread(self, scores, k: int, stream=None):

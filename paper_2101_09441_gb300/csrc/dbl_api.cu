@@ -216,7 +216,7 @@ dbl_status ensure_search_scratch(dbl_qctx *c, int64_t q, cudaStream_t s)
         c->und_cap = cap;
     }
     if (!c->table) {
-        int64_t slots = pow2_at_least(std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n_cap));
+        const int64_t slots = search_table_slots(ix);
         // all or nothing: a failure frees what was taken, so the next call starts over
         auto undo = [&](dbl_status err) {
             for (void **p : {(void **)&c->table, (void **)&c->claimed, (void **)&c->slot_list[0],

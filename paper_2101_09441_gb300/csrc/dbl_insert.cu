@@ -324,6 +324,9 @@ __device__ __forceinline__ VAdj vadj_of_words(uint64_t lo, uint64_t hi)
     return VAdj{(int32_t)(uint32_t)lo, (uint32_t)(lo >> 32), (int32_t)(uint32_t)hi, (int32_t)(uint32_t)(hi >> 32)};
 }
 
+// edges per lane in flight at each stage of the repair's flattened levels
+constexpr int kInsUnroll = 1;
+
 template <int HS, int WD, int TEAM>
 __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, const Stage &st, int64_t max_levels)
 {
@@ -557,8 +560,8 @@ __device__ __forceinline__ void insert_phases(const InsArgs &a, GridSync &gs, co
         uint32_t *cur_mark = a.mark + (size_t)(L & 1) * 2 * (size_t)a.wpd;
         uint32_t *nxt_mark = a.mark + (size_t)((L + 1) & 1) * 2 * (size_t)a.wpd;
         FrontierOut f{(L & 1) ? a.f0 : a.f1, a.c3 + (L + 1) % 3, a.cap, nxt_mark, a.wpd, a.status};
-        expand_level<HS, TEAM>(a.g, RecView{a.rec, 2 * HS, HS}, (L & 1) ? a.f1 : a.f0, ntk, cur_mark, f, a.stats,
-                               warp0, nwarps, st);
+        expand_level<HS, TEAM, kInsUnroll>(a.g, RecView{a.rec, 2 * HS, HS}, (L & 1) ? a.f1 : a.f0, ntk, cur_mark, f,
+                                           a.stats, warp0, nwarps, st);
         if (!gs.sync(a.status)) break;
     }
     if (leader) a.stats[8] += (unsigned long long)L;

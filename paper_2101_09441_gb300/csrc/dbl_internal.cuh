@@ -457,6 +457,19 @@ inline DevGraph dev_graph(const dbl_index *ix)
 
 inline DevGraph prop_graph(const dbl_index *ix) { return ix->prop_graph.vm ? ix->prop_graph : dev_graph(ix); }
 
+// Search states per query context (dbl_options.search_table_log2): at least
+// 2n (so one 64-query group always fits), and room for several large searches
+// at once on small graphs.
+inline int64_t search_table_slots(const dbl_index *ix)
+{
+    if (ix->opt.search_table_log2 > 0) return 1ll << std::min(ix->opt.search_table_log2, 34);
+    const int64_t n = ix->n_cap;
+    const int64_t want = std::max<int64_t>(std::max<int64_t>(1 << 16, 2 * n), std::min<int64_t>(64 * n, 1ll << 24));
+    int64_t p = 1;
+    while (p < want) p <<= 1;
+    return p;
+}
+
 inline int num_sms()
 {
     static int v = 0;

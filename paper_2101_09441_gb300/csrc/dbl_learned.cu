@@ -751,7 +751,8 @@ __global__ void k_spread_max(const unsigned long long *keys, int32_t n, unsigned
     if ((threadIdx.x & 31) == 0 && m) atomicMax(best, m);
 }
 
-__global__ void k_spread_take(DevGraph g, unsigned long long *keys, unsigned long long *best, int32_t *out, int32_t i)
+__global__ void k_spread_take(DevGraph g, unsigned long long *keys, unsigned long long *best, int32_t *out, int32_t i,
+                              int spread)
 {
     const unsigned long long b = *best;
     __syncthreads();
@@ -765,9 +766,28 @@ __global__ void k_spread_take(DevGraph g, unsigned long long *keys, unsigned lon
         out[i] = x;
         keys[x] = 0;
     }
+    if (!spread) return;
     for (int dir = 0; dir < 2; ++dir) {
         const AdjRange r = adj_of(g, dir, x);
         for (int32_t e = threadIdx.x; e < r.bd + r.od; e += blockDim.x) keys[adj_at(g, dir, r, e)] = 0;
+    }
+}
+
+// A vertex in the strongly connected component of one of the index's first
+// `slots` landmarks (its DL_in and DL_out share that landmark's bit) is never
+// taken: every pair it connects, the landmark connects too.
+__global__ void k_drop_covered(const uint64_t *rec, int32_t hs, int32_t wd, int32_t slots, int32_t n,
+                               unsigned long long *keys)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *p = rec + (size_t)i * 2 * hs;
+        bool cov = false;
+        for (int w = 0; w < wd && w * 64 < slots; ++w) {
+            const int rem = slots - w * 64;
+            const uint64_t mask = rem >= 64 ? ~0ull : ((1ull << rem) - 1);
+            cov |= (p[w] & p[hs + w] & mask) != 0;
+        }
+        if (cov) keys[i] = 0;
     }
 }
 
@@ -973,10 +993,11 @@ dbl_status dbl_coverage(dbl_index *ix, const int32_t *u, const int32_t *v, const
     return read_status(ix, s);
 }
 
-dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream)
+// Greedy selection over the score keys: k times the largest remaining key,
+// then (spread) its neighbours excluded.
+static dbl_status select_greedy(dbl_index *ix, const float *scores, int32_t k, int32_t covered_slots, int spread,
+                                int32_t *out, cudaStream_t s)
 {
-    if (!ix || !scores || !out || k <= 0) return dbl::fail(ix, DBL_ERR_INVALID, "select_spread: bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *keys = nullptr;
     dbl_status st = alloc_buf(ix, (void **)&keys, sizeof(unsigned long long) * ((size_t)ix->n + 1), s);
     if (st) return st;
@@ -984,16 +1005,37 @@ dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int3
     cudaMemsetAsync(best, 0, sizeof(unsigned long long), s);
     k_spread_keys<<<grid_cap(ix->n, kBlock), kBlock, 0, s>>>(scores, ix->n, keys);
     ++ix->launches;
+    if (covered_slots > 0) {
+        k_drop_covered<<<grid_cap(ix->n, kBlock), kBlock, 0, s>>>(ix->rec, ix->hs, ix->wd,
+                                                                  std::min<int32_t>(covered_slots, ix->k), ix->n, keys);
+        ++ix->launches;
+    }
     const DevGraph g = dev_graph(ix);
     for (int32_t i = 0; i < k; ++i) {
         k_spread_max<<<grid_cap(ix->n, kBlock), kBlock, 0, s>>>(keys, ix->n, best);
-        k_spread_take<<<1, kBlock, 0, s>>>(g, keys, best, out, i);
+        k_spread_take<<<1, kBlock, 0, s>>>(g, keys, best, out, i, spread);
         ix->launches += 2;
     }
     free_buf(ix, keys, s);
     cudaError_t e = cudaGetLastError();
-    if (e) return cuda_fail(ix, e, "select_spread");
+    if (e) return cuda_fail(ix, e, "select");
     return read_status(ix, s);
+}
+
+dbl_status dbl_select_spread(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream)
+{
+    if (!ix || !scores || !out || k <= 0) return dbl::fail(ix, DBL_ERR_INVALID, "select_spread: bad arguments");
+    return select_greedy(ix, scores, k, 0, 1, out, (cudaStream_t)stream);
+}
+
+dbl_status dbl_select_uncovered(dbl_index *ix, const float *scores, int32_t k, int32_t covered_slots, int32_t spread,
+                                int32_t *out, void *stream)
+{
+    if (!ix || !scores || !out || k <= 0 || covered_slots < 0)
+        return dbl::fail(ix, DBL_ERR_INVALID, "select_uncovered: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dbl_status fs = flush_insertions(ix, s)) return fs;  // the labels it reads include queued batches
+    return select_greedy(ix, scores, k, covered_slots, spread ? 1 : 0, out, s);
 }
 
 dbl_status dbl_select_by_score(dbl_index *ix, const float *scores, int32_t k, int32_t *out, void *stream)

@@ -17,9 +17,10 @@
 // y == v_j marks j found; otherwise j is pruned at y if DL_out(u_j) meets
 // DL_in(y) or y fails BL_Contain(y, v_j) (Algorithm 2's two prunes, in its
 // order); the rest are OR-ed into y's visit bits, and bits new there are
-// pending for the next level.  All groups of a batch run in one wave; if the
-// table or task list overflows, the wave's found answers are kept and the
-// groups are rerun in halves.
+// pending for the next level.  All groups of a batch run in one wave, first
+// in a slice of the table; if that overflows, the wave's found answers are
+// kept and the rest rerun over the whole table, and if that overflows too,
+// in halves.
 #include "dbl_frontier.cuh"
 #include "dbl_internal.cuh"
 #include "dbl_kernels.cuh"
@@ -327,9 +328,8 @@ struct PersistState {
 
 // A wave first hashes its (group, vertex) states into the first kFirstSlots
 // slots of the table (128 MB of slots: the pages stay in the address
-// translation caches; dbl_options.search_first_log2 changes it); a single
-// group that overflows them is rerun over the whole table, which always holds
-// one group.
+// translation caches; dbl_options.search_first_log2 changes it); a wave that
+// overflows them is rerun over the whole table, which always holds one group.
 constexpr int64_t kFirstSlots = 1ll << 22;
 
 constexpr int kMaxProbe = 2048;
@@ -844,7 +844,9 @@ __global__ void k_search_clear(SearchArgs a) { search_clear(a); }
 // All waves and levels of one query batch in one cooperative launch.  Block 0
 // keeps a stack of query ranges (an overflowing wave is split in halves) and
 // the phase counters; every decision is read by all blocks after a barrier.
-// Per level: finalize, barrier, expand, barrier.
+// Per level: finalize, barrier, expand, barrier.  An overflowing wave over
+// the first slots is rerun over the whole table, one over the whole table in
+// halves.
 template <int WD, int WB, int TEAM>
 __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *ps, const uint32_t *n_und,
                                              GridSync &gs, uint32_t *status, int64_t max_levels, const IStage &cst,
@@ -912,7 +914,7 @@ __device__ __forceinline__ void search_waves(const SearchArgs &a, PersistState *
         if (!gs.sync(status)) return;
         if (over && leader) {
             const long long groups = (j1 - j0 + 63) / 64;
-            if (groups <= 1 && !whole && ps->top < 64) {
+            if (!whole && a.first_mask < a.c.slot_mask && ps->top < 64) {
                 ps->stack[ps->top][0] = j0;  // rerun over the whole table
                 ps->stack[ps->top][1] = j1;
                 ps->stack[ps->top][2] = 1;
@@ -1156,8 +1158,10 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
     }
     const int64_t U = h[0];
     if (!U) return DBL_OK;
-    // waves: all groups at once; on overflow rerun the unanswered in halves
-    // (a lone group that overflows the first kFirstSlots slots reruns over the whole table)
+    // waves: all groups at once in the first slots; on overflow the
+    // unanswered rerun over the whole table, then in halves
+    const int64_t first_slots = std::min<int64_t>(
+        c->table_slots, ix->opt.search_first_log2 > 0 ? (1ll << std::min(ix->opt.search_first_log2, 40)) : kFirstSlots);
     struct Range {
         int64_t j0, j1;
         bool whole;
@@ -1171,7 +1175,7 @@ static dbl_status query_t(dbl_index *ix, dbl_qctx *c, const int32_t *u, const in
         if (st) return st;
         if (over) {
             const int64_t groups = (r.j1 - r.j0 + 63) / 64;
-            if (groups <= 1 && !r.whole) {
+            if (!r.whole && first_slots < c->table_slots) {
                 stack.push_back({r.j0, r.j1, true});
                 continue;
             }

@@ -279,11 +279,10 @@ dbl_status dbl_server_create(dbl_index *ix, const dbl_server_options *opt, dbl_s
         o.max_memory < 0)
         return dbl::fail(ix, DBL_ERR_INVALID, "server: bad options");
     if (ix->opt.flags & DBL_FLAG_ASYNC) return dbl::fail(ix, DBL_ERR_INVALID, "server: index must not be ASYNC");
-    // admission by free HBM: each slot needs its search scratch (a 32-byte slot
-    // per 2n vertices, lists, tasks) plus staging for max_batch pairs
+    // admission by free HBM: each slot needs its search scratch (the state
+    // table, lists, tasks) plus staging for max_batch pairs
     const int64_t W = 1 + ix->wd + 2 * ix->wb;
-    int64_t table = 1;
-    while (table < std::max<int64_t>(1 << 16, 2 * (int64_t)ix->n_cap)) table <<= 1;
+    const int64_t table = dbl::search_table_slots(ix);
     const int64_t per_slot = table * (32 + 12) + ((int64_t)ix->n_cap + (ix->m + ix->edge_cap) / dbl::kChunk) * 24 +
                              o.max_batch * (int64_t)(4 + 8 * W + 9 + 1) + (64 << 20);
     size_t free_b = 0, total_b = 0;

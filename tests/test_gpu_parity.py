@@ -741,11 +741,14 @@ def test_phase_trace_and_schedule(tiny):
 
 
 @pytest.mark.parametrize("flags", [0, dbl.FLAG_PERSISTENT])
-def test_search_overflow_reruns(tiny, flags):
+@pytest.mark.parametrize("table_log2", [0, 13])
+def test_search_overflow_reruns(tiny, flags, table_log2):
     """A tiny first-attempt slice of the search table (2^6 slots) makes the
-    waves overflow: they split in halves and lone groups rerun over the whole
-    table; every answer and code still equals the oracle's."""
-    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=flags, search_first_log2=6)
+    waves overflow: they rerun over the whole table, and with a small table
+    (2^13 states) split in halves there too; every answer and code still
+    equals the oracle's."""
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=flags, search_first_log2=6,
+                      search_table_log2=table_log2)
     ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
     ix.insert_edges(D(tiny["ins_src"]), D(tiny["ins_dst"]))
     ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
