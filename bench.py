@@ -49,15 +49,20 @@ UNIT = "ops/s (queries + inserted edges)"
 
 # DRAM traffic per launch from an ncu capture, valid only while the kernel's
 # source is unchanged: {kernel class: (bytes per launch, sha1[:12] of the source file)}.
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (1_151_473_000 + 21_907_712, "8f9253b6c870"),
-                                             "propagate": (54_288_640 + 2_143_744, "141b26251e5d")}
+# query_label: 10M pairs on the 2^24-vertex graph (k = k' = 64, 32-byte L2
+# fetch); propagate_grouped: one insertion launch of the workload's 1M edges;
+# propagate_batch: one of 100,000 (bench.py --kernel-case label / insert).
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (636_669_696 + 19_135_488, "cb03f11777b9"),
+                                             "propagate_grouped": (305_026_048 + 178_522_112, "7c87303a08ac"),
+                                             "propagate_batch": (22_414_592 + 5_921_792, "7c87303a08ac")}
 # Source a traffic figure was measured on: the kernel's own region of its file
 # (None: the whole file) and the headers that file includes; an edit anywhere
 # else does not invalidate the figure, any edit there does.
 KERNEL_SOURCE = {
     "query_label": ("dbl_query.cu", "// ------------------------------------------------------------ label test",
                     "// The undecided pairs of a batch, from the answer array"),
-    "propagate": ("dbl_insert.cu", None, None),
+    "propagate_grouped": ("dbl_insert.cu", None, None),
+    "propagate_batch": ("dbl_insert.cu", None, None),
 }
 KERNEL_HEADERS = ("dbl_frontier.cuh", "dbl_internal.cuh", "dbl_kernels.cuh", "dbl_persistent.cuh")
 
@@ -658,7 +663,8 @@ def roofline(form, ix, steps, w, I, batches, persistent=True, group=False):
 
     def obj(kk):
         ach = kern[kk]["achieved_gbs"]
-        traffic = NCU_TRAFFIC[kk][0] if kk in NCU_TRAFFIC and NCU_TRAFFIC[kk][1] == source_sha(kk) else None
+        tk = kk if kk != "propagate" else ("propagate_grouped" if group else "propagate_batch")
+        traffic = NCU_TRAFFIC[tk][0] if tk in NCU_TRAFFIC and NCU_TRAFFIC[tk][1] == source_sha(tk) else None
         return {"kernel": kk, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": f"hbm_gbs of {src}",
                 "algorithmic_bytes_per_launch": kern[kk]["algorithmic_bytes_per_launch"],
@@ -1234,7 +1240,8 @@ def bench_kernel_case(args):
     flags = dbl.FLAG_PERSISTENT | dbl.FLAG_TIMING | (dbl.FLAG_FINE_L2 if args.fine_l2 else 0)
     if args.kernel_case == "insert":
         flags |= dbl.FLAG_ASYNC | (dbl.FLAG_DEFER if args.defer else 0)
-    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, edge_capacity=max(E, 1 << 20), flags=flags)
+    ix = dbl.DBLIndex(rp, col, args.k, args.kprime, edge_capacity=max(E, 1 << 20), flags=flags,
+                      build_order=args.build_order)
     ix.sync()
     ix.timings()
     for a, b in step_batches(E, args.batch):
@@ -1287,6 +1294,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="label width / leaf threshold sweep instead of the step")
     ap.add_argument("--kernel-case", choices=["label", "insert", "scorer"], default=None,
                     help="a small single-index run of one kernel (for an ncu capture) instead of the step")
+    ap.add_argument("--build-order", type=int, default=0,
+                    help="kernel cases: dbl_options.build_order (1 renumbered build, -1 id order, 0 by size)")
     ap.add_argument("--defer", action="store_true",
                     help="kernel case insert: queue the batches and apply them as one group (DBL_FLAG_DEFER)")
     ap.add_argument("--fine-l2", action=argparse.BooleanOptionalAction, default=True,

@@ -55,7 +55,8 @@ typedef enum {
     DBL_ERR_CAPACITY = 5, /* inserted-edge capacity exhausted; nothing changed */
     DBL_ERR_BUSY = 6,     /* the serving engine refused admission */
     DBL_ERR_POISONED = 7, /* an earlier timeout poisoned the index */
-    DBL_ERR_CANCELLED = 8 /* the serving engine dropped the request before it ran */
+    DBL_ERR_CANCELLED = 8, /* the serving engine dropped the request before it ran */
+    DBL_ERR_IO = 9         /* a file could not be written or read (dbl_save, dbl_load) */
 } dbl_status;
 
 /* Deciding rule of a query, in the order of Algorithm 2. */
@@ -525,6 +526,25 @@ dbl_status dbl_mlp_train_step(dbl_mlp *m, const uint16_t *X, const float *target
  * gave up a bounded wait since it was created (its outputs are invalid). */
 dbl_status dbl_mlp_sync(dbl_mlp *m, void *stream);
 const char *dbl_mlp_last_error(const dbl_mlp *m);
+
+/* Write the index to the file at `path` (created or truncated): its base
+ * graph, landmark and leaf choices, labels (Definitions 1-2), per-vertex
+ * adjacency metadata and the used part of the inserted-edge pools, the vertex
+ * count and the stored-edge count; insertion batches queued under
+ * DBL_FLAG_DEFER are applied first.  Snapshots are not written.  The file's
+ * size is about the device memory the index uses minus its frontier and
+ * scratch buffers.  Synchronous.  DBL_ERR_IO if the file cannot be written
+ * (the index is unchanged either way); DBL_ERR_POISONED for a poisoned index. */
+dbl_status dbl_save(dbl_index *ix, const char *path, void *stream);
+
+/* Read an index written by dbl_save into a new index on the current device.
+ * `opt` (NULL: defaults) supplies the allocator, flags, team and query
+ * options; the capacities (edge_capacity, vertex_capacity, initial_slots)
+ * are the saved index's.  The loaded index answers every query and takes
+ * every later insertion exactly as the saved one would.  Synchronous.
+ * DBL_ERR_IO if the file is missing, short, of another format version or
+ * inconsistent; DBL_ERR_OOM as dbl_build. */
+dbl_status dbl_load(const char *path, const dbl_options *opt, void *stream, dbl_index **out);
 
 /* Message of the last error on this index (or of the last failed build when
  * ix is NULL).  Valid until the next call on the index. */

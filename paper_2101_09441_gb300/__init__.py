@@ -19,8 +19,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libdbl.so")
 
 DBL_OK, DBL_ERR_INVALID, DBL_ERR_OOM, DBL_ERR_CUDA, DBL_ERR_TIMEOUT, DBL_ERR_CAPACITY, DBL_ERR_BUSY, \
-    DBL_ERR_POISONED, DBL_ERR_CANCELLED = range(9)
-STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned", "cancelled"]
+    DBL_ERR_POISONED, DBL_ERR_CANCELLED, DBL_ERR_IO = range(10)
+STATUS_NAMES = ["ok", "invalid", "oom", "cuda", "timeout", "capacity", "busy", "poisoned", "cancelled", "io"]
 CODE_UNDECIDED, CODE_SELF, CODE_DL, CODE_BL, CODE_THM1, CODE_THM2, CODE_BFS_POS, CODE_BFS_NEG = range(8)
 FLAG_ASYNC, FLAG_PERSISTENT, FLAG_TIMING, FLAG_FINE_L2, FLAG_DEFER = 1, 2, 4, 8, 16
 # landmark rankings of dbl_options.landmark_rule: M = |Pre|*|Suc| (Section 4.1), and Table 3's
@@ -38,7 +38,7 @@ EXPORTS = ["dbl_default_options", "dbl_build", "dbl_insert_edges", "dbl_query", 
            "dbl_qctx_create", "dbl_qctx_destroy", "dbl_query_ctx", "dbl_qctx_last_error", "dbl_server_default_options",
            "dbl_server_create", "dbl_server_submit", "dbl_server_wait", "dbl_server_drain", "dbl_server_report",
            "dbl_server_reset_stats", "dbl_server_destroy", "dbl_autotune", "dbl_set_schedule", "dbl_barrier_probe",
-           "dbl_server_cancel", "dbl_select_spread", "dbl_select_uncovered"]
+           "dbl_server_cancel", "dbl_select_spread", "dbl_select_uncovered", "dbl_save", "dbl_load"]
 MLP_PARAMS = 18817
 
 
@@ -138,6 +138,8 @@ def lib():
             L.dbl_select_by_score.argtypes = [P, P, i32, P, P]
             L.dbl_select_spread.argtypes = [P, P, i32, P, P]
             L.dbl_select_uncovered.argtypes = [P, P, i32, i32, i32, P, P]
+            L.dbl_save.argtypes = [P, ctypes.c_char_p, P]
+            L.dbl_load.argtypes = [ctypes.c_char_p, P, P, P]
             L.dbl_mlp_create.argtypes = [P, P, P]
             L.dbl_mlp_destroy.argtypes = [P, P]
             L.dbl_mlp_destroy.restype = None
@@ -190,20 +192,31 @@ class DBLIndex:
         self.n = int(self.row_ptr.numel() - 1)
         self.m = int(self.col.numel())
         self.k, self.kprime = int(k), int(kprime)
+        opt = self._options(edge_capacity=edge_capacity, flags=flags, team=team, query_unroll=query_unroll,
+                            search_first_log2=search_first_log2, landmark_rule=LANDMARK_RULES[landmark_rule],
+                            leaf_r=leaf_r, vertex_capacity=vertex_capacity, initial_slots=initial_slots,
+                            build_split=build_split, build_order=build_order, search_table_log2=search_table_log2,
+                            torch_allocator=torch_allocator)
+        self._opt = opt
+        g = _Graph(self.n, self.m, _ptr(self.row_ptr), _ptr(self.col))
+        self._keep = [t.to(torch.int32).contiguous() if t is not None and t.dtype != torch.uint8 else t
+                      for t in (landmarks, leaf_buckets, leaf_roles)]
+        lm, lb, lr = self._keep
+        h = ctypes.c_void_p()
+        st = L.dbl_build(ctypes.byref(g), _ptr(lm), self.k, _ptr(lb), _ptr(lr), self.kprime, ctypes.byref(opt),
+                         _stream_handle(stream), ctypes.byref(h))
+        if st != DBL_OK:
+            raise DblError(st, L.dbl_last_error(None).decode())
+        self._h = h
+
+    def _options(self, torch_allocator: bool = True, **fields) -> _Options:
+        """dbl_options with the given fields, and (torch_allocator) device
+        memory from PyTorch's caching allocator through the callbacks."""
+        import torch
         opt = _Options()
-        L.dbl_default_options(ctypes.byref(opt))
-        opt.edge_capacity = int(edge_capacity)
-        opt.flags = int(flags)
-        opt.team = int(team)
-        opt.query_unroll = int(query_unroll)
-        opt.search_first_log2 = int(search_first_log2)
-        opt.landmark_rule = LANDMARK_RULES[landmark_rule]
-        opt.leaf_r = int(leaf_r)
-        opt.vertex_capacity = int(vertex_capacity)
-        opt.initial_slots = int(initial_slots)
-        opt.build_split = int(build_split)
-        opt.build_order = int(build_order)
-        opt.search_table_log2 = int(search_table_log2)
+        lib().dbl_default_options(ctypes.byref(opt))
+        for name, value in fields.items():
+            setattr(opt, name, int(value))
         self._refuse = [0, 0]  # allocations to let through, then to refuse (fail_allocations)
         if torch_allocator:
             dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
@@ -230,16 +243,33 @@ class DBLIndex:
             self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
             opt.alloc, opt.free = self._cb
         self._opt = opt
-        g = _Graph(self.n, self.m, _ptr(self.row_ptr), _ptr(self.col))
-        self._keep = [t.to(torch.int32).contiguous() if t is not None and t.dtype != torch.uint8 else t
-                      for t in (landmarks, leaf_buckets, leaf_roles)]
-        lm, lb, lr = self._keep
+        return opt
+
+    def save(self, path: str, stream=None):
+        """dbl_save: write the index (graph, choices, labels, inserted edges) to a file."""
+        self._check(lib().dbl_save(self._h, os.fsencode(path), self._s(stream)))
+
+    @classmethod
+    def load(cls, path: str, device=None, flags: int = 0, team: int = 0, stream=None, torch_allocator: bool = True,
+             query_unroll: int = 0, search_first_log2: int = 0, search_table_log2: int = 0) -> "DBLIndex":
+        """dbl_load: an index read from a file written by save(), on `device`
+        (default: the current CUDA device)."""
+        import torch
+        self = cls.__new__(cls)
+        self._stream = stream
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.row_ptr = self.col = None
+        self._keep = []
+        opt = self._options(flags=flags, team=team, query_unroll=query_unroll, search_first_log2=search_first_log2,
+                            search_table_log2=search_table_log2, torch_allocator=torch_allocator)
         h = ctypes.c_void_p()
-        st = L.dbl_build(ctypes.byref(g), _ptr(lm), self.k, _ptr(lb), _ptr(lr), self.kprime, ctypes.byref(opt),
-                         _stream_handle(stream), ctypes.byref(h))
+        st = lib().dbl_load(os.fsencode(path), ctypes.byref(opt), _stream_handle(stream), ctypes.byref(h))
         if st != DBL_OK:
-            raise DblError(st, L.dbl_last_error(None).decode())
+            raise DblError(st, lib().dbl_last_error(None).decode())
         self._h = h
+        info = self.info()
+        self.n, self.m, self.k, self.kprime = info["n"], info["m"], info["k"], info["kprime"]
+        return self
 
     def barrier_probe(self, spin_limit: int = 1 << 20, absent_block: int = -1, stream=None):
         """dbl_barrier_probe: one cooperative launch on the index's grid barrier

@@ -328,6 +328,18 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
                      const uint8_t *leaf_roles, int32_t kprime, const dbl_options *opt, void *stream,
                      dbl_index **out)
 {
+    return dbl::build_index(g, landmarks, k, leaf_buckets, leaf_roles, kprime, opt, stream, out, true);
+}
+
+}  // extern "C"
+
+namespace dbl {
+// dbl_build, or (labels == false, for dbl_load) the same index with its
+// landmark and leaf choices but no labels computed.
+dbl_status build_index(const dbl_graph *g, const int32_t *landmarks, int32_t k, const int32_t *leaf_buckets,
+                       const uint8_t *leaf_roles, int32_t kprime, const dbl_options *opt, void *stream,
+                       dbl_index **out, bool labels)
+{
     if (!out) return fail(nullptr, DBL_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (!g || g->n < 0 || g->m < 0 || g->m >= (1ll << 31) || !g->row_ptr || (g->m > 0 && !g->col))
@@ -440,10 +452,11 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     cudaMemsetAsync(ix->dirty, 0, 4 * (size_t)ix->dirty_words, s);
     cudaMemsetAsync(ix->d_restore_base, 0xff, 16, s);  // no snapshot yet
 
+    ix->n_build = g->n;
     tbegin(ix, DBL_KERNEL_BUILD_PREP, s);
     if ((st = prep_graph(ix, g, s)) || (st = select_landmarks(ix, landmarks, s)) ||
-        (st = select_leaves(ix, leaf_buckets, leaf_roles, s)) || (st = seed_labels(ix, s)) ||
-        (tend(ix, s), st = build_propagate(ix, s))) {
+        (st = select_leaves(ix, leaf_buckets, leaf_roles, s)) || (labels && (st = seed_labels(ix, s))) ||
+        (tend(ix, s), labels && (st = build_propagate(ix, s)))) {
         std::string msg = ix->err;
         destroy_impl(ix, s);
         return fail(nullptr, st, msg);
@@ -462,6 +475,9 @@ dbl_status dbl_build(const dbl_graph *g, const int32_t *landmarks, int32_t k, co
     *out = ix;
     return DBL_OK;
 }
+}  // namespace dbl
+
+extern "C" {
 
 #define DBL_CHECK_IX(ix)                                                                   \
     do {                                                                                   \

@@ -260,6 +260,7 @@ struct dbl_index {
     int device = 0;
     int32_t n = 0;      // vertices now (grows by dbl_add_vertices)
     int32_t n_cap = 0;  // vertices every per-vertex array is sized for
+    int32_t n_build = 0;  // vertices of the base CSR (the build's graph)
     int64_t m = 0;
     int32_t k = 0, kp = 0, wd = 0, wb = 0, hs = 0, rw = 0;
     // packed labels (k + kprime <= 64): a half is one word, DL in bits
@@ -499,7 +500,10 @@ dbl_status propagate(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s);
 dbl_status barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent, cudaStream_t s);
-void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3, const int32_t *renum = nullptr);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)
+void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3, const int32_t *renum = nullptr);
+dbl_status build_index(const dbl_graph *g, const int32_t *landmarks, int32_t k, const int32_t *leaf_buckets,
+                       const uint8_t *leaf_roles, int32_t kprime, const dbl_options *opt, void *stream,
+                       dbl_index **out, bool labels);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)
 
 // insertion (dbl_insert.cu)
 dbl_status insert_edges(dbl_index *ix, const int32_t *src, const int32_t *dst, int64_t b, cudaStream_t s);

@@ -757,3 +757,67 @@ def test_search_overflow_reruns(tiny, flags, table_log2):
     assert_queries(ix, ref, tiny["q_u"], tiny["q_v"], f"first slice 2^6, flags {flags}")
     ix.sync()
     assert int(ix.stats()[14]) - w0 > 1, "expected several search waves"
+
+
+@pytest.mark.parametrize("k,kp", [(64, 64), (16, 16), (128, 64)])
+def test_save_load_roundtrip(tiny, tmp_path, k, kp):
+    """dbl_save / dbl_load: after half the insertions and 500 added vertices,
+    the loaded index has the same sizes, labels and answers as the saved one,
+    and takes the rest of the insertions (reserved slots, grown segments,
+    edges at the new vertices) to the oracle's labels."""
+    n0, add = int(tiny["n"]), 500
+    s, d = tiny["ins_src"], tiny["ins_dst"]
+    h = s.shape[0] // 2
+    ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), k, kp, flags=dbl.FLAG_PERSISTENT,
+                      vertex_capacity=n0 + add + 8, edge_capacity=1 << 16, initial_slots=2)
+    ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], k, kp).build()
+    ix.insert_edges(D(s[:h]), D(d[:h]))
+    ref.insert_edges(s[:h], d[:h])
+    ix.add_vertices(add)
+    ref.add_vertices(add)
+    rng = np.random.default_rng(23)
+    es = np.concatenate([s[h:], rng.integers(n0, n0 + add, 2000).astype(np.int32)])
+    ed = np.concatenate([d[h:], rng.integers(0, n0, 2000).astype(np.int32)])
+    path = str(tmp_path / "index.dbl")
+    ix.save(path)
+    ld = dbl.DBLIndex.load(path, flags=dbl.FLAG_PERSISTENT)
+    for key in ("n", "k", "kprime", "m", "edges_stored", "edge_capacity", "vertex_capacity", "record_bytes"):
+        assert ld.info()[key] == ix.info()[key], key
+    for a, b in zip(ix.labels(), ld.labels()):
+        assert torch.equal(a, b)
+    qu, qv = tiny["q_u"][:30_000], tiny["q_v"][:30_000]
+    a1, c1 = ix.query(D(qu), D(qv))
+    a2, c2 = ld.query(D(qu), D(qv))
+    assert torch.equal(a1, a2) and torch.equal(c1, c2)
+    for b in range(0, es.shape[0], 1000):
+        ld.insert_edges(D(es[b:b + 1000]), D(ed[b:b + 1000]))
+    ref.insert_edges(es, ed)
+    ld.sync()
+    assert_labels(ld, ref, f"loaded index after the rest of the insertions, k={k} k'={kp}")
+    assert_queries(ld, ref, qu, qv, "loaded index, queries")
+
+
+def test_load_rejects_bad_files(tmp_path):
+    """A missing, foreign or truncated file is DBL_ERR_IO."""
+    with pytest.raises(dbl.DblError) as e:
+        dbl.DBLIndex.load(str(tmp_path / "missing.dbl"))
+    assert e.value.status == dbl.DBL_ERR_IO
+    junk = tmp_path / "junk.dbl"
+    junk.write_bytes(b"not an index" * 100)
+    with pytest.raises(dbl.DblError) as e:
+        dbl.DBLIndex.load(str(junk))
+    assert e.value.status == dbl.DBL_ERR_IO
+    rp = np.array([0, 1, 2, 2], np.int32)
+    col = np.array([1, 2], np.int32)
+    ix = dbl.DBLIndex(D(rp), D(col), 64, 64)
+    good = tmp_path / "good.dbl"
+    ix.save(str(good))
+    data = good.read_bytes()
+    short = tmp_path / "short.dbl"
+    short.write_bytes(data[: len(data) - 8])
+    with pytest.raises(dbl.DblError) as e:
+        dbl.DBLIndex.load(str(short))
+    assert e.value.status == dbl.DBL_ERR_IO
+    ok = dbl.DBLIndex.load(str(good))
+    a, _ = ok.query(D(np.array([0, 2], np.int32)), D(np.array([2, 0], np.int32)))
+    assert a.cpu().tolist() == [1, 0]
