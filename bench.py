@@ -891,7 +891,7 @@ def bench_gpu(args):
     # query part.  Its own timing pass gives the roofline figures.
     grouped = "deferred" in args.forms
     deferred = run_form("deferred", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
-                        sample_clocks=True) if grouped else None
+                        sample_clocks=True, keep=True) if grouped else None
     deferred_t = run_form("deferred_timing", args, w, I, k, kp, lm, leaves, batches, qbatches, *common, S,
                           keep=True) if grouped else None
     ref_form = forms.get("graph") or forms.get("batched") or forms.get("plain")
@@ -922,8 +922,14 @@ def bench_gpu(args):
         k2_forms["fallback_to_degree_rule"] = learned_judge(k2_forms["learned"], k2_forms["graph"])
         k2_forms["learned_vs_plain"] = k2_forms["learned"]["value"] / k2_forms["plain"]["value"]
 
-    # ---- end to end through the host-buffer C-ABI calls, headline index
-    ix = learned["ix"]
+    # ---- end to end through the host-buffer C-ABI calls, on the headline's
+    # index and form (grouped: the uploaded batches wait in the queue and the
+    # query call applies them as one launch)
+    e2e_form = deferred if head is deferred else learned
+    for f in (learned, deferred):
+        if f is not None and f is not e2e_form:
+            f["ix"].close()
+    ix = e2e_form["ix"]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     h_src, h_dst = pin(w["ins_src"]), pin(w["ins_dst"])
     h_qu, h_qv = pin(w["q_u"][q_lo:q_hi]), pin(w["q_v"][q_lo:q_hi])

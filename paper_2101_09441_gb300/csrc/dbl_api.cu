@@ -641,9 +641,11 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
         return fail(ix, DBL_ERR_INVALID, "insert_host: bad batch");
     if (b == 0) return DBL_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    DBL_FLUSH(ix, s);
+    const bool defer = deferring(ix);  // the batch joins the queue; its staging buffer is held until the flush
+    if (!defer) DBL_FLUSH(ix, s);
     dbl_status st;
     if (b > ix->istage_cap) {
+        DBL_FLUSH(ix, s);  // queued batches may still read the buffers replaced here
         // stream-ordered frees: after every insertion queued on s (each waited for its upload)
         for (int k = 0; k < ix->istage_n; ++k) {
             free_buf(ix, ix->istage[k], s);
@@ -674,6 +676,7 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
     // upload.
     const int k = ix->istage_turn;
     ix->istage_turn = (k + 1) % ix->istage_n;
+    if (ix->istage_queued[k]) DBL_FLUSH(ix, s);  // the ring came round to a batch still queued
     char *d = (char *)ix->istage[k];
     cudaStream_t cs = ix->ins_copy_stream;
     cudaStreamWaitEvent(cs, ix->ev_istage_used[k], 0);
@@ -682,7 +685,8 @@ dbl_status dbl_insert_edges_host(dbl_index *ix, const int32_t *src_host, const i
     cudaEventRecord(ix->ev_istage_in[k], cs);
     cudaStreamWaitEvent(s, ix->ev_istage_in[k], 0);
     st = insert_edges(ix, (int32_t *)d, (int32_t *)(d + 4 * ix->istage_cap), b, s);
-    cudaEventRecord(ix->ev_istage_used[k], s);
+    if (defer && !st) ix->istage_queued[k] = true;  // flush_insertions records its use
+    else cudaEventRecord(ix->ev_istage_used[k], s);
     if (st) return st;
     return (ix->opt.flags & DBL_FLAG_ASYNC) ? DBL_OK : read_status(ix, s);
 }

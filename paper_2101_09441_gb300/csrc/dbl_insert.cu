@@ -682,7 +682,7 @@ static dbl_status insert_persistent(dbl_index *ix, const int32_t *src, const int
 // launch by the next call that reads or changes the index otherwise (or
 // when kMaxGroup batches wait).  Every query therefore observes exactly the
 // insertions queued before it.
-static bool deferring(const dbl_index *ix)
+bool deferring(const dbl_index *ix)
 {
     const int32_t f = ix->opt.flags;
     return (f & DBL_FLAG_DEFER) && (f & DBL_FLAG_PERSISTENT) && (f & DBL_FLAG_ASYNC);
@@ -717,7 +717,15 @@ dbl_status flush_insertions(dbl_index *ix, cudaStream_t s)
     ix->pending.clear();
     ix->pending_edges = 0;
     // the queue's scratch was sized when its batches were queued
-    return insert_persistent_list(ix, bl, bl.src[0], bl.dst[0], total, ix->ins_pos, ix->ins_pos + ix->ins_bcap, s);
+    const dbl_status st =
+        insert_persistent_list(ix, bl, bl.src[0], bl.dst[0], total, ix->ins_pos, ix->ins_pos + ix->ins_bcap, s);
+    // host-form staging buffers of the queued batches are free once this launch is done
+    for (int k = 0; k < ix->istage_n; ++k)
+        if (ix->istage_queued[k]) {
+            cudaEventRecord(ix->ev_istage_used[k], s);
+            ix->istage_queued[k] = false;
+        }
+    return st;
 }
 
 void drop_insertions(dbl_index *ix)
@@ -725,6 +733,7 @@ void drop_insertions(dbl_index *ix)
     ix->edges_stored -= ix->pending_edges;
     ix->pending.clear();
     ix->pending_edges = 0;
+    for (int k = 0; k < dbl_index::kMaxIStage; ++k) ix->istage_queued[k] = false;
 }
 
 static unsigned blocks_for(int64_t work, int64_t cap_mult = 16)

@@ -348,6 +348,7 @@ struct dbl_index {
     int istage_turn = 0;
     cudaEvent_t ev_istage_used[kMaxIStage] = {};  // recorded when an insertion is done with its buffer
     cudaEvent_t ev_istage_in[kMaxIStage] = {};    // recorded when a buffer's upload is done
+    bool istage_queued[kMaxIStage] = {};  // its batch waits in the insertion queue (DBL_FLAG_DEFER)
     cudaStream_t copy_stream = nullptr;      // query uploads
     cudaStream_t ins_copy_stream = nullptr;  // insertion uploads (a FIFO of their own: a query upload
                                              //   does not queue behind uploads that wait for insertions)
@@ -501,6 +502,8 @@ dbl_status propagate_persistent(dbl_index *ix, cudaStream_t s);
 dbl_status propagate_records(dbl_index *ix, uint64_t *rec, int32_t hs, cudaStream_t s);
 dbl_status barrier_probe(dbl_index *ix, int64_t spin_limit, int32_t absent, cudaStream_t s);
 void launch_seed_frontier(dbl_index *ix, cudaStream_t s, int dirs = 3, const int32_t *renum = nullptr);
+// insertion batches are queued and applied as one group at the next reading call
+bool deferring(const dbl_index *ix);
 dbl_status build_index(const dbl_graph *g, const int32_t *landmarks, int32_t k, const int32_t *leaf_buckets,
                        const uint8_t *leaf_roles, int32_t kprime, const dbl_options *opt, void *stream,
                        dbl_index **out, bool labels);  // vertices with a non-zero half (dirs: bit 0 forward, bit 1 backward)

@@ -620,7 +620,9 @@ def test_host_buffer_forms(tiny):
 def test_host_buffer_forms_asynchronous(tiny):
     """With FLAG_ASYNC the host-buffer calls only queue their copies and
     kernels (pinned buffers, several insertion batches and query chunks in
-    flight); after a sync the answers equal the oracle's."""
+    flight); with FLAG_DEFER the uploaded batches wait in the queue, holding
+    their staging buffers (40 batches of 250 wrap the ring of 16 buffers and
+    pass the group limit of 32); after a sync the answers equal the oracle's."""
     ref = oracle.OracleIndex(tiny["row_ptr"], tiny["col"], 64, 64).build()
     ref.insert_edges(tiny["ins_src"], tiny["ins_dst"])
     rans, rcode = ref.query(tiny["q_u"], tiny["q_v"], nthreads=8)
@@ -628,15 +630,17 @@ def test_host_buffer_forms_asynchronous(tiny):
     src, dst, qu, qv = pin(tiny["ins_src"]), pin(tiny["ins_dst"]), pin(tiny["q_u"]), pin(tiny["q_v"])
     ans = torch.empty(qu.shape[0], dtype=torch.uint8).pin_memory().numpy()
     code = torch.empty(qu.shape[0], dtype=torch.uint8).pin_memory().numpy()
-    for flags in (dbl.FLAG_ASYNC, dbl.FLAG_ASYNC | dbl.FLAG_PERSISTENT):
+    for flags, bs in ((dbl.FLAG_ASYNC, 1000), (dbl.FLAG_ASYNC | dbl.FLAG_PERSISTENT, 1000),
+                      (dbl.FLAG_ASYNC | dbl.FLAG_PERSISTENT | dbl.FLAG_DEFER, 1000),
+                      (dbl.FLAG_ASYNC | dbl.FLAG_PERSISTENT | dbl.FLAG_DEFER, 250)):
         ix = dbl.DBLIndex(D(tiny["row_ptr"]), D(tiny["col"]), 64, 64, flags=flags)
-        for a in range(0, src.shape[0], 1000):
-            ix.insert_edges_host(src[a:a + 1000], dst[a:a + 1000])
+        for a in range(0, src.shape[0], bs):
+            ix.insert_edges_host(src[a:a + bs], dst[a:a + bs])
         ans[:] = 7
         ix.query_host(qu, qv, with_code=True, out=(ans, code))
         ix.sync()
         torch.cuda.synchronize()
-        assert np.array_equal(ans, rans) and np.array_equal(code, rcode), f"flags {flags}"
+        assert np.array_equal(ans, rans) and np.array_equal(code, rcode), f"flags {flags}, batches of {bs}"
         ix.close()
 
 
