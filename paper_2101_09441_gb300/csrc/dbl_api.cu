@@ -805,20 +805,30 @@ __global__ void k_restore(uint4 *rec, const uint4 *rec_snap, int64_t rec_units, 
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
     const bool full = force_full || *(const volatile uint32_t *)base != slot || *(const volatile uint32_t *)status != 0;
     if (!full) {
-        for (int64_t w = i0; w < dirty_words; w += st) {
-            uint32_t d = dirty[w];
+        // a warp per bitmap word, a lane per vertex: the word's 32 vertices
+        // are adjacent in every array, and the grid's warps walk the words in
+        // order, so the pages in use at any time span a window of about
+        // (warps x 32) vertices instead of the whole arrays
+        const int lane = threadIdx.x & 31;
+        const int64_t nwarps = st >> 5;
+        for (int64_t w = i0 >> 5; w < dirty_words; w += nwarps) {  // warp-uniform
+            const uint32_t d = dirty[w];
             if (!d) continue;
-            dirty[w] = 0;
-            while (d) {
-                const int b = __ffs(d) - 1;
-                d &= d - 1;
-                const int64_t x = w * 32 + b;
-                if (x >= n_snap) break;  // added after the snapshot: not restored (the vertex count goes back)
-                for (int u = 0; u < rec_row_units; ++u)
-                    rec[x * rec_row_units + u] = __ldcs(rec_snap + x * rec_row_units + u);
-                vm[2 * x] = __ldcs(vm_snap + 2 * x);
-                vm[2 * x + 1] = __ldcs(vm_snap + 2 * x + 1);
-            }
+            __syncwarp();
+            if (lane == 0) dirty[w] = 0;
+            const int64_t x = w * 32 + lane;
+            if (!((d >> lane) & 1u) || x >= n_snap) continue;  // vertices added after the snapshot go away
+            uint4 r[8], m0, m1;  // a record is 1, 2, 4 or 8 units of 16 bytes
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < rec_row_units) r[u] = __ldcs(rec_snap + x * rec_row_units + u);
+            m0 = __ldcs(vm_snap + 2 * x);
+            m1 = __ldcs(vm_snap + 2 * x + 1);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < rec_row_units) rec[x * rec_row_units + u] = r[u];
+            vm[2 * x] = m0;
+            vm[2 * x + 1] = m1;
         }
         return;
     }
