@@ -256,31 +256,59 @@ def test_large_graph_incremental_equals_rebuild():
     full.close()
 
 
-def test_large_graph_matches_oracle():
-    """n = 2^24, m = 2^28 (the learned and serving graph), k = k' = 64: every
-    label word after the 1M insertions (batches of 100k, persistent kernels)
-    against the oracle (Algorithm 1 build, then Algorithm 3 and its mirrors
-    edge by edge), and answers and deciding rules of the first 1M of the 10M
-    queries against Algorithm 2 on the oracle."""
+def _large_learned(w, k, kp, E, train_pairs=200_000, steps=200):
+    """The learned landmark slots of the large workload as the benchmark
+    chooses them (plain degree index after the insertions, scorer trained on
+    sampled query outcomes, k/8 degree landmarks kept), and the leaves."""
+    rp, col = D(w["row_ptr"]), D(w["col"])
+    src, dst = D(w["ins_src"]), D(w["ins_dst"])
+    plain = dbl.DBLIndex(rp, col, k, kp, edge_capacity=E, flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC)
+    for a in range(0, E, 100_000):
+        plain.insert_edges(src[a:a + 100_000], dst[a:a + 100_000])
+    tu, tv = dbl_inputs.queries(w["row_ptr"], w["col"], train_pairs, int(w["seed"]) + 300, False,
+                                w["ins_src"], w["ins_dst"])
+    base = max(1, k // 8)
+    scores, _ = L.train_scorer(plain, D(tu), D(tv), base, steps=steps)
+    lm = L.select_landmarks(plain, scores, k, base)
+    _, lb, lr = plain.selection()
+    plain.close()
+    return lm, lb, lr
+
+
+@pytest.mark.parametrize("k,kp,grouped", [(64, 64, True), (128, 64, False)])
+def test_large_graph_matches_oracle(k, kp, grouped):
+    """n = 2^24, m = 2^28 with learned landmarks, in the benchmark's launch
+    configurations: k = k' = 64 with the 1M insertions queued in batches of
+    100k and applied as one group by the query call (the headline form), and
+    k = 128, k' = 64 with one persistent launch per batch (the serving
+    index).  Every label word against the oracle built with the same landmark
+    and leaf sets (Algorithm 1, then Algorithm 3 and its mirrors edge by edge),
+    and the answers and deciding rules of 1M of the 10M queries against
+    Algorithm 2 on the oracle."""
     dbl.build()
     dbl_inputs.build()
     oracle.build()
     w = dbl_inputs.workload("large")
     E = int(w["ins_src"].shape[0])
-    ix = dbl.DBLIndex(D(w["row_ptr"]), D(w["col"]), 64, 64, edge_capacity=E,
-                      flags=dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC)
+    lm, lb, lr = _large_learned(w, k, kp, E)
+    flags = dbl.FLAG_PERSISTENT | dbl.FLAG_ASYNC | (dbl.FLAG_DEFER if grouped else 0)
+    ix = dbl.DBLIndex(D(w["row_ptr"]), D(w["col"]), k, kp, landmarks=lm, leaf_buckets=lb, leaf_roles=lr,
+                      edge_capacity=E, flags=flags)
     src, dst = D(w["ins_src"]), D(w["ins_dst"])
     for a in range(0, E, 100_000):
         ix.insert_edges(src[a:a + 100_000], dst[a:a + 100_000])
     S = 1_000_000
-    ans, code = ix.query(D(w["q_u"][:S]), D(w["q_v"][:S]))
+    qu, qv = w["q_u"][-S:], w["q_v"][-S:]
+    ans, code = ix.query(D(qu), D(qv))
     ix.sync()
     got = labels_np(ix)
     ans, code = ans.cpu().numpy(), code.cpu().numpy()
     ix.close()
-    ref = oracle.OracleIndex(w["row_ptr"], w["col"], 64, 64).build(nthreads=THREADS)
+    ref = oracle.OracleIndex(w["row_ptr"], w["col"], k, kp).build(
+        landmarks=lm.cpu().numpy(), leaf_bucket=lb.cpu().numpy(), leaf_role=lr.cpu().numpy(), nthreads=THREADS)
     ref.insert_edges(w["ins_src"], w["ins_dst"])
-    assert_same_labels(got, ref.labels(), "large graph, batches of 100k, persistent")
-    rans, rcode = ref.query(w["q_u"][:S], w["q_v"][:S], nthreads=THREADS)
+    what = f"large graph, learned landmarks, k={k} k'={kp}, {'grouped' if grouped else 'per batch'}"
+    assert_same_labels(got, ref.labels(), what)
+    rans, rcode = ref.query(qu, qv, nthreads=THREADS)
     bad = np.nonzero((ans != rans) | (code != rcode))[0]
-    assert bad.size == 0, f"large graph: {bad.size} of {S} queries differ, first {bad[:5]}"
+    assert bad.size == 0, f"{what}: {bad.size} of {S} queries differ, first {bad[:5]}"
