@@ -412,10 +412,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         mma_pending = false;
         tc::tc_fence_after();
         uint4 *h1 = reinterpret_cast<uint4 *>(S.h1);
-#pragma unroll 1
-        for (int c = half * 4; c < half * 4 + 4; ++c) {
-            float v[16];
-            tc::tmem_ld16(tmem + lane_base + (uint32_t)(c * 16), v);
+        float v1[64];  // this thread's 64 columns of layer 1, one TMEM load
+        tc::tmem_ld64(tmem + lane_base + (uint32_t)(half * 64), v1);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = half * 4 + cc;
+            const float *v = v1 + cc * 16;
             uint32_t pk[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -449,10 +451,12 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
         mma_pending = false;
         tc::tc_fence_after();
         float acc = 0.f;
-#pragma unroll 1
-        for (int c = half * 4; c < half * 4 + 4; ++c) {
-            float v[16];
-            tc::tmem_ld16(tmem + lane_base + (uint32_t)(kH + c * 16), v);
+        float v2[64];  // this thread's 64 columns of layer 2, one TMEM load
+        tc::tmem_ld64(tmem + lane_base + (uint32_t)(kH + half * 64), v2);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int c = half * 4 + cc;
+            const float *v = v2 + cc * 16;
             uint32_t pk[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
