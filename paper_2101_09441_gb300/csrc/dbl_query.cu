@@ -391,6 +391,45 @@ __device__ __forceinline__ void mark_pending(const SearchCtx &c, int64_t slot, u
 // comes back to u it expands u once more, which adds nothing.  Each thread
 // takes kSetupQ queries per round with all their loads in flight; the task
 // list gets one reservation per block and round (the loop is block-uniform).
+// Writes every lane's nch tasks (x, g, chunks 0 .. nch - 1, mask) from its
+// position pos on, with the warp's lanes sharing the work (a lane whose
+// vertex is a hub of thousands of chunks would otherwise write them alone,
+// and the phase would wait for it); warp-collective.
+__device__ __forceinline__ void warp_write_tasks(const SearchArgs &a, uint32_t nch, uint32_t pos, int32_t x,
+                                                 uint32_t g, unsigned long long mask)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t excl = incl - nch;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    for (uint32_t b0 = 0; b0 < total; b0 += 32) {  // warp-uniform
+        const uint32_t e = b0 + lane;
+        const int owner = flat_owner(excl, e);
+        const uint32_t ch = e - __shfl_sync(kFull, excl, owner);
+        const uint32_t p = __shfl_sync(kFull, pos, owner) + ch;
+        const int32_t ox = __shfl_sync(kFull, x, owner);
+        const uint32_t og = __shfl_sync(kFull, g, owner);
+        const unsigned long long om = __shfl_sync(kFull, mask, owner);
+        if (e >= total) continue;
+        if ((int64_t)p >= a.task_cap) {
+            atomicExch(a.c.overflow, 1u);
+            continue;
+        }
+        SearchTask t;
+        t.x = ox;
+        t.g = og;
+        t.chunk = ch;
+        t.pad = 0;
+        t.mask = om;
+        a.tasks[p] = t;
+    }
+}
+
 constexpr int kSetupQ = 4;
 
 template <int WD, int WB>
@@ -446,19 +485,8 @@ __device__ __forceinline__ void search_setup(const SearchArgs &a, int64_t j0, in
 #pragma unroll
         for (int k = 0; k < kSetupQ; ++k) {
             const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
-            for (uint32_t ch = 0; ch < nch[k]; ++ch, ++pos) {
-                if ((int64_t)pos >= a.task_cap) {
-                    atomicExch(a.c.overflow, 1u);
-                    break;
-                }
-                SearchTask tk;
-                tk.x = u[k];
-                tk.g = (uint32_t)(j >> 6);
-                tk.chunk = ch;
-                tk.pad = 0;
-                tk.mask = 1ull << (j & 63);
-                a.tasks[pos] = tk;
-            }
+            warp_write_tasks(a, nch[k], pos, u[k], (uint32_t)(j >> 6), 1ull << (j & 63));
+            pos += nch[k];
         }
     }
 }
@@ -486,19 +514,7 @@ __device__ __forceinline__ void search_finalize(const SearchArgs &a, const SlotL
         uint32_t total = 0;
         uint32_t pos = block_reserve(nch, n_tasks, &total);
         if (total == 0) continue;
-        for (uint32_t ch = 0; ch < nch; ++ch, ++pos) {
-            if ((int64_t)pos >= a.task_cap) {
-                atomicExch(a.c.overflow, 1u);
-                break;
-            }
-            SearchTask t;
-            t.x = x;
-            t.g = (uint32_t)(key >> 32);
-            t.chunk = ch;
-            t.pad = 0;
-            t.mask = mask;
-            a.tasks[pos] = t;
-        }
+        warp_write_tasks(a, nch, pos, x, (uint32_t)(key >> 32), mask);
     }
 }
 
