@@ -52,9 +52,9 @@ UNIT = "ops/s (queries + inserted edges)"
 # query_label: 10M pairs on the 2^24-vertex graph (k = k' = 64, 32-byte L2
 # fetch); propagate_grouped: one insertion launch of the workload's 1M edges;
 # propagate_batch: one of 100,000 (bench.py --kernel-case label / insert).
-NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (636_669_696 + 19_135_488, "cb03f11777b9"),
-                                             "propagate_grouped": (305_026_048 + 178_522_112, "7c87303a08ac"),
-                                             "propagate_batch": (22_414_592 + 5_921_792, "7c87303a08ac")}
+NCU_TRAFFIC: dict[str, tuple[float, str]] = {"query_label": (636_424_192 + 22_371_584, "fb983a793219"),
+                                             "propagate_grouped": (305_130_240 + 178_975_488, "74298b536cff"),
+                                             "propagate_batch": (22_423_296 + 6_051_840, "74298b536cff")}
 # Source a traffic figure was measured on: the kernel's own region of its file
 # (None: the whole file) and the headers that file includes; an edit anywhere
 # else does not invalidate the figure, any edit there does.
