@@ -788,7 +788,7 @@ def bench_extras(args, world, tdist, local, dev):
 
 def learned_gain_community(args, dev, reps=10):
     """What the learned landmarks gain on a graph with several strongly
-    connected parts of real size (R-MAT gives none: section 8 of the notes):
+    connected parts of real size (on R-MAT it gains nothing measurable):
     128 R-MAT communities of power-law sizes (community c holds a share
     proportional to 1/(c+1)) joined by 2% of the edges, always from an earlier
     to a later community (dbl_inputs.community_dag), n = 500,000, m = 5M.
