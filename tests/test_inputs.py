@@ -77,3 +77,34 @@ def test_loguniform_batches():
     b = dbl_inputs.loguniform_batches(1_000_000, 1, 200_000, 5)
     assert b.sum() == 1_000_000 and b.min() >= 1 and b.max() <= 200_000
     assert len(set(b.tolist())) > 5
+
+
+def test_community_dag_structure():
+    """community_dag: sorted rows, no self-loops or duplicates, ids a
+    permutation of [0, n); edges between communities only from the earlier to
+    the later one, so the condensation of the communities is acyclic (no edge
+    closes a cycle between two communities)."""
+    n, m, C = 20_000, 150_000, 16
+    rp, col = dbl_inputs.community_dag(n, m, C, 1.0, 0.05, 3)
+    assert rp.shape == (n + 1,) and rp[0] == 0 and rp[-1] == col.shape[0] <= m
+    assert np.all(np.diff(rp) >= 0)
+    src = np.repeat(np.arange(n), np.diff(rp))
+    assert not np.any(src == col)
+    key = src.astype(np.int64) * n + col
+    assert np.all(np.diff(key) > 0)                       # rows sorted, no duplicates
+    # recover each vertex's community from the generator's recipe: the same
+    # sizes and the same relabelling
+    w = np.array([(c + 1.0) ** -1.0 for c in range(C)])
+    sizes = np.maximum(64, np.floor(w / w.sum() * n)).astype(np.int64)
+    sizes[0] += n - sizes.sum()
+    comm_of_old = np.repeat(np.arange(C), sizes)
+    perm = dbl_inputs.permutation(n, 4).astype(np.int64)  # seed + 1
+    comm = np.empty(n, np.int64)
+    comm[perm] = comm_of_old
+    cs, cd = comm[src], comm[col]
+    assert np.all(cs <= cd)                               # never from a later community to an earlier one
+    cross = np.count_nonzero(cs < cd)
+    assert 0.02 * m < cross < 0.08 * m                    # about 5% of the edges cross
+    # the largest community holds the largest share of the edges
+    per = np.bincount(cs, minlength=C)
+    assert per.argmax() == 0
