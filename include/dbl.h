@@ -533,17 +533,21 @@ const char *dbl_mlp_last_error(const dbl_mlp *m);
  * count and the stored-edge count; insertion batches queued under
  * DBL_FLAG_DEFER are applied first.  Snapshots are not written.  The file's
  * size is about the device memory the index uses minus its frontier and
- * scratch buffers.  Synchronous.  DBL_ERR_IO if the file cannot be written
- * (the index is unchanged either way); DBL_ERR_POISONED for a poisoned index. */
+ * scratch buffers.  Writes through a 64 MB pinned host buffer.  Synchronous.
+ * DBL_ERR_IO if the file cannot be written (the index is unchanged either
+ * way); DBL_ERR_POISONED for a poisoned index. */
 dbl_status dbl_save(dbl_index *ix, const char *path, void *stream);
 
 /* Read an index written by dbl_save into a new index on the current device.
  * `opt` (NULL: defaults) supplies the allocator, flags, team and query
  * options; the capacities (edge_capacity, vertex_capacity, initial_slots)
  * are the saved index's.  The loaded index answers every query and takes
- * every later insertion exactly as the saved one would.  Synchronous.
- * DBL_ERR_IO if the file is missing, short, of another format version or
- * inconsistent; DBL_ERR_OOM as dbl_build. */
+ * every later insertion exactly as the saved one would.  While the call
+ * runs, the base graph and the landmark and leaf arrays pass through
+ * temporary device buffers taken with cudaMalloc (about 4 bytes per edge and
+ * 9 per vertex; not from the allocator in opt) and a 64 MB pinned host buffer.
+ * Synchronous.  DBL_ERR_IO if the file is missing, short, of another format
+ * version or inconsistent; DBL_ERR_OOM as dbl_build. */
 dbl_status dbl_load(const char *path, const dbl_options *opt, void *stream, dbl_index **out);
 
 /* Message of the last error on this index (or of the last failed build when
