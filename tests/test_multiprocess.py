@@ -136,3 +136,35 @@ def test_sharded_answers_gather_back_in_input_order():
     got = sorted(q.get(timeout=10) for _ in range(world))
     assert all(ok for _, ok, _ in got)
     assert sum(n for _, _, n in got) == 1003
+
+
+def test_build_roofline_arithmetic():
+    """The build's roofline: algorithmic bytes over the propagation time, the
+    preparation reported beside it, against the measured HBM peak."""
+    import bench
+    peaks, _ = bench.measured_peaks()
+    form = {"build_kernel_ms": {"propagate": 10.0, "build_prep": 5.0}, "build_algorithmic_bytes": 20e9,
+            "build_edges_relaxed": 700e6}
+    r = bench.build_roofline(form)
+    assert abs(r["achieved"] - 2000.0) < 1e-9                     # 20 GB in 10 ms
+    assert abs(r["frac"] - 2000.0 / peaks["hbm_gbs"]) < 1e-12
+    assert r["prep_ms"] == 5.0 and r["build_ms"] == 15.0
+    assert abs(r["teps"] - 70e9) < 1e-3
+    assert bench.build_roofline({"build_kernel_ms": {}}) is None
+
+
+def test_learned_judge_keeps_only_what_searches_less_and_repairs_cheaply():
+    import bench
+    ref = {"searched": 1000, "relaxed_per_step": 100_000}
+    assert not bench.learned_judge({"searched": 900, "relaxed_per_step": 120_000}, ref)    # kept
+    assert bench.learned_judge({"searched": 1001, "relaxed_per_step": 100_000}, ref)       # more searches
+    assert bench.learned_judge({"searched": 500, "relaxed_per_step": 10_000_000}, ref)     # repair much dearer
+
+
+def test_ncu_traffic_keys_name_sources_that_exist():
+    """Every stored traffic figure is keyed to a kernel source the bench can
+    hash, so a changed kernel reports null instead of a stale figure."""
+    import bench
+    for kind in bench.NCU_TRAFFIC:
+        assert len(bench.source_sha(kind)) == 12
+    assert bench.NCU_TRAFFIC["propagate_grouped"][0] > bench.NCU_TRAFFIC["propagate_batch"][0]
